@@ -1,0 +1,205 @@
+/*
+ * swift_gpu.h -- C ABI of the B300 (sm_103a) SPH pair-interaction library.
+ *
+ * The library runs the hot path of the SWIFT SPH solver described in
+ * "Task-parallelism in SWIFT for heterogeneous compute architectures"
+ * (arXiv 2505.14538): the density loop with the Newton iteration on the
+ * smoothing length (Sec. 2.1.2, Eqs. 2-6), the gradient loop (Sec. 2.1.3,
+ * Eqs. 10-11) and the force loop (Sec. 2.1.4, Eqs. 7, 9-11, 16-20, 22), over
+ * the self and pair interactions of a periodic grid of cubic cells no finer
+ * than the kernel support (Sec. 2.2, Fig. 3). Everything runs as CUDA kernels
+ * on one GPU; the caller owns every particle array, the library owns only the
+ * opaque context (sorted copies, cell arrays, work lists, status word).
+ *
+ * Conventions shared by every call below:
+ *  - All particle pointers are DEVICE pointers owned by the caller, contiguous,
+ *    and aligned to their element size (16 bytes for float4, 8 for float2).
+ *    They are indexed in the caller's particle order.
+ *  - float4 layouts: pos_h = (x, y, z, h); vel_m = (vx, vy, vz, m). These
+ *    mirror the packed particle records of Sec. 2.3.2.1 (float4 position and
+ *    smoothing length, float4 velocity and mass) as structure-of-arrays.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream). Calls are asynchronous on that stream unless stated otherwise;
+ *    device-side errors are recorded in the context's status word and read
+ *    with swift_gpu_sync_status.
+ *  - Return value: SWIFT_GPU_OK (0) or a negative SWIFT_GPU_ERR_* code for an
+ *    error detected on the host (bad argument, call order, CUDA launch error).
+ *    Nothing is thrown across the ABI.
+ *  - Positions live in the periodic box [0, L)^3; positions outside are wrapped
+ *    (in FP64) for cell assignment and distances use the minimum image.
+ */
+#ifndef SWIFT_GPU_H
+#define SWIFT_GPU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define SWIFT_GPU_OK 0
+#define SWIFT_GPU_ERR_ARG (-1)               /* bad pointer, size, NaN/Inf position, h <= 0 */
+#define SWIFT_GPU_ERR_ORDER (-2)             /* call before its prerequisite (see each call) */
+#define SWIFT_GPU_ERR_CUDA (-3)              /* a CUDA runtime call failed */
+#define SWIFT_GPU_ERR_H_NOT_CONVERGED (-4)   /* Newton on h hit max_iter; detail = count */
+#define SWIFT_GPU_ERR_H_EXCEEDS_CELL (-5)    /* h wanted a support wider than a cell; detail = count */
+#define SWIFT_GPU_ERR_TIMEOUT (-6)           /* a bounded device-side wait gave up */
+#define SWIFT_GPU_ERR_NOMEM (-7)             /* device allocation failed */
+#define SWIFT_GPU_ERR_CAPACITY (-8)          /* n exceeds the context's n_max */
+
+/* swift_gpu_params.flags */
+#define SWIFT_GPU_PLAIN 1         /* one kernel launch per self/pair cell task (the paper's task granularity) */
+#define SWIFT_GPU_NO_H_ITER 2     /* density at the given h: no Newton iteration */
+#define SWIFT_GPU_NO_COMPENSATION 4 /* plain FP32 sums instead of two-sum compensated rho, a, du/dt */
+
+typedef struct {
+  float box[3];        /* periodic box edge lengths L (the box is [0,L)^3) */
+  float gamma_eos;     /* adiabatic index gamma (Sec. 3.1: 5/3) */
+  float eta;           /* resolution: the h iteration targets n = (eta/h)^3 (1.2348: ~48 neighbours) */
+  float kernel_gamma;  /* H/h of the cubic-spline kernel (1.825742) */
+  float alpha_v;       /* viscosity alpha, used when no per-particle array is given (Eq. 16) */
+  float beta_v;        /* signal-velocity beta (Eq. 10; 3) */
+  float alpha_c;       /* conduction alpha, used when no per-particle array is given (Eq. 20) */
+  float h_tol;         /* Newton tolerance: |n - (eta/h)^3| <= h_tol (eta/h)^3 (Sec. 2.1.2: 1e-4) */
+  int max_iter;        /* maximum Newton passes (>= 1) */
+  float h_max;         /* cap on h; 0 = the largest h whose support fits in one cell */
+  float cell_margin;   /* automatic cell width = (1 + cell_margin) * kernel_gamma * max h */
+  int flags;           /* SWIFT_GPU_* flags above */
+} swift_gpu_params;
+
+/* Work-distribution knobs (chosen by swift_gpu_autotune, or set by hand). */
+typedef struct {
+  int threads_per_block; /* 64..1024, multiple of 32 */
+  int max_lanes_per_particle; /* 1, 2, 4 or 8: lanes that share one particle's neighbour scan */
+  int blocks_per_sm;     /* persistent blocks per SM (0 = occupancy maximum) */
+} swift_gpu_tuning;
+
+typedef struct {
+  int64_t n;               /* particles of the last build */
+  int32_t nc[3];           /* cells per axis */
+  float cell_width[3];     /* cell edge lengths */
+  float h_cap;             /* largest h whose support fits in a cell */
+  int64_t n_cells;
+  int64_t n_items;         /* work items (cell chunks of <= 32 active particles) */
+  int32_t density_passes;  /* Newton passes run by the last density call */
+  uint64_t interactions[3];/* pair interactions (density summed over passes, gradient, force) */
+  uint64_t candidates[3];  /* candidate pairs tested by the neighbour scan, same loops */
+  uint64_t launches;       /* kernel launches issued since the context was created */
+} swift_gpu_info;
+
+typedef struct swift_gpu_ctx swift_gpu_ctx;
+
+/* Fill *p with the defaults (unit box, gamma 5/3, eta 1.2348, kernel_gamma
+ * 1.825742, alpha_v 1, beta_v 3, alpha_c 1, h_tol 1e-4, max_iter 30, h_max 0,
+ * cell_margin 0.05, flags 0). Host only; never fails. */
+void swift_gpu_default_params(swift_gpu_params* p);
+
+/* Create a context for up to n_max particles on the current CUDA device.
+ * Allocates every device buffer the calls need (about 300 bytes per particle
+ * plus the cell arrays), so no later call allocates. *ctx is owned by the
+ * caller and freed with swift_gpu_destroy. Errors: ERR_ARG (null/invalid
+ * params, n_max < 1 or > 2^26), ERR_NOMEM, ERR_CUDA. */
+int swift_gpu_create(swift_gpu_ctx** ctx, const swift_gpu_params* p, int64_t n_max);
+
+/* Release every buffer of the context (synchronises the device). NULL is allowed. */
+int swift_gpu_destroy(swift_gpu_ctx* ctx);
+
+/* Replace the physics parameters (same rules as create). Host only. */
+int swift_gpu_set_params(swift_gpu_ctx* ctx, const swift_gpu_params* p);
+
+/* Build the cell grid and the particle order (paper Sec. 2.2: cubic cells,
+ * self and pair tasks; the sort tasks of Sec. 2.2.2 left on the CPU there).
+ * pos_h[n]: float4 (x, y, z, h), device. The cell width is the largest of
+ * min_cell_width and (1 + cell_margin) * kernel_gamma * max_i h_i, rounded up
+ * so an integer number nc >= 3 of cells spans each box edge; cell ids are
+ * computed in FP64 (wrap into [0,L), floor(x nc / L), clamp) and particles are
+ * stably sorted by cell id (ties keep the input order). Device-side errors:
+ * ERR_ARG (NaN/Inf position, h <= 0), ERR_H_EXCEEDS_CELL (support wider than
+ * L/3). Host errors: ERR_ARG, ERR_CAPACITY (n > n_max). n = 0 is allowed. */
+int swift_gpu_build_cells(swift_gpu_ctx* ctx, const float* pos_h, int64_t n, float min_cell_width,
+                          void* stream);
+
+/* Density loop with the Newton iteration on h (Sec. 2.1.2, Eqs. 2-6).
+ * pos_h_in[n]: float4 (x, y, z, h) - the same positions as build_cells; h is
+ *              the starting smoothing length.
+ * vel_m[n]:    float4 (vx, vy, vz, m).
+ * active[n]:   uint8, nonzero = compute this particle; NULL = all active.
+ * Outputs (device, caller order):
+ *   h_out[n]        final smoothing length (inactive: copied from pos_h_in.w)
+ *   rho4[n]         float4 (rho, drho/dh, n, dn/dh) - the part_recv_d record of
+ *                   Sec. 2.3.2.3 (Eq. 2, 5, 6)
+ *   curl_div[n]     float4 (curl v x, y, z, div v) (Eqs. 3-4, differenced form)
+ *   ngb_count[n]    uint32 neighbours j != i with r_ij < H_i (may be NULL)
+ * For inactive particles rho4 and curl_div are INPUTS: they must hold that
+ * particle's last values, which the gradient and force loops read.
+ * Each active particle iterates h <- h - F/F' on F = n - (eta/h)^3 until
+ * |F| <= h_tol (eta/h)^3, at most max_iter passes; all outputs belong to the
+ * final h. Runs as ONE persistent cooperative launch. Device-side status:
+ * ERR_H_NOT_CONVERGED / ERR_H_EXCEEDS_CELL with detail = number of particles
+ * (outputs are still written at their last h), ERR_TIMEOUT.
+ * Requires build_cells (ERR_ORDER otherwise). */
+int swift_gpu_density(swift_gpu_ctx* ctx, const float* pos_h_in, const float* vel_m, const uint8_t* active,
+                      float* h_out, float* rho4, float* curl_div, uint32_t* ngb_count, void* stream);
+
+/* Gradient loop (Sec. 2.1.3): per active i, over j with r_ij < H_i,
+ * v_sig,max = max_j (c_i + c_j - beta mu_ij) (Eqs. 10-11, j = i included) and
+ * the Laplacian of u, 2 sum_j (m_j/rho_j)(u_i - u_j) (dW/dr)/r.
+ * u[n]: internal energy (device, caller order). vsig_lapu[n]: float2 output.
+ * Also evaluates the per-particle ghost step for all particles:
+ * f = 1/Omega (Eq. 8), P = (gamma-1) rho u, c = sqrt(gamma (gamma-1) u),
+ * Balsara B. Requires density (ERR_ORDER otherwise). */
+int swift_gpu_gradient(swift_gpu_ctx* ctx, const float* u, float* vsig_lapu, void* stream);
+
+/* Force loop (Sec. 2.1.4): per active i over j with r_ij < max(H_i, H_j):
+ * pressure acceleration (Eq. 17), du/dt (Eq. 18), artificial viscosity
+ * (Eqs. 7, 9-11, 16) with its heating term, artificial conduction
+ * (Eqs. 19, 20, 22) and dh/dt = -(h/(3 rho)) f sum_j m_j v_ij . grad W(h_i).
+ * u[n] internal energy; alpha_v_i[n], alpha_c_i[n]: per-particle coefficients
+ * or NULL for the constants in the parameters.
+ * accel_dudt[n]: float4 (a_x, a_y, a_z, du/dt) output; dh_dt[n] may be NULL.
+ * reductions: NULL or a DEVICE array of 8 doubles receiving FP64 sums over
+ * active particles: [0..2] sum m a, [3] sum m (v.a + du/dt), [4] sum |m a|,
+ * [5] sum m (|v.a| + |du/dt|), [6] sum m du/dt, [7] number of interactions.
+ * Requires density (ERR_ORDER otherwise); evaluates the ghost step itself. */
+int swift_gpu_force(swift_gpu_ctx* ctx, const float* u, const float* alpha_v_i, const float* alpha_c_i,
+                    float* accel_dudt, float* dh_dt, double* reductions, void* stream);
+
+/* Adjoint of density + ghost + force (not in the paper): given
+ * grad_accel_dudt[n] = float4 (dL/da_x, dL/da_y, dL/da_z, dL/d(du/dt)) for a
+ * scalar loss L of the outputs of the last swift_gpu_force call, write
+ * grad_x[n] (float4, w unused), grad_v[n] (float4, w unused), grad_u[n].
+ * h_mode 0: h held fixed; 1: h = h(x) through the converged h equation
+ * (implicit-function term). Recomputes the density sums instead of storing
+ * pair lists. Requires force (ERR_ORDER otherwise); all particles must have
+ * been active. */
+int swift_gpu_force_backward(swift_gpu_ctx* ctx, const float* grad_accel_dudt, float* grad_x, float* grad_v,
+                             float* grad_u, int h_mode, void* stream);
+
+/* Wait for the stream of the last call and read the device status word:
+ * *status = first device-side error code (0 = none), *detail = its count or
+ * index. Clears the status word. Blocking. */
+int swift_gpu_sync_status(swift_gpu_ctx* ctx, int* status, int64_t* detail);
+
+/* Fill *info (blocking: synchronises the context's last stream). */
+int swift_gpu_get_info(swift_gpu_ctx* ctx, swift_gpu_info* info);
+
+/* Copy the cell id of every particle (caller order) and the sort permutation
+ * (sorted position k -> caller index perm[k]) of the last build into device
+ * arrays cell_id[n], perm[n] (either may be NULL). Asynchronous. */
+int swift_gpu_get_cells(swift_gpu_ctx* ctx, uint32_t* cell_id, uint32_t* perm, void* stream);
+
+/* Read / set the work-distribution knobs. */
+int swift_gpu_get_tuning(swift_gpu_ctx* ctx, swift_gpu_tuning* t);
+int swift_gpu_set_tuning(swift_gpu_ctx* ctx, const swift_gpu_tuning* t);
+
+/* Time the given loop (0 density, 1 gradient, 2 force) on the data of the
+ * last calls for each candidate tuning and keep the fastest. Requires force
+ * to have run once. Blocking; leaves outputs of the last calls unchanged. */
+int swift_gpu_autotune(swift_gpu_ctx* ctx, int loop, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SWIFT_GPU_H */

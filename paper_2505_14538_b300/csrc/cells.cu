@@ -1,0 +1,325 @@
+// cells.cu -- device-side binning of particles into the periodic cell grid
+// (Sec. 2.2, Fig. 3: cubic cells, self and pair interactions) and the stable
+// sort of particles by cell id, all without host synchronisation.
+//
+//   k_scan_h       max of h, NaN / h <= 0 checks
+//   k_grid_setup   nc, widths, h cap, key bits (one thread)
+//   k_cell_ids     FP64 cell id per particle (wrap, floor(x nc / L), clamp)
+//   radix passes   LSD radix sort of (cell id, original index), 8-bit digits,
+//                  stable, so ties keep the input order
+//   k_cell_start   start offset of every cell (empty cells included)
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace sg {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;  // 2048
+constexpr int kRadixThreads = 256;
+constexpr int kRadixItems = 16;
+constexpr int kRadixTile = kRadixThreads * kRadixItems;  // 4096
+
+// ------------------------------------------------------------------ scans
+// Exclusive scan of uint32, three phases: per-tile sums, scan of the sums in
+// one block, then per-tile scans with the offsets.
+__device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned* smem, unsigned* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) smem[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    unsigned s = (lane < (int)(blockDim.x >> 5)) ? smem[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    smem[lane] = s;  // inclusive per warp
+  }
+  __syncthreads();
+  unsigned warp_off = (w > 0) ? smem[w - 1] : 0u;
+  if (total) *total = smem[(blockDim.x >> 5) - 1];
+  unsigned r = warp_off + x - v;
+  __syncthreads();
+  return r;
+}
+
+__global__ void k_scan_tiles(const unsigned* __restrict__ in, int m, unsigned* __restrict__ tile_sums) {
+  __shared__ unsigned sm[32];
+  const int base = blockIdx.x * kScanTile;
+  unsigned s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    int i = base + threadIdx.x * kScanItems + k;
+    s += (i < m) ? in[i] : 0u;
+  }
+  unsigned tot;
+  block_excl_scan(s, sm, &tot);
+  if (threadIdx.x == 0) tile_sums[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_top(unsigned* __restrict__ tile_sums, int ntiles) {
+  __shared__ unsigned sm[32];
+  unsigned carry = 0;
+  for (int base = 0; base < ntiles; base += kScanTile) {
+    unsigned v[kScanItems];
+    unsigned s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      int i = base + threadIdx.x * kScanItems + k;
+      v[k] = (i < ntiles) ? tile_sums[i] : 0u;
+      s += v[k];
+    }
+    unsigned tot;
+    unsigned off = block_excl_scan(s, sm, &tot) + carry;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      int i = base + threadIdx.x * kScanItems + k;
+      if (i < ntiles) tile_sums[i] = off;
+      off += v[k];
+    }
+    carry += tot;
+    __syncthreads();
+  }
+}
+
+__global__ void k_scan_down(const unsigned* __restrict__ in, int m, const unsigned* __restrict__ tile_offs,
+                            unsigned* __restrict__ out) {
+  __shared__ unsigned sm[32];
+  const int base = blockIdx.x * kScanTile;
+  unsigned v[kScanItems];
+  unsigned s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    int i = base + threadIdx.x * kScanItems + k;
+    v[k] = (i < m) ? in[i] : 0u;
+    s += v[k];
+  }
+  unsigned off = block_excl_scan(s, sm, nullptr) + tile_offs[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    int i = base + threadIdx.x * kScanItems + k;
+    if (i < m) out[i] = off;
+    off += v[k];
+  }
+}
+
+int scan_tiles_needed(int64_t m) { return (int)((m + kScanTile - 1) / kScanTile); }
+
+// out may alias in. tile_tmp needs scan_tiles_needed(m) entries.
+void exclusive_scan(Ctx* c, const unsigned* in, unsigned* out, int m, unsigned* tile_tmp, cudaStream_t s) {
+  if (m <= 0) return;
+  int nt = scan_tiles_needed(m);
+  k_scan_tiles<<<nt, kScanThreads, 0, s>>>(in, m, tile_tmp);
+  k_scan_top<<<1, kScanThreads, 0, s>>>(tile_tmp, nt);
+  k_scan_down<<<nt, kScanThreads, 0, s>>>(in, m, tile_tmp, out);
+  c->launches += 3;
+}
+
+// ------------------------------------------------------------- grid setup
+__global__ void k_scan_h(const float4* __restrict__ pos_h, int n, float L0, float L1, float L2,
+                         unsigned* __restrict__ hmax_bits, Status* st) {
+  float hm = 0.0f;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    float4 p = pos_h[i];
+    bool bad = !(isfinite(p.x) && isfinite(p.y) && isfinite(p.z) && isfinite(p.w)) || !(p.w > 0.0f);
+    if (bad) set_error(st, SWIFT_GPU_ERR_ARG);
+    else hm = fmaxf(hm, p.w);
+  }
+  for (int o = 16; o > 0; o >>= 1) hm = fmaxf(hm, __shfl_xor_sync(0xffffffffu, hm, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(hmax_bits, __float_as_uint(hm));  // h > 0: bits order like values
+}
+
+__global__ void k_grid_setup(const unsigned* __restrict__ hmax_bits, Grid* g, Phys ph, float margin,
+                             float min_width, int nc_cap, Status* st) {
+  float hmax = __uint_as_float(*hmax_bits);
+  float want = fmaxf(min_width, (1.0f + margin) * ph.kg * hmax);
+  int nct = 1;
+  for (int a = 0; a < 3; ++a) {
+    int nc = want > 0.0f ? (int)floorf(ph.L[a] / want) : nc_cap;
+    if (nc > nc_cap) nc = nc_cap;
+    if (nc < 3) {
+      nc = 3;
+      if (want > ph.L[a] / 3.0f) set_error(st, SWIFT_GPU_ERR_H_EXCEEDS_CELL);
+    }
+    g->nc[a] = nc;
+    g->L[a] = ph.L[a];
+    g->width[a] = ph.L[a] / (float)nc;
+    nct *= nc;
+  }
+  g->ncells = nct;
+  float wmin = fminf(g->width[0], fminf(g->width[1], g->width[2]));
+  // largest float h with kernel_gamma * h <= wmin in FP64 terms
+  float hc = wmin * (1.0f - 9.5367432e-7f) / ph.kg;  // 2^-20 margin against FP64 rounding of cell ids
+  while ((double)ph.kg * (double)hc > (double)wmin) hc = nextafterf(hc, 0.0f);
+  g->hcap_from_cells = 1;
+  if (ph.h_max > 0.0f && ph.h_max < hc) {
+    hc = ph.h_max;
+    g->hcap_from_cells = 0;
+  }
+  g->hcap = hc;
+  int bits = 0;
+  while ((1 << bits) < nct) ++bits;
+  g->key_bits = bits;
+}
+
+__global__ void k_cell_ids(const float4* __restrict__ pos_h, int n, const Grid* __restrict__ g,
+                           unsigned* __restrict__ keys, unsigned* __restrict__ vals) {
+  const int nx = g->nc[0], ny = g->nc[1], nz = g->nc[2];
+  const double Lx = g->L[0], Ly = g->L[1], Lz = g->L[2];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    float4 p = pos_h[i];
+    // wrap into [0, L) and floor(x nc / L), each FP64 operation rounded once
+    double x = p.x, y = p.y, z = p.z;
+    x = __dsub_rn(x, __dmul_rn(Lx, floor(__ddiv_rn(x, Lx))));
+    y = __dsub_rn(y, __dmul_rn(Ly, floor(__ddiv_rn(y, Ly))));
+    z = __dsub_rn(z, __dmul_rn(Lz, floor(__ddiv_rn(z, Lz))));
+    int cx = (int)floor(__ddiv_rn(__dmul_rn(x, (double)nx), Lx));
+    int cy = (int)floor(__ddiv_rn(__dmul_rn(y, (double)ny), Ly));
+    int cz = (int)floor(__ddiv_rn(__dmul_rn(z, (double)nz), Lz));
+    cx = min(max(cx, 0), nx - 1);
+    cy = min(max(cy, 0), ny - 1);
+    cz = min(max(cz, 0), nz - 1);
+    keys[i] = (unsigned)(cx + nx * (cy + ny * cz));
+    vals[i] = (unsigned)i;
+  }
+}
+
+// ------------------------------------------------------------ radix sort
+// Pass over digit `shift..shift+8`. Histogram layout: hist[d * nblocks + b].
+__global__ void k_radix_count(const unsigned* __restrict__ keys, int n, int shift, const Grid* __restrict__ g,
+                              unsigned* __restrict__ hist) {
+  __shared__ unsigned h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const bool live = shift < g->key_bits;
+  const int base = blockIdx.x * kRadixTile;
+  if (live) {
+    for (int k = 0; k < kRadixItems; ++k) {
+      int i = base + k * kRadixThreads + threadIdx.x;
+      if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+    }
+  } else if (threadIdx.x == 0) {
+    int cnt = min(kRadixTile, n - base);
+    h[0] = cnt > 0 ? cnt : 0;
+  }
+  __syncthreads();
+  hist[threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void k_radix_scatter(const unsigned* __restrict__ kin, const unsigned* __restrict__ vin, int n,
+                                int shift, const Grid* __restrict__ g, const unsigned* __restrict__ offs,
+                                unsigned* __restrict__ kout, unsigned* __restrict__ vout) {
+  __shared__ unsigned run[256];
+  __shared__ unsigned wcnt[kRadixThreads / 32][256];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool live = shift < g->key_bits;
+  run[threadIdx.x] = offs[threadIdx.x * gridDim.x + blockIdx.x];
+  for (int ww = 0; ww < kRadixThreads / 32; ++ww) wcnt[ww][threadIdx.x] = 0;
+  __syncthreads();
+  const int base = blockIdx.x * kRadixTile;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int k = 0; k < kRadixItems; ++k) {
+    int i = base + k * kRadixThreads + threadIdx.x;
+    bool valid = i < n;
+    unsigned key = valid ? kin[i] : 0u;
+    unsigned val = valid ? vin[i] : 0u;
+    unsigned d = live ? ((key >> shift) & 255u) : 0u;
+    unsigned vmask = __ballot_sync(0xffffffffu, valid);
+    unsigned peers = __match_any_sync(0xffffffffu, valid ? d : 0xffffffffu) & vmask;
+    unsigned rank = __popc(peers & lt);
+    if (valid && rank == 0) wcnt[w][d] = __popc(peers);
+    __syncthreads();
+    if (valid) {
+      unsigned pos = run[d] + rank;
+      for (int ww = 0; ww < w; ++ww) pos += wcnt[ww][d];
+      kout[pos] = key;
+      vout[pos] = val;
+    }
+    __syncthreads();
+    unsigned add = 0;
+    for (int ww = 0; ww < kRadixThreads / 32; ++ww) {
+      add += wcnt[ww][threadIdx.x];
+      wcnt[ww][threadIdx.x] = 0;
+    }
+    run[threadIdx.x] += add;
+    __syncthreads();
+  }
+}
+
+__global__ void k_cell_start(const unsigned* __restrict__ skeys, int n, const Grid* __restrict__ g,
+                             int* __restrict__ cell_start) {
+  const int nct = g->ncells;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= n; k += gridDim.x * blockDim.x) {
+    int lo = (k == 0) ? 0 : (int)skeys[k - 1] + 1;
+    int hi = (k == n) ? nct : (int)skeys[k];
+    for (int c = lo; c <= hi; ++c) cell_start[c] = k;
+  }
+}
+
+int build_cells_impl(Ctx* c, const float4* pos_h, int n, float min_width, cudaStream_t s) {
+  c->n = n;
+  cudaMemsetAsync(c->d_hmax_bits, 0, sizeof(unsigned), s);
+  int sm = c->num_sms;
+  if (n > 0) {
+    k_scan_h<<<min((n + 255) / 256, sm * 8), 256, 0, s>>>(pos_h, n, c->phys.L[0], c->phys.L[1], c->phys.L[2],
+                                                         c->d_hmax_bits, c->d_status);
+    c->launches++;
+  }
+  k_grid_setup<<<1, 1, 0, s>>>(c->d_hmax_bits, c->d_grid, c->phys, c->params.cell_margin, min_width, c->nc_cap,
+                               c->d_status);
+  c->launches++;
+  if (n > 0) {
+    int gb = min((n + 255) / 256, sm * 8);
+    k_cell_ids<<<gb, 256, 0, s>>>(pos_h, n, c->d_grid, c->d_keys[0], c->d_vals[0]);
+    c->launches++;
+    const int nb = (n + kRadixTile - 1) / kRadixTile;
+    int src = 0;
+    for (int shift = 0; shift < c->max_key_bits; shift += 8) {
+      k_radix_count<<<nb, kRadixThreads, 0, s>>>(c->d_keys[src], n, shift, c->d_grid, c->d_hist);
+      exclusive_scan(c, c->d_hist, c->d_hist, 256 * nb, c->d_scan_tmp, s);
+      k_radix_scatter<<<nb, kRadixThreads, 0, s>>>(c->d_keys[src], c->d_vals[src], n, shift, c->d_grid,
+                                                    c->d_hist, c->d_keys[1 - src], c->d_vals[1 - src]);
+      c->launches += 2;
+      src = 1 - src;
+    }
+    c->sorted_buf = src;  // keys/vals of this buffer are sorted by cell id
+  }
+  {
+    int gb = min((n + 1 + 255) / 256, sm * 8);
+    k_cell_start<<<max(gb, 1), 256, 0, s>>>(c->d_keys[c->sorted_buf], n, c->d_grid, c->d_cell_start);
+    c->launches++;
+  }
+  return cudaGetLastError() == cudaSuccess ? SWIFT_GPU_OK : SWIFT_GPU_ERR_CUDA;
+}
+
+}  // namespace sg
+
+namespace sg {
+
+__global__ void k_cells_export(const unsigned* __restrict__ skeys, const unsigned* __restrict__ svals, int n,
+                               uint32_t* __restrict__ cell_id, uint32_t* __restrict__ perm) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const unsigned src = svals[k];
+    if (cell_id) cell_id[src] = skeys[k];
+    if (perm) perm[k] = src;
+  }
+}
+
+int cells_export_impl(Ctx* c, uint32_t* cell_id, uint32_t* perm, cudaStream_t s) {
+  if (c->n == 0) return SWIFT_GPU_OK;
+  const int nb = min((c->n + 255) / 256, c->num_sms * 8);
+  k_cells_export<<<nb, 256, 0, s>>>(c->d_keys[c->sorted_buf], c->d_vals[c->sorted_buf], c->n, cell_id, perm);
+  c->launches++;
+  return cudaGetLastError() == cudaSuccess ? SWIFT_GPU_OK : SWIFT_GPU_ERR_CUDA;
+}
+
+}  // namespace sg

@@ -1,0 +1,229 @@
+// common.cuh -- device-side types and helpers shared by the sm_103a kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/swift_gpu.h"
+
+namespace sg {
+
+constexpr int kWarp = 32;
+constexpr int kItemMax = 32;          // particles per work item (one per lane at most)
+constexpr int kListCap = 48;          // per-lane neighbour list entries before a flush
+constexpr int kIndexBits = 26;        // list entry: j index (26 bits) + shift code (6 bits)
+constexpr uint32_t kIndexMask = (1u << kIndexBits) - 1u;
+constexpr float kPi = 3.14159265358979323846f;
+
+// Relative half-width of the band around H^2 in which the FP32 neighbour
+// decision is re-taken in FP64 from the same float inputs (16 ulp of H^2).
+constexpr float kBand = 16.0f * 1.1920929e-7f;
+
+// Device status word (first error wins; detail accumulates).
+struct Status {
+  int code;
+  int pad;
+  unsigned long long detail;
+};
+
+// Cell grid descriptor, computed on the device by the build so that no host
+// synchronisation is needed.
+struct Grid {
+  int nc[3];
+  int ncells;
+  float L[3];
+  float hcap;        // largest h with kernel_gamma*h <= cell width
+  int hcap_from_cells;
+  int key_bits;
+  float width[3];
+};
+
+// Physics constants for the kernels.
+struct Phys {
+  float L[3];
+  float kg;          // kernel_gamma
+  float gamma_eos;
+  float alpha_v, beta_v, alpha_c;
+  double eta3;       // eta^3
+  double h_tol;
+  int max_iter;
+  float h_max;       // user cap (0 = none)
+  int compensated;
+};
+
+struct Item {
+  int cell;
+  int off;   // offset into the particle index list
+  int cnt;   // 1..kItemMax
+  int pad;
+};
+
+// Statistics counters (device, 64-bit).
+enum StatSlot {
+  kStatInterDens = 0, kStatInterGrad, kStatInterForce,
+  kStatCandDens, kStatCandGrad, kStatCandForce,
+  kStatPasses, kStatItems,
+  kStatCount = 16
+};
+
+__device__ __forceinline__ void set_error(Status* st, int code, unsigned long long add = 1) {
+  atomicCAS(&st->code, 0, code);
+  atomicAdd(&st->detail, add);
+}
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+// TwoSum (Knuth): s + c carries the exact running sum of the added terms.
+__device__ __forceinline__ void two_sum_acc(float& s, float& c, float x) {
+  float t = s + x;
+  float bp = t - s;
+  float e = (s - (t - bp)) + (x - bp);
+  s = t;
+  c += e;
+}
+
+// Cubic-spline shape w(q) and dw/dq for q >= 0 (zero beyond q = 1).
+__device__ __forceinline__ void spline(float q, float& w, float& dw) {
+  float s = fmaxf(1.0f - q, 0.0f);
+  float wo = 2.0f * s * s * s;
+  float dwo = -6.0f * s * s;
+  float q2 = q * q;
+  float wi = fmaf(q2, fmaf(6.0f, q, -6.0f), 1.0f);
+  float dwi = q * fmaf(18.0f, q, -12.0f);
+  bool in = q < 0.5f;
+  w = in ? wi : wo;
+  dw = in ? dwi : dwo;
+}
+
+__device__ __forceinline__ float dspline(float q) {
+  float s = fmaxf(1.0f - q, 0.0f);
+  float dwo = -6.0f * s * s;
+  float dwi = q * fmaf(18.0f, q, -12.0f);
+  return q < 0.5f ? dwi : dwo;
+}
+
+__device__ __forceinline__ float r2_of(float dx, float dy, float dz) {
+  return fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+}
+
+// Shift code: bit 2a -> subtract L from the i coordinate on axis a (i sits
+// near the top of the box, j wrapped to the bottom); bit 2a+1 -> subtract L
+// from the j coordinate (j near the top, i near the bottom). Both
+// subtractions are exact in FP32 (Sterbenz), so the FP32 distance keeps the
+// accuracy of a plain difference of nearby coordinates.
+__device__ __forceinline__ void apply_shift(unsigned code, const float L[3], float& xi, float& yi, float& zi,
+                                            float& xj, float& yj, float& zj) {
+  if (code) {
+    if (code & 1u) xi -= L[0];
+    if (code & 2u) xj -= L[0];
+    if (code & 4u) yi -= L[1];
+    if (code & 8u) yj -= L[1];
+    if (code & 16u) zi -= L[2];
+    if (code & 32u) zj -= L[2];
+  }
+}
+
+// The neighbour predicate, re-taken in FP64 exactly as the definition states
+// it: dx = x_i - x_j, dx -= L round(dx/L), r2 = (dx^2 + dy^2) + dz^2 and
+// H = kernel_gamma * h, each operation rounded once (no contraction).
+static __device__ __noinline__ double exact_r2(float xi, float yi, float zi, float xj, float yj, float zj,
+                                        float Lx, float Ly, float Lz) {
+  double L[3] = {(double)Lx, (double)Ly, (double)Lz};
+  double d[3] = {__dsub_rn((double)xi, (double)xj), __dsub_rn((double)yi, (double)yj),
+                 __dsub_rn((double)zi, (double)zj)};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) d[a] = __dsub_rn(d[a], __dmul_rn(L[a], round(__ddiv_rn(d[a], L[a]))));
+  return __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2]));
+}
+
+__device__ __forceinline__ double exact_H2(float kg, float h) {
+  double H = __dmul_rn((double)kg, (double)h);
+  return __dmul_rn(H, H);
+}
+
+// Warp-wide max of an int.
+__device__ __forceinline__ int warp_max(int v) { return __reduce_max_sync(0xffffffffu, v); }
+__device__ __forceinline__ unsigned warp_sum(unsigned v) { return __reduce_add_sync(0xffffffffu, v); }
+
+// Nanosecond timer for bounded waits.
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier for cooperative (co-resident) launches. Bounded: gives up
+// after `limit_ns` and records SWIFT_GPU_ERR_TIMEOUT; returns false then.
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, Status* st,
+                                             unsigned long long limit_ns) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    unsigned nb = gridDim.x * gridDim.y * gridDim.z;
+    volatile unsigned* vgen = gen;
+    unsigned g = *vgen;
+    __threadfence();
+    unsigned arrived = atomicAdd(count, 1u);
+    if (arrived == nb - 1) {
+      atomicExch(count, 0u);
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      unsigned long long t0 = global_ns();
+      while (*vgen == g) {
+        __nanosleep(100);
+        if (global_ns() - t0 > limit_ns) {
+          set_error(st, SWIFT_GPU_ERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// Neighbour-cell ranges of cell c: the 27 cells around it as up to 18
+// contiguous runs of the cell-sorted particle array, each with its periodic
+// shift code.
+struct Range {
+  int begin, end;
+  unsigned code;
+};
+
+__device__ __forceinline__ int cell_ranges(const Grid& g, const int* __restrict__ cell_start, int c,
+                                           Range* r) {
+  const int nx = g.nc[0], ny = g.nc[1], nz = g.nc[2];
+  const int cx = c % nx, cy = (c / nx) % ny, cz = c / (nx * ny);
+  int k = 0;
+  for (int dz = -1; dz <= 1; ++dz) {
+    int z = cz + dz;
+    unsigned cz_code = 0;
+    if (z < 0) { z += nz; cz_code = 32u; }
+    else if (z >= nz) { z -= nz; cz_code = 16u; }
+    for (int dy = -1; dy <= 1; ++dy) {
+      int y = cy + dy;
+      unsigned cy_code = 0;
+      if (y < 0) { y += ny; cy_code = 8u; }
+      else if (y >= ny) { y -= ny; cy_code = 4u; }
+      const int row = nx * (y + ny * z);
+      const unsigned code = cz_code | cy_code;
+      int x0 = cx - 1, x1 = cx + 1;
+      if (x0 < 0) {
+        r[k++] = Range{cell_start[row + nx - 1], cell_start[row + nx], code | 2u};
+        x0 = 0;
+      }
+      if (x1 >= nx) {
+        r[k++] = Range{cell_start[row], cell_start[row + 1], code | 1u};
+        x1 = nx - 1;
+      }
+      r[k++] = Range{cell_start[row + x0], cell_start[row + x1 + 1], code};
+    }
+  }
+  return k;
+}
+
+}  // namespace sg

@@ -1,0 +1,99 @@
+// internal.h -- host-side context shared by the .cu files of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+struct swift_gpu_ctx;
+
+namespace sg {
+
+struct Ctx {
+  int device = 0;
+  int num_sms = 0;
+  swift_gpu_params params{};
+  swift_gpu_tuning tuning{};
+  Phys phys{};
+  int64_t n_max = 0;
+  int nc_cap = 0;
+  int max_key_bits = 0;
+  int n = 0;
+  int sorted_buf = 0;
+  uint64_t launches = 0;
+  int state = 0;  // bit 0 cells, 1 density, 2 ghost, 3 force
+  int all_active = 1;
+  int last_passes = 0;
+  cudaStream_t last_stream = nullptr;
+  // arguments of the last calls (autotune re-runs them; they are idempotent)
+  const float4* last_pos_in = nullptr;
+  const float4* last_vel_in = nullptr;
+  const uint8_t* last_active = nullptr;
+  float* last_h_out = nullptr;
+  float4* last_rho4 = nullptr;
+  float4* last_cd = nullptr;
+  uint32_t* last_ngb = nullptr;
+  const float* last_u = nullptr;
+  const float* last_alpha_v = nullptr;
+  const float* last_alpha_c = nullptr;
+  float2* last_grad_out = nullptr;
+  float4* last_force_out = nullptr;
+  float* last_dhdt = nullptr;
+
+  // device buffers (all allocated at create)
+  Status* d_status = nullptr;
+  Grid* d_grid = nullptr;
+  unsigned* d_hmax_bits = nullptr;
+  unsigned* d_keys[2] = {nullptr, nullptr};
+  unsigned* d_vals[2] = {nullptr, nullptr};
+  unsigned* d_hist = nullptr;
+  unsigned* d_scan_tmp = nullptr;
+  int* d_cell_start = nullptr;
+  float4* d_pos = nullptr;    // sorted (x, y, z, h)
+  float4* d_vel = nullptr;    // sorted (vx, vy, vz, m)
+  float4* d_rho4 = nullptr;   // sorted (rho, drho/dh, n, dn/dh)
+  float4* d_cd = nullptr;     // sorted (curl, div)
+  float* d_h = nullptr;       // sorted h during the Newton iteration
+  float2* d_bracket = nullptr;// sorted Newton bracket (lo, hi)
+  unsigned* d_ngb = nullptr;  // sorted neighbour counts
+  float4* d_ga = nullptr;     // sorted ghost (A = f P/rho^2, f, rho, c)
+  float4* d_gb = nullptr;     // sorted ghost (B, alpha_v, alpha_c P, u)
+  uint8_t* d_act = nullptr;   // sorted active flags
+  Item* d_items0 = nullptr;   // active work items (kept for gradient/force)
+  int* d_plist0 = nullptr;
+  Item* d_items[2] = {nullptr, nullptr};
+  int* d_plist[2] = {nullptr, nullptr};
+  int* d_counters = nullptr;  // per pass: [item_count, plist_count, ticket] x (max passes + 1); + barrier
+  unsigned long long* d_stats = nullptr;
+  double* d_red_partial = nullptr;  // per block partial FP64 reductions
+  float4* d_scratch4[4] = {nullptr, nullptr, nullptr, nullptr};  // adjoint work arrays (sorted)
+  float* d_scratch1[2] = {nullptr, nullptr};
+  int red_blocks = 0;
+  int max_passes = 0;
+
+  // host mirrors
+  Status* h_status = nullptr;  // pinned
+  unsigned long long* h_stats = nullptr;  // pinned
+};
+
+Ctx* from(swift_gpu_ctx* c);
+
+int scan_tiles_needed(int64_t m);
+void exclusive_scan(Ctx* c, const unsigned* in, unsigned* out, int m, unsigned* tile_tmp, cudaStream_t s);
+int build_cells_impl(Ctx* c, const float4* pos_h, int n, float min_width, cudaStream_t s);
+int density_impl(Ctx* c, const float4* pos_h_in, const float4* vel_m, const uint8_t* active, float* h_out,
+                 float4* rho4, float4* curl_div, uint32_t* ngb, cudaStream_t s);
+int ghost_impl(Ctx* c, const float* u, const float* alpha_v, const float* alpha_c, cudaStream_t s);
+int gradient_impl(Ctx* c, float2* vsig_lapu, cudaStream_t s);
+int force_impl(Ctx* c, float4* accel_dudt, float* dh_dt, double* reductions, cudaStream_t s);
+int cells_export_impl(Ctx* c, uint32_t* cell_id, uint32_t* perm, cudaStream_t s);
+int autotune_impl(Ctx* c, int loop, cudaStream_t s);
+int backward_impl(Ctx* c, const float4* grad_ad, float4* grad_x, float4* grad_v, float* grad_u, int h_mode,
+                  cudaStream_t s);
+
+// counters layout helpers
+constexpr int kCtrPerPass = 4;  // item_count, plist_count, ticket, spare
+__host__ __device__ inline int ctr_index(int pass, int which) { return pass * kCtrPerPass + which; }
+
+}  // namespace sg

@@ -1,0 +1,932 @@
+// loops.cu -- the SPH pair-interaction loops of Sec. 2.1 as persistent
+// work-queue kernels for sm_103a.
+//
+// Work decomposition. A work item is a run of <= 32 active particles of one
+// cell (cells with more are split). A warp takes an item from a ticket
+// counter, scans the 27 neighbour cells (self and pair interactions of
+// Sec. 2.2.2 / Fig. 3) as up to 18 contiguous runs of the cell-sorted arrays,
+// and works in two phases per chunk of 32 candidates:
+//   phase 1  the chunk's positions are staged in shared memory with one
+//            coalesced float4 load; every lane tests its particle against
+//            them (r^2 < H^2 with a 16-ulp guard band) and appends hits to a
+//            lane-private neighbour list in shared memory;
+//   phase 2  when a list may overflow (and at the end) every lane walks its
+//            own list and evaluates the full interaction, so the expensive
+//            arithmetic runs with nearly all lanes busy instead of diverging
+//            on the ~15 % hit rate of a cell scan.
+// Items with few particles give each particle 2-8 lanes that split the
+// candidates and are combined with warp shuffles at the end.
+//
+// Pairs whose FP32 r^2 lies within the guard band of H^2 re-take the
+// neighbour decision in FP64 from the same float inputs, so neighbour sets
+// equal those of the FP64 definition exactly.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace sg {
+
+constexpr int kLoopThreads = 256;
+constexpr int kWarpsPerBlock = kLoopThreads / 32;
+constexpr int kCap = 64;  // list entries per lane
+constexpr size_t kWarpSmemBytes = (size_t)kCap * 32 * sizeof(unsigned) + 32 * sizeof(float4);
+constexpr size_t kLoopSmemBytes = kWarpSmemBytes * kWarpsPerBlock;
+constexpr unsigned kFull = 0xffffffffu;
+constexpr unsigned long long kBarrierNs = 5000000000ull;  // 5 s
+
+__device__ __forceinline__ unsigned* warp_list(unsigned char* smem) {
+  return reinterpret_cast<unsigned*>(smem + (threadIdx.x >> 5) * kWarpSmemBytes);
+}
+__device__ __forceinline__ float4* warp_stage(unsigned char* smem) {
+  return reinterpret_cast<float4*>(smem + (threadIdx.x >> 5) * kWarpSmemBytes + (size_t)kCap * 32 * 4);
+}
+
+// Lane layout of an item with cnt particles: L lanes per particle (power of
+// two, L <= lmax), particle slot a = lane % A, sub-lane s = lane / A, A = 32/L.
+__device__ __forceinline__ int lanes_per_particle(int cnt, int lmax) {
+  int p2 = 1;
+  while (p2 < cnt) p2 <<= 1;
+  int L = 32 / p2;
+  return L < lmax ? L : lmax;
+}
+
+// ---------------------------------------------------------------- engine
+// Phase 2: every lane evaluates its listed interactions.
+template <class Op>
+__device__ __forceinline__ void flush(Op& op, typename Op::I& I, const unsigned* list, int cnt) {
+  const unsigned lane = lane_id();
+  const int m = warp_max(cnt);
+  for (int t = 0; t < m; ++t) {
+    if (t < cnt) {
+      unsigned e = list[t * 32 + lane];
+      op.interact(I, (int)(e & kIndexMask), e >> kIndexBits);
+    }
+  }
+}
+
+// Scan the 27 neighbour cells of `cell` for lane particle I.
+template <class Op>
+__device__ __forceinline__ void scan_cells(Op& op, typename Op::I& I, const Grid& g, const int* __restrict__ cell_start,
+                                           const float4* __restrict__ pos, int cell, int L, int s, bool live,
+                                           unsigned* list, float4* stage, unsigned& ncand) {
+  const unsigned lane = lane_id();
+  Range rg[18];
+  const int nr = cell_ranges(g, cell_start, cell, rg);
+  int cnt = 0;
+  for (int q = 0; q < nr; ++q) {
+    const Range r = rg[q];
+    float xi = I.x, yi = I.y, zi = I.z;
+    if (r.code & 1u) xi -= g.L[0];
+    if (r.code & 4u) yi -= g.L[1];
+    if (r.code & 16u) zi -= g.L[2];
+    for (int base = r.begin; base < r.end; base += 32) {
+      const int len = min(32, r.end - base);
+      const int need = (len + L - 1) / L;
+      if (__any_sync(kFull, cnt + need > kCap)) {
+        flush(op, I, list, cnt);
+        cnt = 0;
+      }
+      __syncwarp();
+      if ((int)lane < len) {
+        float4 p = pos[base + lane];
+        if (r.code & 2u) p.x -= g.L[0];
+        if (r.code & 8u) p.y -= g.L[1];
+        if (r.code & 32u) p.z -= g.L[2];
+        stage[lane] = make_float4(p.x, p.y, p.z, op.stage_w(p.w));
+      }
+      __syncwarp();
+      if (live) {
+        for (int k = s; k < len; k += L) {
+          const float4 c = stage[k];
+          const float dx = xi - c.x, dy = yi - c.y, dz = zi - c.z;
+          const float r2 = r2_of(dx, dy, dz);
+          if (op.candidate(I, r2, c.w)) {
+            list[cnt * 32 + lane] = (unsigned)(base + k) | (r.code << kIndexBits);
+            ++cnt;
+          }
+        }
+        ncand += (unsigned)((len - s + L - 1) / L);
+      }
+    }
+  }
+  flush(op, I, list, cnt);
+}
+
+// Warp-level reductions across the L sub-lanes of a particle.
+__device__ __forceinline__ float sub_sum(float v, int A) {
+  for (int o = A; o < 32; o <<= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+__device__ __forceinline__ float sub_max(float v, int A) {
+  for (int o = A; o < 32; o <<= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, o));
+  return v;
+}
+__device__ __forceinline__ unsigned sub_sum_u(unsigned v, int A) {
+  for (int o = A; o < 32; o <<= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+__device__ __forceinline__ void sub_sum2(float& s, float& c, int A) {
+  for (int o = A; o < 32; o <<= 1) {
+    float so = __shfl_xor_sync(kFull, s, o);
+    float co = __shfl_xor_sync(kFull, c, o);
+    float t = s + so;
+    float bp = t - s;
+    float e = (s - (t - bp)) + (so - bp);
+    s = t;
+    c = c + co + e;
+  }
+}
+
+__device__ __forceinline__ int take_ticket(int* ticket) {
+  int t = 0;
+  if (lane_id() == 0) t = atomicAdd(ticket, 1);
+  return __shfl_sync(kFull, t, 0);
+}
+
+// ============================================================ density loop
+struct DensArgs {
+  Grid* grid;
+  const int* cell_start;
+  const unsigned* perm;   // sorted -> caller index
+  int n;
+  Phys ph;
+  int lmax;
+  int single_pass;
+  // caller arrays
+  const float4* pos_in;
+  const float4* vel_in;
+  const uint8_t* active;
+  float* h_out;
+  float4* rho4_io;
+  float4* cd_io;
+  unsigned* ngb_out;
+  // sorted arrays
+  float4* pos;
+  float4* vel;
+  float* h;
+  float2* bracket;
+  float4* rho4;
+  float4* cd;
+  unsigned* ngb;
+  uint8_t* act;
+  // work lists
+  Item* items0;
+  int* plist0;
+  Item* items[2];
+  int* plist[2];
+  int* ctr;
+  unsigned* barrier;  // [count, generation]
+  Status* st;
+  unsigned long long* stats;
+};
+
+struct DensOp {
+  struct I {
+    float x, y, z, h, H2lo, H2hi, invH, c3, c4;
+    float vx, vy, vz;
+    float ns, nc, rs, rc, dn, dr, div, cx, cy, cz;
+    unsigned count;
+    int k;
+  };
+  const float4* __restrict__ pos;
+  const float4* __restrict__ vel;
+  float L[3];
+  float kg;
+  int compensated;
+
+  __device__ __forceinline__ float stage_w(float) const { return 0.0f; }
+  __device__ __forceinline__ bool candidate(const I& i, float r2, float) const { return r2 < i.H2hi; }
+  __device__ __forceinline__ void interact(I& i, int j, unsigned code) const {
+    const float4 pj = pos[j];
+    const float4 vj = vel[j];
+    float xi = i.x, yi = i.y, zi = i.z, xj = pj.x, yj = pj.y, zj = pj.z;
+    apply_shift(code, L, xi, yi, zi, xj, yj, zj);
+    const float dx = xi - xj, dy = yi - yj, dz = zi - zj;
+    const float r2 = r2_of(dx, dy, dz);
+    if (r2 >= i.H2lo) {
+      if (!(exact_r2(i.x, i.y, i.z, pj.x, pj.y, pj.z, L[0], L[1], L[2]) < exact_H2(kg, i.h))) return;
+    }
+    const float invr = r2 > 0.0f ? rsqrtf(r2) : 0.0f;
+    const float r = r2 * invr;
+    float w, dw;
+    spline(r * i.invH, w, dw);
+    const float W = i.c3 * w;
+    const float dW = i.c4 * dw;
+    const float mj = vj.w;
+    if (compensated) {
+      two_sum_acc(i.ns, i.nc, W);
+      two_sum_acc(i.rs, i.rc, mj * W);
+    } else {
+      i.ns += W;
+      i.rs = fmaf(mj, W, i.rs);
+    }
+    const float t = fmaf(r, dW, 3.0f * W);
+    i.dn += t;
+    i.dr = fmaf(mj, t, i.dr);
+    const float g = mj * dW * invr;
+    const float dvx = vj.x - i.vx, dvy = vj.y - i.vy, dvz = vj.z - i.vz;
+    i.div = fmaf(g, fmaf(dvz, dz, fmaf(dvy, dy, dvx * dx)), i.div);
+    i.cx = fmaf(-g, fmaf(dvy, dz, -dvz * dy), i.cx);
+    i.cy = fmaf(-g, fmaf(dvz, dx, -dvx * dz), i.cy);
+    i.cz = fmaf(-g, fmaf(dvx, dy, -dvy * dx), i.cz);
+    i.count += (j != i.k) ? 1u : 0u;
+  }
+};
+
+__device__ __forceinline__ void dens_load_i(DensOp::I& I, const DensArgs& a, int k) {
+  const float4 p = a.pos[k];
+  const float4 v = a.vel[k];
+  const float h = a.h[k];
+  I.x = p.x; I.y = p.y; I.z = p.z; I.h = h;
+  const float H = a.ph.kg * h;
+  const float H2 = H * H;
+  I.H2lo = H2 * (1.0f - kBand);
+  I.H2hi = H2 * (1.0f + kBand);
+  I.invH = 1.0f / H;
+  I.c3 = (8.0f / kPi) * I.invH * I.invH * I.invH;
+  I.c4 = I.c3 * I.invH;
+  I.vx = v.x; I.vy = v.y; I.vz = v.z;
+  I.ns = I.nc = I.rs = I.rc = I.dn = I.dr = I.div = I.cx = I.cy = I.cz = 0.0f;
+  I.count = 0;
+  I.k = k;
+}
+
+__global__ void __launch_bounds__(kLoopThreads) k_density(DensArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const unsigned lane = lane_id();
+  const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const Grid g = *a.grid;
+  unsigned* list = warp_list(smem);
+  float4* stage = warp_stage(smem);
+
+  // ---- prologue: gather into cell order, inputs of inactive particles
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < a.n; k += gridDim.x * blockDim.x) {
+    const unsigned src = a.perm[k];
+    const float4 p = a.pos_in[src];
+    a.pos[k] = p;
+    a.vel[k] = a.vel_in[src];
+    a.h[k] = p.w;
+    const uint8_t act = a.active ? (a.active[src] != 0) : 1;
+    a.act[k] = act;
+    a.bracket[k] = make_float2(0.0f, __int_as_float(0x7f800000));
+    if (!act) {
+      a.rho4[k] = a.rho4_io[src];
+      a.cd[k] = a.cd_io[src];
+      a.ngb[k] = a.ngb_out ? a.ngb_out[src] : 0u;
+    }
+  }
+  // ---- active work items, one warp per cell
+  for (int c = gwarp; c < g.ncells; c += nwarps) {
+    const int cs = a.cell_start[c], ce = a.cell_start[c + 1];
+    if (ce == cs) continue;
+    int total = 0;
+    for (int b = cs; b < ce; b += 32) {
+      const int k = b + (int)lane;
+      const bool on = k < ce && (a.active ? a.active[a.perm[k]] != 0 : true);
+      total += __popc(__ballot_sync(kFull, on));
+    }
+    if (total == 0) continue;
+    const int nit = (total + kItemMax - 1) / kItemMax;
+    int pbase = 0, ibase = 0;
+    if (lane == 0) {
+      pbase = atomicAdd(&a.ctr[ctr_index(0, 1)], total);
+      ibase = atomicAdd(&a.ctr[ctr_index(0, 0)], nit);
+    }
+    pbase = __shfl_sync(kFull, pbase, 0);
+    ibase = __shfl_sync(kFull, ibase, 0);
+    int w = 0;
+    for (int b = cs; b < ce; b += 32) {
+      const int k = b + (int)lane;
+      const bool on = k < ce && (a.active ? a.active[a.perm[k]] != 0 : true);
+      const unsigned m = __ballot_sync(kFull, on);
+      if (on) a.plist0[pbase + w + __popc(m & ((1u << lane) - 1u))] = k;
+      w += __popc(m);
+    }
+    for (int t = (int)lane; t < nit; t += 32)
+      a.items0[ibase + t] = Item{c, pbase + t * kItemMax, min(kItemMax, total - t * kItemMax), 0};
+  }
+  if (!grid_barrier(&a.barrier[0], &a.barrier[1], a.st, kBarrierNs)) return;
+
+  DensOp op;
+  op.pos = a.pos;
+  op.vel = a.vel;
+  op.L[0] = g.L[0]; op.L[1] = g.L[1]; op.L[2] = g.L[2];
+  op.kg = a.ph.kg;
+  op.compensated = a.ph.compensated;
+  unsigned ninter = 0, ncand = 0;
+  const int max_pass = a.single_pass ? 1 : a.ph.max_iter;
+  int pass = 0;
+  for (; pass < max_pass; ++pass) {
+    const int n_items = *((volatile int*)&a.ctr[ctr_index(pass, 0)]);
+    if (n_items == 0) break;
+    const Item* items = pass == 0 ? a.items0 : a.items[pass & 1];
+    const int* plist = pass == 0 ? a.plist0 : a.plist[pass & 1];
+    Item* items_next = a.items[(pass + 1) & 1];
+    int* plist_next = a.plist[(pass + 1) & 1];
+    const bool last = pass == max_pass - 1;
+    for (;;) {
+      const int t = take_ticket(&a.ctr[ctr_index(pass, 2)]);
+      if (t >= n_items) break;
+      const Item it = items[t];
+      const int L = lanes_per_particle(it.cnt, a.lmax);
+      const int A = 32 / L;
+      const int slot = (int)lane % A, s = (int)lane / A;
+      const bool live = slot < it.cnt;
+      DensOp::I I;
+      const int k = live ? plist[it.off + slot] : plist[it.off];
+      dens_load_i(I, a, k);
+      scan_cells(op, I, g, a.cell_start, a.pos, it.cell, L, s, live, list, stage, ncand);
+      // combine sub-lanes
+      sub_sum2(I.ns, I.nc, A);
+      sub_sum2(I.rs, I.rc, A);
+      I.dn = sub_sum(I.dn, A);
+      I.dr = sub_sum(I.dr, A);
+      I.div = sub_sum(I.div, A);
+      I.cx = sub_sum(I.cx, A);
+      I.cy = sub_sum(I.cy, A);
+      I.cz = sub_sum(I.cz, A);
+      I.count = sub_sum_u(I.count, A);
+      bool again = false;
+      if (live && s == 0) {
+        ninter += I.count;
+        // Newton step on F(h) = n(h) - (eta/h)^3 in FP64 (Sec. 2.1.2)
+        const double n = (double)I.ns + (double)I.nc;
+        const double hd = (double)I.h;
+        const double h3 = hd * hd * hd;
+        const double target = a.ph.eta3 / h3;
+        const double F = n - target;
+        bool conv = fabs(F) <= a.ph.h_tol * target;
+        int flag = 0;
+        if (!conv && !last) {
+          const float2 br = a.bracket[k];
+          double lo = br.x, hi = br.y;
+          if (F < 0.0) lo = fmax(lo, hd);
+          else hi = fmin(hi, hd);
+          if (F < 0.0 && I.h >= g.hcap) {
+            flag = g.hcap_from_cells ? SWIFT_GPU_ERR_H_EXCEEDS_CELL : SWIFT_GPU_ERR_H_NOT_CONVERGED;
+          } else {
+            const double dn_dh = -(double)I.dn / hd;
+            const double Fp = dn_dh + 3.0 * a.ph.eta3 / (h3 * hd);
+            double hn = (Fp > 0.0) ? hd - F / Fp : __longlong_as_double(0x7ff8000000000000ll);
+            if (hn == hn) hn = fmin(fmax(hn, 0.5 * hd), 2.0 * hd);
+            if (!(hn == hn) || !(hn > lo) || !(hn < hi)) {
+              if (isfinite(hi) && lo > 0.0) hn = 0.5 * (lo + hi);
+              else if (!isfinite(hi)) hn = 2.0 * hd;
+              else hn = 0.5 * hd;
+            }
+            hn = fmin(hn, (double)g.hcap);
+            const float hf = (float)hn;
+            if (hf == I.h) {
+              conv = true;  // the float h cannot move: converged to FP32 resolution
+            } else {
+              a.h[k] = hf;
+              a.bracket[k] = make_float2((float)lo, (float)hi);
+              again = true;
+            }
+          }
+        } else if (!conv) {
+          flag = SWIFT_GPU_ERR_H_NOT_CONVERGED;
+        }
+        if (!again) {
+          const float rho = I.rs + I.rc;
+          const float invh = 1.0f / I.h;
+          a.rho4[k] = make_float4(rho, -I.dr * invh, I.ns + I.nc, -I.dn * invh);
+          const float ir = 1.0f / rho;
+          a.cd[k] = make_float4(I.cx * ir, I.cy * ir, I.cz * ir, I.div * ir);
+          a.ngb[k] = I.count;
+          if (flag) set_error(a.st, flag);
+        }
+      }
+      // unconverged particles of this item form one item of the next pass
+      const unsigned am = __ballot_sync(kFull, again);
+      if (am) {
+        const int nu = __popc(am);
+        int pbase = 0, ibase = 0;
+        if (lane == 0) {
+          pbase = atomicAdd(&a.ctr[ctr_index(pass + 1, 1)], nu);
+          ibase = atomicAdd(&a.ctr[ctr_index(pass + 1, 0)], 1);
+        }
+        pbase = __shfl_sync(kFull, pbase, 0);
+        ibase = __shfl_sync(kFull, ibase, 0);
+        if (again) plist_next[pbase + __popc(am & ((1u << lane) - 1u))] = k;
+        if (lane == 0) items_next[ibase] = Item{it.cell, pbase, nu, 0};
+      }
+    }
+    if (!grid_barrier(&a.barrier[0], &a.barrier[1], a.st, kBarrierNs)) return;
+  }
+  // ---- epilogue: h into the sorted positions, outputs to caller order
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < a.n; k += gridDim.x * blockDim.x) {
+    const unsigned dst = a.perm[k];
+    const float h = a.h[k];
+    a.pos[k].w = h;
+    a.h_out[dst] = h;
+    if (a.act[k]) {
+      a.rho4_io[dst] = a.rho4[k];
+      a.cd_io[dst] = a.cd[k];
+      if (a.ngb_out) a.ngb_out[dst] = a.ngb[k];
+    }
+  }
+  ninter = warp_sum(ninter);
+  ncand = warp_sum(ncand);
+  if (lane == 0) {
+    atomicAdd(&a.stats[kStatInterDens], (unsigned long long)ninter);
+    atomicAdd(&a.stats[kStatCandDens], (unsigned long long)ncand);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    atomicExch(&a.stats[kStatPasses], (unsigned long long)pass);
+    atomicExch(&a.stats[kStatItems], (unsigned long long)a.ctr[ctr_index(0, 0)]);
+  }
+}
+
+// ============================================================== ghost step
+// Per particle (Eq. 8, equation of state, sound speed, Balsara switch):
+// ga = (A = f P / rho^2, f, rho, c), gb = (B, alpha_v, alpha_c P, u).
+__global__ void k_ghost(int n, const unsigned* __restrict__ perm, const float4* __restrict__ pos,
+                        const float4* __restrict__ rho4, const float4* __restrict__ cd, const float* __restrict__ u,
+                        const float* __restrict__ alpha_v, const float* __restrict__ alpha_c, Phys ph,
+                        float4* __restrict__ ga, float4* __restrict__ gb) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const unsigned src = perm[k];
+    const float h = pos[k].w;
+    const float4 r = rho4[k];
+    const float4 c4 = cd[k];
+    const float uk = u[src];
+    const float rho = r.x;
+    const float omega = 1.0f + h / (3.0f * rho) * r.y;
+    const float f = 1.0f / omega;
+    const float P = (ph.gamma_eos - 1.0f) * rho * uk;
+    const float c = sqrtf(ph.gamma_eos * (ph.gamma_eos - 1.0f) * uk);
+    const float A = f * P / (rho * rho);
+    const float ad = fabsf(c4.w);
+    const float ac = sqrtf(c4.x * c4.x + c4.y * c4.y + c4.z * c4.z);
+    const float B = ad > 0.0f ? ad / (ad + ac + 1e-4f * c / h) : 0.0f;
+    const float av = alpha_v ? alpha_v[src] : ph.alpha_v;
+    const float acoef = alpha_c ? alpha_c[src] : ph.alpha_c;
+    ga[k] = make_float4(A, f, rho, c);
+    gb[k] = make_float4(B, av, acoef * P, uk);
+  }
+}
+
+// ============================================================ gradient loop
+struct GradArgs {
+  Grid* grid;
+  const int* cell_start;
+  const unsigned* perm;
+  Phys ph;
+  int lmax;
+  const float4* pos;
+  const float4* vel;
+  const float4* ga;
+  const float4* gb;
+  const Item* items;
+  const int* plist;
+  const int* ctr;   // item count at ctr[0]
+  int* ticket;
+  float2* out;      // caller order
+  Status* st;
+  unsigned long long* stats;
+};
+
+struct GradOp {
+  struct I {
+    float x, y, z, h, H2lo, H2hi, invH, c4;
+    float vx, vy, vz, c, u;
+    float vsig, lap;
+    unsigned count;
+    int k;
+  };
+  const float4* __restrict__ pos;
+  const float4* __restrict__ vel;
+  const float4* __restrict__ ga;
+  const float4* __restrict__ gb;
+  float L[3];
+  float kg, beta;
+
+  __device__ __forceinline__ float stage_w(float) const { return 0.0f; }
+  __device__ __forceinline__ bool candidate(const I& i, float r2, float) const { return r2 < i.H2hi; }
+  __device__ __forceinline__ void interact(I& i, int j, unsigned code) const {
+    const float4 pj = pos[j];
+    float xi = i.x, yi = i.y, zi = i.z, xj = pj.x, yj = pj.y, zj = pj.z;
+    apply_shift(code, L, xi, yi, zi, xj, yj, zj);
+    const float dx = xi - xj, dy = yi - yj, dz = zi - zj;
+    const float r2 = r2_of(dx, dy, dz);
+    if (!(r2 > 0.0f)) return;  // the particle itself: v_sig term added at load
+    if (r2 >= i.H2lo) {
+      if (!(exact_r2(i.x, i.y, i.z, pj.x, pj.y, pj.z, L[0], L[1], L[2]) < exact_H2(kg, i.h))) return;
+    }
+    const float4 vj = vel[j];
+    const float4 aj = ga[j];
+    const float uj = gb[j].w;
+    const float invr = rsqrtf(r2);
+    const float r = r2 * invr;
+    const float dW = i.c4 * dspline(r * i.invH);
+    const float dvx = i.vx - vj.x, dvy = i.vy - vj.y, dvz = i.vz - vj.z;
+    const float vr = fmaf(dvz, dz, fmaf(dvy, dy, dvx * dx)) * invr;
+    const float mu = fminf(vr, 0.0f);
+    i.vsig = fmaxf(i.vsig, fmaf(-beta, mu, i.c + aj.w));
+    i.lap = fmaf(__fdividef(vj.w, aj.z) * (i.u - uj), dW * invr, i.lap);
+    i.count += 1u;
+  }
+};
+
+__global__ void __launch_bounds__(kLoopThreads) k_gradient(GradArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const unsigned lane = lane_id();
+  const Grid g = *a.grid;
+  unsigned* list = warp_list(smem);
+  float4* stage = warp_stage(smem);
+  GradOp op;
+  op.pos = a.pos; op.vel = a.vel; op.ga = a.ga; op.gb = a.gb;
+  op.L[0] = g.L[0]; op.L[1] = g.L[1]; op.L[2] = g.L[2];
+  op.kg = a.ph.kg;
+  op.beta = a.ph.beta_v;
+  const int n_items = a.ctr[0];
+  unsigned ninter = 0, ncand = 0;
+  for (;;) {
+    const int t = take_ticket(a.ticket);
+    if (t >= n_items) break;
+    const Item it = a.items[t];
+    const int L = lanes_per_particle(it.cnt, a.lmax);
+    const int A = 32 / L;
+    const int slot = (int)lane % A, s = (int)lane / A;
+    const bool live = slot < it.cnt;
+    const int k = live ? a.plist[it.off + slot] : a.plist[it.off];
+    GradOp::I I;
+    const float4 p = a.pos[k];
+    const float4 v = a.vel[k];
+    const float4 gi = a.ga[k];
+    I.x = p.x; I.y = p.y; I.z = p.z; I.h = p.w;
+    const float H = a.ph.kg * p.w;
+    I.H2lo = H * H * (1.0f - kBand);
+    I.H2hi = H * H * (1.0f + kBand);
+    I.invH = 1.0f / H;
+    I.c4 = (8.0f / kPi) * I.invH * I.invH * I.invH * I.invH;
+    I.vx = v.x; I.vy = v.y; I.vz = v.z;
+    I.c = gi.w;
+    I.u = a.gb[k].w;
+    I.vsig = 2.0f * gi.w;
+    I.lap = 0.0f;
+    I.count = 0;
+    I.k = k;
+    scan_cells(op, I, g, a.cell_start, a.pos, it.cell, L, s, live, list, stage, ncand);
+    I.vsig = sub_max(I.vsig, A);
+    I.lap = sub_sum(I.lap, A);
+    I.count = sub_sum_u(I.count, A);
+    if (live && s == 0) {
+      ninter += I.count;
+      a.out[a.perm[k]] = make_float2(I.vsig, 2.0f * I.lap);
+    }
+  }
+  ninter = warp_sum(ninter);
+  ncand = warp_sum(ncand);
+  if (lane == 0) {
+    atomicAdd(&a.stats[kStatInterGrad], (unsigned long long)ninter);
+    atomicAdd(&a.stats[kStatCandGrad], (unsigned long long)ncand);
+  }
+}
+
+// =============================================================== force loop
+struct ForceArgs {
+  Grid* grid;
+  const int* cell_start;
+  const unsigned* perm;
+  Phys ph;
+  int lmax;
+  const float4* pos;
+  const float4* vel;
+  const float4* ga;
+  const float4* gb;
+  const Item* items;
+  const int* plist;
+  const int* ctr;
+  int* ticket;
+  float4* out;      // caller order (a, du/dt)
+  float* dhdt;      // caller order, may be NULL
+  double* red_partial;  // [gridDim.x][8]
+  Status* st;
+  unsigned long long* stats;
+};
+
+struct ForceOp {
+  struct I {
+    float x, y, z, h, H2lo, H2hi, invH, c4;
+    float vx, vy, vz;
+    float A, f, rho, c, B, av, acP, u, P;
+    float axs, axc, ays, ayc, azs, azc, dus, duc, dh;
+    unsigned count;
+    int k;
+  };
+  const float4* __restrict__ pos;
+  const float4* __restrict__ vel;
+  const float4* __restrict__ ga;
+  const float4* __restrict__ gb;
+  float L[3];
+  float kg, beta, gm1;
+  int compensated;
+
+  // staged w: the j support squared (with the guard band)
+  __device__ __forceinline__ float stage_w(float hj) const {
+    const float H = kg * hj;
+    return H * H * (1.0f + kBand);
+  }
+  __device__ __forceinline__ bool candidate(const I& i, float r2, float H2j_hi) const {
+    return r2 < fmaxf(i.H2hi, H2j_hi);
+  }
+  __device__ __forceinline__ void interact(I& i, int j, unsigned code) const {
+    const float4 pj = pos[j];
+    float xi = i.x, yi = i.y, zi = i.z, xj = pj.x, yj = pj.y, zj = pj.z;
+    apply_shift(code, L, xi, yi, zi, xj, yj, zj);
+    const float dx = xi - xj, dy = yi - yj, dz = zi - zj;
+    const float r2 = r2_of(dx, dy, dz);
+    if (!(r2 > 0.0f)) return;  // the particle itself
+    const float Hj = kg * pj.w;
+    const float H2j = Hj * Hj;
+    if (r2 >= fmaxf(i.H2lo, H2j * (1.0f - kBand))) {
+      const double e = exact_r2(i.x, i.y, i.z, pj.x, pj.y, pj.z, L[0], L[1], L[2]);
+      if (!(e < exact_H2(kg, i.h)) && !(e < exact_H2(kg, pj.w))) return;
+    }
+    const float4 vj = vel[j];
+    const float4 aj = ga[j];  // (A, f, rho, c)
+    const float4 bj = gb[j];  // (B, alpha_v, alpha_c P, u)
+    const float invr = rsqrtf(r2);
+    const float r = r2 * invr;
+    const float ex = dx * invr, ey = dy * invr, ez = dz * invr;
+    const float dWi = i.c4 * dspline(r * i.invH);
+    const float invHj = __fdividef(1.0f, Hj);
+    const float ih2 = invHj * invHj;
+    const float dWj = ((8.0f / kPi) * ih2 * ih2) * dspline(r * invHj);
+    const float dvx = i.vx - vj.x, dvy = i.vy - vj.y, dvz = i.vz - vj.z;
+    const float vr = fmaf(dvz, ez, fmaf(dvy, ey, dvx * ex));
+    const float mj = vj.w;
+    const float fsum = fmaf(i.f, dWi, aj.y * dWj);
+    // pressure (Eq. 17) and its work (Eq. 18)
+    const float ps = mj * fmaf(i.A, dWi, aj.x * dWj);
+    float du = mj * i.A * dWi * vr;
+    // artificial viscosity (Eqs. 7, 9-11, 16) and heating
+    const float mu = fminf(vr, 0.0f);
+    const float vsig = fmaf(-beta, mu, i.c + aj.w);
+    const float alpha = 0.25f * (i.av + bj.y) * (i.B + bj.x);
+    const float irs = __fdividef(1.0f, i.rho + aj.z);
+    const float nu = -alpha * mu * vsig * irs;
+    const float vs = 0.5f * mj * nu * fsum;
+    du = fmaf(0.5f * vs, vr, du);
+    // artificial conduction (Eqs. 19, 20, 22)
+    const float Pj = gm1 * aj.z * bj.w;
+    const float Ps = i.P + Pj;
+    const float ac = Ps > 0.0f ? __fdividef(i.acP + bj.z, Ps) : 0.0f;
+    const float dP = 2.0f * fabsf(i.P - Pj) * irs;
+    const float vc = fabsf(vr) + (dP > 0.0f ? dP * rsqrtf(dP) : 0.0f);
+    du = fmaf(ac * vc * mj * (i.u - bj.w), fsum * irs, du);
+    const float as = ps + vs;
+    if (compensated) {
+      two_sum_acc(i.axs, i.axc, -as * ex);
+      two_sum_acc(i.ays, i.ayc, -as * ey);
+      two_sum_acc(i.azs, i.azc, -as * ez);
+      two_sum_acc(i.dus, i.duc, du);
+    } else {
+      i.axs = fmaf(-as, ex, i.axs);
+      i.ays = fmaf(-as, ey, i.ays);
+      i.azs = fmaf(-as, ez, i.azs);
+      i.dus += du;
+    }
+    i.dh = fmaf(mj * dWi, vr, i.dh);
+    i.count += 1u;
+  }
+};
+
+__global__ void __launch_bounds__(kLoopThreads) k_force(ForceArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[kWarpsPerBlock][8];
+  const unsigned lane = lane_id();
+  const Grid g = *a.grid;
+  unsigned* list = warp_list(smem);
+  float4* stage = warp_stage(smem);
+  ForceOp op;
+  op.pos = a.pos; op.vel = a.vel; op.ga = a.ga; op.gb = a.gb;
+  op.L[0] = g.L[0]; op.L[1] = g.L[1]; op.L[2] = g.L[2];
+  op.kg = a.ph.kg;
+  op.beta = a.ph.beta_v;
+  op.gm1 = a.ph.gamma_eos - 1.0f;
+  op.compensated = a.ph.compensated;
+  const int n_items = a.ctr[0];
+  unsigned ninter = 0, ncand = 0;
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (;;) {
+    const int t = take_ticket(a.ticket);
+    if (t >= n_items) break;
+    const Item it = a.items[t];
+    const int L = lanes_per_particle(it.cnt, a.lmax);
+    const int A = 32 / L;
+    const int slot = (int)lane % A, s = (int)lane / A;
+    const bool live = slot < it.cnt;
+    const int k = live ? a.plist[it.off + slot] : a.plist[it.off];
+    ForceOp::I I;
+    const float4 p = a.pos[k];
+    const float4 v = a.vel[k];
+    const float4 gi = a.ga[k];
+    const float4 bi = a.gb[k];
+    I.x = p.x; I.y = p.y; I.z = p.z; I.h = p.w;
+    const float H = a.ph.kg * p.w;
+    I.H2lo = H * H * (1.0f - kBand);
+    I.H2hi = H * H * (1.0f + kBand);
+    I.invH = 1.0f / H;
+    I.c4 = (8.0f / kPi) * I.invH * I.invH * I.invH * I.invH;
+    I.vx = v.x; I.vy = v.y; I.vz = v.z;
+    I.A = gi.x; I.f = gi.y; I.rho = gi.z; I.c = gi.w;
+    I.B = bi.x; I.av = bi.y; I.acP = bi.z; I.u = bi.w;
+    I.P = op.gm1 * gi.z * bi.w;
+    I.axs = I.axc = I.ays = I.ayc = I.azs = I.azc = I.dus = I.duc = I.dh = 0.0f;
+    I.count = 0;
+    I.k = k;
+    scan_cells(op, I, g, a.cell_start, a.pos, it.cell, L, s, live, list, stage, ncand);
+    sub_sum2(I.axs, I.axc, A);
+    sub_sum2(I.ays, I.ayc, A);
+    sub_sum2(I.azs, I.azc, A);
+    sub_sum2(I.dus, I.duc, A);
+    I.dh = sub_sum(I.dh, A);
+    I.count = sub_sum_u(I.count, A);
+    if (live && s == 0) {
+      ninter += I.count;
+      const float ax = I.axs + I.axc, ay = I.ays + I.ayc, az = I.azs + I.azc, du = I.dus + I.duc;
+      const unsigned dst = a.perm[k];
+      a.out[dst] = make_float4(ax, ay, az, du);
+      if (a.dhdt) a.dhdt[dst] = -(I.h / (3.0f * I.rho)) * I.f * I.dh;
+      const double m = v.w;
+      const double max_ = m * ax, may = m * ay, maz = m * az;
+      const double va = (double)v.x * ax + (double)v.y * ay + (double)v.z * az;
+      acc[0] += max_;
+      acc[1] += may;
+      acc[2] += maz;
+      acc[3] += m * (va + (double)du);
+      acc[4] += sqrt(max_ * max_ + may * may + maz * maz);
+      acc[5] += m * (fabs(va) + fabs((double)du));
+      acc[6] += m * (double)du;
+      acc[7] += (double)I.count;
+    }
+  }
+  // block partial of the FP64 reductions (deterministic final sum elsewhere)
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    double x = acc[q];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+    if (lane == 0) red[threadIdx.x >> 5][q] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < 8) {
+    double x = 0.0;
+    for (int w = 0; w < kWarpsPerBlock; ++w) x += red[w][threadIdx.x];
+    a.red_partial[blockIdx.x * 8 + threadIdx.x] = x;
+  }
+  ninter = warp_sum(ninter);
+  ncand = warp_sum(ncand);
+  if (lane == 0) {
+    atomicAdd(&a.stats[kStatInterForce], (unsigned long long)ninter);
+    atomicAdd(&a.stats[kStatCandForce], (unsigned long long)ncand);
+  }
+}
+
+__global__ void k_reduce_partials(const double* __restrict__ part, int nblocks, double* __restrict__ out) {
+  if (threadIdx.x < 8) {
+    double x = 0.0;
+    for (int b = 0; b < nblocks; ++b) x += part[b * 8 + threadIdx.x];
+    out[threadIdx.x] = x;
+  }
+}
+
+// =================================================================== hosts
+static int persistent_blocks(Ctx* c, const void* kern) {
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kLoopThreads, kLoopSmemBytes);
+  if (per_sm < 1) per_sm = 1;
+  if (c->tuning.blocks_per_sm > 0 && c->tuning.blocks_per_sm < per_sm) per_sm = c->tuning.blocks_per_sm;
+  return per_sm * c->num_sms;
+}
+
+static bool g_attr_done = false;
+static void ensure_attrs() {
+  if (g_attr_done) return;
+  cudaFuncSetAttribute(k_density, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLoopSmemBytes);
+  cudaFuncSetAttribute(k_gradient, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLoopSmemBytes);
+  cudaFuncSetAttribute(k_force, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLoopSmemBytes);
+  g_attr_done = true;
+}
+
+int density_impl(Ctx* c, const float4* pos_in, const float4* vel_in, const uint8_t* active, float* h_out,
+                 float4* rho4, float4* cd, uint32_t* ngb, cudaStream_t s) {
+  ensure_attrs();
+  const int nblk = persistent_blocks(c, (const void*)k_density);
+  cudaMemsetAsync(c->d_counters, 0, sizeof(int) * (size_t)(kCtrPerPass * (c->max_passes + 2) + 2), s);
+  DensArgs a;
+  a.grid = c->d_grid;
+  a.cell_start = c->d_cell_start;
+  a.perm = c->d_vals[c->sorted_buf];
+  a.n = c->n;
+  a.ph = c->phys;
+  a.lmax = c->tuning.max_lanes_per_particle;
+  a.single_pass = (c->params.flags & SWIFT_GPU_NO_H_ITER) ? 1 : 0;
+  a.pos_in = pos_in;
+  a.vel_in = vel_in;
+  a.active = active;
+  a.h_out = h_out;
+  a.rho4_io = rho4;
+  a.cd_io = cd;
+  a.ngb_out = ngb;
+  a.pos = c->d_pos;
+  a.vel = c->d_vel;
+  a.h = c->d_h;
+  a.bracket = c->d_bracket;
+  a.rho4 = c->d_rho4;
+  a.cd = c->d_cd;
+  a.ngb = c->d_ngb;
+  a.act = c->d_act;
+  a.items0 = c->d_items0;
+  a.plist0 = c->d_plist0;
+  a.items[0] = c->d_items[0];
+  a.items[1] = c->d_items[1];
+  a.plist[0] = c->d_plist[0];
+  a.plist[1] = c->d_plist[1];
+  a.ctr = c->d_counters;
+  a.barrier = reinterpret_cast<unsigned*>(c->d_counters + kCtrPerPass * (c->max_passes + 2));
+  a.st = c->d_status;
+  a.stats = c->d_stats;
+  void* args[] = {&a};
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_density, dim3(nblk), dim3(kLoopThreads), args,
+                                              kLoopSmemBytes, s);
+  c->launches += 2;
+  c->all_active = active == nullptr;
+  return e == cudaSuccess ? SWIFT_GPU_OK : SWIFT_GPU_ERR_CUDA;
+}
+
+int ghost_impl(Ctx* c, const float* u, const float* alpha_v, const float* alpha_c, cudaStream_t s) {
+  if (c->n == 0) return SWIFT_GPU_OK;
+  const int nb = min((c->n + 255) / 256, c->num_sms * 8);
+  k_ghost<<<nb, 256, 0, s>>>(c->n, c->d_vals[c->sorted_buf], c->d_pos, c->d_rho4, c->d_cd, u, alpha_v, alpha_c,
+                             c->phys, c->d_ga, c->d_gb);
+  c->launches++;
+  return cudaGetLastError() == cudaSuccess ? SWIFT_GPU_OK : SWIFT_GPU_ERR_CUDA;
+}
+
+int gradient_impl(Ctx* c, float2* out, cudaStream_t s) {
+  ensure_attrs();
+  const int nblk = persistent_blocks(c, (const void*)k_gradient);
+  int* ticket = c->d_counters + kCtrPerPass * (c->max_passes + 1) + 0;
+  cudaMemsetAsync(ticket, 0, sizeof(int), s);
+  GradArgs a;
+  a.grid = c->d_grid;
+  a.cell_start = c->d_cell_start;
+  a.perm = c->d_vals[c->sorted_buf];
+  a.ph = c->phys;
+  a.lmax = c->tuning.max_lanes_per_particle;
+  a.pos = c->d_pos;
+  a.vel = c->d_vel;
+  a.ga = c->d_ga;
+  a.gb = c->d_gb;
+  a.items = c->d_items0;
+  a.plist = c->d_plist0;
+  a.ctr = c->d_counters;  // pass-0 item count
+  a.ticket = ticket;
+  a.out = out;
+  a.st = c->d_status;
+  a.stats = c->d_stats;
+  k_gradient<<<nblk, kLoopThreads, kLoopSmemBytes, s>>>(a);
+  c->launches += 2;
+  return cudaGetLastError() == cudaSuccess ? SWIFT_GPU_OK : SWIFT_GPU_ERR_CUDA;
+}
+
+int force_impl(Ctx* c, float4* out, float* dhdt, double* reductions, cudaStream_t s) {
+  ensure_attrs();
+  const int nblk = persistent_blocks(c, (const void*)k_force);
+  int* ticket = c->d_counters + kCtrPerPass * (c->max_passes + 1) + 1;
+  cudaMemsetAsync(ticket, 0, sizeof(int), s);
+  ForceArgs a;
+  a.grid = c->d_grid;
+  a.cell_start = c->d_cell_start;
+  a.perm = c->d_vals[c->sorted_buf];
+  a.ph = c->phys;
+  a.lmax = c->tuning.max_lanes_per_particle;
+  a.pos = c->d_pos;
+  a.vel = c->d_vel;
+  a.ga = c->d_ga;
+  a.gb = c->d_gb;
+  a.items = c->d_items0;
+  a.plist = c->d_plist0;
+  a.ctr = c->d_counters;
+  a.ticket = ticket;
+  a.out = out;
+  a.dhdt = dhdt;
+  a.red_partial = c->d_red_partial;
+  a.st = c->d_status;
+  a.stats = c->d_stats;
+  k_force<<<nblk, kLoopThreads, kLoopSmemBytes, s>>>(a);
+  c->launches += 2;
+  if (reductions) {
+    k_reduce_partials<<<1, 32, 0, s>>>(c->d_red_partial, nblk, reductions);
+    c->launches++;
+  }
+  return cudaGetLastError() == cudaSuccess ? SWIFT_GPU_OK : SWIFT_GPU_ERR_CUDA;
+}
+
+}  // namespace sg

@@ -1,0 +1,60 @@
+// tune.cu -- the autotuner: times one loop over the data of the last calls
+// for each candidate work distribution and keeps the fastest. Every loop is
+// deterministic given its inputs, so re-running it rewrites the same outputs.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace sg {
+
+static int run_loop(Ctx* c, int loop, cudaStream_t s) {
+  if (loop == 0)
+    return density_impl(c, c->last_pos_in, c->last_vel_in, c->last_active, c->last_h_out, c->last_rho4, c->last_cd,
+                        c->last_ngb, s);
+  if (loop == 1) return gradient_impl(c, c->last_grad_out, s);
+  return force_impl(c, c->last_force_out, c->last_dhdt, nullptr, s);
+}
+
+int autotune_impl(Ctx* c, int loop, cudaStream_t s) {
+  if (loop == 1 && !c->last_grad_out) return SWIFT_GPU_ERR_ORDER;
+  const int cand_l[4] = {1, 2, 4, 8};
+  const int cand_b[3] = {0, 1, 2};
+  swift_gpu_tuning best = c->tuning, orig = c->tuning;
+  float best_ms = 1e30f;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return SWIFT_GPU_ERR_CUDA;
+  // the force loop reads the ghost arrays of the force call; gradient those of the gradient call
+  if (loop == 2 || loop == 0) ghost_impl(c, c->last_u, c->last_alpha_v, c->last_alpha_c, s);
+  else ghost_impl(c, c->last_u, nullptr, nullptr, s);
+  int rc = SWIFT_GPU_OK;
+  for (int bi = 0; bi < 3 && rc == SWIFT_GPU_OK; ++bi) {
+    for (int li = 0; li < 4 && rc == SWIFT_GPU_OK; ++li) {
+      c->tuning.max_lanes_per_particle = cand_l[li];
+      c->tuning.blocks_per_sm = cand_b[bi];
+      rc = run_loop(c, loop, s);  // warm-up
+      float tot = 0.0f;
+      for (int r = 0; r < 3 && rc == SWIFT_GPU_OK; ++r) {
+        cudaEventRecord(e0, s);
+        rc = run_loop(c, loop, s);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) rc = SWIFT_GPU_ERR_CUDA;
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        tot += ms;
+      }
+      if (rc == SWIFT_GPU_OK && tot < best_ms) {
+        best_ms = tot;
+        best = c->tuning;
+      }
+    }
+  }
+  c->tuning = rc == SWIFT_GPU_OK ? best : orig;
+  // leave the ghost arrays as the last force call left them
+  ghost_impl(c, c->last_u, c->last_alpha_v, c->last_alpha_c, s);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc;
+}
+
+}  // namespace sg

@@ -1,0 +1,226 @@
+"""Thin PyTorch binding of the C ABI (``include/swift_gpu.h``).
+
+Every method marshals torch CUDA tensors into the pointers the C call takes
+and passes the current CUDA stream; every step of the computation runs in
+the library's kernels. PyTorch only allocates device memory and owns
+streams. Names follow the C entry points (``swift_gpu_<name>`` -> ``<name>``).
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional
+
+import torch
+
+from . import _lib
+
+_F32 = torch.float32
+
+
+class SwiftGPUError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: int = 0):
+        self.code = code
+        self.detail = detail
+        super().__init__(f"{where}: {_lib.ERR_NAMES.get(code, code)} (detail {detail})")
+
+
+def _check(rc: int, where: str):
+    if rc != _lib.OK:
+        raise SwiftGPUError(rc, where)
+
+
+def _ptr(t: Optional[torch.Tensor], dtype=None, cols=None, n=None, name="tensor"):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if n is not None and t.shape[0] != n:
+        raise ValueError(f"{name} must have {n} rows, got {t.shape[0]}")
+    if cols is not None and (t.dim() != 2 or t.shape[1] != cols):
+        raise ValueError(f"{name} must have shape (n, {cols})")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def make_params(**kw) -> _lib.Params:
+    """Library defaults with keyword overrides (box, gamma_eos, eta, kernel_gamma, alpha_v,
+    beta_v, alpha_c, h_tol, max_iter, h_max, cell_margin, flags)."""
+    p = _lib.default_params()
+    for k, v in kw.items():
+        if k == "box":
+            p.box = (ctypes.c_float * 3)(*[float(b) for b in v])
+        elif not hasattr(p, k):
+            raise KeyError(k)
+        else:
+            setattr(p, k, v)
+    return p
+
+
+class Context:
+    """One library context (``swift_gpu_create``) sized for up to ``n_max`` particles."""
+
+    def __init__(self, n_max: int, **params):
+        self.lib = _lib.load()
+        self.params = make_params(**params)
+        self.n_max = int(n_max)
+        self.handle = ctypes.c_void_p()
+        _check(self.lib.swift_gpu_create(ctypes.byref(self.handle), ctypes.byref(self.params),
+                                         ctypes.c_int64(self.n_max)), "swift_gpu_create")
+        self.n = 0
+
+    def close(self):
+        if self.handle:
+            self.lib.swift_gpu_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, **params):
+        self.params = make_params(**{**self._params_dict(), **params})
+        _check(self.lib.swift_gpu_set_params(self.handle, ctypes.byref(self.params)), "swift_gpu_set_params")
+
+    def _params_dict(self):
+        p = self.params
+        return dict(box=tuple(p.box), gamma_eos=p.gamma_eos, eta=p.eta, kernel_gamma=p.kernel_gamma,
+                    alpha_v=p.alpha_v, beta_v=p.beta_v, alpha_c=p.alpha_c, h_tol=p.h_tol, max_iter=p.max_iter,
+                    h_max=p.h_max, cell_margin=p.cell_margin, flags=p.flags)
+
+    # ------------------------------------------------------------ calls
+    def build_cells(self, pos_h: torch.Tensor, min_cell_width: float = 0.0, stream=None):
+        n = pos_h.shape[0]
+        _check(self.lib.swift_gpu_build_cells(self.handle, _ptr(pos_h, _F32, 4, name="pos_h"), ctypes.c_int64(n),
+                                              ctypes.c_float(min_cell_width), _stream(stream)),
+               "swift_gpu_build_cells")
+        self.n = n
+
+    def density(self, pos_h, vel_m, active=None, h_out=None, rho4=None, curl_div=None, ngb_count=None,
+                want_ngb=True, stream=None):
+        n = self.n
+        dev = pos_h.device
+        if active is not None and (rho4 is None or curl_div is None):
+            raise ValueError("with an active subset, rho4 and curl_div carry the inactive particles' values")
+        h_out = h_out if h_out is not None else torch.empty(n, dtype=_F32, device=dev)
+        rho4 = rho4 if rho4 is not None else torch.empty(n, 4, dtype=_F32, device=dev)
+        curl_div = curl_div if curl_div is not None else torch.empty(n, 4, dtype=_F32, device=dev)
+        if ngb_count is None and want_ngb:
+            ngb_count = torch.zeros(n, dtype=torch.int32, device=dev)
+        _check(self.lib.swift_gpu_density(
+            self.handle, _ptr(pos_h, _F32, 4, n, "pos_h"), _ptr(vel_m, _F32, 4, n, "vel_m"),
+            _ptr(active, torch.uint8, None, n, "active"), _ptr(h_out, _F32, None, n, "h_out"),
+            _ptr(rho4, _F32, 4, n, "rho4"), _ptr(curl_div, _F32, 4, n, "curl_div"),
+            _ptr(ngb_count, torch.int32, None, n, "ngb_count"), _stream(stream)), "swift_gpu_density")
+        return dict(h=h_out, rho4=rho4, curl_div=curl_div, ngb=ngb_count)
+
+    def gradient(self, u, vsig_lapu=None, stream=None):
+        n = self.n
+        vsig_lapu = vsig_lapu if vsig_lapu is not None else torch.empty(n, 2, dtype=_F32, device=u.device)
+        _check(self.lib.swift_gpu_gradient(self.handle, _ptr(u, _F32, None, n, "u"),
+                                           _ptr(vsig_lapu, _F32, 2, n, "vsig_lapu"), _stream(stream)),
+               "swift_gpu_gradient")
+        return vsig_lapu
+
+    def force(self, u, alpha_v=None, alpha_c=None, accel_dudt=None, dh_dt=None, reductions=None,
+              want_dh=True, want_reductions=True, stream=None):
+        n = self.n
+        dev = u.device
+        accel_dudt = accel_dudt if accel_dudt is not None else torch.empty(n, 4, dtype=_F32, device=dev)
+        if dh_dt is None and want_dh:
+            dh_dt = torch.empty(n, dtype=_F32, device=dev)
+        if reductions is None and want_reductions:
+            reductions = torch.zeros(8, dtype=torch.float64, device=dev)
+        _check(self.lib.swift_gpu_force(
+            self.handle, _ptr(u, _F32, None, n, "u"), _ptr(alpha_v, _F32, None, n, "alpha_v"),
+            _ptr(alpha_c, _F32, None, n, "alpha_c"), _ptr(accel_dudt, _F32, 4, n, "accel_dudt"),
+            _ptr(dh_dt, _F32, None, n, "dh_dt"), _ptr(reductions, torch.float64, None, None, "reductions"),
+            _stream(stream)), "swift_gpu_force")
+        return dict(accel_dudt=accel_dudt, dh_dt=dh_dt, reductions=reductions)
+
+    def force_backward(self, grad_accel_dudt, h_mode: int = 0, stream=None):
+        n = self.n
+        dev = grad_accel_dudt.device
+        gx = torch.empty(n, 4, dtype=_F32, device=dev)
+        gv = torch.empty(n, 4, dtype=_F32, device=dev)
+        gu = torch.empty(n, dtype=_F32, device=dev)
+        _check(self.lib.swift_gpu_force_backward(
+            self.handle, _ptr(grad_accel_dudt, _F32, 4, n, "grad_accel_dudt"), _ptr(gx), _ptr(gv), _ptr(gu),
+            ctypes.c_int(h_mode), _stream(stream)), "swift_gpu_force_backward")
+        return gx, gv, gu
+
+    def sync_status(self):
+        code = ctypes.c_int()
+        detail = ctypes.c_int64()
+        _check(self.lib.swift_gpu_sync_status(self.handle, ctypes.byref(code), ctypes.byref(detail)),
+               "swift_gpu_sync_status")
+        return code.value, detail.value
+
+    def info(self) -> dict:
+        i = _lib.Info()
+        _check(self.lib.swift_gpu_get_info(self.handle, ctypes.byref(i)), "swift_gpu_get_info")
+        return dict(n=i.n, nc=tuple(i.nc), cell_width=tuple(i.cell_width), h_cap=i.h_cap, n_cells=i.n_cells,
+                    n_items=i.n_items, density_passes=i.density_passes, interactions=tuple(i.interactions),
+                    candidates=tuple(i.candidates), launches=i.launches)
+
+    def cells(self, stream=None):
+        n = self.n
+        dev = torch.device("cuda", torch.cuda.current_device())
+        cid = torch.empty(n, dtype=torch.int32, device=dev)
+        perm = torch.empty(n, dtype=torch.int32, device=dev)
+        _check(self.lib.swift_gpu_get_cells(self.handle, _ptr(cid), _ptr(perm), _stream(stream)),
+               "swift_gpu_get_cells")
+        return cid, perm
+
+    def tuning(self) -> dict:
+        t = _lib.Tuning()
+        _check(self.lib.swift_gpu_get_tuning(self.handle, ctypes.byref(t)), "swift_gpu_get_tuning")
+        return dict(threads_per_block=t.threads_per_block, max_lanes_per_particle=t.max_lanes_per_particle,
+                    blocks_per_sm=t.blocks_per_sm)
+
+    def set_tuning(self, threads_per_block=256, max_lanes_per_particle=4, blocks_per_sm=0):
+        t = _lib.Tuning(threads_per_block, max_lanes_per_particle, blocks_per_sm)
+        _check(self.lib.swift_gpu_set_tuning(self.handle, ctypes.byref(t)), "swift_gpu_set_tuning")
+
+    def autotune(self, loop: int, stream=None):
+        _check(self.lib.swift_gpu_autotune(self.handle, ctypes.c_int(loop), _stream(stream)), "swift_gpu_autotune")
+        return self.tuning()
+
+    # ------------------------------------------------------- whole step
+    def step(self, pos_h, vel_m, u, active=None, rho4=None, curl_div=None, alpha_v=None, alpha_c=None,
+             min_cell_width: float = 0.0, check: bool = True, stream=None):
+        """build_cells -> density (h iteration) -> gradient -> force on one stream.
+
+        With check=True the status word is read after the density call (a
+        host synchronisation); if the h iteration asked for a support wider
+        than a cell, the cells are rebuilt once with room for the new h and
+        the density call is repeated.
+        """
+        self.build_cells(pos_h, min_cell_width, stream)
+        d = self.density(pos_h, vel_m, active, rho4=rho4, curl_div=curl_div, stream=stream)
+        if check:
+            code, detail = self.sync_status()
+            if code == _lib.ERR_H_EXCEEDS_CELL:
+                h_new = d["h"]
+                w = float(self.params.kernel_gamma) * float(h_new.max()) * 1.5
+                self.build_cells(pos_h, max(min_cell_width, w), stream)
+                d = self.density(pos_h, vel_m, active, rho4=rho4, curl_div=curl_div, stream=stream)
+                code, detail = self.sync_status()
+            if code not in (_lib.OK, _lib.ERR_H_NOT_CONVERGED):
+                raise SwiftGPUError(code, "density", detail)
+            d["status"] = (code, detail)
+        g = self.gradient(u, stream=stream)
+        f = self.force(u, alpha_v, alpha_c, stream=stream)
+        out = dict(d)
+        out["vsig_lapu"] = g
+        out.update(f)
+        return out

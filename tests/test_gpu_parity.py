@@ -1,0 +1,249 @@
+"""GPU parity of the sm_103a kernels against the FP64 oracle, through the C ABI.
+
+Tolerances (written here, from the arithmetic): cell ids, permutation and
+neighbour counts bit-exact; rho and h within 1e-5 relative; acceleration and
+du/dt within 1e-4 of each particle's force scale (sum over pairs of the
+magnitude of the pair term); total momentum within 1e-6 of sum |m a|.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2505_14538_b300 import ics
+
+pytestmark = pytest.mark.gpu
+
+KG = float(np.float32(1.825742))
+
+
+@pytest.fixture(scope="module")
+def sph():
+    from paper_2505_14538_b300 import sph as S
+    assert torch.cuda.is_available()
+    return S
+
+
+def dev_arrays(d, vel=None, u=None):
+    n = len(d["pos"])
+    pos_h = np.concatenate([d["pos"], d["h"][:, None]], 1).astype(np.float32)
+    v = d["vel"] if vel is None else vel
+    vel_m = np.concatenate([v, d["m"][:, None]], 1).astype(np.float32)
+    uu = d["u"] if u is None else u
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    return t(pos_h), t(vel_m), t(uu.astype(np.float32))
+
+
+def oracle_params(O, ctx_params, **kw):
+    p = O.Params(box=tuple(float(b) for b in ctx_params.box), gamma_eos=float(ctx_params.gamma_eos),
+                 eta=float(ctx_params.eta), kernel_gamma=float(ctx_params.kernel_gamma),
+                 alpha_v=float(ctx_params.alpha_v), beta_v=float(ctx_params.beta_v),
+                 alpha_c=float(ctx_params.alpha_c))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def run_gpu(sph, d, vel=None, u=None, min_cell_width=0.0, active=None, **params):
+    n = len(d["pos"])
+    ctx = sph.Context(max(n, 1), box=d["box"], **params)
+    pos_h, vel_m, ut = dev_arrays(d, vel, u)
+    act = None if active is None else torch.from_numpy(active.astype(np.uint8)).cuda()
+    ctx.build_cells(pos_h, min_cell_width)
+    out = ctx.density(pos_h, vel_m, act)
+    status = ctx.sync_status()
+    out["vsig_lapu"] = ctx.gradient(ut)
+    out.update(ctx.force(ut))
+    status2 = ctx.sync_status()
+    torch.cuda.synchronize()
+    res = {k: (v.cpu().numpy() if torch.is_tensor(v) else v) for k, v in out.items()}
+    res["status"] = status
+    res["status2"] = status2
+    res["info"] = ctx.info()
+    res["ctx"] = ctx
+    return res
+
+
+def lattice_state(n_side=16, seed=0, jitter=0.1):
+    d = ics.lattice(n_side, jitter=jitter)
+    rng = np.random.default_rng(seed)
+    n = len(d["pos"])
+    vel = rng.normal(0, 0.3, size=(n, 3)).astype(np.float32)
+    u = (d["u"] * rng.uniform(0.5, 1.5, n)).astype(np.float32)
+    return d, vel, u
+
+
+def check_against_oracle(O, d, vel, u, g, ctx, solve_tol=1e-13):
+    """Compare a GPU run with the oracle: h (own solve), then every output at the GPU's h."""
+    n = len(d["pos"])
+    x = d["pos"]
+    info = g["info"]
+    # h: the oracle solves its own h from the same start with the same cap
+    po = oracle_params(O, ctx.params, h_tol=solve_tol, max_iter=60, h_max=float(info["h_cap"]))
+    so = O.solve_h(po, x, vel, d["m"], d["h"])
+    assert np.all(so["converged"] == 1)
+    h_gpu = g["h"].astype(np.float64)
+    assert np.max(np.abs(h_gpu / so["h"] - 1)) < 1e-5
+    # rho from the oracle at its own h
+    assert np.max(np.abs(g["rho4"][:, 0] / so["rho"] - 1)) < 1e-5
+    # everything else at the GPU's final float h
+    pf = oracle_params(O, ctx.params)
+    st = O.step(pf, x, vel, d["m"], u, g["h"], solve=False)
+    assert np.array_equal(g["ngb"].astype(np.int64), st["ngb"])
+    assert np.max(np.abs(g["rho4"][:, 0] / st["rho"] - 1)) < 1e-5
+    assert np.max(np.abs(g["rho4"][:, 2] / st["n"] - 1)) < 1e-5
+    sc_dn = np.abs(st["dn_dh"]).max()
+    assert np.max(np.abs(g["rho4"][:, 3] - st["dn_dh"])) < 1e-5 * sc_dn
+    sc_dr = np.abs(st["drho_dh"]).max()
+    assert np.max(np.abs(g["rho4"][:, 1] - st["drho_dh"])) < 1e-5 * sc_dr
+    cd = g["curl_div"]
+    sc_v = max(np.abs(st["div"]).max(), np.abs(st["curl"]).max(), 1e-30)
+    assert np.max(np.abs(cd[:, 3] - st["div"])) < 1e-5 * sc_v
+    assert np.max(np.abs(cd[:, :3] - st["curl"])) < 1e-5 * sc_v
+    # gradient loop
+    vs = g["vsig_lapu"]
+    assert np.max(np.abs(vs[:, 0] / st["vsig"] - 1)) < 1e-5
+    sc_l = max(np.abs(st["lapu"]).max(), 1e-30)
+    assert np.max(np.abs(vs[:, 1] - st["lapu"])) < 1e-4 * sc_l
+    # force loop: per-particle scale
+    a = g["accel_dudt"]
+    err_a = np.linalg.norm(a[:, :3] - st["accel"], axis=1)
+    assert np.all(err_a <= 1e-4 * st["s_a"] + 1e-30)
+    err_u = np.abs(a[:, 3] - st["dudt"])
+    assert np.all(err_u <= 1e-4 * st["s_u"] + 1e-30)
+    # dh/dt uses the same sum as div v: dh/dt = h f div / 3
+    ref_dh = st["dhdt"]
+    assert np.max(np.abs(g["dh_dt"] - ref_dh)) < 1e-4 * max(np.abs(ref_dh).max(), 1e-30)
+    # FP64 momentum reduction on the device
+    red = g["reductions"]
+    assert np.all(np.abs(red[:3]) <= 1e-6 * red[4])
+    ma = d["m"][:, None].astype(np.float64) * a[:, :3].astype(np.float64)
+    assert abs(red[4] / np.linalg.norm(ma, axis=1).sum() - 1) < 1e-6
+    assert red[7] == st["npairs"].sum()
+    return st
+
+
+def test_cells_bit_exact(sph, O):
+    d, vel, u = lattice_state(16)
+    g = run_gpu(sph, d, vel, u, min_cell_width=0.25)
+    ctx = g["ctx"]
+    info = g["info"]
+    assert info["nc"] == (4, 4, 4)
+    cid, perm = ctx.cells()
+    cid = cid.cpu().numpy().astype(np.uint32)
+    perm = perm.cpu().numpy()
+    ref = O.cell_ids(d["pos"], d["box"], 4)
+    assert np.array_equal(cid, ref)
+    assert np.array_equal(perm, np.argsort(ref, kind="stable"))
+
+
+def test_lattice16_full_pipeline(sph, O):
+    """Jittered 16^3 lattice with random v and u, 4^3 cells: every output against the oracle."""
+    d, vel, u = lattice_state(16)
+    g = run_gpu(sph, d, vel, u, min_cell_width=0.25, h_tol=1e-6)
+    assert g["status"] == (0, 0), g["status"]
+    check_against_oracle(O, d, vel, u, g, g["ctx"])
+    inter = g["info"]["interactions"]
+    assert inter[1] == g["ngb"].sum()
+
+
+def test_sedov_small_auto_cells(sph, O):
+    """Sedov blast at 16^3 with automatic cell width (strong u contrast, viscosity, conduction)."""
+    d = ics.sedov(16)
+    rng = np.random.default_rng(1)
+    vel = rng.normal(0, 0.05, size=(len(d["pos"]), 3)).astype(np.float32)
+    g = run_gpu(sph, d, vel, d["u"], h_tol=1e-6)
+    assert g["status"][0] in (0,), g["status"]
+    check_against_oracle(O, d, vel, d["u"], g, g["ctx"])
+
+
+def test_ragged_uniform_random(sph, O):
+    """3001 uniform random particles (ragged item sizes and tails), non-cubic box, random h."""
+    rng = np.random.default_rng(7)
+    n = 3001
+    box = (1.0, 0.8, 1.25)
+    pos = (rng.uniform(0, 1, (n, 3)) * np.array(box)).astype(np.float32)
+    h = (rng.uniform(0.9, 1.1, n) * 1.2348 * (np.prod(box) / n) ** (1 / 3)).astype(np.float32)
+    d = dict(pos=pos, h=h, m=np.full(n, 1.0 / n, np.float32), u=rng.uniform(0.5, 2, n).astype(np.float32),
+             vel=rng.normal(0, 0.2, (n, 3)).astype(np.float32), box=box)
+    g = run_gpu(sph, d, d["vel"], d["u"], h_tol=1e-6)
+    assert g["status"][0] == 0, g["status"]
+    check_against_oracle(O, d, d["vel"], d["u"], g, g["ctx"])
+
+
+def test_fixed_h_counts_at_input_h(sph, O):
+    """NO_H_ITER: one density pass at the input h; counts bit-exact at that h."""
+    d, vel, u = lattice_state(12, jitter=0.3)
+    g = run_gpu(sph, d, vel, u, flags=2)
+    assert np.array_equal(g["h"], d["h"])
+    st = O.density(O.Params(), d["pos"], vel, d["m"], d["h"])
+    assert np.array_equal(g["ngb"].astype(np.int64), st["ngb"])
+    assert np.max(np.abs(g["rho4"][:, 0] / st["rho"] - 1)) < 1e-5
+
+
+def test_deterministic(sph):
+    d, vel, u = lattice_state(16, seed=3)
+    a = run_gpu(sph, d, vel, u, h_tol=1e-6)
+    b = run_gpu(sph, d, vel, u, h_tol=1e-6)
+    for k in ("h", "rho4", "curl_div", "ngb", "vsig_lapu", "accel_dudt", "dh_dt"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_active_subset_matches_full(sph, O):
+    """Only active particles are recomputed; with the inactive state from a full pass they match it."""
+    d, vel, u = lattice_state(16, seed=5)
+    n = len(d["pos"])
+    full = run_gpu(sph, d, vel, u, h_tol=1e-6)
+    act = ics.active_hash(n, 123, 4)
+    ctx = sph.Context(n, box=d["box"], h_tol=1e-6)
+    # previous state: converged h for everybody, rho4/curl_div from the full pass
+    d2 = dict(d)
+    d2["h"] = full["h"]
+    pos_h, vel_m, ut = dev_arrays(d2, vel, u)
+    rho4 = torch.from_numpy(full["rho4"]).cuda()
+    cd = torch.from_numpy(full["curl_div"]).cuda()
+    ctx.build_cells(pos_h)
+    out = ctx.density(pos_h, vel_m, torch.from_numpy(act).cuda(), rho4=rho4, curl_div=cd)
+    f = ctx.force(ut)
+    torch.cuda.synchronize()
+    on = act.astype(bool)
+    h = out["h"].cpu().numpy()
+    assert np.array_equal(h[~on], full["h"][~on])
+    assert np.max(np.abs(h[on] / full["h"][on] - 1)) < 1e-6
+    a = f["accel_dudt"].cpu().numpy()
+    st = O.step(O.Params(), d["pos"], vel, d["m"], u, h, solve=False)
+    err = np.linalg.norm(a[on, :3] - st["accel"][on], axis=1)
+    assert np.all(err <= 1e-4 * st["s_a"][on])
+
+
+def test_edge_cases(sph):
+    """n = 0 and a single isolated particle (h runs into the cell cap: not converged, status set)."""
+    ctx = sph.Context(8)
+    e = torch.zeros(0, 4, dtype=torch.float32, device="cuda")
+    ctx.build_cells(e)
+    out = ctx.density(e, e.clone())
+    assert out["h"].numel() == 0
+    assert ctx.sync_status() == (0, 0)
+    one = torch.tensor([[0.3, 0.4, 0.5, 0.01]], dtype=torch.float32, device="cuda")
+    vm = torch.tensor([[0.0, 0.0, 0.0, 1.0]], dtype=torch.float32, device="cuda")
+    ctx.build_cells(one)
+    out = ctx.density(one, vm)
+    code, detail = ctx.sync_status()
+    assert code in (-4, -5) and detail == 1
+    info = ctx.info()
+    assert abs(out["h"].item() - info["h_cap"]) < 1e-7
+    assert out["ngb"].item() == 0
+
+
+def test_argument_errors(sph):
+    ctx = sph.Context(16)
+    empty = torch.zeros(0, 4, dtype=torch.float32, device="cuda")
+    with pytest.raises(sph.SwiftGPUError) as e:
+        ctx.density(empty, empty)  # before build_cells
+    assert e.value.code == -2
+    with pytest.raises(sph.SwiftGPUError):
+        ctx.build_cells(torch.zeros(32, 4, dtype=torch.float32, device="cuda"))  # n > n_max
+    nan = torch.full((4, 4), float("nan"), dtype=torch.float32, device="cuda")
+    ctx.build_cells(nan)
+    code, _ = ctx.sync_status()
+    assert code == -1
