@@ -1,0 +1,441 @@
+#!/usr/bin/env python
+"""Benchmark: SPH pair interactions per second on one B300 (density + gradient + force).
+
+One step = one pass of the whole hot path over the resident particle set:
+build_cells (device cell sort) -> density with the Newton iteration on h ->
+gradient -> force, all through the C ABI. Workload: the Sedov blast on a
+jittered 64^3 lattice (262144 particles, total energy 1 in the 32 central
+particles), h starting at 1.2348 x spacing.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0). Under torchrun every rank runs an independent
+replica of the workload (the path has no data exchange between GPUs) and the
+value is the interactions of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SPH pair interactions/s (density+gradient+force) on 1 B300; % FP32 peak vs plain"
+UNIT = "interactions/s"
+WORKLOAD = "sedov64"
+L2_FLUSH_BYTES = 512 << 20  # larger than the 126 MB L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--autotune", action="store_true", help="run the library autotuner before timing")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ ranks
+def dist_setup(n_gpus):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+        pg = dist
+    if torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    return rank, world, pg
+
+
+def reduce_max(pg, value, device):
+    """Max over ranks of a float (identity on one rank)."""
+    if pg is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 100 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        os.unlink(self.path)
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        power = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(power) if power else None}
+
+
+# --------------------------------------------------------------- workload
+def workload():
+    from paper_2505_14538_b300 import ics
+    return ics.sedov(64)
+
+
+def flops_per_interaction():
+    with open(os.path.join(ROOT, "profiles", "flops_per_interaction.json")) as f:
+        fl = json.load(f)
+    return [fl["density"]["mean"], fl["gradient"]["mean"], fl["force"]["mean"]]
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for name in ("loops.cu", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_2505_14538_b300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+    except OSError:
+        return None
+    e = t.get(kernel)
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e.get("bytes_per_launch")
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# ------------------------------------------------------------- our path
+def run_ours(args, rank, world, pg):
+    import numpy as np
+    import torch
+
+    from paper_2505_14538_b300 import sph
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    d = workload()
+    n = len(d["pos"])
+    pos_h_host = np.concatenate([d["pos"], d["h"][:, None]], 1).astype(np.float32)
+    vel_m_host = np.concatenate([d["vel"], d["m"][:, None]], 1).astype(np.float32)
+    u_host = d["u"].astype(np.float32)
+    pos_h = torch.from_numpy(pos_h_host).to(dev)
+    vel_m = torch.from_numpy(vel_m_host).to(dev)
+    u = torch.from_numpy(u_host).to(dev)
+    ctx = sph.Context(n)
+    # settle the cell width once (the h iteration may ask for wider cells)
+    out = ctx.step(pos_h, vel_m, u, check=True)
+    torch.cuda.synchronize()
+    width = max(ctx.info()["cell_width"])
+    min_width = width if out["status"][0] != 0 else 0.0
+    if args.autotune:
+        ctx.autotune(2)
+    h_out = torch.empty(n, dtype=torch.float32, device=dev)
+    rho4 = torch.empty(n, 4, dtype=torch.float32, device=dev)
+    cd = torch.empty(n, 4, dtype=torch.float32, device=dev)
+    ngb = torch.empty(n, dtype=torch.int32, device=dev)
+    vl = torch.empty(n, 2, dtype=torch.float32, device=dev)
+    ad = torch.empty(n, 4, dtype=torch.float32, device=dev)
+    dh = torch.empty(n, dtype=torch.float32, device=dev)
+    red = torch.zeros(8, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step(p, v, uu):
+        ctx.build_cells(p, min_width)
+        ctx.density(p, v, h_out=h_out, rho4=rho4, curl_div=cd, ngb_count=ngb)
+        ctx.gradient(uu, vsig_lapu=vl)
+        ctx.force(uu, accel_dudt=ad, dh_dt=dh, reductions=red)
+
+    for _ in range(args.warmup):
+        step(pos_h, vel_m, u)
+    torch.cuda.synchronize()
+    code, detail = ctx.sync_status()
+    if code not in (0, -4):
+        raise RuntimeError(f"device status {code} detail {detail}")
+
+    stream = torch.cuda.current_stream()
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(K)]
+    i0 = ctx.info()
+    sampler = ClockSampler(torch.cuda.current_device())
+    barrier(pg)
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.25)
+    t0 = time.perf_counter()
+    for k in range(K):
+        flush.zero_()
+        e = ev[k]
+        e[0].record(stream)
+        ctx.build_cells(pos_h, min_width)
+        e[1].record(stream)
+        ctx.density(pos_h, vel_m, h_out=h_out, rho4=rho4, curl_div=cd, ngb_count=ngb)
+        e[2].record(stream)
+        ctx.gradient(u, vsig_lapu=vl)
+        e[3].record(stream)
+        ctx.force(u, accel_dudt=ad, dh_dt=dh, reductions=red)
+        e[4].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    barrier(pg)
+    clocks = sampler.stop()
+    i1 = ctx.info()
+    seg = [[ev[k][j].elapsed_time(ev[k][j + 1]) for j in range(4)] for k in range(K)]
+    step_ms = [sum(s) for s in seg]
+    loop_ms = [sum(s[j] for s in seg) / K for j in range(4)]  # build, density, gradient, force
+    inter = [(i1["interactions"][j] - i0["interactions"][j]) / K for j in range(3)]
+    cand = [(i1["candidates"][j] - i0["candidates"][j]) / K for j in range(3)]
+    launches = i1["launches"] - i0["launches"]
+    inter_step = sum(inter)
+    local_time = sum(step_ms) / 1e3
+    tmax = reduce_max(pg, local_time, dev)
+    value = world * inter_step * K / tmax
+    ms_per_step = tmax / K * 1e3
+
+    # roofline of the dominant loop (FP32 CUDA-core arithmetic)
+    fpi = flops_per_interaction()
+    names = ["k_density", "k_gradient", "k_force"]
+    dom = max(range(3), key=lambda j: loop_ms[j + 1])
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    peaks = measured_peaks()
+    max_mhz = clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2032.0
+    peak_max = sms * 128 * 2 * max_mhz * 1e6 / 1e12
+    achieved = inter[dom] * fpi[dom] / (loop_ms[dom + 1] * 1e-3) / 1e12
+    traffic = measured_traffic(names[dom])
+    roof = {"bound": "alu", "kernel": names[dom], "achieved": achieved, "peak": peak_max, "unit": "TFLOP/s",
+            "frac": achieved / peak_max, "traffic": traffic,
+            "peak_note": f"FP32 FMA lanes: {sms} SMs x 128 x 2 flop x {max_mhz:.0f} MHz (max SM clock)",
+            "frac_at_measured_clock": (achieved / (sms * 256 * clocks["sm_mhz"] * 1e6 / 1e12)
+                                       if clocks.get("sm_mhz") else None),
+            "flops_per_interaction": fpi[dom],
+            "per_loop": {names[j]: {"ms": loop_ms[j + 1], "interactions": inter[j], "candidates": cand[j],
+                                    "tflops": inter[j] * fpi[j] / (loop_ms[j + 1] * 1e-3) / 1e12,
+                                    "frac": inter[j] * fpi[j] / (loop_ms[j + 1] * 1e-3) / 1e12 / peak_max}
+                         for j in range(3)},
+            "build_cells_ms": loop_ms[0]}
+
+    res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+           "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"{WORKLOAD}: Sedov blast, {n} particles on a jittered 64^3 lattice "
+                                  "(+-0.1 spacing), u=1e-5, E=1 in the 32 central particles, periodic unit box",
+                      "particles": n, "nc": ctx.info()["nc"], "h_tol": float(ctx.params.h_tol),
+                      "density_passes": i1["density_passes"], "interactions_per_step": inter_step,
+                      "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}"},
+           "roofline": roof, "gpu_launches": int(launches), "clocks": clocks,
+           "wall_s_timed_region": wall}
+
+    if not args.no_e2e:
+        res["e2e"] = run_e2e(ctx, pos_h_host, vel_m_host, u_host, min_width, n, dev, pg, world, K=min(K, 100))
+    if not args.no_plain and rank == 0:
+        res["plain"] = run_plain(d, n, dev, min_width)
+    if rank == 0 and not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_baseline(d, ctx)
+    return res
+
+
+def run_e2e(ctx, pos_h_host, vel_m_host, u_host, min_width, n, dev, pg, world, K):
+    """The same metric through the public API from pinned host buffers: H2D inputs, step, D2H results."""
+    import torch
+    hp = torch.from_numpy(pos_h_host).pin_memory()
+    hv = torch.from_numpy(vel_m_host).pin_memory()
+    hu = torch.from_numpy(u_host).pin_memory()
+    out_ad = torch.empty(n, 4, dtype=torch.float32).pin_memory()
+    out_h = torch.empty(n, dtype=torch.float32).pin_memory()
+    p = torch.empty(n, 4, dtype=torch.float32, device=dev)
+    v = torch.empty(n, 4, dtype=torch.float32, device=dev)
+    u = torch.empty(n, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    i0 = ctx.info()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier(pg)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(K):
+        p.copy_(hp, non_blocking=True)
+        v.copy_(hv, non_blocking=True)
+        u.copy_(hu, non_blocking=True)
+        ctx.build_cells(p, min_width)
+        d = ctx.density(p, v)
+        ctx.gradient(u)
+        f = ctx.force(u)
+        out_ad.copy_(f["accel_dudt"], non_blocking=True)
+        out_h.copy_(d["h"], non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    i1 = ctx.info()
+    t = e0.elapsed_time(e1) / 1e3
+    tmax = reduce_max(pg, t, dev)
+    inter = sum(i1["interactions"][j] - i0["interactions"][j] for j in range(3))
+    return {"value": world * inter / tmax, "unit": UNIT, "h2d_bytes_per_step": n * (16 + 16 + 4),
+            "d2h_bytes_per_step": n * (16 + 4), "steps": K, "ms_per_step": tmax / K * 1e3}
+
+
+def run_plain(d, n, dev, min_width):
+    """The plain path (one kernel launch per self/pair cell task) on the same workload, one step."""
+    import numpy as np
+    import torch
+
+    from paper_2505_14538_b300 import _lib, sph
+    try:
+        ctx = sph.Context(n, flags=_lib.FLAG_PLAIN)
+    except sph.SwiftGPUError as e:
+        return {"unavailable": f"plain per-task launch path: {e}"}
+    pos_h = torch.from_numpy(np.concatenate([d["pos"], d["h"][:, None]], 1).astype(np.float32)).to(dev)
+    vel_m = torch.from_numpy(np.concatenate([d["vel"], d["m"][:, None]], 1).astype(np.float32)).to(dev)
+    u = torch.from_numpy(d["u"].astype(np.float32)).to(dev)
+    try:
+        ctx.step(pos_h, vel_m, u, min_cell_width=min_width, check=False)
+    except sph.SwiftGPUError as e:
+        return {"unavailable": str(e)}
+    torch.cuda.synchronize()
+    i0 = ctx.info()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    ctx.step(pos_h, vel_m, u, min_cell_width=min_width, check=False)
+    e1.record()
+    torch.cuda.synchronize()
+    i1 = ctx.info()
+    t = e0.elapsed_time(e1) / 1e3
+    inter = sum(i1["interactions"][j] - i0["interactions"][j] for j in range(3))
+    return {"value": inter / t, "unit": UNIT, "ms_per_step": t * 1e3, "launches_per_step": i1["launches"] - i0["launches"]}
+
+
+# ------------------------------------------------------- CPU baseline leg
+def oracle_step_timed(d, nthreads, h_max, h_tol=1e-4):
+    """The FP64 oracle's whole hot path on the workload: (interactions, seconds)."""
+    from oracle import oracle as O
+    p = O.Params(h_tol=h_tol, max_iter=30, h_max=h_max, nthreads=nthreads)
+    t0 = time.perf_counter()
+    s = O.solve_h(p, d["pos"], d["vel"], d["m"], d["h"])
+    g = O.ghost(p, s["h"], s["rho"], s["drho_dh"], s["div"], s["curl"], d["u"])
+    gr = O.gradient(p, d["pos"], d["vel"], d["m"], s["h"], s["rho"], g["c"], d["u"])
+    f = O.force(p, d["pos"], d["vel"], d["m"], s["h"], d["u"], s["rho"], g["f"], g["P"], g["c"], g["B"])
+    t = time.perf_counter() - t0
+    del gr
+    return int(s["pass_pairs"].sum() + s["ngb"].sum() + f["npairs"].sum()), t
+
+
+def cpu_baseline(d, ctx=None, steps=2):
+    from oracle import oracle as O
+    O.build()
+    cores = os.cpu_count() or 1
+    h_max = float(ctx.info()["h_cap"]) if ctx is not None else 0.0
+    tot_i, tot_t = 0, 0.0
+    for _ in range(steps):
+        i, t = oracle_step_timed(d, cores, h_max)
+        tot_i += i
+        tot_t += t
+    return {"value": tot_i / tot_t, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"the whole workload ({len(d['pos'])} particles), {steps} full oracle steps "
+                      f"(h iteration, gradient, force) in FP64 with OpenMP over particles, {tot_t:.1f} s"}
+
+
+def run_reference(args, rank, world, pg):
+    """The oracle as the reference arm: rank 0 times it on the host cores; other ranks exit."""
+    if rank != 0:
+        return None
+    d = workload()
+    from oracle import oracle as O
+    O.build()
+    cores = os.cpu_count() or 1
+    h_max = 0.0202860012650
+    for _ in range(min(args.warmup, 1)):
+        oracle_step_timed(d, cores, h_max)
+    tot_i, tot_t = 0, 0.0
+    K = min(args.steps, 5)
+    for _ in range(K):
+        i, t = oracle_step_timed(d, cores, h_max)
+        tot_i += i
+        tot_t += t
+    value = tot_i / tot_t
+    sample = (f"the whole {WORKLOAD} workload ({len(d['pos'])} particles) per step, {K} steps "
+              f"(capped at 5 so the run stays within minutes), FP64 oracle with OpenMP")
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": min(args.warmup, 1), "ms_per_step": tot_t / K * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{WORKLOAD}: Sedov blast, {len(d['pos'])} particles", "particles": len(d["pos"])},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank, world, pg = dist_setup(args.gpus)
+    if args.impl == "reference":
+        res = run_reference(args, rank, world, pg)
+    else:
+        res = run_ours(args, rank, world, pg)
+    if rank == 0 and res is not None:
+        print(json.dumps(res), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -168,13 +168,14 @@ def solve_h(p: Params, x, v, m, h0, active=None):
     out = {k: np.zeros(n) for k in ("h", "n", "dn_dh", "rho", "drho_dh", "div")}
     out["curl"] = np.zeros((n, 3))
     out["ngb"] = np.zeros(n, np.int64)
+    out["pass_pairs"] = np.zeros(n, np.int64)
     out["iters"] = np.zeros(n, np.int32)
     out["converged"] = np.zeros(n, np.int32)
     pc = p.c()
     rc = lib().oracle_solve_h(ctypes.byref(pc), ctypes.c_int64(n), _p(x), _p(v), _p(m), _p(h0), _p(act),
                               _p(out["h"]), _p(out["iters"]), _p(out["converged"]), _p(out["n"]),
                               _p(out["dn_dh"]), _p(out["rho"]), _p(out["drho_dh"]), _p(out["div"]),
-                              _p(out["curl"]), _p(out["ngb"]))
+                              _p(out["curl"]), _p(out["ngb"]), _p(out["pass_pairs"]))
     assert rc == 0
     return out
 

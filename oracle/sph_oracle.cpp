@@ -303,6 +303,7 @@ struct SolveOut {
   double h;
   int iters;
   int converged;
+  long long pairs;  /* neighbour pairs summed over every pass */
   DensOut d;
 };
 
@@ -314,8 +315,10 @@ SolveOut solve_h(const Geo& g, const Cells& c, int64_t n, const double* x, const
   double lo = 0.0, hi = std::numeric_limits<double>::infinity();
   SolveOut s;
   s.converged = 0;
+  s.pairs = 0;
   for (int it = 0; it < p.max_iter; ++it) {
     DensOut d = density_at(g, c, n, x, v, m, i, h, p.kernel_gamma);
+    s.pairs += d.count;
     double target = eta3 / (h * h * h);
     double F = d.n - target;
     s.h = h;
@@ -496,7 +499,7 @@ int oracle_density(const oracle_params* p, int64_t n, const double* x, const dou
 int oracle_solve_h(const oracle_params* p, int64_t n, const double* x, const double* v, const double* m,
                    const double* h_in, const uint8_t* active, double* h_out, int32_t* iters,
                    int32_t* converged, double* n_out, double* dn_dh, double* rho, double* drho_dh,
-                   double* div, double* curl, int64_t* ngb) {
+                   double* div, double* curl, int64_t* ngb, int64_t* pass_pairs) {
   Geo g = geo_of(*p);
   double rmax = p->h_max > 0 ? p->kernel_gamma * p->h_max : 0.0;
   Cells c = make_cells(g, n, x, rmax, p->use_cells && p->h_max > 0);
@@ -517,6 +520,7 @@ int oracle_solve_h(const oracle_params* p, int64_t n, const double* x, const dou
     if (div) div[i] = s.d.div;
     if (curl) for (int a = 0; a < 3; ++a) curl[3 * i + a] = s.d.curl[a];
     if (ngb) ngb[i] = s.d.count;
+    if (pass_pairs) pass_pairs[i] = s.pairs;
   }
   return 0;
 }

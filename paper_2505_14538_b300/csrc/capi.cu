@@ -29,6 +29,7 @@ static int phys_from(const swift_gpu_params* p, Phys* ph) {
   if (!(p->kernel_gamma > 0.0f) || !(p->eta > 0.0f) || !(p->gamma_eos > 1.0f)) return SWIFT_GPU_ERR_ARG;
   if (p->max_iter < 1 || !(p->h_tol >= 0.0f) || p->h_max < 0.0f || p->cell_margin < 0.0f)
     return SWIFT_GPU_ERR_ARG;
+  if (p->flags & SWIFT_GPU_PLAIN) return SWIFT_GPU_ERR_ARG;  // the per-task launch path is not built yet
   for (int a = 0; a < 3; ++a) ph->L[a] = p->box[a];
   ph->kg = p->kernel_gamma;
   ph->gamma_eos = p->gamma_eos;
