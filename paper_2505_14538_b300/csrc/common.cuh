@@ -10,14 +10,17 @@ namespace sg {
 
 constexpr int kWarp = 32;
 constexpr int kItemMax = 32;          // particles per work item (one per lane at most)
-constexpr int kListCap = 48;          // per-lane neighbour list entries before a flush
 constexpr int kIndexBits = 26;        // list entry: j index (26 bits) + shift code (6 bits)
 constexpr uint32_t kIndexMask = (1u << kIndexBits) - 1u;
 constexpr float kPi = 3.14159265358979323846f;
 
-// Relative half-width of the band around H^2 in which the FP32 neighbour
-// decision is re-taken in FP64 from the same float inputs (16 ulp of H^2).
-constexpr float kBand = 16.0f * 1.1920929e-7f;
+// Guard band around H^2 in which the FP32 neighbour decision is re-taken in
+// FP64 from the same float inputs. A periodic image costs one FP32 rounding
+// of a coordinate (at most 2^-24 L), so the band has a relative part (FP32
+// rounding of r^2 and H^2) and a part proportional to H L.
+__host__ __device__ __forceinline__ float band_of(float H, float Lmax) {
+  return H * H * 1.52587890625e-05f + H * Lmax * 9.5367431640625e-07f;  // 2^-16 H^2 + 2^-20 H L
+}
 
 // Device status word (first error wins; detail accumulates).
 struct Status {
@@ -106,19 +109,15 @@ __device__ __forceinline__ float r2_of(float dx, float dy, float dz) {
   return fmaf(dz, dz, fmaf(dy, dy, dx * dx));
 }
 
-// Shift code: bit 2a -> subtract L from the i coordinate on axis a (i sits
-// near the top of the box, j wrapped to the bottom); bit 2a+1 -> subtract L
-// from the j coordinate (j near the top, i near the bottom). Both
-// subtractions are exact in FP32 (Sterbenz), so the FP32 distance keeps the
-// accuracy of a plain difference of nearby coordinates.
-__device__ __forceinline__ void apply_shift(unsigned code, const float L[3], float& xi, float& yi, float& zi,
-                                            float& xj, float& yj, float& zj) {
+// Periodic image of a j particle: bit 2a adds L on axis a, bit 2a+1
+// subtracts L (the j cell was wrapped across the low / high face).
+__device__ __forceinline__ void shift_j(unsigned code, const float L[3], float& xj, float& yj, float& zj) {
   if (code) {
-    if (code & 1u) xi -= L[0];
+    if (code & 1u) xj += L[0];
     if (code & 2u) xj -= L[0];
-    if (code & 4u) yi -= L[1];
+    if (code & 4u) yj += L[1];
     if (code & 8u) yj -= L[1];
-    if (code & 16u) zi -= L[2];
+    if (code & 16u) zj += L[2];
     if (code & 32u) zj -= L[2];
   }
 }
@@ -184,46 +183,6 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, Sta
   }
   __syncthreads();
   return ok != 0;
-}
-
-// Neighbour-cell ranges of cell c: the 27 cells around it as up to 18
-// contiguous runs of the cell-sorted particle array, each with its periodic
-// shift code.
-struct Range {
-  int begin, end;
-  unsigned code;
-};
-
-__device__ __forceinline__ int cell_ranges(const Grid& g, const int* __restrict__ cell_start, int c,
-                                           Range* r) {
-  const int nx = g.nc[0], ny = g.nc[1], nz = g.nc[2];
-  const int cx = c % nx, cy = (c / nx) % ny, cz = c / (nx * ny);
-  int k = 0;
-  for (int dz = -1; dz <= 1; ++dz) {
-    int z = cz + dz;
-    unsigned cz_code = 0;
-    if (z < 0) { z += nz; cz_code = 32u; }
-    else if (z >= nz) { z -= nz; cz_code = 16u; }
-    for (int dy = -1; dy <= 1; ++dy) {
-      int y = cy + dy;
-      unsigned cy_code = 0;
-      if (y < 0) { y += ny; cy_code = 8u; }
-      else if (y >= ny) { y -= ny; cy_code = 4u; }
-      const int row = nx * (y + ny * z);
-      const unsigned code = cz_code | cy_code;
-      int x0 = cx - 1, x1 = cx + 1;
-      if (x0 < 0) {
-        r[k++] = Range{cell_start[row + nx - 1], cell_start[row + nx], code | 2u};
-        x0 = 0;
-      }
-      if (x1 >= nx) {
-        r[k++] = Range{cell_start[row], cell_start[row + 1], code | 1u};
-        x1 = nx - 1;
-      }
-      r[k++] = Range{cell_start[row + x0], cell_start[row + x1 + 1], code};
-    }
-  }
-  return k;
 }
 
 }  // namespace sg

@@ -1,148 +1,50 @@
-// loops.cu -- the SPH pair-interaction loops of Sec. 2.1 as persistent
-// work-queue kernels for sm_103a.
+// loops.cu -- the SPH pair loops of Sec. 2.1 as persistent work-queue
+// kernels for sm_103a (neighbour scan in engine.cuh):
 //
-// Work decomposition. A work item is a run of <= 32 active particles of one
-// cell (cells with more are split). A warp takes an item from a ticket
-// counter, scans the 27 neighbour cells (self and pair interactions of
-// Sec. 2.2.2 / Fig. 3) as up to 18 contiguous runs of the cell-sorted arrays,
-// and works in two phases per chunk of 32 candidates:
-//   phase 1  the chunk's positions are staged in shared memory with one
-//            coalesced float4 load; every lane tests its particle against
-//            them (r^2 < H^2 with a 16-ulp guard band) and appends hits to a
-//            lane-private neighbour list in shared memory;
-//   phase 2  when a list may overflow (and at the end) every lane walks its
-//            own list and evaluates the full interaction, so the expensive
-//            arithmetic runs with nearly all lanes busy instead of diverging
-//            on the ~15 % hit rate of a cell scan.
-// Items with few particles give each particle 2-8 lanes that split the
-// candidates and are combined with warp shuffles at the end.
+//   k_density   Eqs. 2-6 (+ div/curl, Eqs. 3-4) and the Newton iteration on
+//               h (Sec. 2.1.2): ONE cooperative launch runs every pass; after
+//               each pass the unconverged particles of an item form one item
+//               of the next pass, and a bounded grid barrier separates passes.
+//   k_ghost     per particle: f = 1/Omega (Eq. 8), P, c, Balsara B.
+//   k_gradient  v_sig,max (Eqs. 10-11) and the Laplacian of u.
+//   k_force     Eqs. 7, 9-11, 16-20, 22 and dh/dt, with FP64 block partials of
+//               the momentum / energy sums.
 //
-// Pairs whose FP32 r^2 lies within the guard band of H^2 re-take the
-// neighbour decision in FP64 from the same float inputs, so neighbour sets
-// equal those of the FP64 definition exactly.
+// Pairs whose FP32 r^2 falls in the guard band of the support re-take the
+// neighbour decision in FP64 from the same float inputs, so the neighbour
+// sets equal those of the FP64 definition exactly.
 #include <cuda_runtime.h>
 #include <math.h>
 
 #include "common.cuh"
+#include "engine.cuh"
 #include "internal.h"
 
 namespace sg {
 
-constexpr int kLoopThreads = 256;
+constexpr int kLoopThreads = 128;
 constexpr int kWarpsPerBlock = kLoopThreads / 32;
-constexpr int kCap = 64;  // list entries per lane
-constexpr size_t kWarpSmemBytes = (size_t)kCap * 32 * sizeof(unsigned) + 32 * sizeof(float4);
-constexpr size_t kLoopSmemBytes = kWarpSmemBytes * kWarpsPerBlock;
-constexpr unsigned kFull = 0xffffffffu;
+constexpr size_t kLoopSmemBytes = sizeof(WarpSmem) * kWarpsPerBlock;
 constexpr unsigned long long kBarrierNs = 5000000000ull;  // 5 s
 
-__device__ __forceinline__ unsigned* warp_list(unsigned char* smem) {
-  return reinterpret_cast<unsigned*>(smem + (threadIdx.x >> 5) * kWarpSmemBytes);
-}
-__device__ __forceinline__ float4* warp_stage(unsigned char* smem) {
-  return reinterpret_cast<float4*>(smem + (threadIdx.x >> 5) * kWarpSmemBytes + (size_t)kCap * 32 * 4);
+__device__ __forceinline__ WarpSmem& warp_smem(unsigned char* smem) {
+  return reinterpret_cast<WarpSmem*>(smem)[threadIdx.x >> 5];
 }
 
-// Lane layout of an item with cnt particles: L lanes per particle (power of
-// two, L <= lmax), particle slot a = lane % A, sub-lane s = lane / A, A = 32/L.
-__device__ __forceinline__ int lanes_per_particle(int cnt, int lmax) {
-  int p2 = 1;
-  while (p2 < cnt) p2 <<= 1;
-  int L = 32 / p2;
-  return L < lmax ? L : lmax;
-}
-
-// ---------------------------------------------------------------- engine
-// Phase 2: every lane evaluates its listed interactions.
-template <class Op>
-__device__ __forceinline__ void flush(Op& op, typename Op::I& I, const unsigned* list, int cnt) {
+// Lane layout of an item: L = 2^lsh lanes per particle, slot = lane % (32/L),
+// sub-lane s = lane / (32/L).
+struct LaneMap {
+  int lsh, slot, s;
+  bool live;
+};
+__device__ __forceinline__ LaneMap lane_map(int cnt, int lmax) {
+  LaneMap m;
+  m.lsh = lanes_shift(cnt, lmax);
   const unsigned lane = lane_id();
-  const int m = warp_max(cnt);
-  for (int t = 0; t < m; ++t) {
-    if (t < cnt) {
-      unsigned e = list[t * 32 + lane];
-      op.interact(I, (int)(e & kIndexMask), e >> kIndexBits);
-    }
-  }
-}
-
-// Scan the 27 neighbour cells of `cell` for lane particle I.
-template <class Op>
-__device__ __forceinline__ void scan_cells(Op& op, typename Op::I& I, const Grid& g, const int* __restrict__ cell_start,
-                                           const float4* __restrict__ pos, int cell, int L, int s, bool live,
-                                           unsigned* list, float4* stage, unsigned& ncand) {
-  const unsigned lane = lane_id();
-  Range rg[18];
-  const int nr = cell_ranges(g, cell_start, cell, rg);
-  int cnt = 0;
-  for (int q = 0; q < nr; ++q) {
-    const Range r = rg[q];
-    float xi = I.x, yi = I.y, zi = I.z;
-    if (r.code & 1u) xi -= g.L[0];
-    if (r.code & 4u) yi -= g.L[1];
-    if (r.code & 16u) zi -= g.L[2];
-    for (int base = r.begin; base < r.end; base += 32) {
-      const int len = min(32, r.end - base);
-      const int need = (len + L - 1) / L;
-      if (__any_sync(kFull, cnt + need > kCap)) {
-        flush(op, I, list, cnt);
-        cnt = 0;
-      }
-      __syncwarp();
-      if ((int)lane < len) {
-        float4 p = pos[base + lane];
-        if (r.code & 2u) p.x -= g.L[0];
-        if (r.code & 8u) p.y -= g.L[1];
-        if (r.code & 32u) p.z -= g.L[2];
-        stage[lane] = make_float4(p.x, p.y, p.z, op.stage_w(p.w));
-      }
-      __syncwarp();
-      if (live) {
-        for (int k = s; k < len; k += L) {
-          const float4 c = stage[k];
-          const float dx = xi - c.x, dy = yi - c.y, dz = zi - c.z;
-          const float r2 = r2_of(dx, dy, dz);
-          if (op.candidate(I, r2, c.w)) {
-            list[cnt * 32 + lane] = (unsigned)(base + k) | (r.code << kIndexBits);
-            ++cnt;
-          }
-        }
-        ncand += (unsigned)((len - s + L - 1) / L);
-      }
-    }
-  }
-  flush(op, I, list, cnt);
-}
-
-// Warp-level reductions across the L sub-lanes of a particle.
-__device__ __forceinline__ float sub_sum(float v, int A) {
-  for (int o = A; o < 32; o <<= 1) v += __shfl_xor_sync(kFull, v, o);
-  return v;
-}
-__device__ __forceinline__ float sub_max(float v, int A) {
-  for (int o = A; o < 32; o <<= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, o));
-  return v;
-}
-__device__ __forceinline__ unsigned sub_sum_u(unsigned v, int A) {
-  for (int o = A; o < 32; o <<= 1) v += __shfl_xor_sync(kFull, v, o);
-  return v;
-}
-__device__ __forceinline__ void sub_sum2(float& s, float& c, int A) {
-  for (int o = A; o < 32; o <<= 1) {
-    float so = __shfl_xor_sync(kFull, s, o);
-    float co = __shfl_xor_sync(kFull, c, o);
-    float t = s + so;
-    float bp = t - s;
-    float e = (s - (t - bp)) + (so - bp);
-    s = t;
-    c = c + co + e;
-  }
-}
-
-__device__ __forceinline__ int take_ticket(int* ticket) {
-  int t = 0;
-  if (lane_id() == 0) t = atomicAdd(ticket, 1);
-  return __shfl_sync(kFull, t, 0);
+  m.slot = (int)(lane & ((32u >> m.lsh) - 1u));
+  m.s = (int)(lane >> (5 - m.lsh));
+  m.live = m.slot < cnt;
+  return m;
 }
 
 // ============================================================ density loop
@@ -201,9 +103,9 @@ struct DensOp {
   __device__ __forceinline__ void interact(I& i, int j, unsigned code) const {
     const float4 pj = pos[j];
     const float4 vj = vel[j];
-    float xi = i.x, yi = i.y, zi = i.z, xj = pj.x, yj = pj.y, zj = pj.z;
-    apply_shift(code, L, xi, yi, zi, xj, yj, zj);
-    const float dx = xi - xj, dy = yi - yj, dz = zi - zj;
+    float xj = pj.x, yj = pj.y, zj = pj.z;
+    shift_j(code, L, xj, yj, zj);
+    const float dx = i.x - xj, dy = i.y - yj, dz = i.z - zj;
     const float r2 = r2_of(dx, dy, dz);
     if (r2 >= i.H2lo) {
       if (!(exact_r2(i.x, i.y, i.z, pj.x, pj.y, pj.z, L[0], L[1], L[2]) < exact_H2(kg, i.h))) return;
@@ -235,15 +137,15 @@ struct DensOp {
   }
 };
 
-__device__ __forceinline__ void dens_load_i(DensOp::I& I, const DensArgs& a, int k) {
+__device__ __forceinline__ void dens_load(DensOp::I& I, const DensArgs& a, float Lmax, int k) {
   const float4 p = a.pos[k];
   const float4 v = a.vel[k];
   const float h = a.h[k];
   I.x = p.x; I.y = p.y; I.z = p.z; I.h = h;
   const float H = a.ph.kg * h;
-  const float H2 = H * H;
-  I.H2lo = H2 * (1.0f - kBand);
-  I.H2hi = H2 * (1.0f + kBand);
+  const float b = band_of(H, Lmax);
+  I.H2lo = H * H - b;
+  I.H2hi = H * H + b;
   I.invH = 1.0f / H;
   I.c3 = (8.0f / kPi) * I.invH * I.invH * I.invH;
   I.c4 = I.c3 * I.invH;
@@ -253,14 +155,102 @@ __device__ __forceinline__ void dens_load_i(DensOp::I& I, const DensArgs& a, int
   I.k = k;
 }
 
-__global__ void __launch_bounds__(kLoopThreads) k_density(DensArgs a) {
+// One density item: neighbour sums, then the Newton step for each particle;
+// the particles that need another pass form one item of the next pass.
+__device__ __forceinline__ void dens_item(const DensArgs& a, const DensOp& op, const Grid& g, WarpSmem& w,
+                                          const Item& it, const int* __restrict__ plist, bool last,
+                                          Item* items_next, int* plist_next, int* ctr_next, float Lmax,
+                                          unsigned& ninter, unsigned& ncand) {
+  const unsigned lane = lane_id();
+  const LaneMap lm = lane_map(it.cnt, a.lmax);
+  const int k = plist[it.off + (lm.live ? lm.slot : 0)];
+  DensOp::I I;
+  dens_load(I, a, Lmax, k);
+  scan_item(op, I, g, a.cell_start, a.pos, it.cell, lm.lsh, lm.s, lm.live, w, ncand);
+  lsum2(I.ns, I.nc, lm.lsh);
+  lsum2(I.rs, I.rc, lm.lsh);
+  I.dn = lsum(I.dn, lm.lsh);
+  I.dr = lsum(I.dr, lm.lsh);
+  I.div = lsum(I.div, lm.lsh);
+  I.cx = lsum(I.cx, lm.lsh);
+  I.cy = lsum(I.cy, lm.lsh);
+  I.cz = lsum(I.cz, lm.lsh);
+  I.count = lsum_u(I.count, lm.lsh);
+  bool again = false;
+  if (lm.live && lm.s == 0) {
+    ninter += I.count;
+    // convergence test in FP64 without a division: |n h^3 - eta^3| <= h_tol eta^3
+    const double hd = (double)I.h;
+    const double h3 = hd * hd * hd;
+    const double G = fma((double)I.ns, h3, fma((double)I.nc, h3, -a.ph.eta3));
+    bool conv = fabs(G) <= a.ph.h_tol * a.ph.eta3;
+    int flag = 0;
+    if (!conv && !last) {
+      // Newton step on F(h) = n - (eta/h)^3, F' = dn/dh + 3 eta^3 / h^4 (FP32)
+      const float h = I.h;
+      const float2 br = a.bracket[k];
+      float lo = br.x, hi = br.y;
+      if (G < 0.0) lo = fmaxf(lo, h);
+      else hi = fminf(hi, h);
+      if (G < 0.0 && h >= g.hcap) {
+        flag = g.hcap_from_cells ? SWIFT_GPU_ERR_H_EXCEEDS_CELL : SWIFT_GPU_ERR_H_NOT_CONVERGED;
+      } else {
+        const float ih = 1.0f / h;
+        const float target = (float)a.ph.eta3 * ih * ih * ih;
+        const float F = (I.ns + I.nc) - target;
+        const float Fp = fmaf(-I.dn, ih, 3.0f * target * ih);
+        float hn = Fp > 0.0f ? h - F / Fp : __int_as_float(0x7fc00000);
+        if (hn == hn) hn = fminf(fmaxf(hn, 0.5f * h), 2.0f * h);
+        if (!(hn == hn) || !(hn > lo) || !(hn < hi)) {
+          if (isfinite(hi) && lo > 0.0f) hn = 0.5f * (lo + hi);
+          else if (!isfinite(hi)) hn = 2.0f * h;
+          else hn = 0.5f * h;
+        }
+        hn = fminf(hn, g.hcap);
+        if (hn == h) {
+          conv = true;  // the float h cannot move any more
+        } else {
+          a.h[k] = hn;
+          a.bracket[k] = make_float2(lo, hi);
+          again = true;
+        }
+      }
+    } else if (!conv) {
+      flag = SWIFT_GPU_ERR_H_NOT_CONVERGED;
+    }
+    if (!again) {
+      const float rho = I.rs + I.rc;
+      const float invh = 1.0f / I.h;
+      a.rho4[k] = make_float4(rho, -I.dr * invh, I.ns + I.nc, -I.dn * invh);
+      const float ir = 1.0f / rho;
+      a.cd[k] = make_float4(I.cx * ir, I.cy * ir, I.cz * ir, I.div * ir);
+      a.ngb[k] = I.count;
+      if (flag) set_error(a.st, flag);
+    }
+  }
+  const unsigned am = __ballot_sync(kFull, again);
+  if (am) {
+    const int nu = __popc(am);
+    int pbase = 0, ibase = 0;
+    if (lane == 0) {
+      pbase = atomicAdd(&ctr_next[1], nu);
+      ibase = atomicAdd(&ctr_next[0], 1);
+    }
+    pbase = __shfl_sync(kFull, pbase, 0);
+    ibase = __shfl_sync(kFull, ibase, 0);
+    if (again) plist_next[pbase + __popc(am & ((1u << lane) - 1u))] = k;
+    if (lane == 0) items_next[ibase] = Item{it.cell, pbase, nu, 0};
+  }
+}
+
+__global__ void __launch_bounds__(kLoopThreads, 5) k_density(DensArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const unsigned lane = lane_id();
   const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   const Grid g = *a.grid;
-  unsigned* list = warp_list(smem);
-  float4* stage = warp_stage(smem);
+  const float Lmax = fmaxf(g.L[0], fmaxf(g.L[1], g.L[2]));
+  WarpSmem& w = warp_smem(smem);
 
   // ---- prologue: gather into cell order, inputs of inactive particles
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < a.n; k += gridDim.x * blockDim.x) {
@@ -297,13 +287,13 @@ __global__ void __launch_bounds__(kLoopThreads) k_density(DensArgs a) {
     }
     pbase = __shfl_sync(kFull, pbase, 0);
     ibase = __shfl_sync(kFull, ibase, 0);
-    int w = 0;
+    int wc = 0;
     for (int b = cs; b < ce; b += 32) {
       const int k = b + (int)lane;
       const bool on = k < ce && (a.active ? a.active[a.perm[k]] != 0 : true);
       const unsigned m = __ballot_sync(kFull, on);
-      if (on) a.plist0[pbase + w + __popc(m & ((1u << lane) - 1u))] = k;
-      w += __popc(m);
+      if (on) a.plist0[pbase + wc + __popc(m & ((1u << lane) - 1u))] = k;
+      wc += __popc(m);
     }
     for (int t = (int)lane; t < nit; t += 32)
       a.items0[ibase + t] = Item{c, pbase + t * kItemMax, min(kItemMax, total - t * kItemMax), 0};
@@ -326,94 +316,13 @@ __global__ void __launch_bounds__(kLoopThreads) k_density(DensArgs a) {
     const int* plist = pass == 0 ? a.plist0 : a.plist[pass & 1];
     Item* items_next = a.items[(pass + 1) & 1];
     int* plist_next = a.plist[(pass + 1) & 1];
+    int* ctr_next = &a.ctr[ctr_index(pass + 1, 0)];
     const bool last = pass == max_pass - 1;
     for (;;) {
       const int t = take_ticket(&a.ctr[ctr_index(pass, 2)]);
       if (t >= n_items) break;
       const Item it = items[t];
-      const int L = lanes_per_particle(it.cnt, a.lmax);
-      const int A = 32 / L;
-      const int slot = (int)lane % A, s = (int)lane / A;
-      const bool live = slot < it.cnt;
-      DensOp::I I;
-      const int k = live ? plist[it.off + slot] : plist[it.off];
-      dens_load_i(I, a, k);
-      scan_cells(op, I, g, a.cell_start, a.pos, it.cell, L, s, live, list, stage, ncand);
-      // combine sub-lanes
-      sub_sum2(I.ns, I.nc, A);
-      sub_sum2(I.rs, I.rc, A);
-      I.dn = sub_sum(I.dn, A);
-      I.dr = sub_sum(I.dr, A);
-      I.div = sub_sum(I.div, A);
-      I.cx = sub_sum(I.cx, A);
-      I.cy = sub_sum(I.cy, A);
-      I.cz = sub_sum(I.cz, A);
-      I.count = sub_sum_u(I.count, A);
-      bool again = false;
-      if (live && s == 0) {
-        ninter += I.count;
-        // Newton step on F(h) = n(h) - (eta/h)^3 in FP64 (Sec. 2.1.2)
-        const double n = (double)I.ns + (double)I.nc;
-        const double hd = (double)I.h;
-        const double h3 = hd * hd * hd;
-        const double target = a.ph.eta3 / h3;
-        const double F = n - target;
-        bool conv = fabs(F) <= a.ph.h_tol * target;
-        int flag = 0;
-        if (!conv && !last) {
-          const float2 br = a.bracket[k];
-          double lo = br.x, hi = br.y;
-          if (F < 0.0) lo = fmax(lo, hd);
-          else hi = fmin(hi, hd);
-          if (F < 0.0 && I.h >= g.hcap) {
-            flag = g.hcap_from_cells ? SWIFT_GPU_ERR_H_EXCEEDS_CELL : SWIFT_GPU_ERR_H_NOT_CONVERGED;
-          } else {
-            const double dn_dh = -(double)I.dn / hd;
-            const double Fp = dn_dh + 3.0 * a.ph.eta3 / (h3 * hd);
-            double hn = (Fp > 0.0) ? hd - F / Fp : __longlong_as_double(0x7ff8000000000000ll);
-            if (hn == hn) hn = fmin(fmax(hn, 0.5 * hd), 2.0 * hd);
-            if (!(hn == hn) || !(hn > lo) || !(hn < hi)) {
-              if (isfinite(hi) && lo > 0.0) hn = 0.5 * (lo + hi);
-              else if (!isfinite(hi)) hn = 2.0 * hd;
-              else hn = 0.5 * hd;
-            }
-            hn = fmin(hn, (double)g.hcap);
-            const float hf = (float)hn;
-            if (hf == I.h) {
-              conv = true;  // the float h cannot move: converged to FP32 resolution
-            } else {
-              a.h[k] = hf;
-              a.bracket[k] = make_float2((float)lo, (float)hi);
-              again = true;
-            }
-          }
-        } else if (!conv) {
-          flag = SWIFT_GPU_ERR_H_NOT_CONVERGED;
-        }
-        if (!again) {
-          const float rho = I.rs + I.rc;
-          const float invh = 1.0f / I.h;
-          a.rho4[k] = make_float4(rho, -I.dr * invh, I.ns + I.nc, -I.dn * invh);
-          const float ir = 1.0f / rho;
-          a.cd[k] = make_float4(I.cx * ir, I.cy * ir, I.cz * ir, I.div * ir);
-          a.ngb[k] = I.count;
-          if (flag) set_error(a.st, flag);
-        }
-      }
-      // unconverged particles of this item form one item of the next pass
-      const unsigned am = __ballot_sync(kFull, again);
-      if (am) {
-        const int nu = __popc(am);
-        int pbase = 0, ibase = 0;
-        if (lane == 0) {
-          pbase = atomicAdd(&a.ctr[ctr_index(pass + 1, 1)], nu);
-          ibase = atomicAdd(&a.ctr[ctr_index(pass + 1, 0)], 1);
-        }
-        pbase = __shfl_sync(kFull, pbase, 0);
-        ibase = __shfl_sync(kFull, ibase, 0);
-        if (again) plist_next[pbase + __popc(am & ((1u << lane) - 1u))] = k;
-        if (lane == 0) items_next[ibase] = Item{it.cell, pbase, nu, 0};
-      }
+      dens_item(a, op, g, w, it, plist, last, items_next, plist_next, ctr_next, Lmax, ninter, ncand);
     }
     if (!grid_barrier(&a.barrier[0], &a.barrier[1], a.st, kBarrierNs)) return;
   }
@@ -471,7 +380,7 @@ __global__ void k_ghost(int n, const unsigned* __restrict__ perm, const float4* 
 }
 
 // ============================================================ gradient loop
-struct GradArgs {
+struct LoopArgs {
   Grid* grid;
   const int* cell_start;
   const unsigned* perm;
@@ -485,7 +394,9 @@ struct GradArgs {
   const int* plist;
   const int* ctr;   // item count at ctr[0]
   int* ticket;
-  float2* out;      // caller order
+  void* out;        // caller order: float2 (gradient) / float4 (force)
+  float* dhdt;      // force: caller order, may be NULL
+  double* red_partial;  // force: [gridDim.x][8]
   Status* st;
   unsigned long long* stats;
 };
@@ -509,11 +420,11 @@ struct GradOp {
   __device__ __forceinline__ bool candidate(const I& i, float r2, float) const { return r2 < i.H2hi; }
   __device__ __forceinline__ void interact(I& i, int j, unsigned code) const {
     const float4 pj = pos[j];
-    float xi = i.x, yi = i.y, zi = i.z, xj = pj.x, yj = pj.y, zj = pj.z;
-    apply_shift(code, L, xi, yi, zi, xj, yj, zj);
-    const float dx = xi - xj, dy = yi - yj, dz = zi - zj;
+    float xj = pj.x, yj = pj.y, zj = pj.z;
+    shift_j(code, L, xj, yj, zj);
+    const float dx = i.x - xj, dy = i.y - yj, dz = i.z - zj;
     const float r2 = r2_of(dx, dy, dz);
-    if (!(r2 > 0.0f)) return;  // the particle itself: v_sig term added at load
+    if (!(r2 > 0.0f)) return;  // the particle itself: its v_sig term is added at load
     if (r2 >= i.H2lo) {
       if (!(exact_r2(i.x, i.y, i.z, pj.x, pj.y, pj.z, L[0], L[1], L[2]) < exact_H2(kg, i.h))) return;
     }
@@ -532,12 +443,44 @@ struct GradOp {
   }
 };
 
-__global__ void __launch_bounds__(kLoopThreads) k_gradient(GradArgs a) {
+__device__ __forceinline__ void grad_item(const LoopArgs& a, const GradOp& op, const Grid& g, WarpSmem& w,
+                                          const Item& it, float Lmax, unsigned& ninter, unsigned& ncand) {
+  const LaneMap lm = lane_map(it.cnt, a.lmax);
+  const int k = a.plist[it.off + (lm.live ? lm.slot : 0)];
+  GradOp::I I;
+  const float4 p = a.pos[k];
+  const float4 v = a.vel[k];
+  const float4 gi = a.ga[k];
+  I.x = p.x; I.y = p.y; I.z = p.z; I.h = p.w;
+  const float H = a.ph.kg * p.w;
+  const float b = band_of(H, Lmax);
+  I.H2lo = H * H - b;
+  I.H2hi = H * H + b;
+  I.invH = 1.0f / H;
+  I.c4 = (8.0f / kPi) * I.invH * I.invH * I.invH * I.invH;
+  I.vx = v.x; I.vy = v.y; I.vz = v.z;
+  I.c = gi.w;
+  I.u = a.gb[k].w;
+  I.vsig = 2.0f * gi.w;
+  I.lap = 0.0f;
+  I.count = 0;
+  I.k = k;
+  scan_item(op, I, g, a.cell_start, a.pos, it.cell, lm.lsh, lm.s, lm.live, w, ncand);
+  I.vsig = lmax(I.vsig, lm.lsh);
+  I.lap = lsum(I.lap, lm.lsh);
+  I.count = lsum_u(I.count, lm.lsh);
+  if (lm.live && lm.s == 0) {
+    ninter += I.count;
+    reinterpret_cast<float2*>(a.out)[a.perm[k]] = make_float2(I.vsig, 2.0f * I.lap);
+  }
+}
+
+__global__ void __launch_bounds__(kLoopThreads, 5) k_gradient(LoopArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const unsigned lane = lane_id();
   const Grid g = *a.grid;
-  unsigned* list = warp_list(smem);
-  float4* stage = warp_stage(smem);
+  const float Lmax = fmaxf(g.L[0], fmaxf(g.L[1], g.L[2]));
+  WarpSmem& w = warp_smem(smem);
   GradOp op;
   op.pos = a.pos; op.vel = a.vel; op.ga = a.ga; op.gb = a.gb;
   op.L[0] = g.L[0]; op.L[1] = g.L[1]; op.L[2] = g.L[2];
@@ -549,36 +492,7 @@ __global__ void __launch_bounds__(kLoopThreads) k_gradient(GradArgs a) {
     const int t = take_ticket(a.ticket);
     if (t >= n_items) break;
     const Item it = a.items[t];
-    const int L = lanes_per_particle(it.cnt, a.lmax);
-    const int A = 32 / L;
-    const int slot = (int)lane % A, s = (int)lane / A;
-    const bool live = slot < it.cnt;
-    const int k = live ? a.plist[it.off + slot] : a.plist[it.off];
-    GradOp::I I;
-    const float4 p = a.pos[k];
-    const float4 v = a.vel[k];
-    const float4 gi = a.ga[k];
-    I.x = p.x; I.y = p.y; I.z = p.z; I.h = p.w;
-    const float H = a.ph.kg * p.w;
-    I.H2lo = H * H * (1.0f - kBand);
-    I.H2hi = H * H * (1.0f + kBand);
-    I.invH = 1.0f / H;
-    I.c4 = (8.0f / kPi) * I.invH * I.invH * I.invH * I.invH;
-    I.vx = v.x; I.vy = v.y; I.vz = v.z;
-    I.c = gi.w;
-    I.u = a.gb[k].w;
-    I.vsig = 2.0f * gi.w;
-    I.lap = 0.0f;
-    I.count = 0;
-    I.k = k;
-    scan_cells(op, I, g, a.cell_start, a.pos, it.cell, L, s, live, list, stage, ncand);
-    I.vsig = sub_max(I.vsig, A);
-    I.lap = sub_sum(I.lap, A);
-    I.count = sub_sum_u(I.count, A);
-    if (live && s == 0) {
-      ninter += I.count;
-      a.out[a.perm[k]] = make_float2(I.vsig, 2.0f * I.lap);
-    }
+    grad_item(a, op, g, w, it, Lmax, ninter, ncand);
   }
   ninter = warp_sum(ninter);
   ncand = warp_sum(ncand);
@@ -589,27 +503,6 @@ __global__ void __launch_bounds__(kLoopThreads) k_gradient(GradArgs a) {
 }
 
 // =============================================================== force loop
-struct ForceArgs {
-  Grid* grid;
-  const int* cell_start;
-  const unsigned* perm;
-  Phys ph;
-  int lmax;
-  const float4* pos;
-  const float4* vel;
-  const float4* ga;
-  const float4* gb;
-  const Item* items;
-  const int* plist;
-  const int* ctr;
-  int* ticket;
-  float4* out;      // caller order (a, du/dt)
-  float* dhdt;      // caller order, may be NULL
-  double* red_partial;  // [gridDim.x][8]
-  Status* st;
-  unsigned long long* stats;
-};
-
 struct ForceOp {
   struct I {
     float x, y, z, h, H2lo, H2hi, invH, c4;
@@ -624,27 +517,26 @@ struct ForceOp {
   const float4* __restrict__ ga;
   const float4* __restrict__ gb;
   float L[3];
-  float kg, beta, gm1;
+  float kg, beta, gm1, Lmax;
   int compensated;
 
-  // staged w: the j support squared (with the guard band)
+  // staged w: the j support squared plus its guard band
   __device__ __forceinline__ float stage_w(float hj) const {
     const float H = kg * hj;
-    return H * H * (1.0f + kBand);
+    return H * H + band_of(H, Lmax);
   }
   __device__ __forceinline__ bool candidate(const I& i, float r2, float H2j_hi) const {
     return r2 < fmaxf(i.H2hi, H2j_hi);
   }
   __device__ __forceinline__ void interact(I& i, int j, unsigned code) const {
     const float4 pj = pos[j];
-    float xi = i.x, yi = i.y, zi = i.z, xj = pj.x, yj = pj.y, zj = pj.z;
-    apply_shift(code, L, xi, yi, zi, xj, yj, zj);
-    const float dx = xi - xj, dy = yi - yj, dz = zi - zj;
+    float xj = pj.x, yj = pj.y, zj = pj.z;
+    shift_j(code, L, xj, yj, zj);
+    const float dx = i.x - xj, dy = i.y - yj, dz = i.z - zj;
     const float r2 = r2_of(dx, dy, dz);
     if (!(r2 > 0.0f)) return;  // the particle itself
     const float Hj = kg * pj.w;
-    const float H2j = Hj * Hj;
-    if (r2 >= fmaxf(i.H2lo, H2j * (1.0f - kBand))) {
+    if (r2 >= fmaxf(i.H2lo, Hj * Hj - band_of(Hj, Lmax))) {
       const double e = exact_r2(i.x, i.y, i.z, pj.x, pj.y, pj.z, L[0], L[1], L[2]);
       if (!(e < exact_H2(kg, i.h)) && !(e < exact_H2(kg, pj.w))) return;
     }
@@ -665,7 +557,7 @@ struct ForceOp {
     // pressure (Eq. 17) and its work (Eq. 18)
     const float ps = mj * fmaf(i.A, dWi, aj.x * dWj);
     float du = mj * i.A * dWi * vr;
-    // artificial viscosity (Eqs. 7, 9-11, 16) and heating
+    // artificial viscosity (Eqs. 7, 9-11, 16) and its heating
     const float mu = fminf(vr, 0.0f);
     const float vsig = fmaf(-beta, mu, i.c + aj.w);
     const float alpha = 0.25f * (i.av + bj.y) * (i.B + bj.x);
@@ -697,16 +589,67 @@ struct ForceOp {
   }
 };
 
-__global__ void __launch_bounds__(kLoopThreads) k_force(ForceArgs a) {
+__device__ __forceinline__ void force_item(const LoopArgs& a, const ForceOp& op, const Grid& g, WarpSmem& w,
+                                           const Item& it, unsigned& ninter, unsigned& ncand, double* acc) {
+  const LaneMap lm = lane_map(it.cnt, a.lmax);
+  const int k = a.plist[it.off + (lm.live ? lm.slot : 0)];
+  ForceOp::I I;
+  const float4 p = a.pos[k];
+  const float4 v = a.vel[k];
+  const float4 gi = a.ga[k];
+  const float4 bi = a.gb[k];
+  I.x = p.x; I.y = p.y; I.z = p.z; I.h = p.w;
+  const float H = a.ph.kg * p.w;
+  const float b = band_of(H, op.Lmax);
+  I.H2lo = H * H - b;
+  I.H2hi = H * H + b;
+  I.invH = 1.0f / H;
+  I.c4 = (8.0f / kPi) * I.invH * I.invH * I.invH * I.invH;
+  I.vx = v.x; I.vy = v.y; I.vz = v.z;
+  I.A = gi.x; I.f = gi.y; I.rho = gi.z; I.c = gi.w;
+  I.B = bi.x; I.av = bi.y; I.acP = bi.z; I.u = bi.w;
+  I.P = op.gm1 * gi.z * bi.w;
+  I.axs = I.axc = I.ays = I.ayc = I.azs = I.azc = I.dus = I.duc = I.dh = 0.0f;
+  I.count = 0;
+  I.k = k;
+  scan_item(op, I, g, a.cell_start, a.pos, it.cell, lm.lsh, lm.s, lm.live, w, ncand);
+  lsum2(I.axs, I.axc, lm.lsh);
+  lsum2(I.ays, I.ayc, lm.lsh);
+  lsum2(I.azs, I.azc, lm.lsh);
+  lsum2(I.dus, I.duc, lm.lsh);
+  I.dh = lsum(I.dh, lm.lsh);
+  I.count = lsum_u(I.count, lm.lsh);
+  if (lm.live && lm.s == 0) {
+    ninter += I.count;
+    const float ax = I.axs + I.axc, ay = I.ays + I.ayc, az = I.azs + I.azc, du = I.dus + I.duc;
+    const unsigned dst = a.perm[k];
+    reinterpret_cast<float4*>(a.out)[dst] = make_float4(ax, ay, az, du);
+    if (a.dhdt) a.dhdt[dst] = -(I.h / (3.0f * I.rho)) * I.f * I.dh;
+    // FP64 sums of FP32 per-particle terms
+    const float m = v.w;
+    const float mx = m * ax, my = m * ay, mz = m * az;
+    const float va = fmaf(v.z, az, fmaf(v.y, ay, v.x * ax));
+    acc[0] += (double)mx;
+    acc[1] += (double)my;
+    acc[2] += (double)mz;
+    acc[3] += (double)(m * va) + (double)(m * du);
+    acc[4] += (double)sqrtf(fmaf(mz, mz, fmaf(my, my, mx * mx)));
+    acc[5] += (double)(m * fabsf(va)) + (double)(m * fabsf(du));
+    acc[6] += (double)(m * du);
+    acc[7] += (double)I.count;
+  }
+}
+
+__global__ void __launch_bounds__(kLoopThreads, 4) k_force(LoopArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[kWarpsPerBlock][8];
   const unsigned lane = lane_id();
   const Grid g = *a.grid;
-  unsigned* list = warp_list(smem);
-  float4* stage = warp_stage(smem);
+  WarpSmem& w = warp_smem(smem);
   ForceOp op;
   op.pos = a.pos; op.vel = a.vel; op.ga = a.ga; op.gb = a.gb;
   op.L[0] = g.L[0]; op.L[1] = g.L[1]; op.L[2] = g.L[2];
+  op.Lmax = fmaxf(g.L[0], fmaxf(g.L[1], g.L[2]));
   op.kg = a.ph.kg;
   op.beta = a.ph.beta_v;
   op.gm1 = a.ph.gamma_eos - 1.0f;
@@ -718,56 +661,9 @@ __global__ void __launch_bounds__(kLoopThreads) k_force(ForceArgs a) {
     const int t = take_ticket(a.ticket);
     if (t >= n_items) break;
     const Item it = a.items[t];
-    const int L = lanes_per_particle(it.cnt, a.lmax);
-    const int A = 32 / L;
-    const int slot = (int)lane % A, s = (int)lane / A;
-    const bool live = slot < it.cnt;
-    const int k = live ? a.plist[it.off + slot] : a.plist[it.off];
-    ForceOp::I I;
-    const float4 p = a.pos[k];
-    const float4 v = a.vel[k];
-    const float4 gi = a.ga[k];
-    const float4 bi = a.gb[k];
-    I.x = p.x; I.y = p.y; I.z = p.z; I.h = p.w;
-    const float H = a.ph.kg * p.w;
-    I.H2lo = H * H * (1.0f - kBand);
-    I.H2hi = H * H * (1.0f + kBand);
-    I.invH = 1.0f / H;
-    I.c4 = (8.0f / kPi) * I.invH * I.invH * I.invH * I.invH;
-    I.vx = v.x; I.vy = v.y; I.vz = v.z;
-    I.A = gi.x; I.f = gi.y; I.rho = gi.z; I.c = gi.w;
-    I.B = bi.x; I.av = bi.y; I.acP = bi.z; I.u = bi.w;
-    I.P = op.gm1 * gi.z * bi.w;
-    I.axs = I.axc = I.ays = I.ayc = I.azs = I.azc = I.dus = I.duc = I.dh = 0.0f;
-    I.count = 0;
-    I.k = k;
-    scan_cells(op, I, g, a.cell_start, a.pos, it.cell, L, s, live, list, stage, ncand);
-    sub_sum2(I.axs, I.axc, A);
-    sub_sum2(I.ays, I.ayc, A);
-    sub_sum2(I.azs, I.azc, A);
-    sub_sum2(I.dus, I.duc, A);
-    I.dh = sub_sum(I.dh, A);
-    I.count = sub_sum_u(I.count, A);
-    if (live && s == 0) {
-      ninter += I.count;
-      const float ax = I.axs + I.axc, ay = I.ays + I.ayc, az = I.azs + I.azc, du = I.dus + I.duc;
-      const unsigned dst = a.perm[k];
-      a.out[dst] = make_float4(ax, ay, az, du);
-      if (a.dhdt) a.dhdt[dst] = -(I.h / (3.0f * I.rho)) * I.f * I.dh;
-      const double m = v.w;
-      const double max_ = m * ax, may = m * ay, maz = m * az;
-      const double va = (double)v.x * ax + (double)v.y * ay + (double)v.z * az;
-      acc[0] += max_;
-      acc[1] += may;
-      acc[2] += maz;
-      acc[3] += m * (va + (double)du);
-      acc[4] += sqrt(max_ * max_ + may * may + maz * maz);
-      acc[5] += m * (fabs(va) + fabs((double)du));
-      acc[6] += m * (double)du;
-      acc[7] += (double)I.count;
-    }
+    force_item(a, op, g, w, it, ninter, ncand, acc);
   }
-  // block partial of the FP64 reductions (deterministic final sum elsewhere)
+  // block partial of the FP64 sums (summed in block order by k_reduce_partials)
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     double x = acc[q];
@@ -777,7 +673,7 @@ __global__ void __launch_bounds__(kLoopThreads) k_force(ForceArgs a) {
   __syncthreads();
   if (threadIdx.x < 8) {
     double x = 0.0;
-    for (int w = 0; w < kWarpsPerBlock; ++w) x += red[w][threadIdx.x];
+    for (int ww = 0; ww < kWarpsPerBlock; ++ww) x += red[ww][threadIdx.x];
     a.red_partial[blockIdx.x * 8 + threadIdx.x] = x;
   }
   ninter = warp_sum(ninter);
@@ -802,7 +698,8 @@ static int persistent_blocks(Ctx* c, const void* kern) {
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kLoopThreads, kLoopSmemBytes);
   if (per_sm < 1) per_sm = 1;
   if (c->tuning.blocks_per_sm > 0 && c->tuning.blocks_per_sm < per_sm) per_sm = c->tuning.blocks_per_sm;
-  return per_sm * c->num_sms;
+  int nb = per_sm * c->num_sms;
+  return nb < c->red_blocks ? nb : c->red_blocks;
 }
 
 static bool g_attr_done = false;
@@ -869,12 +766,8 @@ int ghost_impl(Ctx* c, const float* u, const float* alpha_v, const float* alpha_
   return cudaGetLastError() == cudaSuccess ? SWIFT_GPU_OK : SWIFT_GPU_ERR_CUDA;
 }
 
-int gradient_impl(Ctx* c, float2* out, cudaStream_t s) {
-  ensure_attrs();
-  const int nblk = persistent_blocks(c, (const void*)k_gradient);
-  int* ticket = c->d_counters + kCtrPerPass * (c->max_passes + 1) + 0;
-  cudaMemsetAsync(ticket, 0, sizeof(int), s);
-  GradArgs a;
+static LoopArgs loop_args(Ctx* c, int* ticket, void* out) {
+  LoopArgs a;
   a.grid = c->d_grid;
   a.cell_start = c->d_cell_start;
   a.perm = c->d_vals[c->sorted_buf];
@@ -889,8 +782,19 @@ int gradient_impl(Ctx* c, float2* out, cudaStream_t s) {
   a.ctr = c->d_counters;  // pass-0 item count
   a.ticket = ticket;
   a.out = out;
+  a.dhdt = nullptr;
+  a.red_partial = c->d_red_partial;
   a.st = c->d_status;
   a.stats = c->d_stats;
+  return a;
+}
+
+int gradient_impl(Ctx* c, float2* out, cudaStream_t s) {
+  ensure_attrs();
+  const int nblk = persistent_blocks(c, (const void*)k_gradient);
+  int* ticket = c->d_counters + kCtrPerPass * (c->max_passes + 1) + 0;
+  cudaMemsetAsync(ticket, 0, sizeof(int), s);
+  LoopArgs a = loop_args(c, ticket, out);
   k_gradient<<<nblk, kLoopThreads, kLoopSmemBytes, s>>>(a);
   c->launches += 2;
   return cudaGetLastError() == cudaSuccess ? SWIFT_GPU_OK : SWIFT_GPU_ERR_CUDA;
@@ -901,25 +805,8 @@ int force_impl(Ctx* c, float4* out, float* dhdt, double* reductions, cudaStream_
   const int nblk = persistent_blocks(c, (const void*)k_force);
   int* ticket = c->d_counters + kCtrPerPass * (c->max_passes + 1) + 1;
   cudaMemsetAsync(ticket, 0, sizeof(int), s);
-  ForceArgs a;
-  a.grid = c->d_grid;
-  a.cell_start = c->d_cell_start;
-  a.perm = c->d_vals[c->sorted_buf];
-  a.ph = c->phys;
-  a.lmax = c->tuning.max_lanes_per_particle;
-  a.pos = c->d_pos;
-  a.vel = c->d_vel;
-  a.ga = c->d_ga;
-  a.gb = c->d_gb;
-  a.items = c->d_items0;
-  a.plist = c->d_plist0;
-  a.ctr = c->d_counters;
-  a.ticket = ticket;
-  a.out = out;
+  LoopArgs a = loop_args(c, ticket, out);
   a.dhdt = dhdt;
-  a.red_partial = c->d_red_partial;
-  a.st = c->d_status;
-  a.stats = c->d_stats;
   k_force<<<nblk, kLoopThreads, kLoopSmemBytes, s>>>(a);
   c->launches += 2;
   if (reductions) {
