@@ -243,7 +243,7 @@ def interpolate(p: Params, x, m, h, rho, Q):
 
 
 def count_flops(loop: int, q: float = 0.75, approaching: bool = True):
-    """Ops of one interaction of loop 0 density / 1 gradient / 2 force (add, mul, div, sqrt, cmp)."""
+    """Ops of one interaction of loop 0 density / 1 gradient / 2 force / 3 h-iteration step (Eqs. 5-6)."""
     out = (ctypes.c_longlong * 5)()
     lib().oracle_count_flops(ctypes.c_int(loop), ctypes.c_double(q), ctypes.c_int(int(approaching)), out)
     return dict(zip(("add", "mul", "div", "sqrt", "cmp"), list(out)))

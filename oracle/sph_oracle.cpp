@@ -266,10 +266,43 @@ inline void density_pair(const KernelI<T>& k, T r2, T dx, T dy, T dz, T mj, T dv
   }
 }
 
+/* The two sums the h iteration needs, Eq. 5 (n) and Eq. 6 (dn/dh), for one pair. */
+template <class T>
+inline void number_pair(const KernelI<T>& k, T r2, T& n, T& dn) {
+  T r = sqrt_(r2);
+  T W, dWdr;
+  kernel_eval(k, r, W, dWdr);
+  n += W;
+  dn += T(3.0) * W + r * dWdr;
+}
+
 struct DensOut {
   double n, dn_dh, rho, drho_dh, div, curl[3];
   long long count;
 };
+
+/* Eq. 5 and Eq. 6 at h (self included in the sums, not in the count). */
+DensOut number_at(const Geo& g, const Cells& c, int64_t n, const double* x, int64_t i, double h,
+                  double kernel_gamma) {
+  KernelI<double> k = kernel_consts<double>(h, kernel_gamma);
+  double H2 = k.H * k.H;
+  double s = 0.0, ds = 0.0;
+  long long count = 0;
+  for_candidates(c, n, i, [&](int64_t j) {
+    double d[3] = {x[3 * i] - x[3 * j], x[3 * i + 1] - x[3 * j + 1], x[3 * i + 2] - x[3 * j + 2]};
+    min_image(g, d);
+    double r2 = r2_of(d);
+    bool self = (j == i);
+    if (!self && !(r2 < H2)) return;
+    number_pair<double>(k, self ? 0.0 : r2, s, ds);
+    if (!self) count++;
+  });
+  DensOut o{};
+  o.n = s;
+  o.dn_dh = -ds / h;
+  o.count = count;
+  return o;
+}
 
 DensOut density_at(const Geo& g, const Cells& c, int64_t n, const double* x, const double* v,
                    const double* m, int64_t i, double h, double kernel_gamma) {
@@ -298,7 +331,9 @@ DensOut density_at(const Geo& g, const Cells& c, int64_t n, const double* x, con
   return o;
 }
 
-/* Newton-Raphson on F(h) = n(h) - (eta/h)^3 (Sec. 2.1.2). */
+/* Newton-Raphson on F(h) = n(h) - (eta/h)^3 (Sec. 2.1.2). Each iteration
+ * takes Eq. 5 and Eq. 6 at the current h; the remaining density sums are
+ * taken once, at the h the iteration ends on. */
 struct SolveOut {
   double h;
   int iters;
@@ -317,13 +352,12 @@ SolveOut solve_h(const Geo& g, const Cells& c, int64_t n, const double* x, const
   s.converged = 0;
   s.pairs = 0;
   for (int it = 0; it < p.max_iter; ++it) {
-    DensOut d = density_at(g, c, n, x, v, m, i, h, p.kernel_gamma);
+    DensOut d = number_at(g, c, n, x, i, h, p.kernel_gamma);
     s.pairs += d.count;
     double target = eta3 / (h * h * h);
     double F = d.n - target;
     s.h = h;
     s.iters = it + 1;
-    s.d = d;
     if (std::fabs(F) <= p.h_tol * target) {
       s.converged = 1;
       break;
@@ -342,6 +376,7 @@ SolveOut solve_h(const Geo& g, const Cells& c, int64_t n, const double* x, const
     }
     h = std::min(hn, hmax);
   }
+  s.d = density_at(g, c, n, x, v, m, i, s.h, p.kernel_gamma);
   return s;
 }
 
@@ -652,7 +687,8 @@ int oracle_interpolate(const oracle_params* p, int64_t n, const double* x, const
 /*
  * Flop count of one interaction of each loop, from the same templated pair
  * functions instantiated on the counting scalar. loop: 0 density (non-self
- * hit), 1 gradient, 2 force (all terms); q selects the spline branch
+ * hit), 1 gradient, 2 force (all terms), 3 one step of the h iteration
+ * (Eqs. 5-6 only); q selects the spline branch
  * (q < 1/2 or q >= 1/2) of the i-side kernel; approaching selects the
  * mu < 0 branch. out[0..4] = add, mul, div, sqrt, cmp. The neighbour test
  * itself (3 sub, 3 mul, 2 add, 1 cmp) is not included.
@@ -668,6 +704,9 @@ int oracle_count_flops(int loop, double q, int approaching, long long* out) {
   if (loop == 0) {
     DensAcc<Cnt> a{0, 0, 0, 0, 0, 0, 0, 0, 0};
     density_pair<Cnt>(k, r2, dx, dy, dz, Cnt(1.0), dvx, dvy, dvz, false, a);
+  } else if (loop == 3) {
+    Cnt nn(0.0), dn(0.0);
+    number_pair<Cnt>(k, r2, nn, dn);
   } else if (loop == 1) {
     GradAcc<Cnt> a{Cnt(0.0), Cnt(0.0)};
     gradient_pair<Cnt>(k, r2, dx, dy, dz, dvx, dvy, dvz, Cnt(1.0), Cnt(1.1), Cnt(1.0), Cnt(1.0),

@@ -18,7 +18,7 @@ from oracle import oracle as O  # noqa: E402
 
 def main():
     out = {}
-    for loop, name in enumerate(("density", "gradient", "force")):
+    for loop, name in ((0, "density"), (1, "gradient"), (2, "force"), (3, "h_iteration")):
         tot = {}
         for q, w in ((0.3, 0.125), (0.75, 0.875)):
             c = O.count_flops(loop, q, True)
