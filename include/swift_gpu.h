@@ -83,9 +83,10 @@ typedef struct {
   int64_t n_cells;
   int64_t n_items;         /* work items (cell chunks of <= 32 active particles) */
   int32_t density_passes;  /* Newton passes run by the last density call */
-  uint64_t interactions[3];/* pair interactions (density summed over passes, gradient, force) */
+  uint64_t interactions[3];/* pair interactions: density (full sums, every pass), gradient, force */
   uint64_t candidates[3];  /* candidate pairs tested by the neighbour scan, same loops */
   uint64_t launches;       /* kernel launches issued since the context was created */
+  uint64_t h_iteration_pairs; /* pairs of the Newton steps on h that evaluate only Eqs. 5-6 */
 } swift_gpu_info;
 
 typedef struct swift_gpu_ctx swift_gpu_ctx;
@@ -134,8 +135,11 @@ int swift_gpu_build_cells(swift_gpu_ctx* ctx, const float* pos_h, int64_t n, flo
  * For inactive particles rho4 and curl_div are INPUTS: they must hold that
  * particle's last values, which the gradient and force loops read.
  * Each active particle iterates h <- h - F/F' on F = n - (eta/h)^3 until
- * |F| <= h_tol (eta/h)^3, at most max_iter passes; all outputs belong to the
- * final h. Runs as ONE persistent cooperative launch. Device-side status:
+ * |F| <= h_tol (eta/h)^3, at most max_iter steps; all outputs belong to the
+ * final h. Runs as ONE persistent cooperative launch: one neighbour scan
+ * collects every candidate within the largest support a cell allows and the
+ * steps run over those lists; particles whose candidates do not fit take
+ * further scan passes. Device-side status:
  * ERR_H_NOT_CONVERGED / ERR_H_EXCEEDS_CELL with detail = number of particles
  * (outputs are still written at their last h), ERR_TIMEOUT.
  * Requires build_cells (ERR_ORDER otherwise). */

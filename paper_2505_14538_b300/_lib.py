@@ -72,6 +72,7 @@ class Info(ctypes.Structure):
         ("interactions", ctypes.c_uint64 * 3),
         ("candidates", ctypes.c_uint64 * 3),
         ("launches", ctypes.c_uint64),
+        ("h_iteration_pairs", ctypes.c_uint64),
     ]
 
 

@@ -297,6 +297,7 @@ int swift_gpu_get_info(swift_gpu_ctx* h, swift_gpu_info* info) {
   info->candidates[1] = c->h_stats[kStatCandGrad];
   info->candidates[2] = c->h_stats[kStatCandForce];
   info->launches = c->launches;
+  info->h_iteration_pairs = c->h_stats[kStatInterHiter];
   return SWIFT_GPU_OK;
 }
 

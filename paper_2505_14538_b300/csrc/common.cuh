@@ -9,7 +9,7 @@
 namespace sg {
 
 constexpr int kWarp = 32;
-constexpr int kItemMax = 32;          // particles per work item (one per lane at most)
+constexpr int kItemMax = 16;          // particles per work item (at least two lanes each)
 constexpr int kIndexBits = 26;        // list entry: j index (26 bits) + shift code (6 bits)
 constexpr uint32_t kIndexMask = (1u << kIndexBits) - 1u;
 constexpr float kPi = 3.14159265358979323846f;
@@ -65,7 +65,7 @@ struct Item {
 enum StatSlot {
   kStatInterDens = 0, kStatInterGrad, kStatInterForce,
   kStatCandDens, kStatCandGrad, kStatCandForce,
-  kStatPasses, kStatItems,
+  kStatPasses, kStatItems, kStatInterHiter,
   kStatCount = 16
 };
 

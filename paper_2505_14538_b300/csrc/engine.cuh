@@ -139,6 +139,57 @@ __device__ __forceinline__ void scan_item(const Op& op, typename Op::I& I, const
   }
 }
 
+// Phase 1 only, for the h iteration: every candidate with r^2 < R2 (the
+// largest support any h may reach) goes into the lane's list, which is never
+// flushed; `ovf` is set when the list is full (the particle then takes the
+// multi-pass route).
+__device__ __forceinline__ int collect_item(const Grid& g, const int* __restrict__ cell_start,
+                                            const float4* __restrict__ pos, int cell, float xi, float yi, float zi,
+                                            float R2, int lsh, int s, bool live, WarpSmem& w, unsigned& ncand,
+                                            bool& ovf) {
+  const unsigned lane = lane_id();
+  const int total = setup_segments(g, cell_start, cell, w);
+  int cnt = 0;
+  for (int base = 0; base < total; base += 32) {
+    const int len = min(32, total - base);
+    __syncwarp();
+    if ((int)lane < len) {
+      const int p = base + (int)lane;
+      int q = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1)
+        if (q + step < 27 && w.seg_pref[q + step] <= p) q += step;
+      const int j = w.seg_start[q] + (p - w.seg_pref[q]);
+      const unsigned code = w.seg_code[q];
+      float4 pj = pos[j];
+      shift_j(code, g.L, pj.x, pj.y, pj.z);
+      w.stage[lane] = pj;
+      w.stage_idx[lane] = (unsigned)j | (code << kIndexBits);
+    }
+    __syncwarp();
+    if (live) {
+      const int nk = len > s ? ((len - s - 1) >> lsh) + 1 : 0;
+#pragma unroll 4
+      for (int kk = 0; kk < nk; ++kk) {
+        const int k = (kk << lsh) + s;
+        const float4 c = w.stage[k];
+        const float dx = xi - c.x, dy = yi - c.y, dz = zi - c.z;
+        if (r2_of(dx, dy, dz) < R2) {
+          if (cnt < kCap) {
+            w.list[cnt * 32 + lane] = w.stage_idx[k];
+            ++cnt;
+          } else {
+            ovf = true;
+          }
+        }
+      }
+      ncand += (unsigned)nk;
+    }
+  }
+  __syncwarp();
+  return cnt;
+}
+
 // Combination of the sub-lanes of one particle (lanes a, a + A, a + 2A, ...
 // with A = 32 >> lsh).
 __device__ __forceinline__ float lsum(float v, int lsh) {

@@ -108,6 +108,7 @@ struct DensOp {
     const float dx = i.x - xj, dy = i.y - yj, dz = i.z - zj;
     const float r2 = r2_of(dx, dy, dz);
     if (r2 >= i.H2lo) {
+      if (r2 >= i.H2hi) return;
       if (!(exact_r2(i.x, i.y, i.z, pj.x, pj.y, pj.z, L[0], L[1], L[2]) < exact_H2(kg, i.h))) return;
     }
     const float invr = r2 > 0.0f ? rsqrtf(r2) : 0.0f;
@@ -137,36 +138,147 @@ struct DensOp {
   }
 };
 
-__device__ __forceinline__ void dens_load(DensOp::I& I, const DensArgs& a, float Lmax, int k) {
-  const float4 p = a.pos[k];
-  const float4 v = a.vel[k];
-  const float h = a.h[k];
-  I.x = p.x; I.y = p.y; I.z = p.z; I.h = h;
-  const float H = a.ph.kg * h;
+__device__ __forceinline__ void dens_set_h(DensOp::I& I, float h, float kg, float Lmax) {
+  I.h = h;
+  const float H = kg * h;
   const float b = band_of(H, Lmax);
   I.H2lo = H * H - b;
   I.H2hi = H * H + b;
   I.invH = 1.0f / H;
   I.c3 = (8.0f / kPi) * I.invH * I.invH * I.invH;
   I.c4 = I.c3 * I.invH;
+}
+
+__device__ __forceinline__ void dens_load(DensOp::I& I, const DensArgs& a, float Lmax, int k) {
+  const float4 p = a.pos[k];
+  const float4 v = a.vel[k];
+  I.x = p.x; I.y = p.y; I.z = p.z;
+  dens_set_h(I, a.h[k], a.ph.kg, Lmax);
   I.vx = v.x; I.vy = v.y; I.vz = v.z;
   I.ns = I.nc = I.rs = I.rc = I.dn = I.dr = I.div = I.cx = I.cy = I.cz = 0.0f;
   I.count = 0;
   I.k = k;
 }
 
-// One density item: neighbour sums, then the Newton step for each particle;
-// the particles that need another pass form one item of the next pass.
+// One step of the Newton iteration on F(h) = n - (eta/h)^3 (Sec. 2.1.2) from
+// the compensated sum n = ns + nc and dn_acc = sum(3W + r dW/dr) at h.
+// Convergence |n h^3 - eta^3| <= h_tol eta^3 is tested in FP64 (no division);
+// the step itself, F' = dn/dh + 3 eta^3 / h^4 clamped to [h/2, 2h] with
+// bisection on the bracket [lo, hi], is FP32. Returns true with hn set when
+// another evaluation is needed; false when the particle is finished (flag 0:
+// converged; otherwise not converged / capped by the cell width).
+__device__ __forceinline__ bool newton_step(float h, float ns, float nc, float dn_acc, float& lo, float& hi,
+                                            const Grid& g, const Phys& ph, bool last, float& hn, int& flag) {
+  flag = 0;
+  const double hd = (double)h;
+  const double h3 = hd * hd * hd;
+  const double G = fma((double)ns, h3, fma((double)nc, h3, -ph.eta3));
+  if (fabs(G) <= ph.h_tol * ph.eta3) return false;
+  if (last) {
+    flag = SWIFT_GPU_ERR_H_NOT_CONVERGED;
+    return false;
+  }
+  if (G < 0.0) lo = fmaxf(lo, h);
+  else hi = fminf(hi, h);
+  if (G < 0.0 && h >= g.hcap) {
+    flag = g.hcap_from_cells ? SWIFT_GPU_ERR_H_EXCEEDS_CELL : SWIFT_GPU_ERR_H_NOT_CONVERGED;
+    return false;
+  }
+  const float ih = 1.0f / h;
+  const float target = (float)ph.eta3 * ih * ih * ih;
+  const float F = (ns + nc) - target;
+  const float Fp = fmaf(-dn_acc, ih, 3.0f * target * ih);
+  hn = Fp > 0.0f ? h - F / Fp : __int_as_float(0x7fc00000);
+  if (hn == hn) hn = fminf(fmaxf(hn, 0.5f * h), 2.0f * h);
+  if (!(hn == hn) || !(hn > lo) || !(hn < hi)) {
+    if (isfinite(hi) && lo > 0.0f) hn = 0.5f * (lo + hi);
+    else if (!isfinite(hi)) hn = 2.0f * h;
+    else hn = 0.5f * h;
+  }
+  hn = fminf(hn, g.hcap);
+  return hn != h;  // a float h that cannot move is as converged as FP32 allows
+}
+
+// Eqs. 5-6 at the lane particle's current h over its list (one step of the
+// h iteration).
+__device__ __forceinline__ void number_walk(const DensOp& op, const DensOp::I& I, const WarpSmem& w, int cnt,
+                                            float& ns, float& nc, float& dn, unsigned& npairs) {
+  const unsigned lane = lane_id();
+  const int m = __reduce_max_sync(kFull, cnt);
+  for (int t = 0; t < m; ++t) {
+    if (t < cnt) {
+      const unsigned e = w.list[t * 32 + lane];
+      const int j = (int)(e & kIndexMask);
+      const float4 pj = op.pos[j];
+      float xj = pj.x, yj = pj.y, zj = pj.z;
+      shift_j(e >> kIndexBits, op.L, xj, yj, zj);
+      const float dx = I.x - xj, dy = I.y - yj, dz = I.z - zj;
+      const float r2 = r2_of(dx, dy, dz);
+      if (r2 < I.H2hi) {
+        const float invr = r2 > 0.0f ? rsqrtf(r2) : 0.0f;
+        const float r = r2 * invr;
+        float wq, dwq;
+        spline(r * I.invH, wq, dwq);
+        const float W = I.c3 * wq;
+        if (op.compensated) two_sum_acc(ns, nc, W);
+        else ns += W;
+        dn += fmaf(r, I.c4 * dwq, 3.0f * W);
+        npairs += (j != I.k) ? 1u : 0u;
+      }
+    }
+  }
+}
+
+// One density item. In list mode (first pass) the item's candidates within
+// the largest reachable support are collected once and the whole Newton
+// iteration runs over those lists; the full sums (Eqs. 2-6 with div/curl)
+// are then taken at the final h. Otherwise (later passes, and particles whose
+// list overflowed) one neighbour scan gives the sums at the current h and one
+// Newton step; the particles that need another pass form one item of the
+// next pass.
 __device__ __forceinline__ void dens_item(const DensArgs& a, const DensOp& op, const Grid& g, WarpSmem& w,
-                                          const Item& it, const int* __restrict__ plist, bool last,
-                                          Item* items_next, int* plist_next, int* ctr_next, float Lmax,
-                                          unsigned& ninter, unsigned& ncand) {
+                                          const Item& it, const int* __restrict__ plist, bool list_mode,
+                                          bool last, Item* items_next, int* plist_next, int* ctr_next, float Lmax,
+                                          unsigned& ninter, unsigned& nhiter, unsigned& ncand) {
   const unsigned lane = lane_id();
   const LaneMap lm = lane_map(it.cnt, a.lmax);
   const int k = plist[it.off + (lm.live ? lm.slot : 0)];
   DensOp::I I;
   dens_load(I, a, Lmax, k);
-  scan_item(op, I, g, a.cell_start, a.pos, it.cell, lm.lsh, lm.s, lm.live, w, ncand);
+  bool retry = false;  // take the multi-pass route from the starting h
+  int flag = 0;
+  bool step_again = false;
+  float hn = I.h;
+  if (list_mode) {
+    const float Hc = a.ph.kg * g.hcap;
+    const float R2 = Hc * Hc + band_of(Hc, Lmax);
+    bool ovf = false;
+    const int cnt = collect_item(g, a.cell_start, a.pos, it.cell, I.x, I.y, I.z, R2, lm.lsh, lm.s, lm.live, w,
+                                 ncand, ovf);
+    retry = lsum_u(ovf ? 1u : 0u, lm.lsh) != 0;
+    bool done = !lm.live || retry;
+    float lo = 0.0f, hi = __int_as_float(0x7f800000);
+    for (int iter = 0;; ++iter) {
+      float ns = 0.0f, nc = 0.0f, dn = 0.0f;
+      unsigned np = 0;
+      number_walk(op, I, w, done ? 0 : cnt, ns, nc, dn, np);
+      lsum2(ns, nc, lm.lsh);
+      dn = lsum(dn, lm.lsh);
+      np = lsum_u(np, lm.lsh);
+      if (!done) {
+        if (lm.s == 0) nhiter += np;
+        float h1;
+        if (newton_step(I.h, ns, nc, dn, lo, hi, g, a.ph, iter == a.ph.max_iter - 1, h1, flag))
+          dens_set_h(I, h1, a.ph.kg, Lmax);
+        else
+          done = true;
+      }
+      if (!__any_sync(kFull, !done)) break;
+    }
+    flush(op, I, w, (lm.live && !retry) ? cnt : 0);  // full sums at the final h
+  } else {
+    scan_item(op, I, g, a.cell_start, a.pos, it.cell, lm.lsh, lm.s, lm.live, w, ncand);
+  }
   lsum2(I.ns, I.nc, lm.lsh);
   lsum2(I.rs, I.rc, lm.lsh);
   I.dn = lsum(I.dn, lm.lsh);
@@ -178,54 +290,29 @@ __device__ __forceinline__ void dens_item(const DensArgs& a, const DensOp& op, c
   I.count = lsum_u(I.count, lm.lsh);
   bool again = false;
   if (lm.live && lm.s == 0) {
-    ninter += I.count;
-    // convergence test in FP64 without a division: |n h^3 - eta^3| <= h_tol eta^3
-    const double hd = (double)I.h;
-    const double h3 = hd * hd * hd;
-    const double G = fma((double)I.ns, h3, fma((double)I.nc, h3, -a.ph.eta3));
-    bool conv = fabs(G) <= a.ph.h_tol * a.ph.eta3;
-    int flag = 0;
-    if (!conv && !last) {
-      // Newton step on F(h) = n - (eta/h)^3, F' = dn/dh + 3 eta^3 / h^4 (FP32)
-      const float h = I.h;
-      const float2 br = a.bracket[k];
-      float lo = br.x, hi = br.y;
-      if (G < 0.0) lo = fmaxf(lo, h);
-      else hi = fminf(hi, h);
-      if (G < 0.0 && h >= g.hcap) {
-        flag = g.hcap_from_cells ? SWIFT_GPU_ERR_H_EXCEEDS_CELL : SWIFT_GPU_ERR_H_NOT_CONVERGED;
-      } else {
-        const float ih = 1.0f / h;
-        const float target = (float)a.ph.eta3 * ih * ih * ih;
-        const float F = (I.ns + I.nc) - target;
-        const float Fp = fmaf(-I.dn, ih, 3.0f * target * ih);
-        float hn = Fp > 0.0f ? h - F / Fp : __int_as_float(0x7fc00000);
-        if (hn == hn) hn = fminf(fmaxf(hn, 0.5f * h), 2.0f * h);
-        if (!(hn == hn) || !(hn > lo) || !(hn < hi)) {
-          if (isfinite(hi) && lo > 0.0f) hn = 0.5f * (lo + hi);
-          else if (!isfinite(hi)) hn = 2.0f * h;
-          else hn = 0.5f * h;
-        }
-        hn = fminf(hn, g.hcap);
-        if (hn == h) {
-          conv = true;  // the float h cannot move any more
-        } else {
+    if (retry) {
+      again = true;
+    } else {
+      ninter += I.count;
+      if (!list_mode) {
+        float2 br = a.bracket[k];
+        step_again = newton_step(I.h, I.ns, I.nc, I.dn, br.x, br.y, g, a.ph, last, hn, flag);
+        if (step_again) {
           a.h[k] = hn;
-          a.bracket[k] = make_float2(lo, hi);
+          a.bracket[k] = br;
           again = true;
         }
       }
-    } else if (!conv) {
-      flag = SWIFT_GPU_ERR_H_NOT_CONVERGED;
-    }
-    if (!again) {
-      const float rho = I.rs + I.rc;
-      const float invh = 1.0f / I.h;
-      a.rho4[k] = make_float4(rho, -I.dr * invh, I.ns + I.nc, -I.dn * invh);
-      const float ir = 1.0f / rho;
-      a.cd[k] = make_float4(I.cx * ir, I.cy * ir, I.cz * ir, I.div * ir);
-      a.ngb[k] = I.count;
-      if (flag) set_error(a.st, flag);
+      if (!again) {
+        a.h[k] = I.h;
+        const float rho = I.rs + I.rc;
+        const float invh = 1.0f / I.h;
+        a.rho4[k] = make_float4(rho, -I.dr * invh, I.ns + I.nc, -I.dn * invh);
+        const float ir = 1.0f / rho;
+        a.cd[k] = make_float4(I.cx * ir, I.cy * ir, I.cz * ir, I.div * ir);
+        a.ngb[k] = I.count;
+        if (flag) set_error(a.st, flag);
+      }
     }
   }
   const unsigned am = __ballot_sync(kFull, again);
@@ -306,7 +393,7 @@ __global__ void __launch_bounds__(kLoopThreads, 5) k_density(DensArgs a) {
   op.L[0] = g.L[0]; op.L[1] = g.L[1]; op.L[2] = g.L[2];
   op.kg = a.ph.kg;
   op.compensated = a.ph.compensated;
-  unsigned ninter = 0, ncand = 0;
+  unsigned ninter = 0, nhiter = 0, ncand = 0;
   const int max_pass = a.single_pass ? 1 : a.ph.max_iter;
   int pass = 0;
   for (; pass < max_pass; ++pass) {
@@ -322,7 +409,8 @@ __global__ void __launch_bounds__(kLoopThreads, 5) k_density(DensArgs a) {
       const int t = take_ticket(&a.ctr[ctr_index(pass, 2)]);
       if (t >= n_items) break;
       const Item it = items[t];
-      dens_item(a, op, g, w, it, plist, last, items_next, plist_next, ctr_next, Lmax, ninter, ncand);
+      dens_item(a, op, g, w, it, plist, pass == 0 && !a.single_pass, last, items_next, plist_next, ctr_next,
+                Lmax, ninter, nhiter, ncand);
     }
     if (!grid_barrier(&a.barrier[0], &a.barrier[1], a.st, kBarrierNs)) return;
   }
@@ -339,9 +427,11 @@ __global__ void __launch_bounds__(kLoopThreads, 5) k_density(DensArgs a) {
     }
   }
   ninter = warp_sum(ninter);
+  nhiter = warp_sum(nhiter);
   ncand = warp_sum(ncand);
   if (lane == 0) {
     atomicAdd(&a.stats[kStatInterDens], (unsigned long long)ninter);
+    atomicAdd(&a.stats[kStatInterHiter], (unsigned long long)nhiter);
     atomicAdd(&a.stats[kStatCandDens], (unsigned long long)ncand);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {

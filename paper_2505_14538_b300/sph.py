@@ -170,7 +170,7 @@ class Context:
         _check(self.lib.swift_gpu_get_info(self.handle, ctypes.byref(i)), "swift_gpu_get_info")
         return dict(n=i.n, nc=tuple(i.nc), cell_width=tuple(i.cell_width), h_cap=i.h_cap, n_cells=i.n_cells,
                     n_items=i.n_items, density_passes=i.density_passes, interactions=tuple(i.interactions),
-                    candidates=tuple(i.candidates), launches=i.launches)
+                    candidates=tuple(i.candidates), launches=i.launches, h_iteration_pairs=i.h_iteration_pairs)
 
     def cells(self, stream=None):
         n = self.n
