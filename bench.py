@@ -133,14 +133,22 @@ def workload():
 
 
 def flops_per_interaction():
+    """Algorithmic flops of one pair: density (full sums), gradient, force, h-iteration step."""
     with open(os.path.join(ROOT, "profiles", "flops_per_interaction.json")) as f:
         fl = json.load(f)
-    return [fl["density"]["mean"], fl["gradient"]["mean"], fl["force"]["mean"]]
+    return [fl["density"]["mean"], fl["gradient"]["mean"], fl["force"]["mean"], fl["h_iteration"]["mean"]]
+
+
+def step_interactions(i0, i1):
+    """Pair interactions between two info snapshots: [density incl. h-iteration steps, gradient, force]."""
+    d = [i1["interactions"][j] - i0["interactions"][j] for j in range(3)]
+    d[0] += i1["h_iteration_pairs"] - i0["h_iteration_pairs"]
+    return d
 
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for name in ("loops.cu", "common.cuh"):
+    for name in ("loops.cu", "engine.cuh", "common.cuh"):
         with open(os.path.join(ROOT, "paper_2505_14538_b300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -245,7 +253,8 @@ def run_ours(args, rank, world, pg):
     seg = [[ev[k][j].elapsed_time(ev[k][j + 1]) for j in range(4)] for k in range(K)]
     step_ms = [sum(s) for s in seg]
     loop_ms = [sum(s[j] for s in seg) / K for j in range(4)]  # build, density, gradient, force
-    inter = [(i1["interactions"][j] - i0["interactions"][j]) / K for j in range(3)]
+    inter = [x / K for x in step_interactions(i0, i1)]
+    hiter = (i1["h_iteration_pairs"] - i0["h_iteration_pairs"]) / K
     cand = [(i1["candidates"][j] - i0["candidates"][j]) / K for j in range(3)]
     launches = i1["launches"] - i0["launches"]
     inter_step = sum(inter)
@@ -263,18 +272,22 @@ def run_ours(args, rank, world, pg):
     peaks = measured_peaks()
     max_mhz = clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2032.0
     peak_max = sms * 128 * 2 * max_mhz * 1e6 / 1e12
-    achieved = inter[dom] * fpi[dom] / (loop_ms[dom + 1] * 1e-3) / 1e12
+    # density: full-sum pairs at the density count, h-iteration pairs at the Eqs. 5-6 count
+    flops = [(inter[0] - hiter) * fpi[0] + hiter * fpi[3], inter[1] * fpi[1], inter[2] * fpi[2]]
+    achieved = flops[dom] / (loop_ms[dom + 1] * 1e-3) / 1e12
     traffic = measured_traffic(names[dom])
     roof = {"bound": "alu", "kernel": names[dom], "achieved": achieved, "peak": peak_max, "unit": "TFLOP/s",
             "frac": achieved / peak_max, "traffic": traffic,
             "peak_note": f"FP32 FMA lanes: {sms} SMs x 128 x 2 flop x {max_mhz:.0f} MHz (max SM clock)",
             "frac_at_measured_clock": (achieved / (sms * 256 * clocks["sm_mhz"] * 1e6 / 1e12)
                                        if clocks.get("sm_mhz") else None),
-            "flops_per_interaction": fpi[dom],
+            "flops_per_launch": flops[dom],
+            "flops_per_interaction": {"density": fpi[0], "h_iteration": fpi[3], "gradient": fpi[1], "force": fpi[2]},
             "per_loop": {names[j]: {"ms": loop_ms[j + 1], "interactions": inter[j], "candidates": cand[j],
-                                    "tflops": inter[j] * fpi[j] / (loop_ms[j + 1] * 1e-3) / 1e12,
-                                    "frac": inter[j] * fpi[j] / (loop_ms[j + 1] * 1e-3) / 1e12 / peak_max}
+                                    "tflops": flops[j] / (loop_ms[j + 1] * 1e-3) / 1e12,
+                                    "frac": flops[j] / (loop_ms[j + 1] * 1e-3) / 1e12 / peak_max}
                          for j in range(3)},
+            "h_iteration_pairs": hiter,
             "build_cells_ms": loop_ms[0]}
 
     res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
@@ -330,7 +343,7 @@ def run_e2e(ctx, pos_h_host, vel_m_host, u_host, min_width, n, dev, pg, world, K
     i1 = ctx.info()
     t = e0.elapsed_time(e1) / 1e3
     tmax = reduce_max(pg, t, dev)
-    inter = sum(i1["interactions"][j] - i0["interactions"][j] for j in range(3))
+    inter = sum(step_interactions(i0, i1))
     return {"value": world * inter / tmax, "unit": UNIT, "h2d_bytes_per_step": n * (16 + 16 + 4),
             "d2h_bytes_per_step": n * (16 + 4), "steps": K, "ms_per_step": tmax / K * 1e3}
 
@@ -362,7 +375,7 @@ def run_plain(d, n, dev, min_width):
     torch.cuda.synchronize()
     i1 = ctx.info()
     t = e0.elapsed_time(e1) / 1e3
-    inter = sum(i1["interactions"][j] - i0["interactions"][j] for j in range(3))
+    inter = sum(step_interactions(i0, i1))
     return {"value": inter / t, "unit": UNIT, "ms_per_step": t * 1e3, "launches_per_step": i1["launches"] - i0["launches"]}
 
 

@@ -103,7 +103,7 @@ int swift_gpu_create(swift_gpu_ctx** out, const swift_gpu_params* p, int64_t n_m
     return SWIFT_GPU_ERR_CUDA;
   }
   c->tuning.threads_per_block = 256;
-  c->tuning.max_lanes_per_particle = 4;
+  c->tuning.max_lanes_per_particle = 8;
   c->tuning.blocks_per_sm = 0;
   int nc_cap = (int)floor(cbrt(2.0 * (double)n_max));
   if (nc_cap < 3) nc_cap = 3;

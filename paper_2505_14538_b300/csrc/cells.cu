@@ -177,14 +177,17 @@ __global__ void k_cell_ids(const float4* __restrict__ pos_h, int n, const Grid* 
   const double Lx = g->L[0], Ly = g->L[1], Lz = g->L[2];
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     float4 p = pos_h[i];
-    // wrap into [0, L) and floor(x nc / L), each FP64 operation rounded once
+    // wrap into [0, L) and floor(x nc / L), each FP64 operation rounded once.
+    // A float x in [0, L) has floor(x / L) = 0, and x * nc is exact, so the
+    // divisions (slow in FP64) are skipped only where they cannot change the result.
     double x = p.x, y = p.y, z = p.z;
-    x = __dsub_rn(x, __dmul_rn(Lx, floor(__ddiv_rn(x, Lx))));
-    y = __dsub_rn(y, __dmul_rn(Ly, floor(__ddiv_rn(y, Ly))));
-    z = __dsub_rn(z, __dmul_rn(Lz, floor(__ddiv_rn(z, Lz))));
-    int cx = (int)floor(__ddiv_rn(__dmul_rn(x, (double)nx), Lx));
-    int cy = (int)floor(__ddiv_rn(__dmul_rn(y, (double)ny), Ly));
-    int cz = (int)floor(__ddiv_rn(__dmul_rn(z, (double)nz), Lz));
+    if (!(x >= 0.0 && x < Lx)) x = __dsub_rn(x, __dmul_rn(Lx, floor(__ddiv_rn(x, Lx))));
+    if (!(y >= 0.0 && y < Ly)) y = __dsub_rn(y, __dmul_rn(Ly, floor(__ddiv_rn(y, Ly))));
+    if (!(z >= 0.0 && z < Lz)) z = __dsub_rn(z, __dmul_rn(Lz, floor(__ddiv_rn(z, Lz))));
+    const double tx = __dmul_rn(x, (double)nx), ty = __dmul_rn(y, (double)ny), tz = __dmul_rn(z, (double)nz);
+    int cx = (int)floor(Lx == 1.0 ? tx : __ddiv_rn(tx, Lx));
+    int cy = (int)floor(Ly == 1.0 ? ty : __ddiv_rn(ty, Ly));
+    int cz = (int)floor(Lz == 1.0 ? tz : __ddiv_rn(tz, Lz));
     cx = min(max(cx, 0), nx - 1);
     cy = min(max(cy, 0), ny - 1);
     cz = min(max(cz, 0), nz - 1);

@@ -774,12 +774,14 @@ __global__ void __launch_bounds__(kLoopThreads, 4) k_force(LoopArgs a) {
   }
 }
 
+// One warp per quantity; lane l sums blocks l, l+32, ... and the warp then
+// combines the lanes in a fixed order, so the result does not depend on timing.
 __global__ void k_reduce_partials(const double* __restrict__ part, int nblocks, double* __restrict__ out) {
-  if (threadIdx.x < 8) {
-    double x = 0.0;
-    for (int b = 0; b < nblocks; ++b) x += part[b * 8 + threadIdx.x];
-    out[threadIdx.x] = x;
-  }
+  const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double x = 0.0;
+  for (int b = lane; b < nblocks; b += 32) x += part[b * 8 + q];
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  if (lane == 0) out[q] = x;
 }
 
 // =================================================================== hosts
@@ -900,7 +902,7 @@ int force_impl(Ctx* c, float4* out, float* dhdt, double* reductions, cudaStream_
   k_force<<<nblk, kLoopThreads, kLoopSmemBytes, s>>>(a);
   c->launches += 2;
   if (reductions) {
-    k_reduce_partials<<<1, 32, 0, s>>>(c->d_red_partial, nblk, reductions);
+    k_reduce_partials<<<1, 256, 0, s>>>(c->d_red_partial, nblk, reductions);
     c->launches++;
   }
   return cudaGetLastError() == cudaSuccess ? SWIFT_GPU_OK : SWIFT_GPU_ERR_CUDA;
