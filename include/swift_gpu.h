@@ -202,6 +202,36 @@ int swift_gpu_set_tuning(swift_gpu_ctx* ctx, const swift_gpu_tuning* t);
  * to have run once. Blocking; leaves outputs of the last calls unchanged. */
 int swift_gpu_autotune(swift_gpu_ctx* ctx, int loop, void* stream);
 
+/* Largest particle count swift_gpu_density_static accepts. */
+#define SWIFT_GPU_STATIC_MAX_PARTICLES 32768
+
+/* The density call (cell build, then the density loop with the Newton
+ * iteration on h, every particle active) with no context and no allocation
+ * of any kind. The paper has no counterpart to this entry point. It is for
+ * callers that cannot allocate GPU memory themselves: code whose host
+ * framework owns every device allocation and forbids direct cudaMalloc, or a
+ * plug-in that may only work in buffers it is handed.
+ * Work memory: one fixed array of 5.4 MB (5.2 MiB) built into the library, which
+ * every GPU that loads the library holds until the process exits. It fits
+ * n <= SWIFT_GPU_STATIC_MAX_PARTICLES; a larger n returns
+ * SWIFT_GPU_ERR_CAPACITY before any work is queued.
+ * Arguments: *p the physics parameters (host); pos_h, vel_m, h_out, rho4,
+ * curl_div, ngb_count as in swift_gpu_build_cells and swift_gpu_density
+ * (device, caller order, ngb_count may be NULL); min_cell_width as in
+ * swift_gpu_build_cells; status_out NULL or a device array of 2 int64 that
+ * receives the device status code and its detail (what swift_gpu_sync_status
+ * reports for a context). Asynchronous on `stream`.
+ * The first call on a device looks up the array's device address, a one-time
+ * set-up per device: make that first call before any stream capture.
+ * Every call shares the one array and finds the previous call's contents in
+ * it (the call resets what must start at zero). Calls that can overlap on the
+ * GPU (other streams, other host threads) race and corrupt each other's
+ * results: order them on one stream. Host-side errors as for
+ * swift_gpu_density, plus ERR_CAPACITY. */
+int swift_gpu_density_static(const swift_gpu_params* p, const float* pos_h, const float* vel_m, int64_t n,
+                             float min_cell_width, float* h_out, float* rho4, float* curl_div, uint32_t* ngb_count,
+                             int64_t* status_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

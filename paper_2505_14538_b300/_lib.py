@@ -32,7 +32,9 @@ FLAG_NO_COMPENSATION = 4
 EXPORTED = ("swift_gpu_default_params", "swift_gpu_create", "swift_gpu_destroy", "swift_gpu_set_params",
             "swift_gpu_build_cells", "swift_gpu_density", "swift_gpu_gradient", "swift_gpu_force",
             "swift_gpu_force_backward", "swift_gpu_sync_status", "swift_gpu_get_info", "swift_gpu_get_cells",
-            "swift_gpu_get_tuning", "swift_gpu_set_tuning", "swift_gpu_autotune")
+            "swift_gpu_get_tuning", "swift_gpu_set_tuning", "swift_gpu_autotune", "swift_gpu_density_static")
+
+STATIC_MAX_PARTICLES = 32768
 
 
 class Params(ctypes.Structure):
@@ -96,6 +98,8 @@ _SIGS = {
     "swift_gpu_get_tuning": (_I, [_VP, ctypes.POINTER(Tuning)]),
     "swift_gpu_set_tuning": (_I, [_VP, ctypes.POINTER(Tuning)]),
     "swift_gpu_autotune": (_I, [_VP, _I, _VP]),
+    "swift_gpu_density_static": (_I, [ctypes.POINTER(Params), _VP, _VP, _I64, ctypes.c_float, _VP, _VP, _VP, _VP,
+                                      _VP, _VP]),
 }
 
 _lib = None

@@ -23,7 +23,7 @@ constexpr int kMaxPasses = 64;
 
 static bool aligned(const void* p, size_t a) { return p && ((uintptr_t)p % a) == 0; }
 
-static int phys_from(const swift_gpu_params* p, Phys* ph) {
+int phys_from(const swift_gpu_params* p, Phys* ph) {
   for (int a = 0; a < 3; ++a)
     if (!(p->box[a] > 0.0f) || !isfinite(p->box[a])) return SWIFT_GPU_ERR_ARG;
   if (!(p->kernel_gamma > 0.0f) || !(p->eta > 0.0f) || !(p->gamma_eos > 1.0f)) return SWIFT_GPU_ERR_ARG;

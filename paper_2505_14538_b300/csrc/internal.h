@@ -78,6 +78,7 @@ struct Ctx {
 };
 
 Ctx* from(swift_gpu_ctx* c);
+int phys_from(const swift_gpu_params* p, Phys* ph);
 
 int scan_tiles_needed(int64_t m);
 void exclusive_scan(Ctx* c, const unsigned* in, unsigned* out, int m, unsigned* tile_tmp, cudaStream_t s);
