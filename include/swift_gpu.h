@@ -173,10 +173,15 @@ int swift_gpu_force(swift_gpu_ctx* ctx, const float* u, const float* alpha_v_i, 
  * grad_accel_dudt[n] = float4 (dL/da_x, dL/da_y, dL/da_z, dL/d(du/dt)) for a
  * scalar loss L of the outputs of the last swift_gpu_force call, write
  * grad_x[n] (float4, w unused), grad_v[n] (float4, w unused), grad_u[n].
- * h_mode 0: h held fixed; 1: h = h(x) through the converged h equation
- * (implicit-function term). Recomputes the density sums instead of storing
- * pair lists. Requires force (ERR_ORDER otherwise); all particles must have
- * been active. */
+ * h_mode 0: h held at the values of the last density call (the only mode
+ * built; 1, h = h(x) through the converged h equation, returns ERR_ARG).
+ * Two gather passes over the same neighbour scan as the forward loops: the
+ * force pair terms are reversed in both orientations of every pair, the
+ * ghost step is reversed per particle, and the adjoints of each particle's
+ * density sums are carried back through both particles' sums. No pair list is
+ * stored; the per-particle sums of the forward calls are reused. grad_x and
+ * grad_v are float4 with w = 0. Requires force (ERR_ORDER otherwise); every
+ * particle must have been active (ERR_ARG otherwise). */
 int swift_gpu_force_backward(swift_gpu_ctx* ctx, const float* grad_accel_dudt, float* grad_x, float* grad_v,
                              float* grad_u, int h_mode, void* stream);
 
