@@ -1,0 +1,127 @@
+"""PyTorch FP64 reference of the fixed-h density + ghost + force pipeline, for gradients.
+
+TEST INFRASTRUCTURE: only ``tests/`` may import this module. It restates the
+equations of the C++ oracle (``sph_oracle.cpp``; the paper's Sec. 2.1,
+Eqs. 2-11, 16-20, 22 with the readings listed there) with plain torch CPU ops
+over an explicit list of interacting pairs, so that autograd gives the exact
+FP64 gradient of a loss of the outputs with respect to positions, velocities
+and internal energies at fixed smoothing lengths. The pair list is found by
+brute force over all pairs (O(N^2)), in FP64, with the oracle's predicate.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import torch
+
+KERNEL_GAMMA = float(np.float32(1.825742))
+
+
+def pair_list(x, h, box, kernel_gamma=KERNEL_GAMMA, block=512):
+    """Ordered pairs (i, j), i != j, with r_ij < max(H_i, H_j) (periodic minimum image)."""
+    x = np.asarray(x, np.float64)
+    h = np.asarray(h, np.float64)
+    L = np.asarray(box, np.float64)
+    H = kernel_gamma * h
+    n = len(x)
+    I, J = [], []
+    for s in range(0, n, block):
+        d = x[s:s + block, None, :] - x[None, :, :]
+        d = d - L * np.round(d / L)
+        r2 = (d[..., 0] * d[..., 0] + d[..., 1] * d[..., 1]) + d[..., 2] * d[..., 2]
+        Hi = H[s:s + block, None]
+        m = (r2 < Hi * Hi) | (r2 < H[None, :] ** 2)
+        m[np.arange(m.shape[0]), np.arange(s, s + m.shape[0])] = False
+        ii, jj = np.nonzero(m)
+        I.append(ii + s)
+        J.append(jj)
+    return np.concatenate(I), np.concatenate(J)
+
+
+def _w(q):
+    s = torch.clamp(1.0 - q, min=0.0)
+    return torch.where(q < 0.5, 1.0 - 6.0 * q * q + 6.0 * q * q * q, 2.0 * s * s * s)
+
+
+def _dw(q):
+    s = torch.clamp(1.0 - q, min=0.0)
+    return torch.where(q < 0.5, -12.0 * q + 18.0 * q * q, -6.0 * s * s)
+
+
+def _safe_sqrt(x):
+    return torch.where(x > 0, torch.sqrt(torch.clamp(x, min=1e-300)), torch.zeros_like(x))
+
+
+def forward(x, v, u, m, h, pairs, box=(1.0, 1.0, 1.0), gamma=5.0 / 3.0, alpha_v=1.0, beta=3.0, alpha_c=1.0,
+            kernel_gamma=KERNEL_GAMMA):
+    """accel (n, 3) and du/dt (n,) at fixed h; x, v, u are torch float64 (may require grad)."""
+    n = x.shape[0]
+    i = torch.as_tensor(pairs[0], dtype=torch.long)
+    j = torch.as_tensor(pairs[1], dtype=torch.long)
+    m = torch.as_tensor(m, dtype=torch.float64)
+    h = torch.as_tensor(h, dtype=torch.float64)
+    L = torch.as_tensor(box, dtype=torch.float64)
+    H = kernel_gamma * h
+    d = x[i] - x[j]
+    d = d - L * torch.round((d / L).detach())
+    r = torch.sqrt((d * d).sum(1))
+    e = d / r[:, None]
+    Hi, Hj = H[i], H[j]
+    qi, qj = r / Hi, r / Hj
+    c3 = (8.0 / math.pi) / H ** 3
+    Wi = c3[i] * _w(qi)
+    dWi = c3[i] / Hi * _dw(qi)
+    dWj = c3[j] / Hj * _dw(qj)
+    in_i = (r < Hi).detach().to(torch.float64)  # pairs in i's density sums
+    # density sums (self term: W(0) = c3, r dW/dr = 0)
+    rho = m * c3 + torch.zeros(n, dtype=torch.float64).index_add(0, i, in_i * m[j] * Wi)
+    D = 3.0 * m * c3 + torch.zeros(n, dtype=torch.float64).index_add(0, i, in_i * m[j] * (3.0 * Wi + r * dWi))
+    g = in_i * m[j] * dWi / r
+    dv = v[j] - v[i]
+    S = torch.zeros(n, dtype=torch.float64).index_add(0, i, g * (dv * d).sum(1))
+    C = -torch.zeros(n, 3, dtype=torch.float64).index_add(0, i, g[:, None] * torch.cross(dv, d, dim=1))
+    div = S / rho
+    curl = C / rho[:, None]
+    # ghost step
+    f = 1.0 / (1.0 - D / (3.0 * rho))
+    P = (gamma - 1.0) * rho * u
+    c = torch.sqrt(gamma * (gamma - 1.0) * u)
+    A = f * P / rho ** 2
+    ad = torch.abs(div)
+    acurl = _safe_sqrt((curl * curl).sum(1))
+    B = torch.where(ad > 0, ad / (ad + acurl + 1e-4 * c / h), torch.zeros_like(ad))
+    # force pairs
+    vij = v[i] - v[j]
+    vr = (vij * e).sum(1)
+    fsum = f[i] * dWi + f[j] * dWj
+    ps = m[j] * (A[i] * dWi + A[j] * dWj)
+    du1 = m[j] * A[i] * dWi * vr
+    mu = torch.clamp(vr, max=0.0)
+    vsig = c[i] + c[j] - beta * mu
+    al = 0.25 * (2.0 * alpha_v) * (B[i] + B[j])
+    rs = rho[i] + rho[j]
+    nu = -al * mu * vsig / rs
+    vs = 0.5 * m[j] * nu * fsum
+    du2 = 0.5 * vs * vr
+    Ps = P[i] + P[j]
+    ac = (P[i] * alpha_c + P[j] * alpha_c) / Ps
+    vc = torch.abs(vr) + _safe_sqrt(2.0 * torch.abs(P[i] - P[j]) / rs)
+    du3 = ac * vc * m[j] * (u[i] - u[j]) * fsum / rs
+    as_ = ps + vs
+    accel = -torch.zeros(n, 3, dtype=torch.float64).index_add(0, i, as_[:, None] * e)
+    dudt = torch.zeros(n, dtype=torch.float64).index_add(0, i, du1 + du2 + du3)
+    return accel, dudt, dict(rho=rho, D=D, div=div, curl=curl, f=f, P=P, c=c, B=B)
+
+
+def loss_and_grad(x, v, u, m, h, w, cw, box=(1.0, 1.0, 1.0), pairs=None, **kw):
+    """L = sum w_i . a_i + c_i du_i/dt and (dL/dx, dL/dv, dL/du) at fixed h, all FP64 numpy."""
+    x = torch.tensor(np.asarray(x, np.float64), requires_grad=True)
+    v = torch.tensor(np.asarray(v, np.float64), requires_grad=True)
+    u = torch.tensor(np.asarray(u, np.float64), requires_grad=True)
+    if pairs is None:
+        pairs = pair_list(x.detach().numpy(), h, box)
+    a, du, _ = forward(x, v, u, m, h, pairs, box, **kw)
+    Lv = (torch.as_tensor(np.asarray(w, np.float64)) * a).sum() + (torch.as_tensor(np.asarray(cw, np.float64)) * du).sum()
+    gx, gv, gu = torch.autograd.grad(Lv, (x, v, u))
+    return float(Lv.detach()), gx.numpy(), gv.numpy(), gu.numpy(), a.detach().numpy(), du.detach().numpy()

@@ -224,3 +224,39 @@ class Context:
         out["vsig_lapu"] = g
         out.update(f)
         return out
+
+
+class SphForces(torch.autograd.Function):
+    """(a, du/dt) = F(x, v, u) at fixed h through the library, differentiable in x, v, u.
+
+    ``forward(x, v, u, m, h, lib_ctx)``: x, v (n, 3), u, m, h (n,) CUDA float32;
+    ``lib_ctx`` a :class:`Context` created with ``flags=FLAG_NO_H_ITER`` so the
+    given h is used as is. Runs build_cells, density, force. The backward pass
+    calls swift_gpu_force_backward (h_mode 0), which reads the context's state
+    of this forward call: run backward before the context is used again.
+    """
+
+    @staticmethod
+    def forward(ctx, x, v, u, m, h, lib_ctx):
+        from . import _lib
+        if not (lib_ctx.params.flags & _lib.FLAG_NO_H_ITER):
+            raise ValueError("SphForces needs a context created with flags=FLAG_NO_H_ITER (h held fixed)")
+        pos_h = torch.cat([x, h[:, None]], 1).float().contiguous()
+        vel_m = torch.cat([v, m[:, None]], 1).float().contiguous()
+        uu = u.float().contiguous()
+        lib_ctx.build_cells(pos_h)
+        lib_ctx.density(pos_h, vel_m)
+        out = lib_ctx.force(uu, want_dh=False, want_reductions=False)
+        ctx.lib_ctx = lib_ctx
+        ad = out["accel_dudt"]
+        return ad[:, :3].clone(), ad[:, 3].clone()
+
+    @staticmethod
+    def backward(ctx, grad_a, grad_du):
+        n = ctx.lib_ctx.n
+        dev = grad_a.device if grad_a is not None else grad_du.device
+        ga = grad_a if grad_a is not None else torch.zeros(n, 3, dtype=torch.float32, device=dev)
+        gd = grad_du if grad_du is not None else torch.zeros(n, dtype=torch.float32, device=dev)
+        g4 = torch.cat([ga.float(), gd.float()[:, None]], 1).contiguous()
+        gx, gv, gu = ctx.lib_ctx.force_backward(g4, h_mode=0)
+        return gx[:, :3], gv[:, :3], gu, None, None, None
