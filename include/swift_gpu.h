@@ -49,7 +49,9 @@ extern "C" {
 #define SWIFT_GPU_ERR_CAPACITY (-8)          /* n exceeds the context's n_max */
 
 /* swift_gpu_params.flags */
-#define SWIFT_GPU_PLAIN 1         /* one kernel launch per self/pair cell task (the paper's task granularity) */
+#define SWIFT_GPU_PLAIN 1         /* one kernel launch per self/pair cell task (the paper's task granularity,
+                                     Sec. 2.2.2), h iteration driven from the host pass by pass; the baseline
+                                     for the persistent path (no autotune, no force_backward) */
 #define SWIFT_GPU_NO_H_ITER 2     /* density at the given h: no Newton iteration */
 #define SWIFT_GPU_NO_COMPENSATION 4 /* plain FP32 sums instead of two-sum compensated rho, a, du/dt */
 

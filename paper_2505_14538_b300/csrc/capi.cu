@@ -29,7 +29,6 @@ int phys_from(const swift_gpu_params* p, Phys* ph) {
   if (!(p->kernel_gamma > 0.0f) || !(p->eta > 0.0f) || !(p->gamma_eos > 1.0f)) return SWIFT_GPU_ERR_ARG;
   if (p->max_iter < 1 || !(p->h_tol >= 0.0f) || p->h_max < 0.0f || p->cell_margin < 0.0f)
     return SWIFT_GPU_ERR_ARG;
-  if (p->flags & SWIFT_GPU_PLAIN) return SWIFT_GPU_ERR_ARG;  // the per-task launch path is not built yet
   for (int a = 0; a < 3; ++a) ph->L[a] = p->box[a];
   ph->kg = p->kernel_gamma;
   ph->gamma_eos = p->gamma_eos;
@@ -55,8 +54,7 @@ static void free_all(Ctx* c) {
                   c->d_hist, c->d_scan_tmp, c->d_cell_start, c->d_pos, c->d_vel, c->d_rho4, c->d_cd, c->d_h,
                   c->d_bracket, c->d_ngb, c->d_ga, c->d_gb, c->d_act, c->d_items0, c->d_plist0, c->d_items[0],
                   c->d_items[1], c->d_plist[0], c->d_plist[1], c->d_counters, c->d_stats, c->d_red_partial,
-                  c->d_scratch4[0], c->d_scratch4[1], c->d_scratch4[2], c->d_scratch4[3], c->d_scratch1[0],
-                  c->d_scratch1[1]};
+                  c->d_scratch4[0], c->d_scratch1[0], c->d_scratch1[1], c->d_plain_act};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_status) cudaFreeHost(c->h_status);
@@ -128,10 +126,12 @@ int swift_gpu_create(swift_gpu_ctx** out, const swift_gpu_params* p, int64_t n_m
             dalloc(&c->d_items[0], n) && dalloc(&c->d_items[1], n) && dalloc(&c->d_plist[0], n) &&
             dalloc(&c->d_plist[1], n) && dalloc(&c->d_counters, kCtrPerPass * (kMaxPasses + 2) + 2) &&
             dalloc(&c->d_stats, kStatCount) && dalloc(&c->d_red_partial, 8 * (size_t)c->red_blocks) &&
-            dalloc(&c->d_scratch4[0], n) && dalloc(&c->d_scratch4[1], n) && dalloc(&c->d_scratch4[2], n) &&
-            dalloc(&c->d_scratch4[3], n) && dalloc(&c->d_scratch1[0], n) && dalloc(&c->d_scratch1[1], n) &&
+            dalloc(&c->d_scratch4[0], 4 * n) && dalloc(&c->d_scratch1[0], n) && dalloc(&c->d_scratch1[1], n) &&
+            dalloc(&c->d_plain_act, n) &&
             cudaMallocHost((void**)&c->h_status, sizeof(Status)) == cudaSuccess &&
             cudaMallocHost((void**)&c->h_stats, sizeof(unsigned long long) * kStatCount) == cudaSuccess;
+  if (ok)
+    for (int q = 1; q < 4; ++q) c->d_scratch4[q] = c->d_scratch4[0] + q * n;
   if (!ok) {
     cudaGetLastError();
     free_all(c);
@@ -190,9 +190,10 @@ int swift_gpu_density(swift_gpu_ctx* h, const float* pos_h_in, const float* vel_
     return SWIFT_GPU_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   c->last_stream = s;
-  int rc = density_impl(c, reinterpret_cast<const float4*>(pos_h_in), reinterpret_cast<const float4*>(vel_m),
-                        active, h_out, reinterpret_cast<float4*>(rho4), reinterpret_cast<float4*>(curl_div),
-                        ngb_count, s);
+  int (*impl)(Ctx*, const float4*, const float4*, const uint8_t*, float*, float4*, float4*, uint32_t*,
+              cudaStream_t) = (c->params.flags & SWIFT_GPU_PLAIN) ? plain_density_impl : density_impl;
+  int rc = impl(c, reinterpret_cast<const float4*>(pos_h_in), reinterpret_cast<const float4*>(vel_m), active, h_out,
+                reinterpret_cast<float4*>(rho4), reinterpret_cast<float4*>(curl_div), ngb_count, s);
   c->state = rc == SWIFT_GPU_OK ? 3 : 1;
   c->last_pos_in = reinterpret_cast<const float4*>(pos_h_in);
   c->last_vel_in = reinterpret_cast<const float4*>(vel_m);
@@ -212,7 +213,9 @@ int swift_gpu_gradient(swift_gpu_ctx* h, const float* u, float* vsig_lapu, void*
   cudaStream_t s = (cudaStream_t)stream;
   c->last_stream = s;
   int rc = ghost_impl(c, u, nullptr, nullptr, s);
-  if (rc == SWIFT_GPU_OK) rc = gradient_impl(c, reinterpret_cast<float2*>(vsig_lapu), s);
+  if (rc == SWIFT_GPU_OK)
+    rc = (c->params.flags & SWIFT_GPU_PLAIN) ? plain_gradient_impl(c, reinterpret_cast<float2*>(vsig_lapu), s)
+                                             : gradient_impl(c, reinterpret_cast<float2*>(vsig_lapu), s);
   c->last_grad_out = reinterpret_cast<float2*>(vsig_lapu);
   if (rc == SWIFT_GPU_OK) c->state |= 4;
   return rc;
@@ -230,7 +233,10 @@ int swift_gpu_force(swift_gpu_ctx* h, const float* u, const float* alpha_v_i, co
   cudaStream_t s = (cudaStream_t)stream;
   c->last_stream = s;
   int rc = ghost_impl(c, u, alpha_v_i, alpha_c_i, s);
-  if (rc == SWIFT_GPU_OK) rc = force_impl(c, reinterpret_cast<float4*>(accel_dudt), dh_dt, reductions, s);
+  if (rc == SWIFT_GPU_OK)
+    rc = (c->params.flags & SWIFT_GPU_PLAIN)
+             ? plain_force_impl(c, reinterpret_cast<float4*>(accel_dudt), dh_dt, reductions, s)
+             : force_impl(c, reinterpret_cast<float4*>(accel_dudt), dh_dt, reductions, s);
   if (rc == SWIFT_GPU_OK) {
     c->state |= 8;
     c->last_u = u;
@@ -247,7 +253,7 @@ int swift_gpu_force_backward(swift_gpu_ctx* h, const float* grad_accel_dudt, flo
   Ctx* c = from(h);
   if (!c || (h_mode != 0 && h_mode != 1)) return SWIFT_GPU_ERR_ARG;
   if (!(c->state & 8)) return SWIFT_GPU_ERR_ORDER;
-  if (!c->all_active) return SWIFT_GPU_ERR_ARG;
+  if (!c->all_active || (c->params.flags & SWIFT_GPU_PLAIN)) return SWIFT_GPU_ERR_ARG;
   if (c->n > 0 && (!aligned(grad_accel_dudt, 16) || !aligned(grad_x, 16) || !aligned(grad_v, 16) ||
                    !aligned(grad_u, 4)))
     return SWIFT_GPU_ERR_ARG;
@@ -329,7 +335,7 @@ int swift_gpu_set_tuning(swift_gpu_ctx* h, const swift_gpu_tuning* t) {
 
 int swift_gpu_autotune(swift_gpu_ctx* h, int loop, void* stream) {
   Ctx* c = from(h);
-  if (!c || loop < 0 || loop > 2) return SWIFT_GPU_ERR_ARG;
+  if (!c || loop < 0 || loop > 2 || (c->params.flags & SWIFT_GPU_PLAIN)) return SWIFT_GPU_ERR_ARG;
   if (!(c->state & 8)) return SWIFT_GPU_ERR_ORDER;
   cudaStream_t s = (cudaStream_t)stream;
   c->last_stream = s;

@@ -67,7 +67,8 @@ struct Ctx {
   int* d_counters = nullptr;  // per pass: [item_count, plist_count, ticket] x (max passes + 1); + barrier
   unsigned long long* d_stats = nullptr;
   double* d_red_partial = nullptr;  // per block partial FP64 reductions
-  float4* d_scratch4[4] = {nullptr, nullptr, nullptr, nullptr};  // adjoint work arrays (sorted)
+  float4* d_scratch4[4] = {nullptr, nullptr, nullptr, nullptr};  // work arrays (sorted), one block of 4 n_max
+  uint8_t* d_plain_act = nullptr;  // active flags while the per-task path iterates
   float* d_scratch1[2] = {nullptr, nullptr};
   int red_blocks = 0;
   int max_passes = 0;
@@ -88,6 +89,11 @@ int density_impl(Ctx* c, const float4* pos_h_in, const float4* vel_m, const uint
 int ghost_impl(Ctx* c, const float* u, const float* alpha_v, const float* alpha_c, cudaStream_t s);
 int gradient_impl(Ctx* c, float2* vsig_lapu, cudaStream_t s);
 int force_impl(Ctx* c, float4* accel_dudt, float* dh_dt, double* reductions, cudaStream_t s);
+int plain_density_impl(Ctx* c, const float4* pos_h_in, const float4* vel_m, const uint8_t* active, float* h_out,
+                       float4* rho4, float4* curl_div, uint32_t* ngb, cudaStream_t s);
+int plain_gradient_impl(Ctx* c, float2* vsig_lapu, cudaStream_t s);
+int plain_force_impl(Ctx* c, float4* accel_dudt, float* dh_dt, double* reductions, cudaStream_t s);
+void reduce_partials(Ctx* c, int nblocks, double* out, cudaStream_t s);
 int cells_export_impl(Ctx* c, uint32_t* cell_id, uint32_t* perm, cudaStream_t s);
 int autotune_impl(Ctx* c, int loop, cudaStream_t s);
 int backward_impl(Ctx* c, const float4* grad_ad, float4* grad_x, float4* grad_v, float* grad_u, int h_mode,

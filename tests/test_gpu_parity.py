@@ -247,3 +247,14 @@ def test_argument_errors(sph):
     ctx.build_cells(nan)
     code, _ = ctx.sync_status()
     assert code == -1
+
+
+def test_plain_per_task_path(sph, O):
+    """SWIFT_GPU_PLAIN (one launch per self/pair task, host-driven h passes): same checks as the persistent path."""
+    d, vel, u = lattice_state(12, seed=9)
+    g = run_gpu(sph, d, vel, u, h_tol=1e-6, flags=1)
+    assert g["status"][0] == 0, g["status"]
+    check_against_oracle(O, d, vel, u, g, g["ctx"])
+    p = run_gpu(sph, d, vel, u, h_tol=1e-6)
+    assert np.max(np.abs(g["h"] / p["h"] - 1)) < 1e-6
+    assert np.array_equal(g["ngb"], p["ngb"])
