@@ -260,3 +260,50 @@ class SphForces(torch.autograd.Function):
         g4 = torch.cat([ga.float(), gd.float()[:, None]], 1).contiguous()
         gx, gv, gu = ctx.lib_ctx.force_backward(g4, h_mode=0)
         return gx[:, :3], gv[:, :3], gu, None, None, None
+
+
+class StepGraph:
+    """One hot-path step (build_cells, density, gradient, force) captured once in a CUDA graph.
+
+    All inputs and outputs are fixed device tensors (``pos_h``, ``vel_m``, ``u``
+    are read at every replay, so the caller refreshes them in place). The
+    calls are made once outside capture first (the first call of each loop sets
+    kernel attributes), then captured on a side stream; ``replay()`` re-issues
+    the whole step with one launch from the host. The cell width is fixed at
+    capture (``min_cell_width``; 0 lets the device choose it at every replay
+    from the current h, as the direct calls do).
+    """
+
+    def __init__(self, ctx: Context, pos_h, vel_m, u, min_cell_width: float = 0.0, alpha_v=None, alpha_c=None):
+        n = pos_h.shape[0]
+        dev = pos_h.device
+        self.ctx = ctx
+        self.out = dict(h=torch.empty(n, dtype=_F32, device=dev), rho4=torch.empty(n, 4, dtype=_F32, device=dev),
+                        curl_div=torch.empty(n, 4, dtype=_F32, device=dev),
+                        ngb=torch.zeros(n, dtype=torch.int32, device=dev),
+                        vsig_lapu=torch.empty(n, 2, dtype=_F32, device=dev),
+                        accel_dudt=torch.empty(n, 4, dtype=_F32, device=dev), dh_dt=torch.empty(n, dtype=_F32, device=dev),
+                        reductions=torch.zeros(8, dtype=torch.float64, device=dev))
+        o = self.out
+
+        def body():
+            ctx.build_cells(pos_h, min_cell_width)
+            ctx.density(pos_h, vel_m, h_out=o["h"], rho4=o["rho4"], curl_div=o["curl_div"], ngb_count=o["ngb"])
+            ctx.gradient(u, vsig_lapu=o["vsig_lapu"])
+            ctx.force(u, alpha_v, alpha_c, accel_dudt=o["accel_dudt"], dh_dt=o["dh_dt"], reductions=o["reductions"])
+
+        side = torch.cuda.Stream(device=dev)
+        side.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(side):
+            body()
+        torch.cuda.current_stream(dev).wait_stream(side)
+        torch.cuda.synchronize(dev)
+        l0 = ctx.info()["launches"]
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            body()
+        self.launches_per_step = ctx.info()["launches"] - l0
+
+    def replay(self):
+        self.graph.replay()
+        return self.out
