@@ -80,6 +80,12 @@ def barrier(pg):
         pg.barrier()
 
 
+def aggregate(pg, world, interactions_per_step, steps, local_seconds, device):
+    """Whole-job rate: every rank's interactions over the slowest rank's time (replicas, weak scaling)."""
+    tmax = reduce_max(pg, local_seconds, device)
+    return world * interactions_per_step * steps / tmax, tmax
+
+
 # ----------------------------------------------------------------- clocks
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled every 100 ms during the timed region."""
@@ -259,7 +265,7 @@ def run_ours(args, rank, world, pg):
     launches = i1["launches"] - i0["launches"]
     inter_step = sum(inter)
     local_time = sum(step_ms) / 1e3
-    tmax_direct = reduce_max(pg, local_time, dev)
+    value_direct, tmax_direct = aggregate(pg, world, inter_step, K, local_time, dev)
 
     # the same step captured once in a CUDA graph and replayed (the headline)
     graph = sph.StepGraph(ctx, pos_h, vel_m, u, min_width)
@@ -273,8 +279,8 @@ def run_ours(args, rank, world, pg):
         gev[k][1].record(stream)
     torch.cuda.synchronize()
     barrier(pg)
-    tmax = reduce_max(pg, sum(gev[k][0].elapsed_time(gev[k][1]) for k in range(K)) / 1e3, dev)
-    value = world * inter_step * K / tmax
+    value, tmax = aggregate(pg, world, inter_step, K, sum(gev[k][0].elapsed_time(gev[k][1]) for k in range(K)) / 1e3,
+                            dev)
     ms_per_step = tmax / K * 1e3
     launches_graph = graph.launches_per_step * K
     clocks = sampler.stop()  # sampled over both timed regions (direct calls, then graph replays)
@@ -316,7 +322,7 @@ def run_ours(args, rank, world, pg):
                       "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}",
                       "launch": "whole step captured in one CUDA graph, replayed per step"},
            "roofline": roof, "gpu_launches": int(launches_graph), "clocks": clocks,
-           "direct": {"value": world * inter_step * K / tmax_direct, "ms_per_step": tmax_direct / K * 1e3,
+           "direct": {"value": value_direct, "ms_per_step": tmax_direct / K * 1e3,
                       "gpu_launches": int(launches),
                       "note": "the same step as four direct C-ABI calls per step (no graph); per-loop times above"},
            "wall_s_timed_region": wall}
