@@ -107,7 +107,7 @@ def sedov(n_side: int = 64, jitter: float = 0.1, index: int = 2, energy: float =
 
 
 def plummer(n_total: int = 2 ** 21, n_spheres: int = 64, bg_frac: float = 0.1, index: int = 3,
-            a_min: float = 0.005, a_max: float = 0.05, active_mod: int = 10, h_grid: int = 128):
+            a_min: float = 0.005, a_max: float = 0.05, active_mod: int = 10, h_grid: int = 32):
     """Mixture of Plummer spheres plus a uniform background; 1/active_mod of particles active.
 
     Radii follow the Plummer inverse CDF r = a (X^(-2/3) - 1)^(-1/2) truncated at

@@ -201,18 +201,19 @@ class Context:
         """build_cells -> density (h iteration) -> gradient -> force on one stream.
 
         With check=True the status word is read after the density call (a
-        host synchronisation); if the h iteration asked for a support wider
-        than a cell, the cells are rebuilt once with room for the new h and
-        the density call is repeated.
+        host synchronisation); while the h iteration asks for a support wider
+        than a cell, the cells are rebuilt twice as wide (up to a third of the
+        box) and the density call is repeated from the same starting h.
         """
         self.build_cells(pos_h, min_cell_width, stream)
         d = self.density(pos_h, vel_m, active, rho4=rho4, curl_div=curl_div, stream=stream)
         if check:
             code, detail = self.sync_status()
-            if code == _lib.ERR_H_EXCEEDS_CELL:
-                h_new = d["h"]
-                w = float(self.params.kernel_gamma) * float(h_new.max()) * 1.5
-                self.build_cells(pos_h, max(min_cell_width, w), stream)
+            width = max(self.info()["cell_width"])
+            box_third = min(float(b) for b in self.params.box) / 3.0
+            while code == _lib.ERR_H_EXCEEDS_CELL and width < box_third:
+                width = min(2.0 * width, box_third)
+                self.build_cells(pos_h, max(min_cell_width, width), stream)
                 d = self.density(pos_h, vel_m, active, rho4=rho4, curl_div=curl_div, stream=stream)
                 code, detail = self.sync_status()
             if code not in (_lib.OK, _lib.ERR_H_NOT_CONVERGED):
