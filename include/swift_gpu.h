@@ -52,8 +52,13 @@ extern "C" {
 #define SWIFT_GPU_PLAIN 1         /* one kernel launch per self/pair cell task (the paper's task granularity,
                                      Sec. 2.2.2), h iteration driven from the host pass by pass; the baseline
                                      for the persistent path (no autotune, no force_backward) */
-#define SWIFT_GPU_NO_H_ITER 2     /* density at the given h: no Newton iteration */
+#define SWIFT_GPU_NO_H_ITER 2     /* density at the given h: no Newton iteration, no convergence status */
 #define SWIFT_GPU_NO_COMPENSATION 4 /* plain FP32 sums instead of two-sum compensated rho, a, du/dt */
+#define SWIFT_GPU_ADAPTIVE 8      /* adaptive leaves for clustered sets (the task recursion of Sec. 2.2.2 and
+                                     Fig. 3c, which the paper's GPU path lacks, Sec. 4.4.4): each cell is split
+                                     octree-wise into leaves of <= leaf_max particles and every loop scans, for
+                                     the particles of a leaf, only the leaves whose bounding boxes come within
+                                     the larger of the two leaves' supports (not with PLAIN) */
 
 typedef struct {
   float box[3];        /* periodic box edge lengths L (the box is [0,L)^3) */
@@ -68,6 +73,8 @@ typedef struct {
   float h_max;         /* cap on h; 0 = the largest h whose support fits in one cell */
   float cell_margin;   /* automatic cell width = (1 + cell_margin) * kernel_gamma * max h */
   int flags;           /* SWIFT_GPU_* flags above */
+  int leaf_max;        /* ADAPTIVE: a node with more particles is split into its 8 octants (8..1024) */
+  float leaf_margin;   /* ADAPTIVE: the h cap of a leaf is (1 + leaf_margin) * its largest h at the build */
 } swift_gpu_params;
 
 /* Work-distribution knobs (chosen by swift_gpu_autotune, or set by hand). */
@@ -89,18 +96,21 @@ typedef struct {
   uint64_t candidates[3];  /* candidate pairs tested by the neighbour scan, same loops */
   uint64_t launches;       /* kernel launches issued since the context was created */
   uint64_t h_iteration_pairs; /* pairs of the Newton steps on h that evaluate only Eqs. 5-6 */
+  int64_t n_leaves;        /* ADAPTIVE: leaves of the last build (0 otherwise) */
+  int64_t leaf_pairs;      /* ADAPTIVE: entries of the leaf neighbour lists (ordered leaf pairs) */
+  int32_t tree_depth;      /* ADAPTIVE: deepest octree level holding a leaf (cells are level 0) */
 } swift_gpu_info;
 
 typedef struct swift_gpu_ctx swift_gpu_ctx;
 
 /* Fill *p with the defaults (unit box, gamma 5/3, eta 1.2348, kernel_gamma
  * 1.825742, alpha_v 1, beta_v 3, alpha_c 1, h_tol 1e-4, max_iter 30, h_max 0,
- * cell_margin 0.05, flags 0). Host only; never fails. */
+ * cell_margin 0.05, flags 0, leaf_max 32, leaf_margin 0.25). Host only; never fails. */
 void swift_gpu_default_params(swift_gpu_params* p);
 
 /* Create a context for up to n_max particles on the current CUDA device.
- * Allocates every device buffer the calls need (about 300 bytes per particle
- * plus the cell arrays), so no later call allocates. *ctx is owned by the
+ * Allocates every device buffer the calls need (about 650 bytes per particle
+ * plus the cell arrays, the adaptive tree and leaf lists included), so no later call allocates. *ctx is owned by the
  * caller and freed with swift_gpu_destroy. Errors: ERR_ARG (null/invalid
  * params, n_max < 1 or > 2^26), ERR_NOMEM, ERR_CUDA. */
 int swift_gpu_create(swift_gpu_ctx** ctx, const swift_gpu_params* p, int64_t n_max);
@@ -119,7 +129,19 @@ int swift_gpu_set_params(swift_gpu_ctx* ctx, const swift_gpu_params* p);
  * computed in FP64 (wrap into [0,L), floor(x nc / L), clamp) and particles are
  * stably sorted by cell id (ties keep the input order). Device-side errors:
  * ERR_ARG (NaN/Inf position, h <= 0), ERR_H_EXCEEDS_CELL (support wider than
- * L/3). Host errors: ERR_ARG, ERR_CAPACITY (n > n_max). n = 0 is allowed. */
+ * L/3). Host errors: ERR_ARG, ERR_CAPACITY (n > n_max). n = 0 is allowed.
+ * With SWIFT_GPU_ADAPTIVE the particles of a cell are ordered by the Morton
+ * code of their position inside the cell (10 bits per axis, ties by input
+ * order) and the cell tree of Sec. 2.2.2 is built on the device: a node with
+ * more than leaf_max particles is split into its non-empty octants, down to
+ * 10 levels below the cell; the rest are leaves. A leaf's h cap is
+ * min(cell cap, (1 + leaf_margin) * its largest h); its neighbour list holds
+ * every leaf (with periodic image) whose bounding box comes within the
+ * larger of the two leaves' supports kernel_gamma * h_cap. Capacities:
+ * 2 n_max tree nodes beyond the cells (a node that would exceed them stays a
+ * leaf) and 48 n_max list entries (a leaf whose list would end past them
+ * scans the 27 neighbour cells of its cell instead); both keep results exact.
+ * With ADAPTIVE at most 256 cells per axis are used. */
 int swift_gpu_build_cells(swift_gpu_ctx* ctx, const float* pos_h, int64_t n, float min_cell_width,
                           void* stream);
 
@@ -199,6 +221,17 @@ int swift_gpu_get_info(swift_gpu_ctx* ctx, swift_gpu_info* info);
  * (sorted position k -> caller index perm[k]) of the last build into device
  * arrays cell_id[n], perm[n] (either may be NULL). Asynchronous. */
 int swift_gpu_get_cells(swift_gpu_ctx* ctx, uint32_t* cell_id, uint32_t* perm, void* stream);
+
+/* ADAPTIVE only: copy the leaves of the last build into device arrays:
+ * range[2 * l], range[2 * l + 1] = first and one-past-last SORTED position of
+ * leaf l (sorted positions are those of swift_gpu_get_cells' perm),
+ * h_cap[l] = the largest h its particles may take before the h iteration
+ * reports ERR_H_EXCEEDS_CELL, nbr_count[l] = length of its neighbour-leaf
+ * list (itself included). Any pointer may be NULL. Leaves l < max_leaves are
+ * copied; the leaf count is swift_gpu_info.n_leaves. The order of the leaves
+ * is unspecified. Errors: ERR_ORDER (no adaptive build), ERR_ARG. Asynchronous. */
+int swift_gpu_get_leaves(swift_gpu_ctx* ctx, int32_t* range, float* h_cap, int32_t* nbr_count, int64_t max_leaves,
+                         void* stream);
 
 /* Read / set the work-distribution knobs. */
 int swift_gpu_get_tuning(swift_gpu_ctx* ctx, swift_gpu_tuning* t);

@@ -28,11 +28,13 @@ ERR_NAMES = {OK: "OK", ERR_ARG: "ERR_ARG", ERR_ORDER: "ERR_ORDER", ERR_CUDA: "ER
 FLAG_PLAIN = 1
 FLAG_NO_H_ITER = 2
 FLAG_NO_COMPENSATION = 4
+FLAG_ADAPTIVE = 8
 
 EXPORTED = ("swift_gpu_default_params", "swift_gpu_create", "swift_gpu_destroy", "swift_gpu_set_params",
             "swift_gpu_build_cells", "swift_gpu_density", "swift_gpu_gradient", "swift_gpu_force",
             "swift_gpu_force_backward", "swift_gpu_sync_status", "swift_gpu_get_info", "swift_gpu_get_cells",
-            "swift_gpu_get_tuning", "swift_gpu_set_tuning", "swift_gpu_autotune", "swift_gpu_density_static")
+            "swift_gpu_get_tuning", "swift_gpu_set_tuning", "swift_gpu_autotune", "swift_gpu_density_static",
+            "swift_gpu_get_leaves")
 
 STATIC_MAX_PARTICLES = 32768
 
@@ -51,6 +53,8 @@ class Params(ctypes.Structure):
         ("h_max", ctypes.c_float),
         ("cell_margin", ctypes.c_float),
         ("flags", ctypes.c_int),
+        ("leaf_max", ctypes.c_int),
+        ("leaf_margin", ctypes.c_float),
     ]
 
 
@@ -75,6 +79,9 @@ class Info(ctypes.Structure):
         ("candidates", ctypes.c_uint64 * 3),
         ("launches", ctypes.c_uint64),
         ("h_iteration_pairs", ctypes.c_uint64),
+        ("n_leaves", ctypes.c_int64),
+        ("leaf_pairs", ctypes.c_int64),
+        ("tree_depth", ctypes.c_int32),
     ]
 
 
@@ -100,6 +107,7 @@ _SIGS = {
     "swift_gpu_autotune": (_I, [_VP, _I, _VP]),
     "swift_gpu_density_static": (_I, [ctypes.POINTER(Params), _VP, _VP, _I64, ctypes.c_float, _VP, _VP, _VP, _VP,
                                       _VP, _VP]),
+    "swift_gpu_get_leaves": (_I, [_VP, _VP, _VP, _VP, _I64, _VP]),
 }
 
 _lib = None

@@ -43,7 +43,7 @@ __device__ __forceinline__ void spline_d12(float q, float& dw, float& d2w) {
 
 struct AdjArgs {
   Grid* grid;
-  const int* cell_start;
+  Nbr nb;
   const unsigned* perm;
   Phys ph;
   int lmax;
@@ -280,7 +280,7 @@ __device__ __forceinline__ void force_adj_item(const AdjArgs& a, const ForceAdjO
   I.sb = SideBar{0, 0, 0, 0, 0, 0, 0, 0};
   I.k = k;
   unsigned ncand = 0;
-  scan_item(op, I, g, a.cell_start, a.pos, it.cell, lsh, s, live, w, ncand);
+  scan_item(op, I, g, a.nb, a.pos, it.cell, lsh, s, live, w, ncand);
   for (int q = 0; q < 3; ++q) {
     I.xb[q] = lsum(I.xb[q], lsh);
     I.vb[q] = lsum(I.vb[q], lsh);
@@ -487,7 +487,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_dens_adj(AdjArgs a) {
     I.Cb[0] = q.w; I.Cb[1] = a.cby[k]; I.Cb[2] = a.cbz[k];
     I.xb[0] = I.xb[1] = I.xb[2] = I.vb[0] = I.vb[1] = I.vb[2] = 0.0f;
     unsigned ncand = 0;
-    scan_item(op, I, g, a.cell_start, a.pos, it.cell, lsh, s, live, w, ncand);
+    scan_item(op, I, g, a.nb, a.pos, it.cell, lsh, s, live, w, ncand);
     for (int c = 0; c < 3; ++c) {
       I.xb[c] = lsum(I.xb[c], lsh);
       I.vb[c] = lsum(I.vb[c], lsh);
@@ -530,7 +530,7 @@ int backward_impl(Ctx* c, const float4* grad_ad, float4* grad_x, float4* grad_v,
   k_gather_weights<<<nbg, 256, 0, s>>>(c->n, c->d_vals[c->sorted_buf], grad_ad, c->d_scratch4[0]);
   AdjArgs a;
   a.grid = c->d_grid;
-  a.cell_start = c->d_cell_start;
+  a.nb = nbr_of(c);
   a.perm = c->d_vals[c->sorted_buf];
   a.ph = c->phys;
   a.lmax = c->tuning.max_lanes_per_particle;

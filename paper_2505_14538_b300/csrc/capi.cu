@@ -29,6 +29,10 @@ int phys_from(const swift_gpu_params* p, Phys* ph) {
   if (!(p->kernel_gamma > 0.0f) || !(p->eta > 0.0f) || !(p->gamma_eos > 1.0f)) return SWIFT_GPU_ERR_ARG;
   if (p->max_iter < 1 || !(p->h_tol >= 0.0f) || p->h_max < 0.0f || p->cell_margin < 0.0f)
     return SWIFT_GPU_ERR_ARG;
+  if ((p->flags & SWIFT_GPU_ADAPTIVE) &&
+      ((p->flags & SWIFT_GPU_PLAIN) || p->leaf_max < 8 || p->leaf_max > 1024 || !(p->leaf_margin >= 0.0f) ||
+       !isfinite(p->leaf_margin)))
+    return SWIFT_GPU_ERR_ARG;
   for (int a = 0; a < 3; ++a) ph->L[a] = p->box[a];
   ph->kg = p->kernel_gamma;
   ph->gamma_eos = p->gamma_eos;
@@ -54,7 +58,9 @@ static void free_all(Ctx* c) {
                   c->d_hist, c->d_scan_tmp, c->d_cell_start, c->d_pos, c->d_vel, c->d_rho4, c->d_cd, c->d_h,
                   c->d_bracket, c->d_ngb, c->d_ga, c->d_gb, c->d_act, c->d_items0, c->d_plist0, c->d_items[0],
                   c->d_items[1], c->d_plist[0], c->d_plist[1], c->d_counters, c->d_stats, c->d_red_partial,
-                  c->d_scratch4[0], c->d_scratch1[0], c->d_scratch1[1], c->d_plain_act};
+                  c->d_scratch4[0], c->d_scratch1[0], c->d_scratch1[1], c->d_plain_act, c->d_aux[0], c->d_aux[1],
+                  c->d_node_range, c->d_node_kids, c->d_node_lo, c->d_node_hi, c->d_node_leaf, c->d_leaf_range,
+                  c->d_leaf_hcap, c->d_leaf_node, c->d_nbr_off, c->d_nbr, c->d_tree_ctr};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_status) cudaFreeHost(c->h_status);
@@ -81,6 +87,8 @@ void swift_gpu_default_params(swift_gpu_params* p) {
   p->h_max = 0.0f;
   p->cell_margin = 0.05f;
   p->flags = 0;
+  p->leaf_max = 32;
+  p->leaf_margin = 0.25f;
 }
 
 int swift_gpu_create(swift_gpu_ctx** out, const swift_gpu_params* p, int64_t n_max) {
@@ -114,7 +122,17 @@ int swift_gpu_create(swift_gpu_ctx** out, const swift_gpu_params* p, int64_t n_m
   c->max_passes = kMaxPasses;
   const int64_t n = n_max;
   const int64_t nb = (n + 4095) / 4096;
-  const int64_t scan_m = 256 * nb > ncells_max + 1 ? 256 * nb : ncells_max + 1;
+  int64_t scan_m = 256 * nb > ncells_max + 1 ? 256 * nb : ncells_max + 1;
+  if (scan_m < n + 1) scan_m = n + 1;  // leaf-list offsets
+  // adaptive tree: cells (at most kAdaptiveNcCap^3 of them) plus 2 nodes per
+  // particle, all addressable with kIndexBits; leaves are disjoint and non-empty
+  const int64_t acells = ncells_max < (int64_t)kAdaptiveNcCap * kAdaptiveNcCap * kAdaptiveNcCap
+                             ? ncells_max
+                             : (int64_t)kAdaptiveNcCap * kAdaptiveNcCap * kAdaptiveNcCap;
+  const int64_t node_cap = acells + 2 * n < (int64_t)kIndexMask ? acells + 2 * n : (int64_t)kIndexMask;
+  c->node_cap = (int)node_cap;
+  c->leaf_cap = (int)n;
+  c->nbr_cap = (int)(48 * n < (int64_t)INT32_MAX ? 48 * n : (int64_t)INT32_MAX);
   c->red_blocks = c->num_sms * 32;
   bool ok = dalloc(&c->d_status, 1) && dalloc(&c->d_grid, 1) && dalloc(&c->d_hmax_bits, 1) &&
             dalloc(&c->d_keys[0], n) && dalloc(&c->d_keys[1], n) && dalloc(&c->d_vals[0], n) &&
@@ -127,7 +145,12 @@ int swift_gpu_create(swift_gpu_ctx** out, const swift_gpu_params* p, int64_t n_m
             dalloc(&c->d_plist[1], n) && dalloc(&c->d_counters, kCtrPerPass * (kMaxPasses + 2) + 2) &&
             dalloc(&c->d_stats, kStatCount) && dalloc(&c->d_red_partial, 8 * (size_t)c->red_blocks) &&
             dalloc(&c->d_scratch4[0], 4 * n) && dalloc(&c->d_scratch1[0], n) && dalloc(&c->d_scratch1[1], n) &&
-            dalloc(&c->d_plain_act, n) &&
+            dalloc(&c->d_plain_act, n) && dalloc(&c->d_aux[0], n) && dalloc(&c->d_aux[1], n) &&
+            dalloc(&c->d_node_range, node_cap) && dalloc(&c->d_node_kids, node_cap) &&
+            dalloc(&c->d_node_lo, node_cap) && dalloc(&c->d_node_hi, node_cap) && dalloc(&c->d_node_leaf, node_cap) &&
+            dalloc(&c->d_leaf_range, n) && dalloc(&c->d_leaf_hcap, n) && dalloc(&c->d_leaf_node, n) &&
+            dalloc(&c->d_nbr_off, n + 1) && dalloc(&c->d_nbr, (size_t)c->nbr_cap) &&
+            dalloc(&c->d_tree_ctr, kTreeCtrCount) &&
             cudaMallocHost((void**)&c->h_status, sizeof(Status)) == cudaSuccess &&
             cudaMallocHost((void**)&c->h_stats, sizeof(unsigned long long) * kStatCount) == cudaSuccess;
   if (ok)
@@ -141,6 +164,7 @@ int swift_gpu_create(swift_gpu_ctx** out, const swift_gpu_params* p, int64_t n_m
   cudaMemset(c->d_status, 0, sizeof(Status));
   cudaMemset(c->d_stats, 0, sizeof(unsigned long long) * kStatCount);
   cudaMemset(c->d_counters, 0, sizeof(int) * (kCtrPerPass * (kMaxPasses + 2) + 2));
+  cudaMemset(c->d_tree_ctr, 0, sizeof(int) * kTreeCtrCount);
   if (cudaDeviceSynchronize() != cudaSuccess) {
     free_all(c);
     delete h;
@@ -304,7 +328,26 @@ int swift_gpu_get_info(swift_gpu_ctx* h, swift_gpu_info* info) {
   info->candidates[2] = c->h_stats[kStatCandForce];
   info->launches = c->launches;
   info->h_iteration_pairs = c->h_stats[kStatInterHiter];
+  if ((c->state & 1) && c->tree_built) {
+    int tc[kTreeCtrCount];
+    if (cudaMemcpy(tc, c->d_tree_ctr, sizeof(tc), cudaMemcpyDeviceToHost) != cudaSuccess) return SWIFT_GPU_ERR_CUDA;
+    info->n_leaves = tc[kTreeLeaves];
+    info->leaf_pairs = tc[kTreeEntries];
+    info->tree_depth = tc[kTreeDepth];
+  }
   return SWIFT_GPU_OK;
+}
+
+int swift_gpu_get_leaves(swift_gpu_ctx* h, int32_t* range, float* h_cap, int32_t* nbr_count, int64_t max_leaves,
+                         void* stream) {
+  Ctx* c = from(h);
+  if (!c || max_leaves < 0) return SWIFT_GPU_ERR_ARG;
+  if (!(c->state & 1) || !c->tree_built) return SWIFT_GPU_ERR_ORDER;
+  if ((range && !aligned(range, 4)) || (h_cap && !aligned(h_cap, 4)) || (nbr_count && !aligned(nbr_count, 4)))
+    return SWIFT_GPU_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  return leaves_export_impl(c, range, h_cap, nbr_count, max_leaves, s);
 }
 
 int swift_gpu_get_cells(swift_gpu_ctx* h, uint32_t* cell_id, uint32_t* perm, void* stream) {

@@ -4,7 +4,9 @@
 //
 //   k_scan_h       max of h, NaN / h <= 0 checks
 //   k_grid_setup   nc, widths, h cap, key bits (one thread)
-//   k_cell_ids     FP64 cell id per particle (wrap, floor(x nc / L), clamp)
+//   k_cell_ids     FP64 cell id per particle (wrap, floor(x nc / L), clamp);
+//                  with adaptive leaves also the Morton code inside the cell,
+//                  sorted on first so that each cell ends in Morton order
 //   radix passes   LSD radix sort of (cell id, original index), 8-bit digits,
 //                  stable, so ties keep the input order
 //   k_cell_start   start offset of every cell (empty cells included)
@@ -171,8 +173,23 @@ __global__ void k_grid_setup(const unsigned* __restrict__ hmax_bits, Grid* g, Ph
   g->key_bits = bits;
 }
 
+// Spread the 10 low bits of v to every third bit (bit b -> bit 3b).
+__device__ __forceinline__ unsigned spread3(unsigned v) {
+  v &= 0x3ffu;
+  v = (v | (v << 16)) & 0x030000ffu;
+  v = (v | (v << 8)) & 0x0300f00fu;
+  v = (v | (v << 4)) & 0x030c30c3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+
+// Cell id of every particle; with `cell_out` (adaptive leaves) the sort key
+// is instead the 30-bit Morton code of the position inside the cell (10 bits
+// per axis, x in the lowest bit of each 3-bit digit) and the cell id goes to
+// cell_out, morton_out keeping a copy of the code.
 __global__ void k_cell_ids(const float4* __restrict__ pos_h, int n, const Grid* __restrict__ g,
-                           unsigned* __restrict__ keys, unsigned* __restrict__ vals) {
+                           unsigned* __restrict__ keys, unsigned* __restrict__ vals, unsigned* __restrict__ cell_out,
+                           unsigned* __restrict__ morton_out) {
   const int nx = g->nc[0], ny = g->nc[1], nz = g->nc[2];
   const double Lx = g->L[0], Ly = g->L[1], Lz = g->L[2];
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -184,26 +201,45 @@ __global__ void k_cell_ids(const float4* __restrict__ pos_h, int n, const Grid* 
     if (!(x >= 0.0 && x < Lx)) x = __dsub_rn(x, __dmul_rn(Lx, floor(__ddiv_rn(x, Lx))));
     if (!(y >= 0.0 && y < Ly)) y = __dsub_rn(y, __dmul_rn(Ly, floor(__ddiv_rn(y, Ly))));
     if (!(z >= 0.0 && z < Lz)) z = __dsub_rn(z, __dmul_rn(Lz, floor(__ddiv_rn(z, Lz))));
-    const double tx = __dmul_rn(x, (double)nx), ty = __dmul_rn(y, (double)ny), tz = __dmul_rn(z, (double)nz);
-    int cx = (int)floor(Lx == 1.0 ? tx : __ddiv_rn(tx, Lx));
-    int cy = (int)floor(Ly == 1.0 ? ty : __ddiv_rn(ty, Ly));
-    int cz = (int)floor(Lz == 1.0 ? tz : __ddiv_rn(tz, Lz));
+    const double tx0 = __dmul_rn(x, (double)nx), ty0 = __dmul_rn(y, (double)ny), tz0 = __dmul_rn(z, (double)nz);
+    const double tx = Lx == 1.0 ? tx0 : __ddiv_rn(tx0, Lx);
+    const double ty = Ly == 1.0 ? ty0 : __ddiv_rn(ty0, Ly);
+    const double tz = Lz == 1.0 ? tz0 : __ddiv_rn(tz0, Lz);
+    int cx = (int)floor(tx), cy = (int)floor(ty), cz = (int)floor(tz);
     cx = min(max(cx, 0), nx - 1);
     cy = min(max(cy, 0), ny - 1);
     cz = min(max(cz, 0), nz - 1);
-    keys[i] = (unsigned)(cx + nx * (cy + ny * cz));
+    const unsigned cell = (unsigned)(cx + nx * (cy + ny * cz));
+    if (cell_out) {
+      // position inside the cell in units of 1/1024 of its width
+      const unsigned qx = (unsigned)min(max((tx - cx) * 1024.0, 0.0), 1023.0);
+      const unsigned qy = (unsigned)min(max((ty - cy) * 1024.0, 0.0), 1023.0);
+      const unsigned qz = (unsigned)min(max((tz - cz) * 1024.0, 0.0), 1023.0);
+      const unsigned m = spread3(qx) | (spread3(qy) << 1) | (spread3(qz) << 2);
+      keys[i] = m;
+      morton_out[i] = m;
+      cell_out[i] = cell;
+    } else {
+      keys[i] = cell;
+    }
     vals[i] = (unsigned)i;
   }
+}
+
+// keys[k] = src[idx[k]]
+__global__ void k_gather_keys(unsigned* __restrict__ keys, const unsigned* __restrict__ src,
+                              const unsigned* __restrict__ idx, int n) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) keys[k] = src[idx[k]];
 }
 
 // ------------------------------------------------------------ radix sort
 // Pass over digit `shift..shift+8`. Histogram layout: hist[d * nblocks + b].
 __global__ void k_radix_count(const unsigned* __restrict__ keys, int n, int shift, const Grid* __restrict__ g,
-                              unsigned* __restrict__ hist) {
+                              int bits, unsigned* __restrict__ hist) {
   __shared__ unsigned h[256];
   h[threadIdx.x] = 0;
   __syncthreads();
-  const bool live = shift < g->key_bits;
+  const bool live = shift < (bits >= 0 ? bits : g->key_bits);
   const int base = blockIdx.x * kRadixTile;
   if (live) {
     for (int k = 0; k < kRadixItems; ++k) {
@@ -219,12 +255,12 @@ __global__ void k_radix_count(const unsigned* __restrict__ keys, int n, int shif
 }
 
 __global__ void k_radix_scatter(const unsigned* __restrict__ kin, const unsigned* __restrict__ vin, int n,
-                                int shift, const Grid* __restrict__ g, const unsigned* __restrict__ offs,
+                                int shift, const Grid* __restrict__ g, int bits, const unsigned* __restrict__ offs,
                                 unsigned* __restrict__ kout, unsigned* __restrict__ vout) {
   __shared__ unsigned run[256];
   __shared__ unsigned wcnt[kRadixThreads / 32][256];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const bool live = shift < g->key_bits;
+  const bool live = shift < (bits >= 0 ? bits : g->key_bits);
   run[threadIdx.x] = offs[threadIdx.x * gridDim.x + blockIdx.x];
   for (int ww = 0; ww < kRadixThreads / 32; ++ww) wcnt[ww][threadIdx.x] = 0;
   __syncthreads();
@@ -277,29 +313,45 @@ int build_cells_impl(Ctx* c, const float4* pos_h, int n, float min_width, cudaSt
                                                          c->d_hmax_bits, c->d_status);
     c->launches++;
   }
-  k_grid_setup<<<1, 1, 0, s>>>(c->d_hmax_bits, c->d_grid, c->phys, c->params.cell_margin, min_width, c->nc_cap,
+  const bool adaptive = (c->params.flags & SWIFT_GPU_ADAPTIVE) != 0;
+  const int nc_cap = adaptive && c->nc_cap > kAdaptiveNcCap ? kAdaptiveNcCap : c->nc_cap;
+  k_grid_setup<<<1, 1, 0, s>>>(c->d_hmax_bits, c->d_grid, c->phys, c->params.cell_margin, min_width, nc_cap,
                                c->d_status);
   c->launches++;
   if (n > 0) {
     int gb = min((n + 255) / 256, sm * 8);
-    k_cell_ids<<<gb, 256, 0, s>>>(pos_h, n, c->d_grid, c->d_keys[0], c->d_vals[0]);
+    k_cell_ids<<<gb, 256, 0, s>>>(pos_h, n, c->d_grid, c->d_keys[0], c->d_vals[0], adaptive ? c->d_aux[0] : nullptr,
+                                  adaptive ? c->d_aux[1] : nullptr);
     c->launches++;
     const int nb = (n + kRadixTile - 1) / kRadixTile;
     int src = 0;
-    for (int shift = 0; shift < c->max_key_bits; shift += 8) {
-      k_radix_count<<<nb, kRadixThreads, 0, s>>>(c->d_keys[src], n, shift, c->d_grid, c->d_hist);
+    auto pass = [&](int shift, int bits) {
+      k_radix_count<<<nb, kRadixThreads, 0, s>>>(c->d_keys[src], n, shift, c->d_grid, bits, c->d_hist);
       exclusive_scan(c, c->d_hist, c->d_hist, 256 * nb, c->d_scan_tmp, s);
-      k_radix_scatter<<<nb, kRadixThreads, 0, s>>>(c->d_keys[src], c->d_vals[src], n, shift, c->d_grid,
+      k_radix_scatter<<<nb, kRadixThreads, 0, s>>>(c->d_keys[src], c->d_vals[src], n, shift, c->d_grid, bits,
                                                     c->d_hist, c->d_keys[1 - src], c->d_vals[1 - src]);
       c->launches += 2;
       src = 1 - src;
+    };
+    if (adaptive) {
+      // least significant key first: the Morton code inside the cell, then the cell id
+      for (int shift = 0; shift < 30; shift += 8) pass(shift, 30);
+      k_gather_keys<<<gb, 256, 0, s>>>(c->d_keys[src], c->d_aux[0], c->d_vals[src], n);
+      c->launches++;
     }
+    for (int shift = 0; shift < c->max_key_bits; shift += 8) pass(shift, -1);
     c->sorted_buf = src;  // keys/vals of this buffer are sorted by cell id
   }
   {
     int gb = min((n + 1 + 255) / 256, sm * 8);
     k_cell_start<<<max(gb, 1), 256, 0, s>>>(c->d_keys[c->sorted_buf], n, c->d_grid, c->d_cell_start);
     c->launches++;
+  }
+  c->tree_built = 0;
+  if (adaptive) {
+    const int rc = leaves_build(c, pos_h, s);
+    if (rc != SWIFT_GPU_OK) return rc;
+    c->tree_built = 1;
   }
   return cudaGetLastError() == cudaSuccess ? SWIFT_GPU_OK : SWIFT_GPU_ERR_CUDA;
 }

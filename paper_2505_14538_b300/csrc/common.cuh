@@ -41,6 +41,12 @@ struct Grid {
   float width[3];
 };
 
+// Status a particle capped at the cell's h raises: a wider cell would help
+// (ERR_H_EXCEEDS_CELL) unless the user's h_max set the cap.
+__host__ __device__ __forceinline__ int cell_cap_flag(const Grid& g) {
+  return g.hcap_from_cells ? SWIFT_GPU_ERR_H_EXCEEDS_CELL : SWIFT_GPU_ERR_H_NOT_CONVERGED;
+}
+
 // Physics constants for the kernels.
 struct Phys {
   float L[3];
@@ -52,6 +58,36 @@ struct Phys {
   int max_iter;
   float h_max;       // user cap (0 = none)
   int compensated;
+};
+
+// Where the candidate segments of a work item come from: the 27 neighbour
+// cells of the item's cell (uniform grid), or the neighbour-leaf list of the
+// item's leaf (adaptive leaves; Item::cell is then a leaf index). A list
+// entry is a leaf index (kIndexBits) plus the periodic shift code. A leaf
+// whose list does not end within nbr_cap was never written in full; its
+// items scan the 27 neighbour cells of the leaf's cell instead.
+struct Nbr {
+  const int* cell_start;
+  const unsigned* skeys;    // sorted cell ids
+  const int2* leaf_range;   // [first, end) sorted positions of each leaf
+  const int* nbr_off;       // exclusive offsets of the leaf lists
+  const unsigned* nbr;      // leaf index | shift code << kIndexBits
+  const float* leaf_hcap;   // largest h the particles of a leaf may take
+  const int* n_leaves;      // device count of leaves
+  int nbr_cap;
+  int adaptive;
+};
+
+constexpr int kTreeLevels = 10;     // octree levels below a cell (10-bit Morton code per axis)
+constexpr int kAdaptiveNcCap = 256;  // cells per axis with adaptive leaves (the tree refines below)
+
+// Octree counters of an adaptive build (device ints).
+enum TreeCtr {
+  kTreeNodes = 0,                   // [0 .. kTreeLevels]: nodes created at each level
+  kTreeLeaves = kTreeLevels + 1,    // leaf count
+  kTreeDepth,                       // deepest level holding a leaf
+  kTreeEntries,                     // total entries of the leaf lists
+  kTreeCtrCount = 16
 };
 
 struct Item {

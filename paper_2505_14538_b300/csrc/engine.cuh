@@ -1,13 +1,14 @@
 // engine.cuh -- the warp-level neighbour scan shared by every pair loop.
 //
-// A work item is a run of <= 32 active particles of one cell (Sec. 2.2:
-// self and pair interactions of a cell with its 26 neighbours). One warp
-// handles one item:
+// A work item is a run of <= 16 active particles of one cell (Sec. 2.2:
+// self and pair interactions of a cell with its 26 neighbours) or, with
+// adaptive leaves, of one leaf. One warp handles one item:
 //
 //   segments  lanes 0..26 each look up one of the 27 neighbour cells (with
-//             its periodic image) and a warp scan concatenates them into one
-//             candidate sequence, so candidates are taken in full chunks of 32
-//             whatever the cell occupancies;
+//             its periodic image), or up to 32 lanes one entry each of the
+//             leaf's neighbour list, and a warp scan concatenates them into
+//             one candidate sequence, so candidates are taken in full chunks
+//             of 32 whatever the cell or leaf occupancies;
 //   phase 1   a chunk of 32 candidates is staged in shared memory by one
 //             coalesced float4 load per lane; each lane tests its particle
 //             against its share of the chunk (r^2 < support^2 + guard band)
@@ -32,9 +33,9 @@ struct WarpSmem {
   unsigned list[kCap * 32];  // lane-private lists, entry t of lane l at [t * 32 + l]
   float4 stage[32];          // current chunk: shifted position + per-loop w
   unsigned stage_idx[32];    // current chunk: j | shift code << kIndexBits
-  int seg_start[27];
-  unsigned seg_code[27];
-  int seg_pref[28];
+  int seg_start[32];
+  unsigned seg_code[32];
+  int seg_pref[33];
 };
 
 // log2 of the lanes per particle for an item of cnt particles (L = 2^lsh <= lmax).
@@ -44,22 +45,63 @@ __device__ __forceinline__ int lanes_shift(int cnt, int lmax) {
   return lsh;
 }
 
-// Segments of the 27 neighbour cells of `cell`; returns the candidate count.
-__device__ __forceinline__ int setup_segments(const Grid& g, const int* __restrict__ cell_start, int cell,
-                                              WarpSmem& w) {
+// The candidate segments of an item: the 27 neighbour cells of `cell`, or
+// nseg entries of a leaf list from list_off.
+struct Segs {
+  int cell;
+  int list_off;
+  int nseg;
+  bool list;
+};
+
+__device__ __forceinline__ Segs item_segments(const Nbr& nb, int item_cell) {
+  Segs q;
+  q.cell = item_cell;
+  q.list_off = 0;
+  q.nseg = 27;
+  q.list = false;
+  if (nb.adaptive) {
+    const int b = nb.nbr_off[item_cell], e = nb.nbr_off[item_cell + 1];
+    if (e <= nb.nbr_cap) {
+      q.list_off = b;
+      q.nseg = e - b;
+      q.list = true;
+    } else {
+      q.cell = (int)nb.skeys[nb.leaf_range[item_cell].x];
+    }
+  }
+  return q;
+}
+
+// Segments sb .. sb + bn - 1 (bn = min(32, nseg - sb) >= 1) of an item, one
+// per lane, concatenated by a warp scan; returns their candidate count.
+__device__ __forceinline__ int setup_segments(const Grid& g, const Nbr& nb, const Segs& q, int sb, WarpSmem& w,
+                                              int& bn) {
   const unsigned lane = lane_id();
-  const int nx = g.nc[0], ny = g.nc[1], nz = g.nc[2];
+  bn = min(32, q.nseg - sb);
   int len = 0;
-  if (lane < 27) {
-    const int cx = cell % nx, cy = (cell / nx) % ny, cz = cell / (nx * ny);
-    int x = cx + (int)(lane % 3u) - 1, y = cy + (int)((lane / 3u) % 3u) - 1, z = cz + (int)(lane / 9u) - 1;
-    unsigned code = 0;
-    if (x < 0) { x += nx; code |= 2u; } else if (x >= nx) { x -= nx; code |= 1u; }
-    if (y < 0) { y += ny; code |= 8u; } else if (y >= ny) { y -= ny; code |= 4u; }
-    if (z < 0) { z += nz; code |= 32u; } else if (z >= nz) { z -= nz; code |= 16u; }
-    const int c = x + nx * (y + ny * z);
-    const int b = cell_start[c];
-    len = cell_start[c + 1] - b;
+  if ((int)lane < bn) {
+    int b;
+    unsigned code;
+    if (q.list) {
+      const unsigned e = nb.nbr[q.list_off + sb + (int)lane];
+      const int2 r = nb.leaf_range[e & kIndexMask];
+      b = r.x;
+      len = r.y - r.x;
+      code = e >> kIndexBits;
+    } else {
+      const int nx = g.nc[0], ny = g.nc[1], nz = g.nc[2];
+      const int cell = q.cell;
+      const int cx = cell % nx, cy = (cell / nx) % ny, cz = cell / (nx * ny);
+      int x = cx + (int)(lane % 3u) - 1, y = cy + (int)((lane / 3u) % 3u) - 1, z = cz + (int)(lane / 9u) - 1;
+      code = 0;
+      if (x < 0) { x += nx; code |= 2u; } else if (x >= nx) { x -= nx; code |= 1u; }
+      if (y < 0) { y += ny; code |= 8u; } else if (y >= ny) { y -= ny; code |= 4u; }
+      if (z < 0) { z += nz; code |= 32u; } else if (z >= nz) { z -= nz; code |= 16u; }
+      const int c = x + nx * (y + ny * z);
+      b = nb.cell_start[c];
+      len = nb.cell_start[c + 1] - b;
+    }
     w.seg_start[lane] = b;
     w.seg_code[lane] = code;
   }
@@ -69,10 +111,25 @@ __device__ __forceinline__ int setup_segments(const Grid& g, const int* __restri
     int y = __shfl_up_sync(kFull, incl, o);
     if ((int)lane >= o) incl += y;
   }
-  if (lane < 27) w.seg_pref[lane + 1] = incl;
+  if ((int)lane < bn) w.seg_pref[lane + 1] = incl;
   if (lane == 0) w.seg_pref[0] = 0;
   __syncwarp();
-  return __shfl_sync(kFull, incl, 26);
+  return __shfl_sync(kFull, incl, bn - 1);
+}
+
+// Stage candidate `p` (< the batch total) of the current segment batch: its
+// position with the periodic shift applied, and its list entry.
+__device__ __forceinline__ void stage_candidate(const Grid& g, const float4* __restrict__ pos, const WarpSmem& w,
+                                                int bn, int p, float4& pj, unsigned& entry) {
+  int q = 0;
+#pragma unroll
+  for (int step = 16; step > 0; step >>= 1)
+    if (q + step < bn && w.seg_pref[q + step] <= p) q += step;
+  const int j = w.seg_start[q] + (p - w.seg_pref[q]);
+  const unsigned code = w.seg_code[q];
+  pj = pos[j];
+  shift_j(code, g.L, pj.x, pj.y, pj.z);
+  entry = (unsigned)j | (code << kIndexBits);
 }
 
 // Phase 2: each lane evaluates the interactions in its list.
@@ -89,17 +146,27 @@ __device__ __forceinline__ void flush(const Op& op, typename Op::I& I, const War
 }
 
 // Full neighbour scan of one item for lane particle I (sub-lane s of the
-// 2^lsh lanes that share the particle). One flush site keeps the inlined
-// interaction code in a single copy.
+// 2^lsh lanes that share the particle). Segments come in batches of up to
+// 32; candidates are taken in chunks of 32 within a batch. One flush site
+// keeps the inlined interaction code in a single copy.
 template <class Op>
-__device__ __forceinline__ void scan_item(const Op& op, typename Op::I& I, const Grid& g,
-                                          const int* __restrict__ cell_start, const float4* __restrict__ pos,
-                                          int cell, int lsh, int s, bool live, WarpSmem& w, unsigned& ncand) {
+__device__ __forceinline__ void scan_item(const Op& op, typename Op::I& I, const Grid& g, const Nbr& nb,
+                                          const float4* __restrict__ pos, int cell, int lsh, int s, bool live,
+                                          WarpSmem& w, unsigned& ncand) {
   const unsigned lane = lane_id();
-  const int total = setup_segments(g, cell_start, cell, w);
+  const Segs q = item_segments(nb, cell);
+  const int nseg = q.nseg;
+  int bn = 0, sb = 0;
+  int total = nseg > 0 ? setup_segments(g, nb, q, 0, w, bn) : 0;
   const int per = 32 >> lsh;  // candidates a lane tests per chunk (at most)
   int cnt = 0;
   for (int base = 0;; base += 32) {
+    while (base >= total && sb + 32 < nseg) {
+      sb += 32;
+      base = 0;
+      __syncwarp();
+      total = setup_segments(g, nb, q, sb, w, bn);
+    }
     const bool done = base >= total;
     if (done || __any_sync(kFull, cnt > kCap - per)) {
       flush(op, I, w, cnt);
@@ -109,17 +176,11 @@ __device__ __forceinline__ void scan_item(const Op& op, typename Op::I& I, const
     const int len = min(32, total - base);
     __syncwarp();
     if ((int)lane < len) {
-      const int p = base + (int)lane;
-      int q = 0;
-#pragma unroll
-      for (int step = 16; step > 0; step >>= 1)
-        if (q + step < 27 && w.seg_pref[q + step] <= p) q += step;
-      const int j = w.seg_start[q] + (p - w.seg_pref[q]);
-      const unsigned code = w.seg_code[q];
-      float4 pj = pos[j];
-      shift_j(code, g.L, pj.x, pj.y, pj.z);
+      float4 pj;
+      unsigned entry;
+      stage_candidate(g, pos, w, bn, base + (int)lane, pj, entry);
       w.stage[lane] = make_float4(pj.x, pj.y, pj.z, op.stage_w(pj.w));
-      w.stage_idx[lane] = (unsigned)j | (code << kIndexBits);
+      w.stage_idx[lane] = entry;
     }
     __syncwarp();
     if (live) {
@@ -143,47 +204,46 @@ __device__ __forceinline__ void scan_item(const Op& op, typename Op::I& I, const
 // largest support any h may reach) goes into the lane's list, which is never
 // flushed; `ovf` is set when the list is full (the particle then takes the
 // multi-pass route).
-__device__ __forceinline__ int collect_item(const Grid& g, const int* __restrict__ cell_start,
-                                            const float4* __restrict__ pos, int cell, float xi, float yi, float zi,
-                                            float R2, int lsh, int s, bool live, WarpSmem& w, unsigned& ncand,
-                                            bool& ovf) {
+__device__ __forceinline__ int collect_item(const Grid& g, const Nbr& nb, const float4* __restrict__ pos, int cell,
+                                            float xi, float yi, float zi, float R2, int lsh, int s, bool live,
+                                            WarpSmem& w, unsigned& ncand, bool& ovf) {
   const unsigned lane = lane_id();
-  const int total = setup_segments(g, cell_start, cell, w);
+  const Segs q = item_segments(nb, cell);
+  const int nseg = q.nseg;
   int cnt = 0;
-  for (int base = 0; base < total; base += 32) {
-    const int len = min(32, total - base);
+  for (int sb = 0; sb < nseg; sb += 32) {
+    int bn;
     __syncwarp();
-    if ((int)lane < len) {
-      const int p = base + (int)lane;
-      int q = 0;
-#pragma unroll
-      for (int step = 16; step > 0; step >>= 1)
-        if (q + step < 27 && w.seg_pref[q + step] <= p) q += step;
-      const int j = w.seg_start[q] + (p - w.seg_pref[q]);
-      const unsigned code = w.seg_code[q];
-      float4 pj = pos[j];
-      shift_j(code, g.L, pj.x, pj.y, pj.z);
-      w.stage[lane] = pj;
-      w.stage_idx[lane] = (unsigned)j | (code << kIndexBits);
-    }
-    __syncwarp();
-    if (live) {
-      const int nk = len > s ? ((len - s - 1) >> lsh) + 1 : 0;
+    const int total = setup_segments(g, nb, q, sb, w, bn);
+    for (int base = 0; base < total; base += 32) {
+      const int len = min(32, total - base);
+      __syncwarp();
+      if ((int)lane < len) {
+        float4 pj;
+        unsigned entry;
+        stage_candidate(g, pos, w, bn, base + (int)lane, pj, entry);
+        w.stage[lane] = pj;
+        w.stage_idx[lane] = entry;
+      }
+      __syncwarp();
+      if (live) {
+        const int nk = len > s ? ((len - s - 1) >> lsh) + 1 : 0;
 #pragma unroll 4
-      for (int kk = 0; kk < nk; ++kk) {
-        const int k = (kk << lsh) + s;
-        const float4 c = w.stage[k];
-        const float dx = xi - c.x, dy = yi - c.y, dz = zi - c.z;
-        if (r2_of(dx, dy, dz) < R2) {
-          if (cnt < kCap) {
-            w.list[cnt * 32 + lane] = w.stage_idx[k];
-            ++cnt;
-          } else {
-            ovf = true;
+        for (int kk = 0; kk < nk; ++kk) {
+          const int k = (kk << lsh) + s;
+          const float4 c = w.stage[k];
+          const float dx = xi - c.x, dy = yi - c.y, dz = zi - c.z;
+          if (r2_of(dx, dy, dz) < R2) {
+            if (cnt < kCap) {
+              w.list[cnt * 32 + lane] = w.stage_idx[k];
+              ++cnt;
+            } else {
+              ovf = true;
+            }
           }
         }
+        ncand += (unsigned)nk;
       }
-      ncand += (unsigned)nk;
     }
   }
   __syncwarp();

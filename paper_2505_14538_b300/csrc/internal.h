@@ -73,6 +73,22 @@ struct Ctx {
   int red_blocks = 0;
   int max_passes = 0;
 
+  // adaptive leaves (built when params.flags has SWIFT_GPU_ADAPTIVE)
+  int tree_built = 0;            // the last build made leaves; the loops take their segments from them
+  int node_cap = 0, leaf_cap = 0, nbr_cap = 0;
+  unsigned* d_aux[2] = {nullptr, nullptr};  // caller order: cell id, Morton code inside the cell
+  int2* d_node_range = nullptr;  // [first, end) sorted positions
+  int2* d_node_kids = nullptr;   // (first child, child count); 0 children: leaf or empty
+  float4* d_node_lo = nullptr;   // (bounding box low corner, reach kernel_gamma * h_cap)
+  float4* d_node_hi = nullptr;   // (bounding box high corner, h_cap)
+  int* d_node_leaf = nullptr;    // leaf index of a leaf node, -1 otherwise
+  int2* d_leaf_range = nullptr;
+  float* d_leaf_hcap = nullptr;
+  int* d_leaf_node = nullptr;
+  int* d_nbr_off = nullptr;      // leaf list lengths, then their exclusive offsets (leaf_cap + 1)
+  unsigned* d_nbr = nullptr;     // leaf index | shift code << kIndexBits
+  int* d_tree_ctr = nullptr;     // TreeCtr
+
   // host mirrors
   Status* h_status = nullptr;  // pinned
   unsigned long long* h_stats = nullptr;  // pinned
@@ -94,6 +110,9 @@ int plain_density_impl(Ctx* c, const float4* pos_h_in, const float4* vel_m, cons
 int plain_gradient_impl(Ctx* c, float2* vsig_lapu, cudaStream_t s);
 int plain_force_impl(Ctx* c, float4* accel_dudt, float* dh_dt, double* reductions, cudaStream_t s);
 void reduce_partials(Ctx* c, int nblocks, double* out, cudaStream_t s);
+int leaves_build(Ctx* c, const float4* pos_h, cudaStream_t s);
+int leaves_export_impl(Ctx* c, int32_t* range, float* hcap, int32_t* nbr_count, int64_t max_leaves, cudaStream_t s);
+Nbr nbr_of(Ctx* c);
 int cells_export_impl(Ctx* c, uint32_t* cell_id, uint32_t* perm, cudaStream_t s);
 int autotune_impl(Ctx* c, int loop, cudaStream_t s);
 int backward_impl(Ctx* c, const float4* grad_ad, float4* grad_x, float4* grad_v, float* grad_u, int h_mode,

@@ -51,7 +51,7 @@ __device__ __forceinline__ LaneMap lane_map(int cnt, int lmax) {
 // ============================================================ density loop
 struct DensArgs {
   Grid* grid;
-  const int* cell_start;
+  Nbr nb;
   const unsigned* perm;   // sorted -> caller index
   int n;
   Phys ph;
@@ -146,12 +146,18 @@ __device__ __forceinline__ void dens_item(const DensArgs& a, const DensOp& op, c
   int flag = 0;
   bool step_again = false;
   float hn = I.h;
+  // h cap of the item: the cell's, or its leaf's with adaptive leaves
+  float hcap = g.hcap;
+  int cap_flag = cell_cap_flag(g);
+  if (a.nb.adaptive) {
+    hcap = a.nb.leaf_hcap[it.cell];
+    if (hcap < g.hcap) cap_flag = SWIFT_GPU_ERR_H_EXCEEDS_CELL;
+  }
   if (list_mode) {
-    const float Hc = a.ph.kg * g.hcap;
+    const float Hc = a.ph.kg * hcap;
     const float R2 = Hc * Hc + band_of(Hc, Lmax);
     bool ovf = false;
-    const int cnt = collect_item(g, a.cell_start, a.pos, it.cell, I.x, I.y, I.z, R2, lm.lsh, lm.s, lm.live, w,
-                                 ncand, ovf);
+    const int cnt = collect_item(g, a.nb, a.pos, it.cell, I.x, I.y, I.z, R2, lm.lsh, lm.s, lm.live, w, ncand, ovf);
     retry = lsum_u(ovf ? 1u : 0u, lm.lsh) != 0;
     bool done = !lm.live || retry;
     float lo = 0.0f, hi = __int_as_float(0x7f800000);
@@ -165,7 +171,7 @@ __device__ __forceinline__ void dens_item(const DensArgs& a, const DensOp& op, c
       if (!done) {
         if (lm.s == 0) nhiter += np;
         float h1;
-        if (newton_step(I.h, ns, nc, dn, lo, hi, g, a.ph, iter == a.ph.max_iter - 1, h1, flag))
+        if (newton_step(I.h, ns, nc, dn, lo, hi, hcap, cap_flag, a.ph, iter == a.ph.max_iter - 1, h1, flag))
           dens_set_h(I, h1, a.ph.kg, Lmax);
         else
           done = true;
@@ -174,7 +180,7 @@ __device__ __forceinline__ void dens_item(const DensArgs& a, const DensOp& op, c
     }
     flush(op, I, w, (lm.live && !retry) ? cnt : 0);  // full sums at the final h
   } else {
-    scan_item(op, I, g, a.cell_start, a.pos, it.cell, lm.lsh, lm.s, lm.live, w, ncand);
+    scan_item(op, I, g, a.nb, a.pos, it.cell, lm.lsh, lm.s, lm.live, w, ncand);
   }
   lsum2(I.ns, I.nc, lm.lsh);
   lsum2(I.rs, I.rc, lm.lsh);
@@ -191,9 +197,9 @@ __device__ __forceinline__ void dens_item(const DensArgs& a, const DensOp& op, c
       again = true;
     } else {
       ninter += I.count;
-      if (!list_mode) {
+      if (!list_mode && !a.single_pass) {  // NO_H_ITER: the sums at the given h, no Newton step
         float2 br = a.bracket[k];
-        step_again = newton_step(I.h, I.ns, I.nc, I.dn, br.x, br.y, g, a.ph, last, hn, flag);
+        step_again = newton_step(I.h, I.ns, I.nc, I.dn, br.x, br.y, hcap, cap_flag, a.ph, last, hn, flag);
         if (step_again) {
           a.h[k] = hn;
           a.bracket[k] = br;
@@ -252,9 +258,18 @@ __global__ void __launch_bounds__(kLoopThreads, 5) k_density(DensArgs a) {
       a.ngb[k] = a.ngb_out ? a.ngb_out[src] : 0u;
     }
   }
-  // ---- active work items, one warp per cell
-  for (int c = gwarp; c < g.ncells; c += nwarps) {
-    const int cs = a.cell_start[c], ce = a.cell_start[c + 1];
+  // ---- active work items, one warp per cell (or per leaf)
+  const int nunits = a.nb.adaptive ? *a.nb.n_leaves : g.ncells;
+  for (int c = gwarp; c < nunits; c += nwarps) {
+    int cs, ce;
+    if (a.nb.adaptive) {
+      const int2 r = a.nb.leaf_range[c];
+      cs = r.x;
+      ce = r.y;
+    } else {
+      cs = a.nb.cell_start[c];
+      ce = a.nb.cell_start[c + 1];
+    }
     if (ce == cs) continue;
     int total = 0;
     for (int b = cs; b < ce; b += 32) {
@@ -369,7 +384,7 @@ __global__ void k_ghost(int n, const unsigned* __restrict__ perm, const float4* 
 // ============================================================ gradient loop
 struct LoopArgs {
   Grid* grid;
-  const int* cell_start;
+  Nbr nb;
   const unsigned* perm;
   Phys ph;
   int lmax;
@@ -410,7 +425,7 @@ __device__ __forceinline__ void grad_item(const LoopArgs& a, const GradOp& op, c
   I.lap = 0.0f;
   I.count = 0;
   I.k = k;
-  scan_item(op, I, g, a.cell_start, a.pos, it.cell, lm.lsh, lm.s, lm.live, w, ncand);
+  scan_item(op, I, g, a.nb, a.pos, it.cell, lm.lsh, lm.s, lm.live, w, ncand);
   I.vsig = lmax(I.vsig, lm.lsh);
   I.lap = lsum(I.lap, lm.lsh);
   I.count = lsum_u(I.count, lm.lsh);
@@ -471,7 +486,7 @@ __device__ __forceinline__ void force_item(const LoopArgs& a, const ForceOp& op,
   I.axs = I.axc = I.ays = I.ayc = I.azs = I.azc = I.dus = I.duc = I.dh = 0.0f;
   I.count = 0;
   I.k = k;
-  scan_item(op, I, g, a.cell_start, a.pos, it.cell, lm.lsh, lm.s, lm.live, w, ncand);
+  scan_item(op, I, g, a.nb, a.pos, it.cell, lm.lsh, lm.s, lm.live, w, ncand);
   lsum2(I.axs, I.axc, lm.lsh);
   lsum2(I.ays, I.ayc, lm.lsh);
   lsum2(I.azs, I.azc, lm.lsh);
@@ -584,7 +599,7 @@ int density_impl(Ctx* c, const float4* pos_in, const float4* vel_in, const uint8
   cudaMemsetAsync(c->d_counters, 0, sizeof(int) * (size_t)(kCtrPerPass * (c->max_passes + 2) + 2), s);
   DensArgs a;
   a.grid = c->d_grid;
-  a.cell_start = c->d_cell_start;
+  a.nb = nbr_of(c);
   a.perm = c->d_vals[c->sorted_buf];
   a.n = c->n;
   a.ph = c->phys;
@@ -635,7 +650,7 @@ int ghost_impl(Ctx* c, const float* u, const float* alpha_v, const float* alpha_
 static LoopArgs loop_args(Ctx* c, int* ticket, void* out) {
   LoopArgs a;
   a.grid = c->d_grid;
-  a.cell_start = c->d_cell_start;
+  a.nb = nbr_of(c);
   a.perm = c->d_vals[c->sorted_buf];
   a.ph = c->phys;
   a.lmax = c->tuning.max_lanes_per_particle;

@@ -83,11 +83,13 @@ __device__ __forceinline__ void dens_set_h(DensOp::I& I, float h, float kg, floa
 // the compensated sum n = ns + nc and dn_acc = sum(3W + r dW/dr) at h.
 // Convergence |n h^3 - eta^3| <= h_tol eta^3 is tested in FP64 (no division);
 // the step itself, F' = dn/dh + 3 eta^3 / h^4 clamped to [h/2, 2h] with
-// bisection on the bracket [lo, hi], is FP32. Returns true with hn set when
-// another evaluation is needed; false when the particle is finished (flag 0:
-// converged; otherwise not converged / capped by the cell width).
+// bisection on the bracket [lo, hi], is FP32. h never exceeds hcap (the cell
+// or leaf cap); a particle that needs more is finished with flag cap_flag.
+// Returns true with hn set when another evaluation is needed; false when the
+// particle is finished (flag 0: converged; otherwise not converged / capped).
 __device__ __forceinline__ bool newton_step(float h, float ns, float nc, float dn_acc, float& lo, float& hi,
-                                            const Grid& g, const Phys& ph, bool last, float& hn, int& flag) {
+                                            float hcap, int cap_flag, const Phys& ph, bool last, float& hn,
+                                            int& flag) {
   flag = 0;
   const double hd = (double)h;
   const double h3 = hd * hd * hd;
@@ -99,8 +101,8 @@ __device__ __forceinline__ bool newton_step(float h, float ns, float nc, float d
   }
   if (G < 0.0) lo = fmaxf(lo, h);
   else hi = fminf(hi, h);
-  if (G < 0.0 && h >= g.hcap) {
-    flag = g.hcap_from_cells ? SWIFT_GPU_ERR_H_EXCEEDS_CELL : SWIFT_GPU_ERR_H_NOT_CONVERGED;
+  if (G < 0.0 && h >= hcap) {
+    flag = cap_flag;
     return false;
   }
   const float ih = 1.0f / h;
@@ -114,7 +116,7 @@ __device__ __forceinline__ bool newton_step(float h, float ns, float nc, float d
     else if (!isfinite(hi)) hn = 2.0f * h;
     else hn = 0.5f * h;
   }
-  hn = fminf(hn, g.hcap);
+  hn = fminf(hn, hcap);
   return hn != h;  // a float h that cannot move is as converged as FP32 allows
 }
 

@@ -137,7 +137,7 @@ __global__ void k_plain_dens_prologue(PlainDensState s) {
 }
 
 // The host's ghost task for the h iteration: one Newton step per particle.
-__global__ void k_plain_newton(PlainDensState s, int last) {
+__global__ void k_plain_newton(PlainDensState s, int last, int fixed_h) {
   const Grid g = *s.grid;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < s.n; k += gridDim.x * blockDim.x) {
     if (!s.need[k]) continue;
@@ -150,7 +150,7 @@ __global__ void k_plain_newton(PlainDensState s, int last) {
     float2 br = s.bracket[k];
     float hn = h;
     int flag = 0;
-    if (newton_step(h, ns, nc, dn, br.x, br.y, g, s.ph, last != 0, hn, flag)) {
+    if (!fixed_h && newton_step(h, ns, nc, dn, br.x, br.y, g.hcap, cell_cap_flag(g), s.ph, last != 0, hn, flag)) {
       s.h[k] = hn;
       s.bracket[k] = br;
       atomicAdd(s.remaining, 1);
@@ -426,7 +426,7 @@ int plain_density_impl(Ctx* c, const float4* pos_in, const float4* vel_in, const
     for (const Task& t : tasks) k_plain_dens<<<1, kTaskThreads, 0, s>>>(a, op, t);
     c->launches += tasks.size();
     cudaMemsetAsync(st.remaining, 0, sizeof(int), s);
-    k_plain_newton<<<nb, 256, 0, s>>>(st, pass == max_pass - 1);
+    k_plain_newton<<<nb, 256, 0, s>>>(st, pass == max_pass - 1, (c->params.flags & SWIFT_GPU_NO_H_ITER) ? 1 : 0);
     c->launches++;
     if (cudaMemcpyAsync(&remaining, st.remaining, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)

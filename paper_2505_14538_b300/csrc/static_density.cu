@@ -109,7 +109,7 @@ extern "C" int swift_gpu_density_static(const swift_gpu_params* p, const float* 
   Ctx c;  // on the stack: no host allocation either
   if (phys_from(p, &c.phys) != SWIFT_GPU_OK) return SWIFT_GPU_ERR_ARG;
   c.params = *p;
-  if (c.params.flags & SWIFT_GPU_PLAIN) return SWIFT_GPU_ERR_ARG;
+  if (c.params.flags & (SWIFT_GPU_PLAIN | SWIFT_GPU_ADAPTIVE)) return SWIFT_GPU_ERR_ARG;
   if (cudaGetDevice(&c.device) != cudaSuccess || c.device < 0 || c.device >= kMaxDevices) return SWIFT_GPU_ERR_CUDA;
   if (cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, c.device) != cudaSuccess)
     return SWIFT_GPU_ERR_CUDA;

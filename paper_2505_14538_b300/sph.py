@@ -170,7 +170,20 @@ class Context:
         _check(self.lib.swift_gpu_get_info(self.handle, ctypes.byref(i)), "swift_gpu_get_info")
         return dict(n=i.n, nc=tuple(i.nc), cell_width=tuple(i.cell_width), h_cap=i.h_cap, n_cells=i.n_cells,
                     n_items=i.n_items, density_passes=i.density_passes, interactions=tuple(i.interactions),
-                    candidates=tuple(i.candidates), launches=i.launches, h_iteration_pairs=i.h_iteration_pairs)
+                    candidates=tuple(i.candidates), launches=i.launches, h_iteration_pairs=i.h_iteration_pairs,
+                    n_leaves=i.n_leaves, leaf_pairs=i.leaf_pairs, tree_depth=i.tree_depth)
+
+    def leaves(self, stream=None):
+        """Adaptive builds: (range (L, 2) int32 sorted [first, end), h_cap (L,), nbr_count (L,)) on the device."""
+        nl = self.info()["n_leaves"]
+        dev = torch.device("cuda", torch.cuda.current_device())
+        rng = torch.empty((nl, 2), dtype=torch.int32, device=dev)
+        hcap = torch.empty(nl, dtype=_F32, device=dev)
+        cnt = torch.empty(nl, dtype=torch.int32, device=dev)
+        if nl:
+            _check(self.lib.swift_gpu_get_leaves(self.handle, _ptr(rng), _ptr(hcap), _ptr(cnt), ctypes.c_int64(nl),
+                                                 _stream(stream)), "swift_gpu_get_leaves")
+        return rng, hcap, cnt
 
     def cells(self, stream=None):
         n = self.n
@@ -201,9 +214,12 @@ class Context:
         """build_cells -> density (h iteration) -> gradient -> force on one stream.
 
         With check=True the status word is read after the density call (a
-        host synchronisation); while the h iteration asks for a support wider
-        than a cell, the cells are rebuilt twice as wide (up to a third of the
-        box) and the density call is repeated from the same starting h.
+        host synchronisation). While the h iteration asks for a support wider
+        than its cap, the density call is repeated: on the uniform grid with
+        cells twice as wide (up to a third of the box) from the same starting
+        h; with adaptive leaves from the capped h, the leaves rebuilt around
+        it (their caps grow by 1 + leaf_margin), and with wider cells only
+        when h reached the cell cap.
         """
         self.build_cells(pos_h, min_cell_width, stream)
         d = self.density(pos_h, vel_m, active, rho4=rho4, curl_div=curl_div, stream=stream)
@@ -211,10 +227,23 @@ class Context:
             code, detail = self.sync_status()
             width = max(self.info()["cell_width"])
             box_third = min(float(b) for b in self.params.box) / 3.0
-            while code == _lib.ERR_H_EXCEEDS_CELL and width < box_third:
-                width = min(2.0 * width, box_third)
-                self.build_cells(pos_h, max(min_cell_width, width), stream)
-                d = self.density(pos_h, vel_m, active, rho4=rho4, curl_div=curl_div, stream=stream)
+            adaptive = bool(self.params.flags & _lib.FLAG_ADAPTIVE)
+            pos_cur = pos_h
+            for _ in range(32):
+                if code != _lib.ERR_H_EXCEEDS_CELL:
+                    break
+                at_cell_cap = float(d["h"].max()) >= 0.999 * self.info()["h_cap"]
+                if at_cell_cap or not adaptive:
+                    if width >= box_third:
+                        break
+                    width = min(2.0 * width, box_third)
+                if adaptive:
+                    pos_cur = pos_cur.clone()
+                    pos_cur[:, 3] = d["h"]
+                self.build_cells(pos_cur, max(min_cell_width, width) if (at_cell_cap or not adaptive) else
+                                 min_cell_width, stream)
+                width = max(width, max(self.info()["cell_width"]))
+                d = self.density(pos_cur, vel_m, active, rho4=rho4, curl_div=curl_div, stream=stream)
                 code, detail = self.sync_status()
             if code not in (_lib.OK, _lib.ERR_H_NOT_CONVERGED):
                 raise SwiftGPUError(code, "density", detail)
