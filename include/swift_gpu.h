@@ -80,7 +80,7 @@ typedef struct {
 /* Work-distribution knobs (chosen by swift_gpu_autotune, or set by hand). */
 typedef struct {
   int threads_per_block; /* 64..1024, multiple of 32 */
-  int max_lanes_per_particle; /* 1, 2, 4 or 8: lanes that share one particle's neighbour scan */
+  int max_lanes_per_particle; /* 1, 2, 4, 8, 16 or 32: lanes that share one particle's neighbour scan */
   int blocks_per_sm;     /* persistent blocks per SM (0 = occupancy maximum) */
 } swift_gpu_tuning;
 
@@ -105,11 +105,11 @@ typedef struct swift_gpu_ctx swift_gpu_ctx;
 
 /* Fill *p with the defaults (unit box, gamma 5/3, eta 1.2348, kernel_gamma
  * 1.825742, alpha_v 1, beta_v 3, alpha_c 1, h_tol 1e-4, max_iter 30, h_max 0,
- * cell_margin 0.05, flags 0, leaf_max 32, leaf_margin 0.25). Host only; never fails. */
+ * cell_margin 0.05, flags 0, leaf_max 32, leaf_margin 0.1). Host only; never fails. */
 void swift_gpu_default_params(swift_gpu_params* p);
 
 /* Create a context for up to n_max particles on the current CUDA device.
- * Allocates every device buffer the calls need (about 650 bytes per particle
+ * Allocates every device buffer the calls need (about 600 bytes per particle
  * plus the cell arrays, the adaptive tree and leaf lists included), so no later call allocates. *ctx is owned by the
  * caller and freed with swift_gpu_destroy. Errors: ERR_ARG (null/invalid
  * params, n_max < 1 or > 2^26), ERR_NOMEM, ERR_CUDA. */
@@ -139,8 +139,10 @@ int swift_gpu_set_params(swift_gpu_ctx* ctx, const swift_gpu_params* p);
  * every leaf (with periodic image) whose bounding box comes within the
  * larger of the two leaves' supports kernel_gamma * h_cap. Capacities:
  * 2 n_max tree nodes beyond the cells (a node that would exceed them stays a
- * leaf) and 48 n_max list entries (a leaf whose list would end past them
+ * leaf) and max(48 n_max, 2^22) list entries (a leaf whose list would end past them
  * scans the 27 neighbour cells of its cell instead); both keep results exact.
+ * Where the lists lie in the store is unspecified; each list's order is
+ * fixed by the tree, so results do not depend on it.
  * With ADAPTIVE at most 256 cells per axis are used. */
 int swift_gpu_build_cells(swift_gpu_ctx* ctx, const float* pos_h, int64_t n, float min_cell_width,
                           void* stream);
@@ -227,7 +229,9 @@ int swift_gpu_get_cells(swift_gpu_ctx* ctx, uint32_t* cell_id, uint32_t* perm, v
  * leaf l (sorted positions are those of swift_gpu_get_cells' perm),
  * h_cap[l] = the largest h its particles may take before the h iteration
  * reports ERR_H_EXCEEDS_CELL, nbr_count[l] = length of its neighbour-leaf
- * list (itself included). Any pointer may be NULL. Leaves l < max_leaves are
+ * list (itself included), or -1 when the leaf has no list (the list store
+ * was full, or the tree walk ran out of its stack) and its particles scan
+ * the 27 neighbour cells of their cell instead. Any pointer may be NULL. Leaves l < max_leaves are
  * copied; the leaf count is swift_gpu_info.n_leaves. The order of the leaves
  * is unspecified. Errors: ERR_ORDER (no adaptive build), ERR_ARG. Asynchronous. */
 int swift_gpu_get_leaves(swift_gpu_ctx* ctx, int32_t* range, float* h_cap, int32_t* nbr_count, int64_t max_leaves,

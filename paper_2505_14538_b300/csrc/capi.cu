@@ -59,8 +59,8 @@ static void free_all(Ctx* c) {
                   c->d_bracket, c->d_ngb, c->d_ga, c->d_gb, c->d_act, c->d_items0, c->d_plist0, c->d_items[0],
                   c->d_items[1], c->d_plist[0], c->d_plist[1], c->d_counters, c->d_stats, c->d_red_partial,
                   c->d_scratch4[0], c->d_scratch1[0], c->d_scratch1[1], c->d_plain_act, c->d_aux[0], c->d_aux[1],
-                  c->d_node_range, c->d_node_kids, c->d_node_lo, c->d_node_hi, c->d_node_leaf, c->d_leaf_range,
-                  c->d_leaf_hcap, c->d_leaf_node, c->d_nbr_off, c->d_nbr, c->d_tree_ctr};
+                  c->d_node_range, c->d_node, c->d_node_link, c->d_node_parent, c->d_node_done, c->d_node_flag,
+                  c->d_leaf_range, c->d_leaf_hcap, c->d_leaf_node, c->d_nbr_span, c->d_nbr, c->d_tree_ctr};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_status) cudaFreeHost(c->h_status);
@@ -88,7 +88,7 @@ void swift_gpu_default_params(swift_gpu_params* p) {
   p->cell_margin = 0.05f;
   p->flags = 0;
   p->leaf_max = 32;
-  p->leaf_margin = 0.25f;
+  p->leaf_margin = 0.1f;
 }
 
 int swift_gpu_create(swift_gpu_ctx** out, const swift_gpu_params* p, int64_t n_max) {
@@ -109,7 +109,7 @@ int swift_gpu_create(swift_gpu_ctx** out, const swift_gpu_params* p, int64_t n_m
     return SWIFT_GPU_ERR_CUDA;
   }
   c->tuning.threads_per_block = 256;
-  c->tuning.max_lanes_per_particle = 8;
+  c->tuning.max_lanes_per_particle = 32;
   c->tuning.blocks_per_sm = 0;
   int nc_cap = (int)floor(cbrt(2.0 * (double)n_max));
   if (nc_cap < 3) nc_cap = 3;
@@ -123,7 +123,6 @@ int swift_gpu_create(swift_gpu_ctx** out, const swift_gpu_params* p, int64_t n_m
   const int64_t n = n_max;
   const int64_t nb = (n + 4095) / 4096;
   int64_t scan_m = 256 * nb > ncells_max + 1 ? 256 * nb : ncells_max + 1;
-  if (scan_m < n + 1) scan_m = n + 1;  // leaf-list offsets
   // adaptive tree: cells (at most kAdaptiveNcCap^3 of them) plus 2 nodes per
   // particle, all addressable with kIndexBits; leaves are disjoint and non-empty
   const int64_t acells = ncells_max < (int64_t)kAdaptiveNcCap * kAdaptiveNcCap * kAdaptiveNcCap
@@ -132,7 +131,9 @@ int swift_gpu_create(swift_gpu_ctx** out, const swift_gpu_params* p, int64_t n_m
   const int64_t node_cap = acells + 2 * n < (int64_t)kIndexMask ? acells + 2 * n : (int64_t)kIndexMask;
   c->node_cap = (int)node_cap;
   c->leaf_cap = (int)n;
-  c->nbr_cap = (int)(48 * n < (int64_t)INT32_MAX ? 48 * n : (int64_t)INT32_MAX);
+  if (scan_m < node_cap + 1) scan_m = node_cap + 1;  // leaf flags of the tree nodes
+  int64_t nbr_cap = 48 * n > ((int64_t)1 << 22) ? 48 * n : ((int64_t)1 << 22);  // at least 16 MB of lists
+  c->nbr_cap = (int)(nbr_cap < (int64_t)INT32_MAX ? nbr_cap : (int64_t)INT32_MAX);
   c->red_blocks = c->num_sms * 32;
   bool ok = dalloc(&c->d_status, 1) && dalloc(&c->d_grid, 1) && dalloc(&c->d_hmax_bits, 1) &&
             dalloc(&c->d_keys[0], n) && dalloc(&c->d_keys[1], n) && dalloc(&c->d_vals[0], n) &&
@@ -146,10 +147,11 @@ int swift_gpu_create(swift_gpu_ctx** out, const swift_gpu_params* p, int64_t n_m
             dalloc(&c->d_stats, kStatCount) && dalloc(&c->d_red_partial, 8 * (size_t)c->red_blocks) &&
             dalloc(&c->d_scratch4[0], 4 * n) && dalloc(&c->d_scratch1[0], n) && dalloc(&c->d_scratch1[1], n) &&
             dalloc(&c->d_plain_act, n) && dalloc(&c->d_aux[0], n) && dalloc(&c->d_aux[1], n) &&
-            dalloc(&c->d_node_range, node_cap) && dalloc(&c->d_node_kids, node_cap) &&
-            dalloc(&c->d_node_lo, node_cap) && dalloc(&c->d_node_hi, node_cap) && dalloc(&c->d_node_leaf, node_cap) &&
+            dalloc(&c->d_node_range, node_cap) && dalloc(&c->d_node, 2 * node_cap) &&
+            dalloc(&c->d_node_link, node_cap) && dalloc(&c->d_node_parent, node_cap) &&
+            dalloc(&c->d_node_done, node_cap) && dalloc(&c->d_node_flag, node_cap + 1) &&
             dalloc(&c->d_leaf_range, n) && dalloc(&c->d_leaf_hcap, n) && dalloc(&c->d_leaf_node, n) &&
-            dalloc(&c->d_nbr_off, n + 1) && dalloc(&c->d_nbr, (size_t)c->nbr_cap) &&
+            dalloc(&c->d_nbr_span, n) && dalloc(&c->d_nbr, (size_t)c->nbr_cap) &&
             dalloc(&c->d_tree_ctr, kTreeCtrCount) &&
             cudaMallocHost((void**)&c->h_status, sizeof(Status)) == cudaSuccess &&
             cudaMallocHost((void**)&c->h_stats, sizeof(unsigned long long) * kStatCount) == cudaSuccess;
@@ -370,7 +372,8 @@ int swift_gpu_set_tuning(swift_gpu_ctx* h, const swift_gpu_tuning* t) {
   Ctx* c = from(h);
   if (!c || !t) return SWIFT_GPU_ERR_ARG;
   const int l = t->max_lanes_per_particle;
-  if (t->threads_per_block != 256 || !(l == 1 || l == 2 || l == 4 || l == 8) || t->blocks_per_sm < 0)
+  if (t->threads_per_block != 256 || !(l == 1 || l == 2 || l == 4 || l == 8 || l == 16 || l == 32) ||
+      t->blocks_per_sm < 0)
     return SWIFT_GPU_ERR_ARG;
   c->tuning = *t;
   return SWIFT_GPU_OK;

@@ -212,9 +212,10 @@ __global__ void k_cell_ids(const float4* __restrict__ pos_h, int n, const Grid* 
     const unsigned cell = (unsigned)(cx + nx * (cy + ny * cz));
     if (cell_out) {
       // position inside the cell in units of 1/1024 of its width
-      const unsigned qx = (unsigned)min(max((tx - cx) * 1024.0, 0.0), 1023.0);
-      const unsigned qy = (unsigned)min(max((ty - cy) * 1024.0, 0.0), 1023.0);
-      const unsigned qz = (unsigned)min(max((tz - cz) * 1024.0, 0.0), 1023.0);
+      // (the fraction is exact in FP64; its FP32 rounding only orders particles)
+      const unsigned qx = (unsigned)fminf(fmaxf((float)(tx - cx) * 1024.0f, 0.0f), 1023.0f);
+      const unsigned qy = (unsigned)fminf(fmaxf((float)(ty - cy) * 1024.0f, 0.0f), 1023.0f);
+      const unsigned qz = (unsigned)fminf(fmaxf((float)(tz - cz) * 1024.0f, 0.0f), 1023.0f);
       const unsigned m = spread3(qx) | (spread3(qy) << 1) | (spread3(qz) << 2);
       keys[i] = m;
       morton_out[i] = m;

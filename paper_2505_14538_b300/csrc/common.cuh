@@ -70,7 +70,7 @@ struct Nbr {
   const int* cell_start;
   const unsigned* skeys;    // sorted cell ids
   const int2* leaf_range;   // [first, end) sorted positions of each leaf
-  const int* nbr_off;       // exclusive offsets of the leaf lists
+  const int2* nbr_span;     // (first entry, length) of each leaf's list
   const unsigned* nbr;      // leaf index | shift code << kIndexBits
   const float* leaf_hcap;   // largest h the particles of a leaf may take
   const int* n_leaves;      // device count of leaves
@@ -86,7 +86,8 @@ enum TreeCtr {
   kTreeNodes = 0,                   // [0 .. kTreeLevels]: nodes created at each level
   kTreeLeaves = kTreeLevels + 1,    // leaf count
   kTreeDepth,                       // deepest level holding a leaf
-  kTreeEntries,                     // total entries of the leaf lists
+  kTreeEntries,                     // total entries of the leaf lists (reserved by the walk)
+  kTreeTicket,                      // walk work tickets
   kTreeCtrCount = 16
 };
 

@@ -18,8 +18,8 @@
 //             arithmetic runs on converged lanes instead of diverging on the
 //             ~15 % hit rate of a 27-cell scan.
 //
-// With few particles in an item, L = 2, 4 or 8 lanes share one particle and
-// split its candidates.
+// With few particles in an item, L = 2, 4, 8, 16 or 32 lanes share one
+// particle and split its candidates.
 #pragma once
 
 #include "common.cuh"
@@ -40,7 +40,7 @@ struct WarpSmem {
 
 // log2 of the lanes per particle for an item of cnt particles (L = 2^lsh <= lmax).
 __device__ __forceinline__ int lanes_shift(int cnt, int lmax) {
-  int lsh = cnt <= 4 ? 3 : cnt <= 8 ? 2 : cnt <= 16 ? 1 : 0;
+  int lsh = cnt <= 1 ? 5 : cnt <= 2 ? 4 : cnt <= 4 ? 3 : cnt <= 8 ? 2 : cnt <= 16 ? 1 : 0;
   while ((1 << lsh) > lmax) --lsh;
   return lsh;
 }
@@ -61,10 +61,10 @@ __device__ __forceinline__ Segs item_segments(const Nbr& nb, int item_cell) {
   q.nseg = 27;
   q.list = false;
   if (nb.adaptive) {
-    const int b = nb.nbr_off[item_cell], e = nb.nbr_off[item_cell + 1];
-    if (e <= nb.nbr_cap) {
-      q.list_off = b;
-      q.nseg = e - b;
+    const int2 sp = nb.nbr_span[item_cell];
+    if (sp.y <= nb.nbr_cap - sp.x) {
+      q.list_off = sp.x;
+      q.nseg = sp.y;
       q.list = true;
     } else {
       q.cell = (int)nb.skeys[nb.leaf_range[item_cell].x];

@@ -78,14 +78,15 @@ struct Ctx {
   int node_cap = 0, leaf_cap = 0, nbr_cap = 0;
   unsigned* d_aux[2] = {nullptr, nullptr};  // caller order: cell id, Morton code inside the cell
   int2* d_node_range = nullptr;  // [first, end) sorted positions
-  int2* d_node_kids = nullptr;   // (first child, child count); 0 children: leaf or empty
-  float4* d_node_lo = nullptr;   // (bounding box low corner, reach kernel_gamma * h_cap)
-  float4* d_node_hi = nullptr;   // (bounding box high corner, h_cap)
-  int* d_node_leaf = nullptr;    // leaf index of a leaf node, -1 otherwise
+  float4* d_node = nullptr;      // 2 per node: (box low corner, reach kernel_gamma * h_cap), (box high corner, link)
+  int* d_node_link = nullptr;    // link word of each node while the tree is built
+  int* d_node_parent = nullptr;  // parent node (-1 for cells)
+  int* d_node_done = nullptr;    // children finished (bottom-up pass)
+  unsigned* d_node_flag = nullptr;  // leaf flags, then their exclusive scan (node_cap + 1)
   int2* d_leaf_range = nullptr;
   float* d_leaf_hcap = nullptr;
   int* d_leaf_node = nullptr;
-  int* d_nbr_off = nullptr;      // leaf list lengths, then their exclusive offsets (leaf_cap + 1)
+  int2* d_nbr_span = nullptr;    // per leaf: (first list entry, list length)
   unsigned* d_nbr = nullptr;     // leaf index | shift code << kIndexBits
   int* d_tree_ctr = nullptr;     // TreeCtr
 

@@ -4,17 +4,20 @@
 // order:
 //
 //   k_tree_gather  sorted positions and Morton codes
-//   k_tree_level   one launch per level (cells are level 0, at most
-//                  kTreeLevels below): one warp per node reduces its
-//                  particles' bounding box and largest h; a node with more
-//                  than leaf_max particles is split into its non-empty
-//                  octants (binary search of the level's Morton digit inside
-//                  the node's range), any other node is a leaf
+//   k_tree_split   one launch per level (cells are level 0, at most
+//                  kTreeLevels below): a node with more than leaf_max
+//                  particles is split into its non-empty octants (binary
+//                  search of the level's Morton digit inside the node's
+//                  range), any other node is a leaf
+//   k_leaf_number  leaf indices from a scan of the leaf flags
+//   k_leaf_finish  one warp per leaf reduces its particles' bounding box and
+//                  largest h; the boxes and reaches of the inner nodes follow
+//                  bottom-up (the last child to finish completes its parent)
 //   k_leaf_walk    one warp per leaf walks the trees of the 27 neighbour
 //                  cells (periodic images included) with a shared-memory
 //                  stack, descends into nodes whose bounding box comes within
 //                  the larger reach (kernel_gamma * h_cap) of the two sides,
-//                  and counts (pass 0) or writes (pass 1) its neighbour leaves
+//                  and writes its neighbour leaves as one contiguous list
 //
 // Every pair that any loop may need is covered: a pair (i, j) is a candidate
 // only when its FP32 r^2 is below max(H_i, H_j)^2 plus the guard band, and
@@ -32,10 +35,15 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kTreeThreads = 256;
 constexpr int kWalkThreads = 128;
 constexpr int kWalkWarps = kWalkThreads / 32;
-// Walk stack per warp: 27 roots plus at most 32 * 8 children pushed per step
-// for each of the kTreeLevels + 1 depths that can lie on the stack at once.
-constexpr int kStack = 3072;
-static_assert(27 + (kTreeLevels + 1) * 256 <= kStack, "walk stack too small");
+// Walk stack per warp. A step pops P entries (one per lane) and pushes at
+// most 8 children for each. With g = kStack - (entries on the stack): while
+// g >= kDfsGap, P = min(32, (g - 80) / 7), so at least 80 entries stay free;
+// below that P = 1, a depth-first walk, which adds at most 7 entries for
+// each of the kTreeLevels levels (70 < 80) before it unwinds. The stack thus
+// never overflows; the overflow guard below only backs that bound up.
+constexpr int kStack = 1024;
+constexpr int kDfsGap = 87;
+static_assert(kStack >= 27 + kDfsGap, "walk stack too small for its roots");
 
 __global__ void k_tree_gather(const float4* __restrict__ pos_h, const unsigned* __restrict__ perm,
                               const unsigned* __restrict__ morton, int n, float4* __restrict__ pos,
@@ -53,10 +61,11 @@ struct TreeArgs {
   const unsigned* mk;      // sorted Morton codes inside the cell
   const int* cell_start;
   int2* node_range;
-  int2* node_kids;
-  float4* node_lo;
-  float4* node_hi;
-  int* node_leaf;
+  float4* node;            // 2 per node: (low corner, reach), (high corner, link)
+  int* node_link;
+  int* node_parent;
+  int* node_done;
+  unsigned* node_flag;     // 1 for a leaf (then its exclusive scan: the leaf index)
   int2* leaf_range;
   float* leaf_hcap;
   int* leaf_node;
@@ -67,58 +76,52 @@ struct TreeArgs {
   float kg;
 };
 
-__global__ void __launch_bounds__(kTreeThreads) k_tree_level(TreeArgs a, int level) {
+// Link word of a node (the w of its second float4, as int bits): child
+// count << 27 | first child for an inner node, the leaf index for a leaf
+// (child count 0); kEmptyLink for an empty cell.
+constexpr int kLinkShift = 27;
+constexpr int kLinkMask = (1 << kLinkShift) - 1;
+constexpr int kEmptyLink = 0x7fffffff;
+constexpr int kLeafMark = -1;
+static_assert(kIndexBits <= kLinkShift, "node and leaf indices must fit the link word");
+
+// Top-down, one launch per level: split decisions from the particle counts
+// alone (no particle is read but the Morton codes of the binary searches).
+__global__ void __launch_bounds__(kTreeThreads) k_tree_split(TreeArgs a, int level) {
   const unsigned lane = lane_id();
   const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   const Grid& g = *a.grid;
-  const float hcap_cell = g.hcap;
   int begin = 0;
   for (int m = 0; m < level; ++m) begin += m == 0 ? g.ncells : a.tctr[kTreeNodes + m];
   int size = level == 0 ? g.ncells : a.tctr[kTreeNodes + level];
   size = min(size, a.node_cap - begin);  // nodes past the capacity were never created
   const int next_begin = begin + size;
   const float inf = __int_as_float(0x7f800000);
+  bool made_leaf = false;
   for (int i = gwarp; i < size; i += nwarps) {
     const int v = begin + i;
     int s, e;
     if (level == 0) {
       s = a.cell_start[v];
       e = a.cell_start[v + 1];
-      if (lane == 0) a.node_range[v] = make_int2(s, e);
+      if (lane == 0) {
+        a.node_range[v] = make_int2(s, e);
+        a.node_parent[v] = -1;
+      }
     } else {
       const int2 r = a.node_range[v];
       s = r.x;
       e = r.y;
     }
-    if (e == s) {  // empty cell (children are never empty)
+    if (e == s) {  // empty cell, or a slot left by a node that ran out of capacity
       if (lane == 0) {
-        a.node_lo[v] = make_float4(inf, inf, inf, 0.0f);
-        a.node_hi[v] = make_float4(-inf, -inf, -inf, 0.0f);
-        a.node_kids[v] = make_int2(0, 0);
-        a.node_leaf[v] = -1;
+        a.node[2 * v] = make_float4(inf, inf, inf, 0.0f);
+        a.node[2 * v + 1] = make_float4(-inf, -inf, -inf, __int_as_float(kEmptyLink));
+        a.node_link[v] = kEmptyLink;
       }
       continue;
     }
-    float lx = inf, ly = inf, lz = inf, hx = -inf, hy = -inf, hz = -inf, hm = 0.0f;
-    for (int k = s + (int)lane; k < e; k += 32) {
-      const float4 p = a.pos[k];
-      lx = fminf(lx, p.x); ly = fminf(ly, p.y); lz = fminf(lz, p.z);
-      hx = fmaxf(hx, p.x); hy = fmaxf(hy, p.y); hz = fmaxf(hz, p.z);
-      hm = fmaxf(hm, p.w);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      lx = fminf(lx, __shfl_xor_sync(kFull, lx, o));
-      ly = fminf(ly, __shfl_xor_sync(kFull, ly, o));
-      lz = fminf(lz, __shfl_xor_sync(kFull, lz, o));
-      hx = fmaxf(hx, __shfl_xor_sync(kFull, hx, o));
-      hy = fmaxf(hy, __shfl_xor_sync(kFull, hy, o));
-      hz = fmaxf(hz, __shfl_xor_sync(kFull, hz, o));
-      hm = fmaxf(hm, __shfl_xor_sync(kFull, hm, o));
-    }
-    const float hcap = fminf(hcap_cell, (1.0f + a.margin) * hm);
-    const float reach = a.kg * hcap;
     bool split = (e - s) > a.leaf_max && level < kTreeLevels;
     int cbase = 0, nch = 0;
     if (split) {
@@ -147,24 +150,107 @@ __global__ void __launch_bounds__(kTreeThreads) k_tree_level(TreeArgs a, int lev
         for (int t = (int)lane; t < nch; t += 32)
           if (cbase + t < a.node_cap) a.node_range[cbase + t] = make_int2(s, s);
       } else if (nonempty) {
-        a.node_range[cbase + __popc(m & ((1u << lane) - 1u))] = make_int2(lb, nxt);
+        const int c = cbase + __popc(m & ((1u << lane) - 1u));
+        a.node_range[c] = make_int2(lb, nxt);
+        a.node_parent[c] = v;
       }
     }
     if (lane == 0) {
-      a.node_lo[v] = make_float4(lx, ly, lz, reach);
-      a.node_hi[v] = make_float4(hx, hy, hz, hcap);
-      if (split) {
-        a.node_kids[v] = make_int2(cbase, nch);
-        a.node_leaf[v] = -1;
-      } else {
-        const int li = atomicAdd(&a.tctr[kTreeLeaves], 1);  // leaves are disjoint and non-empty: li < n
-        a.leaf_range[li] = make_int2(s, e);
-        a.leaf_hcap[li] = hcap;
-        a.leaf_node[li] = v;
-        a.node_kids[v] = make_int2(0, 0);
-        a.node_leaf[v] = li;
-        atomicMax(&a.tctr[kTreeDepth], level);
+      a.node_link[v] = split ? ((nch << kLinkShift) | cbase) : kLeafMark;
+      a.node_flag[v] = split ? 0u : 1u;
+    }
+    made_leaf |= !split;
+  }
+  if (lane == 0 && made_leaf && *((volatile int*)&a.tctr[kTreeDepth]) < level) atomicMax(&a.tctr[kTreeDepth], level);
+}
+
+// Leaf index of every leaf node from the exclusive scan of the leaf flags.
+__global__ void k_leaf_number(const unsigned* __restrict__ scan, int node_cap, int* __restrict__ node_link,
+                              int* __restrict__ leaf_node, int* __restrict__ tctr) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < node_cap; v += gridDim.x * blockDim.x) {
+    const unsigned li = scan[v];
+    if (scan[v + 1] != li) {
+      leaf_node[li] = v;
+      node_link[v] = (int)li;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) tctr[kTreeLeaves] = (int)scan[node_cap];
+}
+
+// One warp per leaf: bounding box and largest h of its particles; then up
+// the tree, the last child to finish writes its parent's box (the union of
+// the children's) and reach (the largest of theirs), and carries on.
+__global__ void __launch_bounds__(kTreeThreads) k_leaf_finish(TreeArgs a) {
+  const unsigned lane = lane_id();
+  const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const float hcap_cell = a.grid->hcap;
+  const float inf = __int_as_float(0x7f800000);
+  const int nleaves = a.tctr[kTreeLeaves];
+  for (int li = gwarp; li < nleaves; li += nwarps) {
+    int v = a.leaf_node[li];
+    const int2 r = a.node_range[v];
+    float lx = inf, ly = inf, lz = inf, hx = -inf, hy = -inf, hz = -inf, hm = 0.0f;
+    for (int k = r.x + (int)lane; k < r.y; k += 32) {
+      const float4 p = a.pos[k];
+      lx = fminf(lx, p.x); ly = fminf(ly, p.y); lz = fminf(lz, p.z);
+      hx = fmaxf(hx, p.x); hy = fmaxf(hy, p.y); hz = fmaxf(hz, p.z);
+      hm = fmaxf(hm, p.w);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lx = fminf(lx, __shfl_xor_sync(kFull, lx, o));
+      ly = fminf(ly, __shfl_xor_sync(kFull, ly, o));
+      lz = fminf(lz, __shfl_xor_sync(kFull, lz, o));
+      hx = fmaxf(hx, __shfl_xor_sync(kFull, hx, o));
+      hy = fmaxf(hy, __shfl_xor_sync(kFull, hy, o));
+      hz = fmaxf(hz, __shfl_xor_sync(kFull, hz, o));
+      hm = fmaxf(hm, __shfl_xor_sync(kFull, hm, o));
+    }
+    const float hcap = fminf(hcap_cell, (1.0f + a.margin) * hm);
+    if (lane == 0) {
+      a.leaf_range[li] = r;
+      a.leaf_hcap[li] = hcap;
+      a.node[2 * v] = make_float4(lx, ly, lz, a.kg * hcap);
+      a.node[2 * v + 1] = make_float4(hx, hy, hz, __int_as_float(li));
+    }
+    for (;;) {
+      int p = -1, done = 0, link = 0;
+      if (lane == 0) {
+        p = a.node_parent[v];
+        if (p >= 0) {
+          __threadfence();  // this node's record before the count
+          done = atomicAdd(&a.node_done[p], 1);
+          link = a.node_link[p];
+        }
       }
+      p = __shfl_sync(kFull, p, 0);
+      done = __shfl_sync(kFull, done, 0);
+      link = __shfl_sync(kFull, link, 0);
+      const int nch = link >> kLinkShift;
+      if (p < 0 || done != nch - 1) break;  // a sibling is still running: it finishes the parent
+      __threadfence();
+      const int first = link & kLinkMask;
+      float4 cl = make_float4(inf, inf, inf, 0.0f), ch = make_float4(-inf, -inf, -inf, 0.0f);
+      if ((int)lane < nch) {
+        cl = __ldcg(&a.node[2 * (first + (int)lane)]);  // from L2: written by other warps
+        ch = __ldcg(&a.node[2 * (first + (int)lane) + 1]);
+      }
+#pragma unroll
+      for (int o = 4; o > 0; o >>= 1) {
+        cl.x = fminf(cl.x, __shfl_xor_sync(kFull, cl.x, o));
+        cl.y = fminf(cl.y, __shfl_xor_sync(kFull, cl.y, o));
+        cl.z = fminf(cl.z, __shfl_xor_sync(kFull, cl.z, o));
+        cl.w = fmaxf(cl.w, __shfl_xor_sync(kFull, cl.w, o));
+        ch.x = fmaxf(ch.x, __shfl_xor_sync(kFull, ch.x, o));
+        ch.y = fmaxf(ch.y, __shfl_xor_sync(kFull, ch.y, o));
+        ch.z = fmaxf(ch.z, __shfl_xor_sync(kFull, ch.z, o));
+      }
+      if (lane == 0) {
+        a.node[2 * p] = cl;
+        a.node[2 * p + 1] = make_float4(ch.x, ch.y, ch.z, __int_as_float(link));
+      }
+      v = p;
     }
   }
 }
@@ -172,114 +258,144 @@ __global__ void __launch_bounds__(kTreeThreads) k_tree_level(TreeArgs a, int lev
 struct WalkArgs {
   const Grid* grid;
   const unsigned* skeys;   // sorted cell ids
-  const int2* node_kids;
-  const float4* node_lo;
-  const float4* node_hi;
-  const int* node_leaf;
+  const float4* node;
   const int2* leaf_range;
   const int* leaf_node;
-  const int* tctr;
-  int* nbr_off;            // pass 0: counts out; pass 1: offsets in
+  int* tctr;               // list entries reserved so far at kTreeEntries, tickets at kTreeTicket
+  int2* nbr_span;          // per leaf: (first entry, length)
   unsigned* nbr;
   int nbr_cap;
-  Status* st;
 };
 
-__global__ void __launch_bounds__(kWalkThreads) k_leaf_walk(WalkArgs a, int fill) {
-  __shared__ unsigned stack_all[kWalkWarps][kStack];
-  unsigned* st = stack_all[threadIdx.x >> 5];
+constexpr int kOutBuf = 512;      // list entries a warp keeps in shared memory before reserving
+constexpr int kWalkChunk = 8;     // leaves per ticket
+constexpr size_t kWalkSmemBytes = sizeof(unsigned) * kWalkWarps * (kStack + kOutBuf);
+
+// Walk of the trees around leaf li: every leaf (with periodic image) whose
+// box comes within the larger reach; entry t of the list goes to out[t] when
+// t < out_cap. Returns the list length; `overflow` when the stack ran out.
+__device__ __forceinline__ int walk_leaf(const WalkArgs& a, const Grid& g, int li, unsigned* st, unsigned* out,
+                                         int out_cap, bool& overflow) {
   const unsigned lane = lane_id();
-  const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  const Grid& g = *a.grid;
   const float L[3] = {g.L[0], g.L[1], g.L[2]};
   const float Lmax = fmaxf(L[0], fmaxf(L[1], L[2]));
   const int nx = g.nc[0], ny = g.nc[1], nz = g.nc[2];
-  const int nleaves = a.tctr[kTreeLeaves];
-  for (int li = gwarp; li < nleaves; li += nwarps) {
-    const int va = a.leaf_node[li];
-    const float4 la = a.node_lo[va], ha = a.node_hi[va];
-    const int cell = (int)a.skeys[a.leaf_range[li].x];
+  const int va = a.leaf_node[li];
+  const float4 la = a.node[2 * va], ha = a.node[2 * va + 1];
+  const int cell = (int)a.skeys[a.leaf_range[li].x];
+  __syncwarp();
+  if (lane < 27) {
+    const int cx = cell % nx, cy = (cell / nx) % ny, cz = cell / (nx * ny);
+    int x = cx + (int)(lane % 3u) - 1, y = cy + (int)((lane / 3u) % 3u) - 1, z = cz + (int)(lane / 9u) - 1;
+    unsigned code = 0;
+    if (x < 0) { x += nx; code |= 2u; } else if (x >= nx) { x -= nx; code |= 1u; }
+    if (y < 0) { y += ny; code |= 8u; } else if (y >= ny) { y -= ny; code |= 4u; }
+    if (z < 0) { z += nz; code |= 32u; } else if (z >= nz) { z -= nz; code |= 16u; }
+    st[lane] = (unsigned)(x + nx * (y + ny * z)) | (code << kIndexBits);
+  }
+  int sp = 27;
+  int count = 0;
+  overflow = false;
+  __syncwarp();
+  while (sp > 0 && !overflow) {
+    const int gap = kStack - sp;
+    const int take = min(sp, gap >= kDfsGap ? min(32, (gap - 80) / 7) : 1);
+    unsigned e = 0;
+    if ((int)lane < take) e = st[sp - take + (int)lane];
+    sp -= take;
     __syncwarp();
-    if (lane < 27) {
-      const int cx = cell % nx, cy = (cell / nx) % ny, cz = cell / (nx * ny);
-      int x = cx + (int)(lane % 3u) - 1, y = cy + (int)((lane / 3u) % 3u) - 1, z = cz + (int)(lane / 9u) - 1;
-      unsigned code = 0;
-      if (x < 0) { x += nx; code |= 2u; } else if (x >= nx) { x -= nx; code |= 1u; }
-      if (y < 0) { y += ny; code |= 8u; } else if (y >= ny) { y -= ny; code |= 4u; }
-      if (z < 0) { z += nz; code |= 32u; } else if (z >= nz) { z -= nz; code |= 16u; }
-      st[lane] = (unsigned)(x + nx * (y + ny * z)) | (code << kIndexBits);
+    bool pass = false;
+    int link = 0;
+    const unsigned code = e >> kIndexBits;
+    if ((int)lane < take) {
+      const int b = (int)(e & kIndexMask);
+      float4 lb = a.node[2 * b], hb = a.node[2 * b + 1];
+      link = __float_as_int(hb.w);
+      shift_j(code, L, lb.x, lb.y, lb.z);
+      shift_j(code, L, hb.x, hb.y, hb.z);
+      const float gx = fmaxf(fmaxf(lb.x - ha.x, la.x - hb.x), 0.0f);
+      const float gy = fmaxf(fmaxf(lb.y - ha.y, la.y - hb.y), 0.0f);
+      const float gz = fmaxf(fmaxf(lb.z - ha.z, la.z - hb.z), 0.0f);
+      const float R = fmaxf(la.w, lb.w);
+      // the particle test is r2 < H^2 + band(H) with H <= R; 2^-12 extra slack
+      pass = r2_of(gx, gy, gz) < (R * R + band_of(R, Lmax)) * 1.000244140625f;
     }
-    int sp = 27;
-    int count = 0;
-    const int off = fill ? a.nbr_off[li] : 0;
-    bool overflow = false;
+    const int nch = link >> kLinkShift;  // empty cells never pass
+    const bool is_leaf = pass && nch == 0;
+    const unsigned lm = __ballot_sync(kFull, is_leaf);
+    if (is_leaf) {
+      const int t = count + __popc(lm & ((1u << lane) - 1u));
+      if (t < out_cap) out[t] = (unsigned)(link & kLinkMask) | (code << kIndexBits);
+    }
+    count += __popc(lm);
+    const int nk = pass ? nch : 0;
+    int incl = nk;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(kFull, incl, o);
+      if ((int)lane >= o) incl += y;
+    }
+    const int tot = __shfl_sync(kFull, incl, 31);
+    if (sp + tot > kStack) {
+      overflow = true;  // (never, by the bound above) this leaf's items would scan the 27 cells
+    } else {
+      const int first = link & kLinkMask;
+      for (int t = 0; t < nk; ++t) st[sp + incl - nk + t] = (unsigned)(first + t) | (code << kIndexBits);
+      sp += tot;
+    }
     __syncwarp();
-    while (sp > 0) {
-      const int take = min(32, sp);
-      unsigned e = 0;
-      if ((int)lane < take) e = st[sp - take + (int)lane];
-      sp -= take;
-      __syncwarp();
-      bool pass = false;
-      int2 kids = make_int2(0, 0);
-      int leaf = -1;
-      const unsigned code = e >> kIndexBits;
-      if ((int)lane < take) {
-        const int b = (int)(e & kIndexMask);
-        float4 lb = a.node_lo[b], hb = a.node_hi[b];
-        shift_j(code, L, lb.x, lb.y, lb.z);
-        shift_j(code, L, hb.x, hb.y, hb.z);
-        const float gx = fmaxf(fmaxf(lb.x - ha.x, la.x - hb.x), 0.0f);
-        const float gy = fmaxf(fmaxf(lb.y - ha.y, la.y - hb.y), 0.0f);
-        const float gz = fmaxf(fmaxf(lb.z - ha.z, la.z - hb.z), 0.0f);
-        const float R = fmaxf(la.w, lb.w);
-        // the particle test is r2 < H^2 + band(H) with H <= R; 2^-12 extra slack
-        pass = r2_of(gx, gy, gz) < (R * R + band_of(R, Lmax)) * 1.000244140625f;
-        if (pass) {
-          kids = a.node_kids[b];
-          leaf = a.node_leaf[b];
+  }
+  return count;
+}
+
+// Warps take kWalkChunk leaves per ticket; per leaf: walk once into shared
+// memory, reserve the list's place with one atomic and copy it out (a list
+// longer than the buffer is walked a second time straight into its place).
+// Each list is contiguous and in walk order; where the lists lie does not
+// change any result. A leaf whose walk ran out of stack gets no list.
+__global__ void __launch_bounds__(kWalkThreads) k_leaf_walk(WalkArgs a) {
+  extern __shared__ __align__(16) unsigned wsmem[];
+  unsigned* st = wsmem + (threadIdx.x >> 5) * (kStack + kOutBuf);
+  unsigned* buf = st + kStack;
+  const unsigned lane = lane_id();
+  const Grid& g = *a.grid;
+  const int nleaves = a.tctr[kTreeLeaves];
+  for (;;) {
+    int l0 = 0;
+    if (lane == 0) l0 = atomicAdd(&a.tctr[kTreeTicket], kWalkChunk);
+    l0 = __shfl_sync(kFull, l0, 0);
+    if (l0 >= nleaves) break;
+    for (int li = l0; li < min(l0 + kWalkChunk, nleaves); ++li) {
+      bool overflow = false;
+      const int count = walk_leaf(a, g, li, st, buf, kOutBuf, overflow);
+      int base = 0;
+      if (lane == 0 && !overflow) base = atomicAdd(&a.tctr[kTreeEntries], count);
+      base = __shfl_sync(kFull, base, 0);
+      const int room = a.nbr_cap - base;  // entries of this list that fit (a list past the cap is unused)
+      if (!overflow) {
+        if (count <= kOutBuf) {
+          for (int t = (int)lane; t < count && t < room; t += 32) a.nbr[base + t] = buf[t];
+        } else if (room > 0) {
+          walk_leaf(a, g, li, st, a.nbr + base, room, overflow);
         }
       }
-      const bool is_leaf = pass && leaf >= 0;
-      const unsigned lm = __ballot_sync(kFull, is_leaf);
-      if (fill && is_leaf) {
-        const int t = off + count + __popc(lm & ((1u << lane) - 1u));
-        if (t < a.nbr_cap) a.nbr[t] = (unsigned)leaf | (code << kIndexBits);  // a list past the cap is unused
-      }
-      count += __popc(lm);
-      int nk = (pass && leaf < 0) ? kids.y : 0;
-      int incl = nk;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(kFull, incl, o);
-        if ((int)lane >= o) incl += y;
-      }
-      const int tot = __shfl_sync(kFull, incl, 31);
-      if (sp + tot > kStack) {
-        overflow = true;  // cannot happen for trees of kTreeLevels levels; guards the stack
-      } else {
-        for (int t = 0; t < nk; ++t)
-          st[sp + incl - nk + t] = (unsigned)(kids.x + t) | (code << kIndexBits);
-        sp += tot;
-      }
-      __syncwarp();
-    }
-    if (lane == 0) {
-      if (overflow) set_error(a.st, SWIFT_GPU_ERR_CAPACITY);
-      if (!fill) a.nbr_off[li] = count;
+      if (lane == 0) a.nbr_span[li] = overflow ? make_int2(0, 0x7fffffff) : make_int2(base, count);
     }
   }
 }
 
-// Total list length (lists past the capacity are replaced by cell scans).
-__global__ void k_tree_finish(int* tctr, const int* nbr_off) { tctr[kTreeEntries] = nbr_off[tctr[kTreeLeaves]]; }
+static bool g_walk_attr = false;
 
 int leaves_build(Ctx* c, const float4* pos_h, cudaStream_t s) {
   const int n = c->n;
   cudaMemsetAsync(c->d_tree_ctr, 0, sizeof(int) * kTreeCtrCount, s);
-  cudaMemsetAsync(c->d_nbr_off, 0, sizeof(int) * (size_t)(n + 1), s);
   if (n == 0) return cudaGetLastError() == cudaSuccess ? SWIFT_GPU_OK : SWIFT_GPU_ERR_CUDA;
+  if (!g_walk_attr) {
+    cudaFuncSetAttribute(k_leaf_walk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWalkSmemBytes);
+    g_walk_attr = true;
+  }
+  cudaMemsetAsync(c->d_node_flag, 0, sizeof(unsigned) * ((size_t)c->node_cap + 1), s);
+  cudaMemsetAsync(c->d_node_done, 0, sizeof(int) * (size_t)c->node_cap, s);
   const int sm = c->num_sms;
   const unsigned* perm = c->d_vals[c->sorted_buf];
   unsigned* mk = c->d_keys[1 - c->sorted_buf];  // free after the sort
@@ -291,10 +407,11 @@ int leaves_build(Ctx* c, const float4* pos_h, cudaStream_t s) {
   t.mk = mk;
   t.cell_start = c->d_cell_start;
   t.node_range = c->d_node_range;
-  t.node_kids = c->d_node_kids;
-  t.node_lo = c->d_node_lo;
-  t.node_hi = c->d_node_hi;
-  t.node_leaf = c->d_node_leaf;
+  t.node = c->d_node;
+  t.node_link = c->d_node_link;
+  t.node_parent = c->d_node_parent;
+  t.node_done = c->d_node_done;
+  t.node_flag = c->d_node_flag;
   t.leaf_range = c->d_leaf_range;
   t.leaf_hcap = c->d_leaf_hcap;
   t.leaf_node = c->d_leaf_node;
@@ -303,32 +420,28 @@ int leaves_build(Ctx* c, const float4* pos_h, cudaStream_t s) {
   t.leaf_max = c->params.leaf_max;
   t.margin = c->params.leaf_margin;
   t.kg = c->phys.kg;
-  const int tree_blocks = sm * 4;
+  const int tree_blocks = sm * 8;
   for (int level = 0; level <= kTreeLevels; ++level) {
-    k_tree_level<<<tree_blocks, kTreeThreads, 0, s>>>(t, level);
+    k_tree_split<<<tree_blocks, kTreeThreads, 0, s>>>(t, level);
     c->launches++;
   }
+  exclusive_scan(c, c->d_node_flag, c->d_node_flag, c->node_cap + 1, c->d_scan_tmp, s);
+  k_leaf_number<<<min((c->node_cap + 255) / 256, sm * 16), 256, 0, s>>>(c->d_node_flag, c->node_cap,
+                                                                      c->d_node_link, c->d_leaf_node, c->d_tree_ctr);
+  k_leaf_finish<<<tree_blocks, kTreeThreads, 0, s>>>(t);
+  c->launches += 2;
   WalkArgs w;
   w.grid = c->d_grid;
   w.skeys = c->d_keys[c->sorted_buf];
-  w.node_kids = c->d_node_kids;
-  w.node_lo = c->d_node_lo;
-  w.node_hi = c->d_node_hi;
-  w.node_leaf = c->d_node_leaf;
+  w.node = c->d_node;
   w.leaf_range = c->d_leaf_range;
   w.leaf_node = c->d_leaf_node;
   w.tctr = c->d_tree_ctr;
-  w.nbr_off = c->d_nbr_off;
+  w.nbr_span = c->d_nbr_span;
   w.nbr = c->d_nbr;
   w.nbr_cap = c->nbr_cap;
-  w.st = c->d_status;
-  const int walk_blocks = sm * 8;
-  k_leaf_walk<<<walk_blocks, kWalkThreads, 0, s>>>(w, 0);
-  exclusive_scan(c, reinterpret_cast<const unsigned*>(c->d_nbr_off), reinterpret_cast<unsigned*>(c->d_nbr_off),
-                 n + 1, c->d_scan_tmp, s);
-  k_leaf_walk<<<walk_blocks, kWalkThreads, 0, s>>>(w, 1);
-  k_tree_finish<<<1, 1, 0, s>>>(c->d_tree_ctr, c->d_nbr_off);
-  c->launches += 3;
+  k_leaf_walk<<<sm * 8, kWalkThreads, kWalkSmemBytes, s>>>(w);
+  c->launches++;
   return cudaGetLastError() == cudaSuccess ? SWIFT_GPU_OK : SWIFT_GPU_ERR_CUDA;
 }
 
@@ -337,7 +450,7 @@ Nbr nbr_of(Ctx* c) {
   b.cell_start = c->d_cell_start;
   b.skeys = c->d_keys[c->sorted_buf];
   b.leaf_range = c->d_leaf_range;
-  b.nbr_off = c->d_nbr_off;
+  b.nbr_span = c->d_nbr_span;
   b.nbr = c->d_nbr;
   b.leaf_hcap = c->d_leaf_hcap;
   b.n_leaves = c->d_tree_ctr ? c->d_tree_ctr + kTreeLeaves : nullptr;
@@ -347,8 +460,8 @@ Nbr nbr_of(Ctx* c) {
 }
 
 __global__ void k_leaves_export(const int2* __restrict__ range, const float* __restrict__ hcap,
-                                const int* __restrict__ off, const int* __restrict__ tctr, int64_t max_leaves,
-                                int32_t* __restrict__ out_range, float* __restrict__ out_hcap,
+                                const int2* __restrict__ span, const int* __restrict__ tctr, int nbr_cap,
+                                int64_t max_leaves, int32_t* __restrict__ out_range, float* __restrict__ out_hcap,
                                 int32_t* __restrict__ out_cnt) {
   const int nl = tctr[kTreeLeaves];
   const int m = (int)min((int64_t)nl, max_leaves);
@@ -359,7 +472,10 @@ __global__ void k_leaves_export(const int2* __restrict__ range, const float* __r
       out_range[2 * l + 1] = r.y;
     }
     if (out_hcap) out_hcap[l] = hcap[l];
-    if (out_cnt) out_cnt[l] = off[l + 1] - off[l];
+    if (out_cnt) {
+      const int2 sp = span[l];
+      out_cnt[l] = sp.y <= nbr_cap - sp.x ? sp.y : -1;  // -1: no list, the leaf's items scan the cells
+    }
   }
 }
 
@@ -367,8 +483,8 @@ int leaves_export_impl(Ctx* c, int32_t* range, float* hcap, int32_t* nbr_count, 
   if (max_leaves <= 0 || c->n == 0) return SWIFT_GPU_OK;
   const int64_t m = max_leaves < c->n ? max_leaves : c->n;
   const int nb = (int)((m + 255) / 256 < c->num_sms * 8 ? (m + 255) / 256 : c->num_sms * 8);
-  k_leaves_export<<<nb, 256, 0, s>>>(c->d_leaf_range, c->d_leaf_hcap, c->d_nbr_off, c->d_tree_ctr, max_leaves, range,
-                                     hcap, nbr_count);
+  k_leaves_export<<<nb, 256, 0, s>>>(c->d_leaf_range, c->d_leaf_hcap, c->d_nbr_span, c->d_tree_ctr, c->nbr_cap,
+                                     max_leaves, range, hcap, nbr_count);
   c->launches++;
   return cudaGetLastError() == cudaSuccess ? SWIFT_GPU_OK : SWIFT_GPU_ERR_CUDA;
 }

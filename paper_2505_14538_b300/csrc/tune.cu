@@ -18,7 +18,7 @@ static int run_loop(Ctx* c, int loop, cudaStream_t s) {
 
 int autotune_impl(Ctx* c, int loop, cudaStream_t s) {
   if (loop == 1 && !c->last_grad_out) return SWIFT_GPU_ERR_ORDER;
-  const int cand_l[4] = {1, 2, 4, 8};
+  const int cand_l[6] = {1, 2, 4, 8, 16, 32};
   const int cand_b[3] = {0, 1, 2};
   swift_gpu_tuning best = c->tuning, orig = c->tuning;
   float best_ms = 1e30f;
@@ -29,7 +29,7 @@ int autotune_impl(Ctx* c, int loop, cudaStream_t s) {
   else ghost_impl(c, c->last_u, nullptr, nullptr, s);
   int rc = SWIFT_GPU_OK;
   for (int bi = 0; bi < 3 && rc == SWIFT_GPU_OK; ++bi) {
-    for (int li = 0; li < 4 && rc == SWIFT_GPU_OK; ++li) {
+    for (int li = 0; li < 6 && rc == SWIFT_GPU_OK; ++li) {
       c->tuning.max_lanes_per_particle = cand_l[li];
       c->tuning.blocks_per_sm = cand_b[bi];
       rc = run_loop(c, loop, s);  // warm-up

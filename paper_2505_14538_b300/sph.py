@@ -200,7 +200,7 @@ class Context:
         return dict(threads_per_block=t.threads_per_block, max_lanes_per_particle=t.max_lanes_per_particle,
                     blocks_per_sm=t.blocks_per_sm)
 
-    def set_tuning(self, threads_per_block=256, max_lanes_per_particle=8, blocks_per_sm=0):
+    def set_tuning(self, threads_per_block=256, max_lanes_per_particle=32, blocks_per_sm=0):
         t = _lib.Tuning(threads_per_block, max_lanes_per_particle, blocks_per_sm)
         _check(self.lib.swift_gpu_set_tuning(self.handle, ctypes.byref(t)), "swift_gpu_set_tuning")
 

@@ -104,7 +104,7 @@ def test_adaptive_leaf_structure(sph):
     rng, hcap, cnt = rng_t.cpu().numpy(), hcap_t.cpu().numpy(), cnt_t.cpu().numpy()
     cid, perm = cid.cpu().numpy().astype(np.int64), perm.cpu().numpy().astype(np.int64)
     assert len(rng) == info["n_leaves"] > 0
-    assert cnt.sum() == info["leaf_pairs"] and np.all(cnt >= 1)
+    assert np.all(cnt >= 1) and cnt.sum() == info["leaf_pairs"]  # every leaf got its list here
     # a partition of the sorted positions into contiguous runs
     order = np.argsort(rng[:, 0])
     r = rng[order]
