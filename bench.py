@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-clustered", action="store_true", help="skip the clustered (Plummer) active-step comparison")
     ap.add_argument("--autotune", action="store_true", help="run the library autotuner before timing")
     return ap.parse_args()
 
@@ -155,7 +156,7 @@ def step_interactions(i0, i1):
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for name in ("loops.cu", "engine.cuh", "common.cuh"):
+    for name in ("loops.cu", "engine.cuh", "common.cuh", "ops.cuh"):
         with open(os.path.join(ROOT, "paper_2505_14538_b300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -331,6 +332,8 @@ def run_ours(args, rank, world, pg):
         res["e2e"] = run_e2e(ctx, pos_h_host, vel_m_host, u_host, min_width, n, dev, pg, world, K=min(K, 100))
     if not args.no_plain and rank == 0:
         res["plain"] = run_plain(d, n, dev, min_width)
+    if not args.no_clustered and rank == 0:
+        res["clustered"] = run_clustered(dev)
     if rank == 0 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(d, ctx)
     return res
@@ -403,6 +406,69 @@ def run_plain(d, n, dev, min_width):
     t = e0.elapsed_time(e1) / 1e3
     inter = sum(step_interactions(i0, i1))
     return {"value": inter / t, "unit": UNIT, "ms_per_step": t * 1e3, "launches_per_step": i1["launches"] - i0["launches"]}
+
+
+def run_clustered(dev, steps=5):
+    """Clustered set: 2^21 particles (64 Plummer spheres + 10 % uniform background), 10 % active.
+
+    One active step = build_cells, density (h iteration for the active
+    particles), gradient and force, timed on the uniform grid and with
+    adaptive leaves after an all-active step has set h, rho and curl/div.
+    """
+    import numpy as np
+    import torch
+
+    from paper_2505_14538_b300 import _lib, ics, sph
+    d = ics.plummer(2 ** 21)
+    n = len(d["pos"])
+    pos_h = torch.from_numpy(np.concatenate([d["pos"], d["h"][:, None]], 1).astype(np.float32)).to(dev)
+    vel_m = torch.from_numpy(np.concatenate([d["vel"], d["m"][:, None]], 1).astype(np.float32)).to(dev)
+    u = torch.from_numpy(d["u"].astype(np.float32)).to(dev)
+    act = torch.from_numpy(d["active"].astype(np.uint8)).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    res = {"workload": f"plummer2M: {n} particles, 64 Plummer spheres (a in [0.005, 0.05], log-uniform, "
+                       "truncated at 10 a) + 10 % uniform background, periodic unit box",
+           "active": int(d["active"].sum()), "steps": steps}
+    for name, flags in (("uniform", 0), ("adaptive", _lib.FLAG_ADAPTIVE)):
+        ctx = sph.Context(n, flags=flags, max_iter=40)
+        warm = ctx.step(pos_h, vel_m, u)  # every particle active: the state the active steps start from
+        torch.cuda.synchronize()
+        p2 = pos_h.clone()
+        p2[:, 3] = warm["h"]
+        rho4 = warm["rho4"].clone()
+        cd = warm["curl_div"].clone()
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(steps + 1)]
+        for k in range(steps + 1):  # the first is a warm-up
+            if k == 1:
+                i0 = ctx.info()
+            flush.zero_()
+            e = ev[k]
+            e[0].record()
+            ctx.build_cells(p2)
+            e[1].record()
+            ctx.density(p2, vel_m, act, rho4=rho4, curl_div=cd)
+            e[2].record()
+            ctx.gradient(u)
+            e[3].record()
+            ctx.force(u)
+            e[4].record()
+        torch.cuda.synchronize()
+        code, detail = ctx.sync_status()
+        i1 = ctx.info()
+        loop = [sum(ev[k][j].elapsed_time(ev[k][j + 1]) for k in range(1, steps + 1)) / steps for j in range(4)]
+        inter = sum(step_interactions(i0, i1)) / steps
+        r = {"ms_per_step": sum(loop), "build_ms": loop[0], "density_ms": loop[1], "gradient_ms": loop[2],
+             "force_ms": loop[3], "interactions_per_step": inter, "value": inter / (sum(loop) * 1e-3),
+             "unit": UNIT, "candidates_per_step": [(i1["candidates"][j] - i0["candidates"][j]) / steps
+                                                   for j in range(3)],
+             "nc": i1["nc"], "status": [code, detail]}
+        if flags:
+            r.update({"leaves": i1["n_leaves"], "leaf_pairs": i1["leaf_pairs"], "tree_depth": i1["tree_depth"],
+                      "leaf_max": int(ctx.params.leaf_max), "leaf_margin": float(ctx.params.leaf_margin)})
+        res[name] = r
+        del ctx
+    res["adaptive_speedup"] = res["uniform"]["ms_per_step"] / res["adaptive"]["ms_per_step"]
+    return res
 
 
 # ------------------------------------------------------- CPU baseline leg

@@ -1,0 +1,138 @@
+"""Full-size parity on sampled particles, in the launch configurations the benchmark times.
+
+* Sedov blast, 64^3 particles: the whole step captured in a CUDA graph and
+  replayed (the benchmark's headline configuration), uniform grid.
+* Plummer mixture, 2^21 particles, 10 % active: one active step with
+  adaptive leaves after an all-active step (the benchmark's clustered run).
+
+The oracle evaluates only a random sample of particles plus the neighbours
+their force needs, at the GPU's final h. Tolerances as in the small parity
+tests: neighbour counts exact; rho, n, dn/dh, v_sig 1e-5 relative; a and
+du/dt within 1e-4 of each particle's force scale. Convergence of the h
+iteration is checked on the sample against the oracle's own sums.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2505_14538_b300 import ics
+
+pytestmark = pytest.mark.gpu
+
+KG = float(np.float32(1.825742))
+ETA = float(np.float32(1.2348))
+
+
+@pytest.fixture(scope="module")
+def sph():
+    from paper_2505_14538_b300 import sph as S
+    assert torch.cuda.is_available()
+    return S
+
+
+def force_neighbours(x, h, sample, box=(1.0, 1.0, 1.0)):
+    """Union of the sample and every j with r_ij < max(H_i, H_j) for some sampled i (FP64, minimum image)."""
+    L = np.asarray(box, np.float64)
+    H = KG * h.astype(np.float64)
+    xs = x.astype(np.float64)
+    keep = np.zeros(len(x), bool)
+    keep[sample] = True
+    for i in sample:
+        d = xs - xs[i]
+        d -= L * np.round(d / L)
+        r2 = (d * d).sum(1)
+        keep |= r2 < np.maximum(H[i], H) ** 2
+    return keep
+
+
+def check_sample(O, d, vel, u, h, out, sample, h_tol, active_all=True):
+    x, m = d["pos"], d["m"]
+    n = len(x)
+    smask = np.zeros(n, np.uint8)
+    smask[sample] = 1
+    p = O.Params()
+    # density at the GPU's h, sampled
+    od = O.density(p, x, vel, m, h, active=smask)
+    ngb = out["ngb"]
+    assert np.array_equal(ngb[sample].astype(np.int64), od["ngb"][sample])
+    rho4 = out["rho4"]
+    assert np.max(np.abs(rho4[sample, 0] / od["rho"][sample] - 1)) < 1e-5
+    assert np.max(np.abs(rho4[sample, 2] / od["n"][sample] - 1)) < 1e-5
+    # the h iteration converged on the oracle's own sums (GPU tolerance plus the 1e-5 agreement)
+    nh3 = od["n"][sample] * h[sample].astype(np.float64) ** 3
+    assert np.all(np.abs(nh3 - ETA ** 3) <= (h_tol + 1e-5) * ETA ** 3 * 1.01)
+    # force and gradient: density for the sample and its neighbours, then the sampled loops
+    keep = force_neighbours(x, h, sample, d["box"])
+    od2 = O.density(p, x, vel, m, h, active=keep.astype(np.uint8))
+    g = O.ghost(p, h, od2["rho"], od2["drho_dh"], od2["div"], od2["curl"], u)
+    gr = O.gradient(p, x, vel, m, h, od2["rho"], g["c"], u, active=smask)
+    of = O.force(p, x, vel, m, h, u, od2["rho"], g["f"], g["P"], g["c"], g["B"], active=smask)
+    vs = out["vsig_lapu"]
+    assert np.max(np.abs(vs[sample, 0] / gr["vsig"][sample] - 1)) < 1e-5
+    sc_l = max(np.abs(gr["lapu"][sample]).max(), 1e-30)
+    assert np.max(np.abs(vs[sample, 1] - gr["lapu"][sample])) < 1e-4 * sc_l
+    a = out["accel_dudt"]
+    err_a = np.linalg.norm(a[sample, :3] - of["accel"][sample], axis=1)
+    assert np.all(err_a <= 1e-4 * of["s_a"][sample] + 1e-30)
+    err_u = np.abs(a[sample, 3] - of["dudt"][sample])
+    assert np.all(err_u <= 1e-4 * of["s_u"][sample] + 1e-30)
+
+
+def test_sedov64_graph_replay_sampled(sph, O):
+    d = ics.sedov(64)
+    n = len(d["pos"])
+    vel = d["vel"].astype(np.float32)
+    u = d["u"].astype(np.float32)
+    pos_h = torch.from_numpy(np.concatenate([d["pos"], d["h"][:, None]], 1).astype(np.float32)).cuda()
+    vel_m = torch.from_numpy(np.concatenate([vel, d["m"][:, None]], 1).astype(np.float32)).cuda()
+    ut = torch.from_numpy(u).cuda()
+    ctx = sph.Context(n)
+    first = ctx.step(pos_h, vel_m, ut, check=True)  # settles the cell width as the benchmark does
+    torch.cuda.synchronize()
+    min_width = max(ctx.info()["cell_width"]) if first["status"][0] != 0 else 0.0
+    graph = sph.StepGraph(ctx, pos_h, vel_m, ut, min_width)
+    for _ in range(2):
+        o = graph.replay()
+    torch.cuda.synchronize()
+    assert ctx.sync_status()[0] in (0, -4)
+    out = {k: v.cpu().numpy() for k, v in o.items() if torch.is_tensor(v)}
+    h = out["h"]
+    rng = np.random.default_rng(64)
+    sample = np.concatenate([rng.choice(n, 48, replace=False),
+                             np.argsort(u)[-16:]])  # and the hottest (blast) particles
+    check_sample(O, d, vel, u, h, out, sample, float(ctx.params.h_tol))
+
+
+def test_plummer_2m_adaptive_active_step_sampled(sph, O):
+    d = ics.plummer(2 ** 21)
+    n = len(d["pos"])
+    vel = d["vel"].astype(np.float32)
+    u = d["u"].astype(np.float32)
+    pos_h = torch.from_numpy(np.concatenate([d["pos"], d["h"][:, None]], 1).astype(np.float32)).cuda()
+    vel_m = torch.from_numpy(np.concatenate([vel, d["m"][:, None]], 1).astype(np.float32)).cuda()
+    ut = torch.from_numpy(u).cuda()
+    act = torch.from_numpy(d["active"].astype(np.uint8)).cuda()
+    ctx = sph.Context(n, flags=8, max_iter=40)
+    warm = ctx.step(pos_h, vel_m, ut)
+    torch.cuda.synchronize()
+    p2 = pos_h.clone()
+    p2[:, 3] = warm["h"]
+    rho4, cd = warm["rho4"].clone(), warm["curl_div"].clone()
+    ctx.build_cells(p2)
+    dd = ctx.density(p2, vel_m, act, rho4=rho4, curl_div=cd)
+    gg = ctx.gradient(ut)
+    ff = ctx.force(ut)
+    torch.cuda.synchronize()
+    assert ctx.sync_status() == (0, 0)
+    out = {"h": dd["h"], "rho4": dd["rho4"], "ngb": dd["ngb"], "vsig_lapu": gg, "accel_dudt": ff["accel_dudt"]}
+    out = {k: v.cpu().numpy() for k, v in out.items()}
+    h = out["h"]
+    on = np.nonzero(d["active"])[0]
+    rng = np.random.default_rng(21)
+    # random active particles, and active ones in the densest regions (smallest h)
+    sample = np.unique(np.concatenate([rng.choice(on, 40, replace=False), on[np.argsort(h[on])[:12]]]))
+    check_sample(O, d, vel, u, h, out, sample, float(ctx.params.h_tol))
+    # inactive particles keep their h and their density inputs
+    off = ~d["active"].astype(bool)
+    assert np.array_equal(h[off], warm["h"].cpu().numpy()[off])
