@@ -66,6 +66,8 @@ struct AdjArgs {
   float4* grad_x;      // caller order
   float4* grad_v;
   float* grad_u;
+  const unsigned* nlist;  // candidate lists kept by the density call (NULL: scan)
+  const int2* item_nl;
 };
 
 // One side of a force pair: the per-particle inputs and, after the reverse
@@ -207,7 +209,9 @@ struct ForceAdjOp {
     const float r2 = r2_of(d[0], d[1], d[2]);
     if (!(r2 > 0.0f)) return;
     const float Hj = kg * pj.w;
-    if (r2 >= fmaxf(i.H2lo, Hj * Hj - band_of(Hj, Lmax))) {
+    const float bj_band = band_of(Hj, Lmax);
+    if (r2 >= fmaxf(i.H2lo, Hj * Hj - bj_band)) {
+      if (r2 >= fmaxf(i.H2hi, Hj * Hj + bj_band)) return;  // outside both supports
       const double ex = exact_r2(i.x, i.y, i.z, pj.x, pj.y, pj.z, L[0], L[1], L[2]);
       if (!(ex < exact_H2(kg, i.h)) && !(ex < exact_H2(kg, pj.w))) return;
     }
@@ -251,7 +255,7 @@ struct ForceAdjOp {
 };
 
 __device__ __forceinline__ void force_adj_item(const AdjArgs& a, const ForceAdjOp& op, const Grid& g, WarpSmem& w,
-                                               const Item& it) {
+                                               const Item& it, int t) {
   const int lsh = lanes_shift(it.cnt, a.lmax);
   const unsigned lane = lane_id();
   const int slot = (int)(lane & ((32u >> lsh) - 1u)), s = (int)(lane >> (5 - lsh));
@@ -280,7 +284,9 @@ __device__ __forceinline__ void force_adj_item(const AdjArgs& a, const ForceAdjO
   I.sb = SideBar{0, 0, 0, 0, 0, 0, 0, 0};
   I.k = k;
   unsigned ncand = 0;
-  scan_item(op, I, g, a.nb, a.pos, it.cell, lsh, s, live, w, ncand);
+  int sm;
+  const unsigned* sl = kept_list(a.nlist, a.item_nl, t, sm);
+  scan_item(op, I, g, a.nb, a.pos, it.cell, lsh, s, live, w, ncand, sl, sm);
   for (int q = 0; q < 3; ++q) {
     I.xb[q] = lsum(I.xb[q], lsh);
     I.vb[q] = lsum(I.vb[q], lsh);
@@ -358,7 +364,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_force_adj(AdjArgs a) {
   for (;;) {
     const int t = take_ticket(a.ticket);
     if (t >= n_items) break;
-    force_adj_item(a, op, g, w, a.items[t]);
+    force_adj_item(a, op, g, w, a.items[t], t);
   }
 }
 
@@ -427,8 +433,10 @@ struct DensAdjOp {
     if (!(r2 > 0.0f)) return;
     const float Hj = kg * pj.w;
     const float H2j = Hj * Hj;
+    const float bj_band = band_of(Hj, Lmax);
+    if (r2 >= fmaxf(i.H2hi, H2j + bj_band)) return;  // outside both supports
     bool in_k = r2 < i.H2lo;
-    bool in_j = r2 < H2j - band_of(Hj, Lmax);
+    bool in_j = r2 < H2j - bj_band;
     if (!in_k || !in_j) {
       const double ex = exact_r2(i.x, i.y, i.z, pj.x, pj.y, pj.z, L[0], L[1], L[2]);
       in_k = ex < exact_H2(kg, i.h);
@@ -487,7 +495,9 @@ __global__ void __launch_bounds__(kAdjThreads) k_dens_adj(AdjArgs a) {
     I.Cb[0] = q.w; I.Cb[1] = a.cby[k]; I.Cb[2] = a.cbz[k];
     I.xb[0] = I.xb[1] = I.xb[2] = I.vb[0] = I.vb[1] = I.vb[2] = 0.0f;
     unsigned ncand = 0;
-    scan_item(op, I, g, a.nb, a.pos, it.cell, lsh, s, live, w, ncand);
+    int sm;
+    const unsigned* sl = kept_list(a.nlist, a.item_nl, t, sm);
+    scan_item(op, I, g, a.nb, a.pos, it.cell, lsh, s, live, w, ncand, sl, sm);
     for (int c = 0; c < 3; ++c) {
       I.xb[c] = lsum(I.xb[c], lsh);
       I.vb[c] = lsum(I.vb[c], lsh);
@@ -531,6 +541,9 @@ int backward_impl(Ctx* c, const float4* grad_ad, float4* grad_x, float4* grad_v,
   AdjArgs a;
   a.grid = c->d_grid;
   a.nb = nbr_of(c);
+  const bool lists = kept_lists_usable(c);
+  a.nlist = lists ? c->d_nlist : nullptr;
+  a.item_nl = lists ? c->d_item_nl : nullptr;
   a.perm = c->d_vals[c->sorted_buf];
   a.ph = c->phys;
   a.lmax = c->tuning.max_lanes_per_particle;

@@ -60,7 +60,8 @@ static void free_all(Ctx* c) {
                   c->d_items[1], c->d_plist[0], c->d_plist[1], c->d_counters, c->d_stats, c->d_red_partial,
                   c->d_scratch4[0], c->d_scratch1[0], c->d_scratch1[1], c->d_plain_act, c->d_aux[0], c->d_aux[1],
                   c->d_node_range, c->d_node, c->d_node_link, c->d_node_parent, c->d_node_done, c->d_node_flag,
-                  c->d_leaf_range, c->d_leaf_hcap, c->d_leaf_node, c->d_nbr_span, c->d_nbr, c->d_tree_ctr};
+                  c->d_leaf_range, c->d_leaf_hcap, c->d_leaf_node, c->d_nbr_span, c->d_nbr, c->d_tree_ctr,
+                  c->d_nlist, c->d_item_nl, c->d_nl_ctr};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_status) cudaFreeHost(c->h_status);
@@ -132,6 +133,8 @@ int swift_gpu_create(swift_gpu_ctx** out, const swift_gpu_params* p, int64_t n_m
   c->node_cap = (int)node_cap;
   c->leaf_cap = (int)n;
   if (scan_m < node_cap + 1) scan_m = node_cap + 1;  // leaf flags of the tree nodes
+  // kept candidate lists: 128 entries per particle (a list that does not fit leaves its item to scan)
+  c->nl_cap = 128 * n < ((int64_t)1 << 31) - 64 ? 128 * n : ((int64_t)1 << 31) - 64;
   int64_t nbr_cap = 48 * n > ((int64_t)1 << 22) ? 48 * n : ((int64_t)1 << 22);  // at least 16 MB of lists
   c->nbr_cap = (int)(nbr_cap < (int64_t)INT32_MAX ? nbr_cap : (int64_t)INT32_MAX);
   c->red_blocks = c->num_sms * 32;
@@ -152,7 +155,8 @@ int swift_gpu_create(swift_gpu_ctx** out, const swift_gpu_params* p, int64_t n_m
             dalloc(&c->d_node_done, node_cap) && dalloc(&c->d_node_flag, node_cap + 1) &&
             dalloc(&c->d_leaf_range, n) && dalloc(&c->d_leaf_hcap, n) && dalloc(&c->d_leaf_node, n) &&
             dalloc(&c->d_nbr_span, n) && dalloc(&c->d_nbr, (size_t)c->nbr_cap) &&
-            dalloc(&c->d_tree_ctr, kTreeCtrCount) &&
+            dalloc(&c->d_tree_ctr, kTreeCtrCount) && dalloc(&c->d_nlist, (size_t)c->nl_cap) &&
+            dalloc(&c->d_item_nl, n) && dalloc(&c->d_nl_ctr, 1) &&
             cudaMallocHost((void**)&c->h_status, sizeof(Status)) == cudaSuccess &&
             cudaMallocHost((void**)&c->h_stats, sizeof(unsigned long long) * kStatCount) == cudaSuccess;
   if (ok)

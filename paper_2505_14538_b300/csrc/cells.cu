@@ -307,6 +307,7 @@ __global__ void k_cell_start(const unsigned* __restrict__ skeys, int n, const Gr
 
 int build_cells_impl(Ctx* c, const float4* pos_h, int n, float min_width, cudaStream_t s) {
   c->n = n;
+  c->nl_lmax = 0;  // kept candidate lists belong to the previous build
   cudaMemsetAsync(c->d_hmax_bits, 0, sizeof(unsigned), s);
   int sm = c->num_sms;
   if (n > 0) {

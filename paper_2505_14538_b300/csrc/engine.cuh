@@ -28,6 +28,7 @@ namespace sg {
 
 constexpr int kCap = 64;  // list entries per lane before a flush
 constexpr unsigned kFull = 0xffffffffu;
+constexpr unsigned kNoEntry = 0xffffffffu;  // padding of a stored candidate list
 
 struct WarpSmem {
   unsigned list[kCap * 32];  // lane-private lists, entry t of lane l at [t * 32 + l]
@@ -132,6 +133,16 @@ __device__ __forceinline__ void stage_candidate(const Grid& g, const float4* __r
   entry = (unsigned)j | (code << kIndexBits);
 }
 
+// The candidate list the density call kept for pass-0 item t, if any.
+__device__ __forceinline__ const unsigned* kept_list(const unsigned* nlist, const int2* item_nl, int t, int& m) {
+  m = 0;
+  if (!nlist) return nullptr;
+  const int2 sp = item_nl[t];
+  if (sp.x < 0) return nullptr;
+  m = sp.y;
+  return nlist + sp.x;
+}
+
 // Phase 2: each lane evaluates the interactions in its list.
 template <class Op>
 __device__ __forceinline__ void flush(const Op& op, typename Op::I& I, const WarpSmem& w, int cnt) {
@@ -145,46 +156,77 @@ __device__ __forceinline__ void flush(const Op& op, typename Op::I& I, const War
   }
 }
 
+// Next chunk of an item's candidates: moves `base` past the current chunk
+// (to the next batch of segments when the batch is used up) and returns the
+// chunk's length, 0 at the end.
+__device__ __forceinline__ int next_chunk(const Grid& g, const Nbr& nb, const Segs& q, WarpSmem& w, int& sb,
+                                          int& bn, int& total, int& base) {
+  base += 32;
+  while (base >= total && sb + 32 < q.nseg) {
+    sb += 32;
+    base = 0;
+    __syncwarp();
+    total = setup_segments(g, nb, q, sb, w, bn);
+  }
+  return base < total ? min(32, total - base) : 0;
+}
+
 // Full neighbour scan of one item for lane particle I (sub-lane s of the
 // 2^lsh lanes that share the particle). Segments come in batches of up to
-// 32; candidates are taken in chunks of 32 within a batch. One flush site
-// keeps the inlined interaction code in a single copy.
+// 32; candidates are taken in chunks of 32 within a batch. The loads of the
+// next chunk are issued before the current one is tested (software
+// pipelining: the test hides their latency). One flush site keeps the
+// inlined interaction code in a single copy.
+//
+// With a stored list (`sl`: the item's lane-interleaved candidate list kept
+// by the density call, entry t of lane l at sl[t * 32 + l], kNoEntry after
+// the lane's last) the scan is skipped: the lane's entries go straight into
+// its shared-memory list for the one flush.
 template <class Op>
 __device__ __forceinline__ void scan_item(const Op& op, typename Op::I& I, const Grid& g, const Nbr& nb,
                                           const float4* __restrict__ pos, int cell, int lsh, int s, bool live,
-                                          WarpSmem& w, unsigned& ncand) {
+                                          WarpSmem& w, unsigned& ncand, const unsigned* __restrict__ sl = nullptr,
+                                          int sm = 0) {
   const unsigned lane = lane_id();
-  const Segs q = item_segments(nb, cell);
-  const int nseg = q.nseg;
-  int bn = 0, sb = 0;
-  int total = nseg > 0 ? setup_segments(g, nb, q, 0, w, bn) : 0;
-  const int per = 32 >> lsh;  // candidates a lane tests per chunk (at most)
   int cnt = 0;
-  for (int base = 0;; base += 32) {
-    while (base >= total && sb + 32 < nseg) {
-      sb += 32;
-      base = 0;
-      __syncwarp();
-      total = setup_segments(g, nb, q, sb, w, bn);
+  int bn = 0, sb = 0, base = -32, total = 0, len = 0;
+  Segs q;
+  q.nseg = 0;
+  if (sl) {
+    for (int t = 0; t < sm; ++t) {
+      const unsigned e = sl[t * 32 + (int)lane];
+      w.list[t * 32 + (int)lane] = e;
+      cnt += e != kNoEntry ? 1 : 0;  // the lane's entries come first
     }
-    const bool done = base >= total;
+    if (!live) cnt = 0;
+    ncand += (unsigned)cnt;
+  } else {
+    q = item_segments(nb, cell);
+    if (q.nseg > 0) total = setup_segments(g, nb, q, 0, w, bn);
+    len = next_chunk(g, nb, q, w, sb, bn, total, base);
+  }
+  float4 pj = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  unsigned ej = 0;
+  if ((int)lane < len) stage_candidate(g, pos, w, bn, base + (int)lane, pj, ej);
+  const int per = 32 >> lsh;  // candidates a lane tests per chunk (at most)
+  for (;;) {
+    const bool done = len == 0;
     if (done || __any_sync(kFull, cnt > kCap - per)) {
       flush(op, I, w, cnt);
       cnt = 0;
       if (done) break;
     }
-    const int len = min(32, total - base);
     __syncwarp();
     if ((int)lane < len) {
-      float4 pj;
-      unsigned entry;
-      stage_candidate(g, pos, w, bn, base + (int)lane, pj, entry);
       w.stage[lane] = make_float4(pj.x, pj.y, pj.z, op.stage_w(pj.w));
-      w.stage_idx[lane] = entry;
+      w.stage_idx[lane] = ej;
     }
+    const int cur = len;
     __syncwarp();
+    len = next_chunk(g, nb, q, w, sb, bn, total, base);
+    if ((int)lane < len) stage_candidate(g, pos, w, bn, base + (int)lane, pj, ej);
     if (live) {
-      const int nk = len > s ? ((len - s - 1) >> lsh) + 1 : 0;
+      const int nk = cur > s ? ((cur - s - 1) >> lsh) + 1 : 0;
 #pragma unroll 4
       for (int kk = 0; kk < nk; ++kk) {
         const int k = (kk << lsh) + s;
@@ -203,47 +245,46 @@ __device__ __forceinline__ void scan_item(const Op& op, typename Op::I& I, const
 // Phase 1 only, for the h iteration: every candidate with r^2 < R2 (the
 // largest support any h may reach) goes into the lane's list, which is never
 // flushed; `ovf` is set when the list is full (the particle then takes the
-// multi-pass route).
+// multi-pass route). Pipelined like scan_item.
 __device__ __forceinline__ int collect_item(const Grid& g, const Nbr& nb, const float4* __restrict__ pos, int cell,
                                             float xi, float yi, float zi, float R2, int lsh, int s, bool live,
                                             WarpSmem& w, unsigned& ncand, bool& ovf) {
   const unsigned lane = lane_id();
   const Segs q = item_segments(nb, cell);
-  const int nseg = q.nseg;
+  int bn = 0, sb = 0, base = -32, total = 0;
+  if (q.nseg > 0) total = setup_segments(g, nb, q, 0, w, bn);
+  int len = next_chunk(g, nb, q, w, sb, bn, total, base);
+  float4 pj = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  unsigned ej = 0;
+  if ((int)lane < len) stage_candidate(g, pos, w, bn, base + (int)lane, pj, ej);
   int cnt = 0;
-  for (int sb = 0; sb < nseg; sb += 32) {
-    int bn;
+  while (len > 0) {
     __syncwarp();
-    const int total = setup_segments(g, nb, q, sb, w, bn);
-    for (int base = 0; base < total; base += 32) {
-      const int len = min(32, total - base);
-      __syncwarp();
-      if ((int)lane < len) {
-        float4 pj;
-        unsigned entry;
-        stage_candidate(g, pos, w, bn, base + (int)lane, pj, entry);
-        w.stage[lane] = pj;
-        w.stage_idx[lane] = entry;
-      }
-      __syncwarp();
-      if (live) {
-        const int nk = len > s ? ((len - s - 1) >> lsh) + 1 : 0;
+    if ((int)lane < len) {
+      w.stage[lane] = pj;
+      w.stage_idx[lane] = ej;
+    }
+    const int cur = len;
+    __syncwarp();
+    len = next_chunk(g, nb, q, w, sb, bn, total, base);
+    if ((int)lane < len) stage_candidate(g, pos, w, bn, base + (int)lane, pj, ej);
+    if (live) {
+      const int nk = cur > s ? ((cur - s - 1) >> lsh) + 1 : 0;
 #pragma unroll 4
-        for (int kk = 0; kk < nk; ++kk) {
-          const int k = (kk << lsh) + s;
-          const float4 c = w.stage[k];
-          const float dx = xi - c.x, dy = yi - c.y, dz = zi - c.z;
-          if (r2_of(dx, dy, dz) < R2) {
-            if (cnt < kCap) {
-              w.list[cnt * 32 + lane] = w.stage_idx[k];
-              ++cnt;
-            } else {
-              ovf = true;
-            }
+      for (int kk = 0; kk < nk; ++kk) {
+        const int k = (kk << lsh) + s;
+        const float4 c = w.stage[k];
+        const float dx = xi - c.x, dy = yi - c.y, dz = zi - c.z;
+        if (r2_of(dx, dy, dz) < R2) {
+          if (cnt < kCap) {
+            w.list[cnt * 32 + lane] = w.stage_idx[k];
+            ++cnt;
+          } else {
+            ovf = true;
           }
         }
-        ncand += (unsigned)nk;
       }
+      ncand += (unsigned)nk;
     }
   }
   __syncwarp();

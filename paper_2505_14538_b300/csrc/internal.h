@@ -90,6 +90,13 @@ struct Ctx {
   unsigned* d_nbr = nullptr;     // leaf index | shift code << kIndexBits
   int* d_tree_ctr = nullptr;     // TreeCtr
 
+  // candidate lists kept by the density call for the later loops
+  unsigned* d_nlist = nullptr;
+  long long nl_cap = 0;
+  int2* d_item_nl = nullptr;
+  unsigned long long* d_nl_ctr = nullptr;
+  int nl_lmax = 0;  // lanes-per-particle limit they were built with (0: none)
+
   // host mirrors
   Status* h_status = nullptr;  // pinned
   unsigned long long* h_stats = nullptr;  // pinned
@@ -118,6 +125,12 @@ int cells_export_impl(Ctx* c, uint32_t* cell_id, uint32_t* perm, cudaStream_t s)
 int autotune_impl(Ctx* c, int loop, cudaStream_t s);
 int backward_impl(Ctx* c, const float4* grad_ad, float4* grad_x, float4* grad_v, float* grad_u, int h_mode,
                   cudaStream_t s);
+
+// The kept candidate lists match the current lane layout (the persistent
+// density call of the last build made them).
+inline bool kept_lists_usable(const Ctx* c) {
+  return c->d_nlist && c->nl_lmax != 0 && c->nl_lmax == c->tuning.max_lanes_per_particle;
+}
 
 // counters layout helpers
 constexpr int kCtrPerPass = 4;  // item_count, plist_count, ticket, spare

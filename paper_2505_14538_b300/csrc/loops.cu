@@ -83,6 +83,11 @@ struct DensArgs {
   unsigned* barrier;  // [count, generation]
   Status* st;
   unsigned long long* stats;
+  // candidate lists kept for the gradient / force / adjoint loops (NULL: none)
+  unsigned* nlist;
+  long long nl_cap;
+  unsigned long long* nl_ctr;
+  int2* item_nl;       // per pass-0 item: (first entry, entries per lane) or (-1, 0)
 };
 
 __device__ __forceinline__ void dens_load(DensOp::I& I, const DensArgs& a, float Lmax, int k) {
@@ -133,10 +138,33 @@ __device__ __forceinline__ void number_walk(const DensOp& op, const DensOp::I& I
 // list overflowed) one neighbour scan gives the sums at the current h and one
 // Newton step; the particles that need another pass form one item of the
 // next pass.
+// The candidates a pass-0 item collects (every j within the cap's support,
+// a superset of every pair the later loops need, since no h exceeds its cap)
+// are kept in HBM, lane-interleaved as in shared memory and padded with
+// kNoEntry, so the gradient, force and adjoint loops need not scan again.
+__device__ __forceinline__ void keep_list(const DensArgs& a, const WarpSmem& w, int item_idx, bool ok, int cnt,
+                                          bool live) {
+  const unsigned lane = lane_id();
+  int2 span = make_int2(-1, 0);
+  if (__all_sync(kFull, ok)) {
+    const int m = __reduce_max_sync(kFull, live ? cnt : 0);
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(a.nl_ctr, (unsigned long long)m * 32ull);
+    base = __shfl_sync(kFull, base, 0);
+    if (base + (unsigned long long)m * 32ull <= (unsigned long long)a.nl_cap) {
+      for (int t = 0; t < m; ++t)
+        a.nlist[base + (unsigned long long)(t * 32 + (int)lane)] =
+            (live && t < cnt) ? w.list[t * 32 + lane] : kNoEntry;
+      span = make_int2((int)base, m);
+    }
+  }
+  if (lane == 0) a.item_nl[item_idx] = span;
+}
+
 __device__ __forceinline__ void dens_item(const DensArgs& a, const DensOp& op, const Grid& g, WarpSmem& w,
                                           const Item& it, const int* __restrict__ plist, bool list_mode,
                                           bool last, Item* items_next, int* plist_next, int* ctr_next, float Lmax,
-                                          unsigned& ninter, unsigned& nhiter, unsigned& ncand) {
+                                          unsigned& ninter, unsigned& nhiter, unsigned& ncand, int item_idx) {
   const unsigned lane = lane_id();
   const LaneMap lm = lane_map(it.cnt, a.lmax);
   const int k = plist[it.off + (lm.live ? lm.slot : 0)];
@@ -159,6 +187,11 @@ __device__ __forceinline__ void dens_item(const DensArgs& a, const DensOp& op, c
     bool ovf = false;
     const int cnt = collect_item(g, a.nb, a.pos, it.cell, I.x, I.y, I.z, R2, lm.lsh, lm.s, lm.live, w, ncand, ovf);
     retry = lsum_u(ovf ? 1u : 0u, lm.lsh) != 0;
+    // kept only where every h (active or not) is within this item's cap: the
+    // uniform grid with the cell-derived cap (leaves have caps of their own,
+    // and a user h_max may lie below an inactive particle's h)
+    if (a.item_nl && item_idx >= 0)
+      keep_list(a, w, item_idx, !retry && !a.nb.adaptive && g.hcap_from_cells, cnt, lm.live);
     bool done = !lm.live || retry;
     float lo = 0.0f, hi = __int_as_float(0x7f800000);
     for (int iter = 0;; ++iter) {
@@ -180,6 +213,7 @@ __device__ __forceinline__ void dens_item(const DensArgs& a, const DensOp& op, c
     }
     flush(op, I, w, (lm.live && !retry) ? cnt : 0);  // full sums at the final h
   } else {
+    if (a.item_nl && item_idx >= 0 && lane == 0) a.item_nl[item_idx] = make_int2(-1, 0);
     scan_item(op, I, g, a.nb, a.pos, it.cell, lm.lsh, lm.s, lm.live, w, ncand);
   }
   lsum2(I.ns, I.nc, lm.lsh);
@@ -322,7 +356,7 @@ __global__ void __launch_bounds__(kLoopThreads, 5) k_density(DensArgs a) {
       if (t >= n_items) break;
       const Item it = items[t];
       dens_item(a, op, g, w, it, plist, pass == 0 && !a.single_pass, last, items_next, plist_next, ctr_next,
-                Lmax, ninter, nhiter, ncand);
+                Lmax, ninter, nhiter, ncand, pass == 0 ? t : -1);
     }
     if (!grid_barrier(&a.barrier[0], &a.barrier[1], a.st, kBarrierNs)) return;
   }
@@ -401,10 +435,13 @@ struct LoopArgs {
   double* red_partial;  // force: [gridDim.x][8]
   Status* st;
   unsigned long long* stats;
+  const unsigned* nlist;  // candidate lists kept by the density call (NULL: scan)
+  const int2* item_nl;
 };
 
+
 __device__ __forceinline__ void grad_item(const LoopArgs& a, const GradOp& op, const Grid& g, WarpSmem& w,
-                                          const Item& it, float Lmax, unsigned& ninter, unsigned& ncand) {
+                                          const Item& it, int t, float Lmax, unsigned& ninter, unsigned& ncand) {
   const LaneMap lm = lane_map(it.cnt, a.lmax);
   const int k = a.plist[it.off + (lm.live ? lm.slot : 0)];
   GradOp::I I;
@@ -425,7 +462,9 @@ __device__ __forceinline__ void grad_item(const LoopArgs& a, const GradOp& op, c
   I.lap = 0.0f;
   I.count = 0;
   I.k = k;
-  scan_item(op, I, g, a.nb, a.pos, it.cell, lm.lsh, lm.s, lm.live, w, ncand);
+  int sm;
+  const unsigned* sl = kept_list(a.nlist, a.item_nl, t, sm);
+  scan_item(op, I, g, a.nb, a.pos, it.cell, lm.lsh, lm.s, lm.live, w, ncand, sl, sm);
   I.vsig = lmax(I.vsig, lm.lsh);
   I.lap = lsum(I.lap, lm.lsh);
   I.count = lsum_u(I.count, lm.lsh);
@@ -452,7 +491,7 @@ __global__ void __launch_bounds__(kLoopThreads, 5) k_gradient(LoopArgs a) {
     const int t = take_ticket(a.ticket);
     if (t >= n_items) break;
     const Item it = a.items[t];
-    grad_item(a, op, g, w, it, Lmax, ninter, ncand);
+    grad_item(a, op, g, w, it, t, Lmax, ninter, ncand);
   }
   ninter = warp_sum(ninter);
   ncand = warp_sum(ncand);
@@ -464,7 +503,7 @@ __global__ void __launch_bounds__(kLoopThreads, 5) k_gradient(LoopArgs a) {
 
 // =============================================================== force loop
 __device__ __forceinline__ void force_item(const LoopArgs& a, const ForceOp& op, const Grid& g, WarpSmem& w,
-                                           const Item& it, unsigned& ninter, unsigned& ncand, double* acc) {
+                                           const Item& it, int t, unsigned& ninter, unsigned& ncand, double* acc) {
   const LaneMap lm = lane_map(it.cnt, a.lmax);
   const int k = a.plist[it.off + (lm.live ? lm.slot : 0)];
   ForceOp::I I;
@@ -486,7 +525,9 @@ __device__ __forceinline__ void force_item(const LoopArgs& a, const ForceOp& op,
   I.axs = I.axc = I.ays = I.ayc = I.azs = I.azc = I.dus = I.duc = I.dh = 0.0f;
   I.count = 0;
   I.k = k;
-  scan_item(op, I, g, a.nb, a.pos, it.cell, lm.lsh, lm.s, lm.live, w, ncand);
+  int sm;
+  const unsigned* sl = kept_list(a.nlist, a.item_nl, t, sm);
+  scan_item(op, I, g, a.nb, a.pos, it.cell, lm.lsh, lm.s, lm.live, w, ncand, sl, sm);
   lsum2(I.axs, I.axc, lm.lsh);
   lsum2(I.ays, I.ayc, lm.lsh);
   lsum2(I.azs, I.azc, lm.lsh);
@@ -535,7 +576,7 @@ __global__ void __launch_bounds__(kLoopThreads, 4) k_force(LoopArgs a) {
     const int t = take_ticket(a.ticket);
     if (t >= n_items) break;
     const Item it = a.items[t];
-    force_item(a, op, g, w, it, ninter, ncand, acc);
+    force_item(a, op, g, w, it, t, ninter, ncand, acc);
   }
   // block partial of the FP64 sums (summed in block order by k_reduce_partials)
 #pragma unroll
@@ -630,11 +671,17 @@ int density_impl(Ctx* c, const float4* pos_in, const float4* vel_in, const uint8
   a.barrier = reinterpret_cast<unsigned*>(c->d_counters + kCtrPerPass * (c->max_passes + 2));
   a.st = c->d_status;
   a.stats = c->d_stats;
+  a.nlist = c->d_nlist;
+  a.nl_cap = c->nl_cap;
+  a.nl_ctr = c->d_nl_ctr;
+  a.item_nl = c->d_nlist ? c->d_item_nl : nullptr;
+  if (c->d_nl_ctr) cudaMemsetAsync(c->d_nl_ctr, 0, sizeof(unsigned long long), s);
   void* args[] = {&a};
   cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_density, dim3(nblk), dim3(kLoopThreads), args,
                                               kLoopSmemBytes, s);
   c->launches += 2;
   c->all_active = active == nullptr;
+  c->nl_lmax = a.item_nl ? c->tuning.max_lanes_per_particle : 0;  // lists follow this lane layout
   return e == cudaSuccess ? SWIFT_GPU_OK : SWIFT_GPU_ERR_CUDA;
 }
 
@@ -667,6 +714,9 @@ static LoopArgs loop_args(Ctx* c, int* ticket, void* out) {
   a.red_partial = c->d_red_partial;
   a.st = c->d_status;
   a.stats = c->d_stats;
+  const bool lists = kept_lists_usable(c);
+  a.nlist = lists ? c->d_nlist : nullptr;
+  a.item_nl = lists ? c->d_item_nl : nullptr;
   return a;
 }
 

@@ -145,6 +145,7 @@ struct GradOp {
     const float r2 = r2_of(dx, dy, dz);
     if (!(r2 > 0.0f)) return;  // the particle itself: its v_sig term is added at load
     if (r2 >= i.H2lo) {
+      if (r2 >= i.H2hi) return;  // outside the support (entries of a stored list may be)
       if (!(exact_r2(i.x, i.y, i.z, pj.x, pj.y, pj.z, L[0], L[1], L[2]) < exact_H2(kg, i.h))) return;
     }
     const float4 vj = vel[j];
@@ -195,7 +196,9 @@ struct ForceOp {
     const float r2 = r2_of(dx, dy, dz);
     if (!(r2 > 0.0f)) return;  // the particle itself
     const float Hj = kg * pj.w;
-    if (r2 >= fmaxf(i.H2lo, Hj * Hj - band_of(Hj, Lmax))) {
+    const float bj_band = band_of(Hj, Lmax);
+    if (r2 >= fmaxf(i.H2lo, Hj * Hj - bj_band)) {
+      if (r2 >= fmaxf(i.H2hi, Hj * Hj + bj_band)) return;  // outside both supports
       const double e = exact_r2(i.x, i.y, i.z, pj.x, pj.y, pj.z, L[0], L[1], L[2]);
       if (!(e < exact_H2(kg, i.h)) && !(e < exact_H2(kg, pj.w))) return;
     }

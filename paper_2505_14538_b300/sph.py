@@ -225,24 +225,24 @@ class Context:
         d = self.density(pos_h, vel_m, active, rho4=rho4, curl_div=curl_div, stream=stream)
         if check:
             code, detail = self.sync_status()
-            width = max(self.info()["cell_width"])
             box_third = min(float(b) for b in self.params.box) / 3.0
             adaptive = bool(self.params.flags & _lib.FLAG_ADAPTIVE)
             pos_cur = pos_h
             for _ in range(32):
                 if code != _lib.ERR_H_EXCEEDS_CELL:
                     break
-                at_cell_cap = float(d["h"].max()) >= 0.999 * self.info()["h_cap"]
-                if at_cell_cap or not adaptive:
-                    if width >= box_third:
+                info = self.info()
+                width = max(info["cell_width"])
+                if not adaptive or float(d["h"].max()) >= 0.999 * info["h_cap"]:
+                    if width >= 0.999 * box_third:
                         break
-                    width = min(2.0 * width, box_third)
+                    min_w = max(min_cell_width, min(2.0 * width, box_third))
+                else:
+                    min_w = min_cell_width  # only leaf caps were reached
                 if adaptive:
                     pos_cur = pos_cur.clone()
                     pos_cur[:, 3] = d["h"]
-                self.build_cells(pos_cur, max(min_cell_width, width) if (at_cell_cap or not adaptive) else
-                                 min_cell_width, stream)
-                width = max(width, max(self.info()["cell_width"]))
+                self.build_cells(pos_cur, min_w, stream)
                 d = self.density(pos_cur, vel_m, active, rho4=rho4, curl_div=curl_div, stream=stream)
                 code, detail = self.sync_status()
             if code not in (_lib.OK, _lib.ERR_H_NOT_CONVERGED):
