@@ -195,6 +195,18 @@ int swift_gpu_gradient(swift_gpu_ctx* ctx, const float* u, float* vsig_lapu, voi
 int swift_gpu_force(swift_gpu_ctx* ctx, const float* u, const float* alpha_v_i, const float* alpha_c_i,
                     float* accel_dudt, float* dh_dt, double* reductions, void* stream);
 
+/* Gradient and force loops in one pass over the pairs (an optimisation, not
+ * in the paper): the outputs of swift_gpu_gradient followed by
+ * swift_gpu_force with the same u, alpha_v_i, alpha_c_i (the gradient loop
+ * reads no alpha). The force pair set r < max(H_i, H_j) contains the
+ * gradient's r < H_i, so each pair is evaluated once for both, in the same
+ * order as the two calls: vsig_lapu is bitwise the same; accel_dudt and
+ * dh_dt agree to a few FP32 roundings (multiply-adds may be fused
+ * differently). Arguments as in the two calls; requires density (ERR_ORDER
+ * otherwise). */
+int swift_gpu_gradient_force(swift_gpu_ctx* ctx, const float* u, const float* alpha_v_i, const float* alpha_c_i,
+                             float* vsig_lapu, float* accel_dudt, float* dh_dt, double* reductions, void* stream);
+
 /* Adjoint of density + ghost + force (not in the paper): given
  * grad_accel_dudt[n] = float4 (dL/da_x, dL/da_y, dL/da_z, dL/d(du/dt)) for a
  * scalar loss L of the outputs of the last swift_gpu_force call, write

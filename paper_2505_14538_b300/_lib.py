@@ -34,7 +34,7 @@ EXPORTED = ("swift_gpu_default_params", "swift_gpu_create", "swift_gpu_destroy",
             "swift_gpu_build_cells", "swift_gpu_density", "swift_gpu_gradient", "swift_gpu_force",
             "swift_gpu_force_backward", "swift_gpu_sync_status", "swift_gpu_get_info", "swift_gpu_get_cells",
             "swift_gpu_get_tuning", "swift_gpu_set_tuning", "swift_gpu_autotune", "swift_gpu_density_static",
-            "swift_gpu_get_leaves")
+            "swift_gpu_get_leaves", "swift_gpu_gradient_force")
 
 STATIC_MAX_PARTICLES = 32768
 
@@ -108,6 +108,7 @@ _SIGS = {
     "swift_gpu_density_static": (_I, [ctypes.POINTER(Params), _VP, _VP, _I64, ctypes.c_float, _VP, _VP, _VP, _VP,
                                       _VP, _VP]),
     "swift_gpu_get_leaves": (_I, [_VP, _VP, _VP, _VP, _I64, _VP]),
+    "swift_gpu_gradient_force": (_I, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
 }
 
 _lib = None

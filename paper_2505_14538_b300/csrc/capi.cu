@@ -278,6 +278,41 @@ int swift_gpu_force(swift_gpu_ctx* h, const float* u, const float* alpha_v_i, co
   return rc;
 }
 
+int swift_gpu_gradient_force(swift_gpu_ctx* h, const float* u, const float* alpha_v_i, const float* alpha_c_i,
+                             float* vsig_lapu, float* accel_dudt, float* dh_dt, double* reductions, void* stream) {
+  Ctx* c = from(h);
+  if (!c) return SWIFT_GPU_ERR_ARG;
+  if (!(c->state & 2)) return SWIFT_GPU_ERR_ORDER;
+  if (c->n > 0 && (!aligned(u, 4) || !aligned(vsig_lapu, 8) || !aligned(accel_dudt, 16) ||
+                   (dh_dt && !aligned(dh_dt, 4)) || (alpha_v_i && !aligned(alpha_v_i, 4)) ||
+                   (alpha_c_i && !aligned(alpha_c_i, 4))))
+    return SWIFT_GPU_ERR_ARG;
+  if (reductions && !aligned(reductions, 8)) return SWIFT_GPU_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  int rc = ghost_impl(c, u, alpha_v_i, alpha_c_i, s);
+  if (rc == SWIFT_GPU_OK) {
+    if (c->params.flags & SWIFT_GPU_PLAIN) {
+      rc = plain_gradient_impl(c, reinterpret_cast<float2*>(vsig_lapu), s);
+      if (rc == SWIFT_GPU_OK)
+        rc = plain_force_impl(c, reinterpret_cast<float4*>(accel_dudt), dh_dt, reductions, s);
+    } else {
+      rc = grad_force_impl(c, reinterpret_cast<float2*>(vsig_lapu), reinterpret_cast<float4*>(accel_dudt), dh_dt,
+                           reductions, s);
+    }
+  }
+  if (rc == SWIFT_GPU_OK) {
+    c->state |= 4 | 8;
+    c->last_u = u;
+    c->last_alpha_v = alpha_v_i;
+    c->last_alpha_c = alpha_c_i;
+    c->last_grad_out = reinterpret_cast<float2*>(vsig_lapu);
+    c->last_force_out = reinterpret_cast<float4*>(accel_dudt);
+    c->last_dhdt = dh_dt;
+  }
+  return rc;
+}
+
 int swift_gpu_force_backward(swift_gpu_ctx* h, const float* grad_accel_dudt, float* grad_x, float* grad_v,
                              float* grad_u, int h_mode, void* stream) {
   Ctx* c = from(h);

@@ -113,6 +113,8 @@ int density_impl(Ctx* c, const float4* pos_h_in, const float4* vel_m, const uint
 int ghost_impl(Ctx* c, const float* u, const float* alpha_v, const float* alpha_c, cudaStream_t s);
 int gradient_impl(Ctx* c, float2* vsig_lapu, cudaStream_t s);
 int force_impl(Ctx* c, float4* accel_dudt, float* dh_dt, double* reductions, cudaStream_t s);
+int grad_force_impl(Ctx* c, float2* vsig_lapu, float4* accel_dudt, float* dh_dt, double* reductions,
+                    cudaStream_t s);
 int plain_density_impl(Ctx* c, const float4* pos_h_in, const float4* vel_m, const uint8_t* active, float* h_out,
                        float4* rho4, float4* curl_div, uint32_t* ngb, cudaStream_t s);
 int plain_gradient_impl(Ctx* c, float2* vsig_lapu, cudaStream_t s);

@@ -16,6 +16,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "engine.cuh"
 #include "internal.h"
@@ -431,6 +433,7 @@ struct LoopArgs {
   const int* ctr;   // item count at ctr[0]
   int* ticket;
   void* out;        // caller order: float2 (gradient) / float4 (force)
+  float2* out2;     // fused gradient + force: the gradient's float2 output
   float* dhdt;      // force: caller order, may be NULL
   double* red_partial;  // force: [gridDim.x][8]
   Status* st;
@@ -502,11 +505,16 @@ __global__ void __launch_bounds__(kLoopThreads, 5) k_gradient(LoopArgs a) {
 }
 
 // =============================================================== force loop
-__device__ __forceinline__ void force_item(const LoopArgs& a, const ForceOp& op, const Grid& g, WarpSmem& w,
-                                           const Item& it, int t, unsigned& ninter, unsigned& ncand, double* acc) {
+// kGrad: the gradient loop fused in (GradForceOp), writing both outputs.
+template <bool kGrad>
+__device__ __forceinline__ void force_item(const LoopArgs& a,
+                                           const typename std::conditional<kGrad, GradForceOp, ForceOp>::type& op,
+                                           const Grid& g, WarpSmem& w, const Item& it, int t, unsigned& ninter,
+                                           unsigned& nginter, unsigned& ncand, double* acc) {
+  using Op = typename std::conditional<kGrad, GradForceOp, ForceOp>::type;
   const LaneMap lm = lane_map(it.cnt, a.lmax);
   const int k = a.plist[it.off + (lm.live ? lm.slot : 0)];
-  ForceOp::I I;
+  typename Op::I I;
   const float4 p = a.pos[k];
   const float4 v = a.vel[k];
   const float4 gi = a.ga[k];
@@ -525,6 +533,11 @@ __device__ __forceinline__ void force_item(const LoopArgs& a, const ForceOp& op,
   I.axs = I.axc = I.ays = I.ayc = I.azs = I.azc = I.dus = I.duc = I.dh = 0.0f;
   I.count = 0;
   I.k = k;
+  if constexpr (kGrad) {
+    I.vsig = 2.0f * gi.w;  // the j = i term of v_sig,max
+    I.lap = 0.0f;
+    I.gcount = 0;
+  }
   int sm;
   const unsigned* sl = kept_list(a.nlist, a.item_nl, t, sm);
   scan_item(op, I, g, a.nb, a.pos, it.cell, lm.lsh, lm.s, lm.live, w, ncand, sl, sm);
@@ -534,12 +547,21 @@ __device__ __forceinline__ void force_item(const LoopArgs& a, const ForceOp& op,
   lsum2(I.dus, I.duc, lm.lsh);
   I.dh = lsum(I.dh, lm.lsh);
   I.count = lsum_u(I.count, lm.lsh);
+  if constexpr (kGrad) {
+    I.vsig = lmax(I.vsig, lm.lsh);
+    I.lap = lsum(I.lap, lm.lsh);
+    I.gcount = lsum_u(I.gcount, lm.lsh);
+  }
   if (lm.live && lm.s == 0) {
     ninter += I.count;
     const float ax = I.axs + I.axc, ay = I.ays + I.ayc, az = I.azs + I.azc, du = I.dus + I.duc;
     const unsigned dst = a.perm[k];
     reinterpret_cast<float4*>(a.out)[dst] = make_float4(ax, ay, az, du);
     if (a.dhdt) a.dhdt[dst] = -(I.h / (3.0f * I.rho)) * I.f * I.dh;
+    if constexpr (kGrad) {
+      nginter += I.gcount;
+      a.out2[dst] = make_float2(I.vsig, 2.0f * I.lap);
+    }
     // FP64 sums of FP32 per-particle terms
     const float m = v.w;
     const float mx = m * ax, my = m * ay, mz = m * az;
@@ -555,13 +577,15 @@ __device__ __forceinline__ void force_item(const LoopArgs& a, const ForceOp& op,
   }
 }
 
-__global__ void __launch_bounds__(kLoopThreads, 4) k_force(LoopArgs a) {
+template <bool kGrad>
+__device__ __forceinline__ void force_kernel_body(const LoopArgs& a) {
+  using Op = typename std::conditional<kGrad, GradForceOp, ForceOp>::type;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[kWarpsPerBlock][8];
   const unsigned lane = lane_id();
   const Grid g = *a.grid;
   WarpSmem& w = warp_smem(smem);
-  ForceOp op;
+  Op op;
   op.pos = a.pos; op.vel = a.vel; op.ga = a.ga; op.gb = a.gb;
   op.L[0] = g.L[0]; op.L[1] = g.L[1]; op.L[2] = g.L[2];
   op.Lmax = fmaxf(g.L[0], fmaxf(g.L[1], g.L[2]));
@@ -570,13 +594,13 @@ __global__ void __launch_bounds__(kLoopThreads, 4) k_force(LoopArgs a) {
   op.gm1 = a.ph.gamma_eos - 1.0f;
   op.compensated = a.ph.compensated;
   const int n_items = a.ctr[0];
-  unsigned ninter = 0, ncand = 0;
+  unsigned ninter = 0, nginter = 0, ncand = 0;
   double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   for (;;) {
     const int t = take_ticket(a.ticket);
     if (t >= n_items) break;
     const Item it = a.items[t];
-    force_item(a, op, g, w, it, t, ninter, ncand, acc);
+    force_item<kGrad>(a, op, g, w, it, t, ninter, nginter, ncand, acc);
   }
   // block partial of the FP64 sums (summed in block order by k_reduce_partials)
 #pragma unroll
@@ -597,7 +621,19 @@ __global__ void __launch_bounds__(kLoopThreads, 4) k_force(LoopArgs a) {
     atomicAdd(&a.stats[kStatInterForce], (unsigned long long)ninter);
     atomicAdd(&a.stats[kStatCandForce], (unsigned long long)ncand);
   }
+  if constexpr (kGrad) {
+    nginter = warp_sum(nginter);
+    if (lane == 0) {
+      atomicAdd(&a.stats[kStatInterGrad], (unsigned long long)nginter);
+      atomicAdd(&a.stats[kStatCandGrad], (unsigned long long)ncand);
+    }
+  }
 }
+
+__global__ void __launch_bounds__(kLoopThreads, 4) k_force(LoopArgs a) { force_kernel_body<false>(a); }
+
+// Gradient (Eqs. 10-11, Laplacian of u) and force in one pass over the pairs.
+__global__ void __launch_bounds__(kLoopThreads, 4) k_grad_force(LoopArgs a) { force_kernel_body<true>(a); }
 
 // One warp per quantity; lane l sums blocks l, l+32, ... and the warp then
 // combines the lanes in a fixed order, so the result does not depend on timing.
@@ -625,6 +661,7 @@ static void ensure_attrs() {
   cudaFuncSetAttribute(k_density, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLoopSmemBytes);
   cudaFuncSetAttribute(k_gradient, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLoopSmemBytes);
   cudaFuncSetAttribute(k_force, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLoopSmemBytes);
+  cudaFuncSetAttribute(k_grad_force, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLoopSmemBytes);
   g_attr_done = true;
 }
 
@@ -710,6 +747,7 @@ static LoopArgs loop_args(Ctx* c, int* ticket, void* out) {
   a.ctr = c->d_counters;  // pass-0 item count
   a.ticket = ticket;
   a.out = out;
+  a.out2 = nullptr;
   a.dhdt = nullptr;
   a.red_partial = c->d_red_partial;
   a.st = c->d_status;
@@ -739,6 +777,23 @@ int force_impl(Ctx* c, float4* out, float* dhdt, double* reductions, cudaStream_
   LoopArgs a = loop_args(c, ticket, out);
   a.dhdt = dhdt;
   k_force<<<nblk, kLoopThreads, kLoopSmemBytes, s>>>(a);
+  c->launches += 2;
+  if (reductions) {
+    k_reduce_partials<<<1, 256, 0, s>>>(c->d_red_partial, nblk, reductions);
+    c->launches++;
+  }
+  return cudaGetLastError() == cudaSuccess ? SWIFT_GPU_OK : SWIFT_GPU_ERR_CUDA;
+}
+
+int grad_force_impl(Ctx* c, float2* grad_out, float4* out, float* dhdt, double* reductions, cudaStream_t s) {
+  ensure_attrs();
+  const int nblk = persistent_blocks(c, (const void*)k_grad_force);
+  int* ticket = c->d_counters + kCtrPerPass * (c->max_passes + 1) + 1;
+  cudaMemsetAsync(ticket, 0, sizeof(int), s);
+  LoopArgs a = loop_args(c, ticket, out);
+  a.out2 = grad_out;
+  a.dhdt = dhdt;
+  k_grad_force<<<nblk, kLoopThreads, kLoopSmemBytes, s>>>(a);
   c->launches += 2;
   if (reductions) {
     k_reduce_partials<<<1, 256, 0, s>>>(c->d_red_partial, nblk, reductions);

@@ -251,4 +251,91 @@ struct ForceOp {
   }
 };
 
+// The gradient and force loops in one pass over the same pairs: the force
+// pair set (r < max(H_i, H_j)) is a superset of the gradient's (r < H_i), so
+// one interaction evaluates the force terms and, for r < H_i, the gradient
+// terms with the gradient loop's own expressions (identical results to the
+// two loops run one after the other).
+struct GradForceOp : ForceOp {
+  struct I : ForceOp::I {
+    float vsig, lap;
+    unsigned gcount;
+  };
+  __device__ __forceinline__ bool candidate(const I& i, float r2, float H2j_hi) const {
+    return ForceOp::candidate(i, r2, H2j_hi);
+  }
+  __device__ __forceinline__ void interact(I& i, int j, unsigned code) const {
+    const float4 pj = pos[j];
+    float xj = pj.x, yj = pj.y, zj = pj.z;
+    shift_j(code, L, xj, yj, zj);
+    const float dx = i.x - xj, dy = i.y - yj, dz = i.z - zj;
+    const float r2 = r2_of(dx, dy, dz);
+    if (!(r2 > 0.0f)) return;  // the particle itself
+    const float Hj = kg * pj.w;
+    const float bj_band = band_of(Hj, Lmax);
+    // membership in i's support (gradient) and in either support (force),
+    // in FP32 where the guard band allows, else in FP64 from the same floats
+    bool in_i = r2 < i.H2lo;
+    bool in_f = in_i || r2 < Hj * Hj - bj_band;
+    if (!in_f) {
+      if (r2 >= fmaxf(i.H2hi, Hj * Hj + bj_band)) return;  // outside both supports
+      const double e = exact_r2(i.x, i.y, i.z, pj.x, pj.y, pj.z, L[0], L[1], L[2]);
+      in_i = e < exact_H2(kg, i.h);
+      in_f = in_i || e < exact_H2(kg, pj.w);
+      if (!in_f) return;
+    } else if (!in_i && r2 < i.H2hi) {
+      in_i = exact_r2(i.x, i.y, i.z, pj.x, pj.y, pj.z, L[0], L[1], L[2]) < exact_H2(kg, i.h);
+    }
+    const float4 vj = vel[j];
+    const float4 aj = ga[j];  // (A, f, rho, c)
+    const float4 bj = gb[j];  // (B, alpha_v, alpha_c P, u)
+    const float invr = rsqrtf(r2);
+    const float r = r2 * invr;
+    const float ex = dx * invr, ey = dy * invr, ez = dz * invr;
+    const float dWi = i.c4 * dspline(r * i.invH);
+    const float dvx = i.vx - vj.x, dvy = i.vy - vj.y, dvz = i.vz - vj.z;
+    if (in_i) {  // gradient loop (as GradOp)
+      const float vrg = fmaf(dvz, dz, fmaf(dvy, dy, dvx * dx)) * invr;
+      i.vsig = fmaxf(i.vsig, fmaf(-beta, fminf(vrg, 0.0f), i.c + aj.w));
+      i.lap = fmaf(__fdividef(vj.w, aj.z) * (i.u - bj.w), dWi * invr, i.lap);
+      i.gcount += 1u;
+    }
+    const float invHj = __fdividef(1.0f, Hj);
+    const float ih2 = invHj * invHj;
+    const float dWj = ((8.0f / kPi) * ih2 * ih2) * dspline(r * invHj);
+    const float vr = fmaf(dvz, ez, fmaf(dvy, ey, dvx * ex));
+    const float mj = vj.w;
+    const float fsum = fmaf(i.f, dWi, aj.y * dWj);
+    const float ps = mj * fmaf(i.A, dWi, aj.x * dWj);
+    float du = mj * i.A * dWi * vr;
+    const float mu = fminf(vr, 0.0f);
+    const float vsig = fmaf(-beta, mu, i.c + aj.w);
+    const float alpha = 0.25f * (i.av + bj.y) * (i.B + bj.x);
+    const float irs = __fdividef(1.0f, i.rho + aj.z);
+    const float nu = -alpha * mu * vsig * irs;
+    const float vs = 0.5f * mj * nu * fsum;
+    du = fmaf(0.5f * vs, vr, du);
+    const float Pj = gm1 * aj.z * bj.w;
+    const float Ps = i.P + Pj;
+    const float ac = Ps > 0.0f ? __fdividef(i.acP + bj.z, Ps) : 0.0f;
+    const float dP = 2.0f * fabsf(i.P - Pj) * irs;
+    const float vc = fabsf(vr) + (dP > 0.0f ? dP * rsqrtf(dP) : 0.0f);
+    du = fmaf(ac * vc * mj * (i.u - bj.w), fsum * irs, du);
+    const float as = ps + vs;
+    if (compensated) {
+      two_sum_acc(i.axs, i.axc, -as * ex);
+      two_sum_acc(i.ays, i.ayc, -as * ey);
+      two_sum_acc(i.azs, i.azc, -as * ez);
+      two_sum_acc(i.dus, i.duc, du);
+    } else {
+      i.axs = fmaf(-as, ex, i.axs);
+      i.ays = fmaf(-as, ey, i.ays);
+      i.azs = fmaf(-as, ez, i.azs);
+      i.dus += du;
+    }
+    i.dh = fmaf(mj * dWi, vr, i.dh);
+    i.count += 1u;
+  }
+};
+
 }  // namespace sg

@@ -147,6 +147,24 @@ class Context:
             _stream(stream)), "swift_gpu_force")
         return dict(accel_dudt=accel_dudt, dh_dt=dh_dt, reductions=reductions)
 
+    def gradient_force(self, u, alpha_v=None, alpha_c=None, vsig_lapu=None, accel_dudt=None, dh_dt=None,
+                       reductions=None, want_dh=True, want_reductions=True, stream=None):
+        """swift_gpu_gradient_force: the outputs of gradient() and force() from one pass over the pairs."""
+        n = self.n
+        dev = u.device
+        vsig_lapu = vsig_lapu if vsig_lapu is not None else torch.empty(n, 2, dtype=_F32, device=dev)
+        accel_dudt = accel_dudt if accel_dudt is not None else torch.empty(n, 4, dtype=_F32, device=dev)
+        if dh_dt is None and want_dh:
+            dh_dt = torch.empty(n, dtype=_F32, device=dev)
+        if reductions is None and want_reductions:
+            reductions = torch.zeros(8, dtype=torch.float64, device=dev)
+        _check(self.lib.swift_gpu_gradient_force(
+            self.handle, _ptr(u, _F32, None, n, "u"), _ptr(alpha_v, _F32, None, n, "alpha_v"),
+            _ptr(alpha_c, _F32, None, n, "alpha_c"), _ptr(vsig_lapu, _F32, 2, n, "vsig_lapu"),
+            _ptr(accel_dudt, _F32, 4, n, "accel_dudt"), _ptr(dh_dt, _F32, None, n, "dh_dt"),
+            _ptr(reductions, torch.float64, None, None, "reductions"), _stream(stream)), "swift_gpu_gradient_force")
+        return dict(vsig_lapu=vsig_lapu, accel_dudt=accel_dudt, dh_dt=dh_dt, reductions=reductions)
+
     def force_backward(self, grad_accel_dudt, h_mode: int = 0, stream=None):
         n = self.n
         dev = grad_accel_dudt.device
@@ -210,8 +228,11 @@ class Context:
 
     # ------------------------------------------------------- whole step
     def step(self, pos_h, vel_m, u, active=None, rho4=None, curl_div=None, alpha_v=None, alpha_c=None,
-             min_cell_width: float = 0.0, check: bool = True, stream=None):
+             min_cell_width: float = 0.0, check: bool = True, fused: bool = True, stream=None):
         """build_cells -> density (h iteration) -> gradient -> force on one stream.
+
+        fused=True runs gradient and force as one call (swift_gpu_gradient_force,
+        the same outputs); fused=False as the two calls.
 
         With check=True the status word is read after the density call (a
         host synchronisation). While the h iteration asks for a support wider
@@ -248,11 +269,12 @@ class Context:
             if code not in (_lib.OK, _lib.ERR_H_NOT_CONVERGED):
                 raise SwiftGPUError(code, "density", detail)
             d["status"] = (code, detail)
-        g = self.gradient(u, stream=stream)
-        f = self.force(u, alpha_v, alpha_c, stream=stream)
         out = dict(d)
-        out["vsig_lapu"] = g
-        out.update(f)
+        if fused:
+            out.update(self.gradient_force(u, alpha_v, alpha_c, stream=stream))
+        else:
+            out["vsig_lapu"] = self.gradient(u, stream=stream)
+            out.update(self.force(u, alpha_v, alpha_c, stream=stream))
         return out
 
 
@@ -293,7 +315,7 @@ class SphForces(torch.autograd.Function):
 
 
 class StepGraph:
-    """One hot-path step (build_cells, density, gradient, force) captured once in a CUDA graph.
+    """One hot-path step (build_cells, density, gradient + force) captured once in a CUDA graph.
 
     All inputs and outputs are fixed device tensors (``pos_h``, ``vel_m``, ``u``
     are read at every replay, so the caller refreshes them in place). The
@@ -304,7 +326,8 @@ class StepGraph:
     from the current h, as the direct calls do).
     """
 
-    def __init__(self, ctx: Context, pos_h, vel_m, u, min_cell_width: float = 0.0, alpha_v=None, alpha_c=None):
+    def __init__(self, ctx: Context, pos_h, vel_m, u, min_cell_width: float = 0.0, alpha_v=None, alpha_c=None,
+                 fused: bool = True):
         n = pos_h.shape[0]
         dev = pos_h.device
         self.ctx = ctx
@@ -319,8 +342,13 @@ class StepGraph:
         def body():
             ctx.build_cells(pos_h, min_cell_width)
             ctx.density(pos_h, vel_m, h_out=o["h"], rho4=o["rho4"], curl_div=o["curl_div"], ngb_count=o["ngb"])
-            ctx.gradient(u, vsig_lapu=o["vsig_lapu"])
-            ctx.force(u, alpha_v, alpha_c, accel_dudt=o["accel_dudt"], dh_dt=o["dh_dt"], reductions=o["reductions"])
+            if fused:
+                ctx.gradient_force(u, alpha_v, alpha_c, vsig_lapu=o["vsig_lapu"], accel_dudt=o["accel_dudt"],
+                                   dh_dt=o["dh_dt"], reductions=o["reductions"])
+            else:
+                ctx.gradient(u, vsig_lapu=o["vsig_lapu"])
+                ctx.force(u, alpha_v, alpha_c, accel_dudt=o["accel_dudt"], dh_dt=o["dh_dt"],
+                          reductions=o["reductions"])
 
         side = torch.cuda.Stream(device=dev)
         side.wait_stream(torch.cuda.current_stream(dev))

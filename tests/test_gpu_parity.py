@@ -276,3 +276,42 @@ def test_step_graph_replays_bit_identically(sph):
         for k in ("h", "rho4", "curl_div", "ngb", "vsig_lapu", "accel_dudt", "dh_dt"):
             assert torch.equal(out[k], ref[k]), k
     assert g.launches_per_step > 5
+
+
+@pytest.mark.parametrize("flags", [0, 8])
+def test_gradient_force_fused_equals_separate(sph, flags):
+    """swift_gpu_gradient_force evaluates the pairs of gradient() then force() in the same order: v_sig and the
+    Laplacian bitwise, a and du/dt to a few FP32 roundings (the compiler may fuse a multiply-add differently),
+    the FP64 sums to their own rounding (uniform grid and adaptive leaves)."""
+    d, vel, u = lattice_state(16, seed=13, jitter=0.3)
+    n = len(d["pos"])
+    rng = np.random.default_rng(4)
+    av = torch.from_numpy(rng.uniform(0.1, 2.0, n).astype(np.float32)).cuda()
+    ac = torch.from_numpy(rng.uniform(0.0, 1.0, n).astype(np.float32)).cuda()
+    outs = []
+    for fused in (False, True):
+        ctx = sph.Context(n, box=d["box"], flags=flags, leaf_max=8)
+        pos_h, vel_m, ut = dev_arrays(d, vel, u)
+        ctx.build_cells(pos_h)
+        ctx.density(pos_h, vel_m)
+        if fused:
+            o = ctx.gradient_force(ut, av, ac)
+        else:
+            o = {"vsig_lapu": ctx.gradient(ut)}
+            o.update(ctx.force(ut, av, ac))
+        torch.cuda.synchronize()
+        assert ctx.sync_status() == (0, 0)
+        outs.append((o, ctx.info()))
+    (a, ia), (b, ib) = outs
+    assert torch.equal(a["vsig_lapu"], b["vsig_lapu"])
+    ad_a, ad_b = a["accel_dudt"].cpu().numpy(), b["accel_dudt"].cpu().numpy()
+    sc_a = np.abs(ad_b[:, :3]).max()
+    assert np.max(np.abs(ad_a[:, :3] - ad_b[:, :3])) <= 1e-6 * sc_a
+    assert np.max(np.abs(ad_a[:, 3] - ad_b[:, 3])) <= 1e-6 * np.abs(ad_b[:, 3]).max()
+    dh_a, dh_b = a["dh_dt"].cpu().numpy(), b["dh_dt"].cpu().numpy()
+    assert np.max(np.abs(dh_a - dh_b)) <= 1e-6 * np.abs(dh_b).max()
+    ra, rb = a["reductions"].cpu().numpy(), b["reductions"].cpu().numpy()
+    assert np.all(np.abs(ra[:3] - rb[:3]) <= 1e-6 * rb[4])  # momentum: against sum |m a|
+    assert abs(ra[3] - rb[3]) <= 1e-6 * rb[5] and abs(ra[6] - rb[6]) <= 1e-6 * rb[5]  # energy: against its abs sum
+    assert np.all(np.abs(ra[[4, 5]] - rb[[4, 5]]) <= 1e-6 * rb[[4, 5]]) and ra[7] == rb[7]
+    assert ia["interactions"][1:] == ib["interactions"][1:]
