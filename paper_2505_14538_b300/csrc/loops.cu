@@ -183,6 +183,10 @@ __device__ __forceinline__ void dens_item(const DensArgs& a, const DensOp& op, c
     hcap = a.nb.leaf_hcap[it.cell];
     if (hcap < g.hcap) cap_flag = SWIFT_GPU_ERR_H_EXCEEDS_CELL;
   }
+  // Newton bracket of the list mode, and whether its last step was taken on
+  // the prediction that it converges: the final sums then verify it
+  float lo = 0.0f, hi = __int_as_float(0x7f800000);
+  bool prov = false;
   if (list_mode) {
     const float Hc = a.ph.kg * hcap;
     const float R2 = Hc * Hc + band_of(Hc, Lmax);
@@ -195,7 +199,11 @@ __device__ __forceinline__ void dens_item(const DensArgs& a, const DensOp& op, c
     if (a.item_nl && item_idx >= 0)
       keep_list(a, w, item_idx, !retry && !a.nb.adaptive && g.hcap_from_cells, cnt, lm.live);
     bool done = !lm.live || retry;
-    float lo = 0.0f, hi = __int_as_float(0x7f800000);
+    // a step whose relative residual |n h^3 - eta^3| / eta^3 is below this
+    // leaves, by Newton's quadratic convergence, a residual well inside
+    // h_tol: the walk that would only confirm it is skipped
+    const float e3 = (float)a.ph.eta3;
+    const float pred = 0.3f * sqrtf((float)a.ph.h_tol);
     for (int iter = 0;; ++iter) {
       float ns = 0.0f, nc = 0.0f, dn = 0.0f;
       unsigned np = 0;
@@ -206,10 +214,16 @@ __device__ __forceinline__ void dens_item(const DensArgs& a, const DensOp& op, c
       if (!done) {
         if (lm.s == 0) nhiter += np;
         float h1;
-        if (newton_step(I.h, ns, nc, dn, lo, hi, hcap, cap_flag, a.ph, iter == a.ph.max_iter - 1, h1, flag))
+        const float h0 = I.h;
+        if (newton_step(h0, ns, nc, dn, lo, hi, hcap, cap_flag, a.ph, iter == a.ph.max_iter - 1, h1, flag)) {
           dens_set_h(I, h1, a.ph.kg, Lmax);
-        else
+          if (fabsf(fmaf(ns + nc, h0 * h0 * h0, -e3)) < pred * e3 && iter + 2 < a.ph.max_iter) {
+            done = true;
+            prov = true;
+          }
+        } else {
           done = true;
+        }
       }
       if (!__any_sync(kFull, !done)) break;
     }
@@ -233,7 +247,16 @@ __device__ __forceinline__ void dens_item(const DensArgs& a, const DensOp& op, c
       again = true;
     } else {
       ninter += I.count;
-      if (!list_mode && !a.single_pass) {  // NO_H_ITER: the sums at the given h, no Newton step
+      if (prov) {
+        // the predicted step, verified on the final sums (n at the new h);
+        // a particle that is not converged after all continues next pass
+        float2 br = make_float2(lo, hi);
+        if (newton_step(I.h, I.ns, I.nc, I.dn, br.x, br.y, hcap, cap_flag, a.ph, last, hn, flag)) {
+          a.h[k] = hn;
+          a.bracket[k] = br;
+          again = true;
+        }
+      } else if (!list_mode && !a.single_pass) {  // NO_H_ITER: the sums at the given h, no Newton step
         float2 br = a.bracket[k];
         step_again = newton_step(I.h, I.ns, I.nc, I.dn, br.x, br.y, hcap, cap_flag, a.ph, last, hn, flag);
         if (step_again) {
@@ -510,7 +533,7 @@ template <bool kGrad>
 __device__ __forceinline__ void force_item(const LoopArgs& a,
                                            const typename std::conditional<kGrad, GradForceOp, ForceOp>::type& op,
                                            const Grid& g, WarpSmem& w, const Item& it, int t, unsigned& ninter,
-                                           unsigned& nginter, unsigned& ncand, double* acc) {
+                                           unsigned& nginter, unsigned& ncand, float* acc, float* accc) {
   using Op = typename std::conditional<kGrad, GradForceOp, ForceOp>::type;
   const LaneMap lm = lane_map(it.cnt, a.lmax);
   const int k = a.plist[it.off + (lm.live ? lm.slot : 0)];
@@ -562,18 +585,20 @@ __device__ __forceinline__ void force_item(const LoopArgs& a,
       nginter += I.gcount;
       a.out2[dst] = make_float2(I.vsig, 2.0f * I.lap);
     }
-    // FP64 sums of FP32 per-particle terms
+    // compensated per-thread sums of the FP32 per-particle terms (FP64 beyond the thread)
     const float m = v.w;
     const float mx = m * ax, my = m * ay, mz = m * az;
     const float va = fmaf(v.z, az, fmaf(v.y, ay, v.x * ax));
-    acc[0] += (double)mx;
-    acc[1] += (double)my;
-    acc[2] += (double)mz;
-    acc[3] += (double)(m * va) + (double)(m * du);
-    acc[4] += (double)sqrtf(fmaf(mz, mz, fmaf(my, my, mx * mx)));
-    acc[5] += (double)(m * fabsf(va)) + (double)(m * fabsf(du));
-    acc[6] += (double)(m * du);
-    acc[7] += (double)I.count;
+    two_sum_acc(acc[0], accc[0], mx);
+    two_sum_acc(acc[1], accc[1], my);
+    two_sum_acc(acc[2], accc[2], mz);
+    two_sum_acc(acc[3], accc[3], m * va);
+    two_sum_acc(acc[3], accc[3], m * du);
+    two_sum_acc(acc[4], accc[4], sqrtf(fmaf(mz, mz, fmaf(my, my, mx * mx))));
+    two_sum_acc(acc[5], accc[5], m * fabsf(va));
+    two_sum_acc(acc[5], accc[5], m * fabsf(du));
+    two_sum_acc(acc[6], accc[6], m * du);
+    acc[7] += (float)I.count;  // exact: counts stay far below 2^24 per thread
   }
 }
 
@@ -595,17 +620,19 @@ __device__ __forceinline__ void force_kernel_body(const LoopArgs& a) {
   op.compensated = a.ph.compensated;
   const int n_items = a.ctr[0];
   unsigned ninter = 0, nginter = 0, ncand = 0;
-  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  // per-thread partials of the global sums: FP32 TwoSum pairs (sum, error),
+  // carried into FP64 for the block and global sums
+  float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0}, accc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   for (;;) {
     const int t = take_ticket(a.ticket);
     if (t >= n_items) break;
     const Item it = a.items[t];
-    force_item<kGrad>(a, op, g, w, it, t, ninter, nginter, ncand, acc);
+    force_item<kGrad>(a, op, g, w, it, t, ninter, nginter, ncand, acc, accc);
   }
   // block partial of the FP64 sums (summed in block order by k_reduce_partials)
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
-    double x = acc[q];
+    double x = (double)acc[q] + (double)accc[q];
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
     if (lane == 0) red[threadIdx.x >> 5][q] = x;
   }

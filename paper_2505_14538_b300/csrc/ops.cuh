@@ -81,7 +81,7 @@ __device__ __forceinline__ void dens_set_h(DensOp::I& I, float h, float kg, floa
 
 // One step of the Newton iteration on F(h) = n - (eta/h)^3 (Sec. 2.1.2) from
 // the compensated sum n = ns + nc and dn_acc = sum(3W + r dW/dr) at h.
-// Convergence |n h^3 - eta^3| <= h_tol eta^3 is tested in FP64 (no division);
+// Convergence |n h^3 - eta^3| <= h_tol eta^3 is decided as in FP64 (no division);
 // the step itself, F' = dn/dh + 3 eta^3 / h^4 clamped to [h/2, 2h] with
 // bisection on the bracket [lo, hi], is FP32. h never exceeds hcap (the cell
 // or leaf cap); a particle that needs more is finished with flag cap_flag.
@@ -91,17 +91,38 @@ __device__ __forceinline__ bool newton_step(float h, float ns, float nc, float d
                                             float hcap, int cap_flag, const Phys& ph, bool last, float& hn,
                                             int& flag) {
   flag = 0;
-  const double hd = (double)h;
-  const double h3 = hd * hd * hd;
-  const double G = fma((double)ns, h3, fma((double)nc, h3, -ph.eta3));
-  if (fabs(G) <= ph.h_tol * ph.eta3) return false;
+  // G = (ns + nc) h^3 - eta^3 in FP32 first: its error is below 8 ulp of
+  // max(n h^3, eta^3), so outside that margin around the tolerance both the
+  // convergence decision and the sign of G are those of the FP64 value;
+  // inside it (rare) G is taken in FP64.
+  const float e3 = (float)ph.eta3;
+  const float n32 = ns + nc;
+  const float h3f = h * h * h;
+  const float Gf = fmaf(n32, h3f, -e3);
+  const float tol = (float)(ph.h_tol * ph.eta3);
+  const float margin = 4.76837158203125e-7f * fmaxf(n32 * h3f, e3);  // 8 * 2^-24
+  bool conv, neg;
+  if (fabsf(Gf) + margin <= tol) {
+    conv = true;
+    neg = false;
+  } else if (fabsf(Gf) - margin > tol) {
+    conv = false;
+    neg = Gf < 0.0f;
+  } else {
+    const double hd = (double)h;
+    const double h3 = hd * hd * hd;
+    const double G = fma((double)ns, h3, fma((double)nc, h3, -ph.eta3));
+    conv = fabs(G) <= ph.h_tol * ph.eta3;
+    neg = G < 0.0;
+  }
+  if (conv) return false;
   if (last) {
     flag = SWIFT_GPU_ERR_H_NOT_CONVERGED;
     return false;
   }
-  if (G < 0.0) lo = fmaxf(lo, h);
+  if (neg) lo = fmaxf(lo, h);
   else hi = fminf(hi, h);
-  if (G < 0.0 && h >= hcap) {
+  if (neg && h >= hcap) {
     flag = cap_flag;
     return false;
   }
