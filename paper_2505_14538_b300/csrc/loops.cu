@@ -104,42 +104,47 @@ __device__ __forceinline__ void dens_load(DensOp::I& I, const DensArgs& a, float
 }
 
 // Eqs. 5-6 at the lane particle's current h over its list (one step of the
-// h iteration).
+// h iteration). Entries go four at a time: the four position loads are issued
+// before any of them is used, so a warp keeps four loads in flight; the sums
+// are taken in list order, as one at a time would.
 __device__ __forceinline__ void number_walk(const DensOp& op, const DensOp::I& I, const WarpSmem& w, int cnt,
                                             float& ns, float& nc, float& dn, unsigned& npairs) {
   const unsigned lane = lane_id();
   const int m = __reduce_max_sync(kFull, cnt);
-  for (int t = 0; t < m; ++t) {
-    if (t < cnt) {
-      const unsigned e = w.list[t * 32 + lane];
-      const int j = (int)(e & kIndexMask);
-      const float4 pj = op.pos[j];
-      float xj = pj.x, yj = pj.y, zj = pj.z;
-      shift_j(e >> kIndexBits, op.L, xj, yj, zj);
-      const float dx = I.x - xj, dy = I.y - yj, dz = I.z - zj;
-      const float r2 = r2_of(dx, dy, dz);
-      if (r2 < I.H2hi) {
-        const float invr = r2 > 0.0f ? rsqrtf(r2) : 0.0f;
-        const float r = r2 * invr;
-        float wq, dwq;
-        spline(r * I.invH, wq, dwq);
-        const float W = I.c3 * wq;
-        if (op.compensated) two_sum_acc(ns, nc, W);
-        else ns += W;
-        dn += fmaf(r, I.c4 * dwq, 3.0f * W);
-        npairs += (j != I.k) ? 1u : 0u;
+  for (int t0 = 0; t0 < m; t0 += 4) {
+    unsigned e[4];
+    float4 pj[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int t = t0 + q;
+      e[q] = t < cnt ? w.list[t * 32 + lane] : (unsigned)I.k;  // past the end: the particle itself (r = 0)
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) pj[q] = op.pos[e[q] & kIndexMask];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (t0 + q < cnt) {
+        const int j = (int)(e[q] & kIndexMask);
+        float xj = pj[q].x, yj = pj[q].y, zj = pj[q].z;
+        shift_j(e[q] >> kIndexBits, op.L, xj, yj, zj);
+        const float dx = I.x - xj, dy = I.y - yj, dz = I.z - zj;
+        const float r2 = r2_of(dx, dy, dz);
+        if (r2 < I.H2hi) {
+          const float invr = r2 > 0.0f ? rsqrtf(r2) : 0.0f;
+          const float r = r2 * invr;
+          float wq, dwq;
+          spline(r * I.invH, wq, dwq);
+          const float W = I.c3 * wq;
+          if (op.compensated) two_sum_acc(ns, nc, W);
+          else ns += W;
+          dn += fmaf(r, I.c4 * dwq, 3.0f * W);
+          npairs += (j != I.k) ? 1u : 0u;
+        }
       }
     }
   }
 }
 
-// One density item. In list mode (first pass) the item's candidates within
-// the largest reachable support are collected once and the whole Newton
-// iteration runs over those lists; the full sums (Eqs. 2-6 with div/curl)
-// are then taken at the final h. Otherwise (later passes, and particles whose
-// list overflowed) one neighbour scan gives the sums at the current h and one
-// Newton step; the particles that need another pass form one item of the
-// next pass.
 // The candidates a pass-0 item collects (every j within the cap's support,
 // a superset of every pair the later loops need, since no h exceeds its cap)
 // are kept in HBM, lane-interleaved as in shared memory and padded with
