@@ -22,6 +22,8 @@
 // particle and split its candidates.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace sg {
@@ -156,6 +158,34 @@ __device__ __forceinline__ void flush(const Op& op, typename Op::I& I, const War
   }
 }
 
+// Phase 2 for an Op that splits an interaction into load(j) and the
+// arithmetic: two entries at a time, both entries' records loaded first.
+template <class Op>
+__device__ __forceinline__ void flush2(const Op& op, typename Op::I& I, const WarpSmem& w, int cnt) {
+  const unsigned lane = lane_id();
+  const int m = __reduce_max_sync(kFull, cnt);
+  for (int t = 0; t < m; t += 2) {
+    const unsigned e0 = t < cnt ? w.list[t * 32 + lane] : (unsigned)I.k;
+    const unsigned e1 = t + 1 < cnt ? w.list[(t + 1) * 32 + lane] : (unsigned)I.k;
+    typename Op::Rec r0, r1;
+    op.load((int)(e0 & kIndexMask), r0);
+    op.load((int)(e1 & kIndexMask), r1);
+    if (t < cnt) op.interact(I, (int)(e0 & kIndexMask), e0 >> kIndexBits, r0);
+    if (t + 1 < cnt) op.interact(I, (int)(e1 & kIndexMask), e1 >> kIndexBits, r1);
+  }
+}
+
+template <class Op, class = void>
+struct has_load : std::false_type {};
+template <class Op>
+struct has_load<Op, decltype((void)sizeof(typename Op::Rec))> : std::true_type {};
+
+template <class Op>
+__device__ __forceinline__ void flush_any(const Op& op, typename Op::I& I, const WarpSmem& w, int cnt) {
+  if constexpr (has_load<Op>::value) flush2(op, I, w, cnt);
+  else flush(op, I, w, cnt);
+}
+
 // Next chunk of an item's candidates: moves `base` past the current chunk
 // (to the next batch of segments when the batch is used up) and returns the
 // chunk's length, 0 at the end.
@@ -212,7 +242,7 @@ __device__ __forceinline__ void scan_item(const Op& op, typename Op::I& I, const
   for (;;) {
     const bool done = len == 0;
     if (done || __any_sync(kFull, cnt > kCap - per)) {
-      flush(op, I, w, cnt);
+      flush_any(op, I, w, cnt);
       cnt = 0;
       if (done) break;
     }

@@ -285,8 +285,23 @@ struct GradForceOp : ForceOp {
   __device__ __forceinline__ bool candidate(const I& i, float r2, float H2j_hi) const {
     return ForceOp::candidate(i, r2, H2j_hi);
   }
+  // The four records of particle j, loaded ahead of the arithmetic.
+  struct Rec {
+    float4 pj, vj, aj, bj;
+  };
+  __device__ __forceinline__ void load(int j, Rec& r) const {
+    r.pj = pos[j];
+    r.vj = vel[j];
+    r.aj = ga[j];
+    r.bj = gb[j];
+  }
   __device__ __forceinline__ void interact(I& i, int j, unsigned code) const {
-    const float4 pj = pos[j];
+    Rec r;
+    load(j, r);
+    interact(i, j, code, r);
+  }
+  __device__ __forceinline__ void interact(I& i, int j, unsigned code, const Rec& rec) const {
+    const float4 pj = rec.pj;
     float xj = pj.x, yj = pj.y, zj = pj.z;
     shift_j(code, L, xj, yj, zj);
     const float dx = i.x - xj, dy = i.y - yj, dz = i.z - zj;
@@ -307,9 +322,9 @@ struct GradForceOp : ForceOp {
     } else if (!in_i && r2 < i.H2hi) {
       in_i = exact_r2(i.x, i.y, i.z, pj.x, pj.y, pj.z, L[0], L[1], L[2]) < exact_H2(kg, i.h);
     }
-    const float4 vj = vel[j];
-    const float4 aj = ga[j];  // (A, f, rho, c)
-    const float4 bj = gb[j];  // (B, alpha_v, alpha_c P, u)
+    const float4 vj = rec.vj;
+    const float4 aj = rec.aj;  // (A, f, rho, c)
+    const float4 bj = rec.bj;  // (B, alpha_v, alpha_c P, u)
     const float invr = rsqrtf(r2);
     const float r = r2 * invr;
     const float ex = dx * invr, ey = dy * invr, ez = dz * invr;
