@@ -54,8 +54,12 @@ __device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned* smem, 
   return r;
 }
 
-__global__ void k_scan_tiles(const unsigned* __restrict__ in, int m, unsigned* __restrict__ tile_sums) {
+// `gate` (may be NULL): the scan is skipped when *gate == 0 (a radix pass
+// over key bits the cells do not use).
+__global__ void k_scan_tiles(const unsigned* __restrict__ in, int m, unsigned* __restrict__ tile_sums,
+                             const int* __restrict__ gate) {
   __shared__ unsigned sm[32];
+  if (gate && *gate == 0) return;
   const int base = blockIdx.x * kScanTile;
   unsigned s = 0;
 #pragma unroll
@@ -68,8 +72,9 @@ __global__ void k_scan_tiles(const unsigned* __restrict__ in, int m, unsigned* _
   if (threadIdx.x == 0) tile_sums[blockIdx.x] = tot;
 }
 
-__global__ void k_scan_top(unsigned* __restrict__ tile_sums, int ntiles) {
+__global__ void k_scan_top(unsigned* __restrict__ tile_sums, int ntiles, const int* __restrict__ gate) {
   __shared__ unsigned sm[32];
+  if (gate && *gate == 0) return;
   unsigned carry = 0;
   for (int base = 0; base < ntiles; base += kScanTile) {
     unsigned v[kScanItems];
@@ -94,8 +99,9 @@ __global__ void k_scan_top(unsigned* __restrict__ tile_sums, int ntiles) {
 }
 
 __global__ void k_scan_down(const unsigned* __restrict__ in, int m, const unsigned* __restrict__ tile_offs,
-                            unsigned* __restrict__ out) {
+                            unsigned* __restrict__ out, const int* __restrict__ gate) {
   __shared__ unsigned sm[32];
+  if (gate && *gate == 0) return;
   const int base = blockIdx.x * kScanTile;
   unsigned v[kScanItems];
   unsigned s = 0;
@@ -117,12 +123,13 @@ __global__ void k_scan_down(const unsigned* __restrict__ in, int m, const unsign
 int scan_tiles_needed(int64_t m) { return (int)((m + kScanTile - 1) / kScanTile); }
 
 // out may alias in. tile_tmp needs scan_tiles_needed(m) entries.
-void exclusive_scan(Ctx* c, const unsigned* in, unsigned* out, int m, unsigned* tile_tmp, cudaStream_t s) {
+void exclusive_scan(Ctx* c, const unsigned* in, unsigned* out, int m, unsigned* tile_tmp, cudaStream_t s,
+                    const int* gate) {
   if (m <= 0) return;
   int nt = scan_tiles_needed(m);
-  k_scan_tiles<<<nt, kScanThreads, 0, s>>>(in, m, tile_tmp);
-  k_scan_top<<<1, kScanThreads, 0, s>>>(tile_tmp, nt);
-  k_scan_down<<<nt, kScanThreads, 0, s>>>(in, m, tile_tmp, out);
+  k_scan_tiles<<<nt, kScanThreads, 0, s>>>(in, m, tile_tmp, gate);
+  k_scan_top<<<1, kScanThreads, 0, s>>>(tile_tmp, nt, gate);
+  k_scan_down<<<nt, kScanThreads, 0, s>>>(in, m, tile_tmp, out, gate);
   c->launches += 3;
 }
 
@@ -171,6 +178,7 @@ __global__ void k_grid_setup(const unsigned* __restrict__ hmax_bits, Grid* g, Ph
   int bits = 0;
   while ((1 << bits) < nct) ++bits;
   g->key_bits = bits;
+  for (int q = 0; q < kMaxKeyPasses; ++q) g->pass_live[q] = 8 * q < bits ? 1 : 0;
 }
 
 // Spread the 10 low bits of v to every third bit (bit b -> bit 3b).
@@ -192,8 +200,32 @@ __global__ void k_cell_ids(const float4* __restrict__ pos_h, int n, const Grid* 
                            unsigned* __restrict__ morton_out) {
   const int nx = g->nc[0], ny = g->nc[1], nz = g->nc[2];
   const double Lx = g->L[0], Ly = g->L[1], Lz = g->L[2];
+  const float ncf[3] = {(float)nx, (float)ny, (float)nz};
+  const float Lf[3] = {g->L[0], g->L[1], g->L[2]};
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     float4 p = pos_h[i];
+    vals[i] = (unsigned)i;
+    if (!cell_out) {
+      // FP32 first: t = x nc / L carries at most 3 roundings (< 2^-22 t), so
+      // a fraction of t farther than 8 ulps from an integer floors as the FP64
+      // value does; closer ones (and positions outside [0, L)) take FP64.
+      const float xs[3] = {p.x, p.y, p.z};
+      int cf[3];
+      bool ok = true;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const float t = Lf[q] == 1.0f ? xs[q] * ncf[q] : (xs[q] * ncf[q]) / Lf[q];
+        const float fl = floorf(t);
+        const float fr = t - fl;
+        const float eta = 4.76837158203125e-7f * fmaxf(t, 1.0f);  // 8 * 2^-24
+        ok = ok && xs[q] >= 0.0f && xs[q] < Lf[q] && fr > eta && fr < 1.0f - eta;
+        cf[q] = min(max((int)fl, 0), (q == 0 ? nx : q == 1 ? ny : nz) - 1);
+      }
+      if (ok) {
+        keys[i] = (unsigned)(cf[0] + nx * (cf[1] + ny * cf[2]));
+        continue;
+      }
+    }
     // wrap into [0, L) and floor(x nc / L), each FP64 operation rounded once.
     // A float x in [0, L) has floor(x / L) = 0, and x * nc is exact, so the
     // divisions (slow in FP64) are skipped only where they cannot change the result.
@@ -223,7 +255,6 @@ __global__ void k_cell_ids(const float4* __restrict__ pos_h, int n, const Grid* 
     } else {
       keys[i] = cell;
     }
-    vals[i] = (unsigned)i;
   }
 }
 
@@ -262,6 +293,17 @@ __global__ void k_radix_scatter(const unsigned* __restrict__ kin, const unsigned
   __shared__ unsigned wcnt[kRadixThreads / 32][256];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool live = shift < (bits >= 0 ? bits : g->key_bits);
+  if (!live) {  // the digit is 0 for every key: the stable order is the input order
+    const int base = blockIdx.x * kRadixTile;
+    for (int k = threadIdx.x; k < kRadixTile; k += kRadixThreads) {
+      const int i = base + k;
+      if (i < n) {
+        kout[i] = kin[i];
+        vout[i] = vin[i];
+      }
+    }
+    return;
+  }
   run[threadIdx.x] = offs[threadIdx.x * gridDim.x + blockIdx.x];
   for (int ww = 0; ww < kRadixThreads / 32; ++ww) wcnt[ww][threadIdx.x] = 0;
   __syncthreads();
@@ -329,7 +371,8 @@ int build_cells_impl(Ctx* c, const float4* pos_h, int n, float min_width, cudaSt
     int src = 0;
     auto pass = [&](int shift, int bits) {
       k_radix_count<<<nb, kRadixThreads, 0, s>>>(c->d_keys[src], n, shift, c->d_grid, bits, c->d_hist);
-      exclusive_scan(c, c->d_hist, c->d_hist, 256 * nb, c->d_scan_tmp, s);
+      const int* gate = bits >= 0 ? nullptr : &c->d_grid->pass_live[shift / 8];
+      exclusive_scan(c, c->d_hist, c->d_hist, 256 * nb, c->d_scan_tmp, s, gate);
       k_radix_scatter<<<nb, kRadixThreads, 0, s>>>(c->d_keys[src], c->d_vals[src], n, shift, c->d_grid, bits,
                                                     c->d_hist, c->d_keys[1 - src], c->d_vals[1 - src]);
       c->launches += 2;

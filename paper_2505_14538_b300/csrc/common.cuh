@@ -31,6 +31,8 @@ struct Status {
 
 // Cell grid descriptor, computed on the device by the build so that no host
 // synchronisation is needed.
+constexpr int kMaxKeyPasses = 4;  // 8-bit radix passes over a cell id (at most 2^30 cells)
+
 struct Grid {
   int nc[3];
   int ncells;
@@ -39,6 +41,7 @@ struct Grid {
   int hcap_from_cells;
   int key_bits;
   float width[3];
+  int pass_live[kMaxKeyPasses];  // radix pass q sorts bits 8q.. of the cell id (0: all zero)
 };
 
 // Status a particle capped at the cell's h raises: a wider cell would help

@@ -106,7 +106,8 @@ Ctx* from(swift_gpu_ctx* c);
 int phys_from(const swift_gpu_params* p, Phys* ph);
 
 int scan_tiles_needed(int64_t m);
-void exclusive_scan(Ctx* c, const unsigned* in, unsigned* out, int m, unsigned* tile_tmp, cudaStream_t s);
+void exclusive_scan(Ctx* c, const unsigned* in, unsigned* out, int m, unsigned* tile_tmp, cudaStream_t s,
+                    const int* gate = nullptr);
 int build_cells_impl(Ctx* c, const float4* pos_h, int n, float min_width, cudaStream_t s);
 int density_impl(Ctx* c, const float4* pos_h_in, const float4* vel_m, const uint8_t* active, float* h_out,
                  float4* rho4, float4* curl_div, uint32_t* ngb, cudaStream_t s);

@@ -322,44 +322,76 @@ __global__ void __launch_bounds__(kLoopThreads, 5) k_density(DensArgs a) {
       a.ngb[k] = a.ngb_out ? a.ngb_out[src] : 0u;
     }
   }
-  // ---- active work items, one warp per cell (or per leaf)
-  const int nunits = a.nb.adaptive ? *a.nb.n_leaves : g.ncells;
-  for (int c = gwarp; c < nunits; c += nwarps) {
-    int cs, ce;
-    if (a.nb.adaptive) {
-      const int2 r = a.nb.leaf_range[c];
-      cs = r.x;
-      ce = r.y;
-    } else {
-      cs = a.nb.cell_start[c];
-      ce = a.nb.cell_start[c + 1];
+  // ---- active work items (runs of <= kItemMax active particles of a cell or
+  // leaf). Each block takes a contiguous run of cells: its warps count the
+  // active particles first, one atomic per counter reserves the block's
+  // share, and the second sweep writes the items (two atomics per block, not
+  // per cell).
+  {
+    __shared__ int s_tot[kWarpsPerBlock], s_nit[kWarpsPerBlock], s_base[2];
+    const int nunits = a.nb.adaptive ? *a.nb.n_leaves : g.ncells;
+    const int wib = (int)(threadIdx.x >> 5);
+    const int per_block = (nunits + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int c_lo = (int)blockIdx.x * per_block, c_hi = min(nunits, c_lo + per_block);
+    auto range = [&](int c, int& cs, int& ce) {
+      if (a.nb.adaptive) {
+        const int2 r = a.nb.leaf_range[c];
+        cs = r.x;
+        ce = r.y;
+      } else {
+        cs = a.nb.cell_start[c];
+        ce = a.nb.cell_start[c + 1];
+      }
+    };
+    int wtot = 0, wnit = 0;
+    for (int c = c_lo + wib; c < c_hi; c += kWarpsPerBlock) {
+      int cs, ce;
+      range(c, cs, ce);
+      int total = 0;
+      for (int b = cs; b < ce; b += 32) {
+        const int k = b + (int)lane;
+        const bool on = k < ce && (a.active ? a.active[a.perm[k]] != 0 : true);
+        total += __popc(__ballot_sync(kFull, on));
+      }
+      wtot += total;
+      wnit += (total + kItemMax - 1) / kItemMax;
     }
-    if (ce == cs) continue;
-    int total = 0;
-    for (int b = cs; b < ce; b += 32) {
-      const int k = b + (int)lane;
-      const bool on = k < ce && (a.active ? a.active[a.perm[k]] != 0 : true);
-      total += __popc(__ballot_sync(kFull, on));
-    }
-    if (total == 0) continue;
-    const int nit = (total + kItemMax - 1) / kItemMax;
-    int pbase = 0, ibase = 0;
     if (lane == 0) {
-      pbase = atomicAdd(&a.ctr[ctr_index(0, 1)], total);
-      ibase = atomicAdd(&a.ctr[ctr_index(0, 0)], nit);
+      s_tot[wib] = wtot;
+      s_nit[wib] = wnit;
     }
-    pbase = __shfl_sync(kFull, pbase, 0);
-    ibase = __shfl_sync(kFull, ibase, 0);
-    int wc = 0;
-    for (int b = cs; b < ce; b += 32) {
-      const int k = b + (int)lane;
-      const bool on = k < ce && (a.active ? a.active[a.perm[k]] != 0 : true);
-      const unsigned m = __ballot_sync(kFull, on);
-      if (on) a.plist0[pbase + wc + __popc(m & ((1u << lane) - 1u))] = k;
-      wc += __popc(m);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int pt = 0, it = 0;
+      for (int q = 0; q < kWarpsPerBlock; ++q) {
+        const int tq = s_tot[q], nq = s_nit[q];
+        s_tot[q] = pt;
+        s_nit[q] = it;
+        pt += tq;
+        it += nq;
+      }
+      s_base[0] = pt ? atomicAdd(&a.ctr[ctr_index(0, 1)], pt) : 0;
+      s_base[1] = it ? atomicAdd(&a.ctr[ctr_index(0, 0)], it) : 0;
     }
-    for (int t = (int)lane; t < nit; t += 32)
-      a.items0[ibase + t] = Item{c, pbase + t * kItemMax, min(kItemMax, total - t * kItemMax), 0};
+    __syncthreads();
+    int pbase = s_base[0] + s_tot[wib], ibase = s_base[1] + s_nit[wib];
+    for (int c = c_lo + wib; c < c_hi; c += kWarpsPerBlock) {
+      int cs, ce;
+      range(c, cs, ce);
+      int wc = 0;
+      for (int b = cs; b < ce; b += 32) {
+        const int k = b + (int)lane;
+        const bool on = k < ce && (a.active ? a.active[a.perm[k]] != 0 : true);
+        const unsigned m = __ballot_sync(kFull, on);
+        if (on) a.plist0[pbase + wc + __popc(m & ((1u << lane) - 1u))] = k;
+        wc += __popc(m);
+      }
+      const int nit = (wc + kItemMax - 1) / kItemMax;
+      for (int t = (int)lane; t < nit; t += 32)
+        a.items0[ibase + t] = Item{c, pbase + t * kItemMax, min(kItemMax, wc - t * kItemMax), 0};
+      pbase += wc;
+      ibase += nit;
+    }
   }
   if (!grid_barrier(&a.barrier[0], &a.barrier[1], a.st, kBarrierNs)) return;
 
