@@ -203,12 +203,19 @@ def zeldovich(n_side: int = 256, index: int = 5, max_contrast: float = 100.0, sp
     amp[0, 0, 0] = 0.0
     dk = dk * amp
     ks = (KX, KY, KZ)
-    psi = [np.fft.irfftn(1j * kk * dk / k2, s=(n, n, n)) for kk in ks]
-    grad = [[np.fft.irfftn(-ks[a] * ks[b] * dk / k2, s=(n, n, n)) for b in range(3)] for a in range(3)]
-    J = np.stack([np.stack(g, -1) for g in grad], -2)  # (..., a, b) = d psi_a / d q_b
+    psi = [np.fft.irfftn(1j * kk * dk / k2, s=(n, n, n), axes=(0, 1, 2)) for kk in ks]
+    grad = [[np.fft.irfftn(-ks[a] * ks[b] * dk / k2, s=(n, n, n), axes=(0, 1, 2)).ravel() for b in range(3)] for a in range(3)]
+    # det(I + A J) = 1 + A tr J + A^2 (sum of the principal 2x2 minors) + A^3 det J, per grid point
+    J = grad  # J[a][b] = d psi_a / d q_b
+    tr = J[0][0] + J[1][1] + J[2][2]
+    m2 = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) + (J[0][0] * J[2][2] - J[0][2] * J[2][0]) + \
+         (J[1][1] * J[2][2] - J[1][2] * J[2][1])
+    dt = (J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0])
+          + J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]))
+    del grad, J
 
     def min_det(A):
-        return np.linalg.det(np.eye(3) + A * J).min()
+        return (1.0 + A * (tr + A * (m2 + A * dt))).min()
 
     target = 1.0 / max_contrast
     lo, hi = 0.0, 1.0

@@ -4,6 +4,8 @@
   replayed (the benchmark's headline configuration), uniform grid.
 * Plummer mixture, 2^21 particles, 10 % active: one active step with
   adaptive leaves after an all-active step (the benchmark's clustered run).
+* Zel'dovich-displaced 256^3 lattice (16.7M particles, density contrast
+  100): a whole step from the lattice h with adaptive leaves.
 
 The oracle evaluates only a random sample of particles plus the neighbours
 their force needs, at the GPU's final h. Tolerances as in the small parity
@@ -32,17 +34,34 @@ def sph():
 
 
 def force_neighbours(x, h, sample, box=(1.0, 1.0, 1.0)):
-    """Union of the sample and every j with r_ij < max(H_i, H_j) for some sampled i (FP64, minimum image)."""
+    """Union of the sample and every j with r_ij < max(H_i, H_j) for some sampled i (FP64, minimum image).
+
+    Candidates come from the 27 cells around each sampled particle on a grid
+    no finer than the largest support, then the exact test is applied.
+    """
     L = np.asarray(box, np.float64)
     H = KG * h.astype(np.float64)
     xs = x.astype(np.float64)
+    nc = np.maximum(np.floor(L / H.max()).astype(np.int64), 1)
+    c = np.minimum((np.mod(xs, L) / L * nc).astype(np.int64), nc - 1)
+    lin = c[:, 0] + nc[0] * (c[:, 1] + nc[1] * c[:, 2])
+    order = np.argsort(lin, kind="stable")
+    start = np.searchsorted(lin[order], np.arange(nc.prod() + 1))
     keep = np.zeros(len(x), bool)
     keep[sample] = True
     for i in sample:
-        d = xs - xs[i]
+        cand = []
+        for dz in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    q = (c[i] + np.array([dx, dy, dz])) % nc
+                    cl = q[0] + nc[0] * (q[1] + nc[1] * q[2])
+                    cand.append(order[start[cl]:start[cl + 1]])
+        cand = np.unique(np.concatenate(cand))
+        d = xs[cand] - xs[i]
         d -= L * np.round(d / L)
         r2 = (d * d).sum(1)
-        keep |= r2 < np.maximum(H[i], H) ** 2
+        keep[cand[r2 < np.maximum(H[i], H[cand]) ** 2]] = True
     return keep
 
 
@@ -136,3 +155,26 @@ def test_plummer_2m_adaptive_active_step_sampled(sph, O):
     # inactive particles keep their h and their density inputs
     off = ~d["active"].astype(bool)
     assert np.array_equal(h[off], warm["h"].cpu().numpy()[off])
+
+
+def test_zeldovich_256_adaptive_sampled(sph, O):
+    """256^3 lattice displaced by a Zel'dovich field (density contrast 100): a full step with adaptive leaves."""
+    d = ics.zeldovich(256)
+    n = len(d["pos"])
+    vel = d["vel"].astype(np.float32)
+    u = d["u"].astype(np.float32)
+    pos_h = torch.from_numpy(np.concatenate([d["pos"], d["h"][:, None]], 1).astype(np.float32)).cuda()
+    vel_m = torch.from_numpy(np.concatenate([vel, d["m"][:, None]], 1).astype(np.float32)).cuda()
+    ut = torch.from_numpy(u).cuda()
+    ctx = sph.Context(n, flags=8, max_iter=40)
+    o = ctx.step(pos_h, vel_m, ut)
+    torch.cuda.synchronize()
+    assert o["status"][0] == 0, o["status"]
+    out = {k: o[k].cpu().numpy() for k in ("h", "rho4", "ngb", "vsig_lapu", "accel_dudt")}
+    h = out["h"]
+    assert h.max() / h.min() > 2.0  # the h range the contrast implies
+    rng = np.random.default_rng(256)
+    sample = np.unique(np.concatenate([rng.choice(n, 40, replace=False), np.argsort(h)[:12], np.argsort(h)[-12:]]))
+    check_sample(O, d, vel, u, h, out, sample, float(ctx.params.h_tol))
+    red = o["reductions"].cpu().numpy()
+    assert np.all(np.abs(red[:3]) <= 1e-6 * red[4])  # momentum, FP64 on the device

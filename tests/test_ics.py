@@ -1,0 +1,51 @@
+"""Seeded input generators (CPU): each workload has the shape it is documented to have."""
+import numpy as np
+
+from paper_2505_14538_b300 import ics
+
+
+def test_lattice_and_sedov():
+    d = ics.lattice(8, jitter=0.1)
+    assert d["pos"].shape == (512, 3) and np.all((d["pos"] >= 0) & (d["pos"] < 1))
+    s = ics.sedov(16)
+    n = len(s["pos"])
+    # total injected energy 1 (E = sum m u over the hot particles, on top of the background)
+    e = float(np.sum(s["m"].astype(np.float64) * (s["u"].astype(np.float64) - 1e-5)))
+    assert abs(e - 1.0) < 1e-4 and n == 4096
+
+
+def test_plummer_counts_and_active_fraction():
+    d = ics.plummer(n_total=2 ** 14, n_spheres=8)
+    assert len(d["pos"]) == 2 ** 14
+    frac = d["active"].mean()
+    assert 0.08 < frac < 0.12
+
+
+def test_kh_density_ratio():
+    d = ics.kh()
+    y = d["pos"][:, 1]
+    inside = np.abs(y - 0.5) < 0.25
+    assert abs(inside.sum() / (~inside).sum() - 21 / 11) < 1e-9
+
+
+def test_zeldovich_contrast_matches_determinant():
+    """The amplitude puts the largest 1/det(I + grad psi) at max_contrast (checked with numpy's det)."""
+    n = 16
+    d = ics.zeldovich(n, max_contrast=20.0)
+    # rebuild the displacement gradient from the same seeded field and take det directly
+    rng = np.random.default_rng(ics.SEED_BASE + 5)
+    noise = rng.normal(size=(n, n, n))
+    dk = np.fft.rfftn(noise)
+    k1 = np.fft.fftfreq(n, 1.0 / n) * 2 * np.pi
+    kz = np.fft.rfftfreq(n, 1.0 / n) * 2 * np.pi
+    KX, KY, KZ = np.meshgrid(k1, k1, kz, indexing="ij")
+    k2 = KX ** 2 + KY ** 2 + KZ ** 2
+    k2[0, 0, 0] = 1.0
+    amp = np.sqrt(k2 ** (-1.0))
+    amp[0, 0, 0] = 0.0
+    dk = dk * amp
+    ks = (KX, KY, KZ)
+    J = np.stack([np.stack([np.fft.irfftn(-ks[a] * ks[b] * dk / k2, s=(n, n, n), axes=(0, 1, 2)) for b in range(3)], -1)
+                  for a in range(3)], -2)
+    det = np.linalg.det(np.eye(3) + d["amplitude"] * J)
+    assert abs(1.0 / det.min() - 20.0) < 1e-6 * 20.0
