@@ -124,3 +124,72 @@ def test_adjoint_matches_oracle_finite_differences(O):
             assert abs(g - fds[0]) <= 1e-4 * scale[nm], (nm, k, comp, g, fds[0])
             checked += 1
     assert checked >= 12
+
+
+def test_adjoint_kh32_full_size_finite_differences(O):
+    """The full 32^3 Kelvin-Helmholtz slab: GPU adjoint vs central differences of the oracle's loss.
+
+    At fixed h, moving particle k changes only the densities within one support
+    of it and the forces within two, so each difference quotient evaluates the
+    oracle on the particles within 3.2 of the largest support (forces) and 4.3
+    (densities) of k: the loss terms outside do not change. Samples lie more
+    than three supports from the slab faces, where all neighbours share u (the
+    conduction term, which carries u_i - u_j, is then smooth).
+    """
+    d = ics.kh()
+    n = len(d["pos"])
+    rng = np.random.default_rng(11)
+    vel = (d["vel"] + rng.normal(0, 0.05, (n, 3))).astype(np.float32)
+    u = d["u"].astype(np.float32)
+    w = rng.normal(size=(n, 3))
+    cw = rng.normal(size=n)
+    gx, gv, gu, _ = _run_gpu(d, vel, u, w, cw)
+    x = d["pos"].astype(np.float64)
+    v = vel.astype(np.float64)
+    uu = u.astype(np.float64)
+    m = d["m"]
+    h = d["h"]
+    L = np.asarray(d["box"], np.float64)
+    Hmax = float(np.float32(1.825742)) * float(h.max())
+    y = x[:, 1]
+    far = (np.abs(y - 0.25) > 3 * Hmax) & (np.abs(y - 0.75) > 3 * Hmax)
+    p = O.Params(box=d["box"])
+
+    def local_loss(k, xx, vv, ux):
+        dd = x - x[k]
+        dd -= L * np.round(dd / L)
+        r2 = (dd * dd).sum(1)
+        act_f = (r2 < (3.2 * Hmax) ** 2).astype(np.uint8)
+        act_d = (r2 < (4.3 * Hmax) ** 2).astype(np.uint8)
+        od = O.density(p, xx, vv, m, h, active=act_d)
+        g = O.ghost(p, h, od["rho"], od["drho_dh"], od["div"], od["curl"], ux)
+        of = O.force(p, xx, vv, m, h, ux, od["rho"], g["f"], g["P"], g["c"], g["B"], active=act_f)
+        on = act_f.astype(bool)
+        return float((w[on] * of["accel"][on]).sum() + (cw[on] * of["dudt"][on]).sum())
+
+    scale = {"x": np.abs(gx).max(), "v": np.abs(gv).max(), "u": np.abs(gu).max()}
+    checked = 0
+    for k in rng.choice(np.nonzero(far)[0], 12, replace=False):
+        for nm, comp in (("x", 0), ("x", 1), ("v", 2), ("u", None)):
+            base = {"x": x, "v": v, "u": uu}[nm]
+            fds = []
+            for delta in (1e-6, 5e-7):
+                vals = []
+                step = delta * (max(abs(base[k]), 0.05) if comp is None else 0.05)
+                for sg in (1, -1):
+                    arr = base.copy()
+                    if comp is None:
+                        arr[k] += sg * step
+                    else:
+                        arr[k, comp] += sg * step
+                    args = {"x": x, "v": v, "u": uu}
+                    args[nm] = arr
+                    vals.append(local_loss(k, args["x"], args["v"], args["u"]))
+                fds.append((vals[0] - vals[1]) / (2 * step))
+            if abs(fds[0] - fds[1]) > 1e-5 * scale[nm]:
+                continue  # a kink of the loss inside the stencil (support edge, mu = 0)
+            got = {"x": gx, "v": gv, "u": gu}[nm]
+            g = got[k, comp] if comp is not None else got[k]
+            assert abs(g - fds[0]) <= 1e-4 * scale[nm], (nm, k, comp, g, fds[0])
+            checked += 1
+    assert checked >= 30
