@@ -25,8 +25,9 @@
  *  - Return value: SWIFT_GPU_OK (0) or a negative SWIFT_GPU_ERR_* code for an
  *    error detected on the host (bad argument, call order, CUDA launch error).
  *    Nothing is thrown across the ABI.
- *  - Positions live in the periodic box [0, L)^3; positions outside are wrapped
- *    (in FP64) for cell assignment and distances use the minimum image.
+ *  - Positions live in the periodic box [0, L)^3; positions outside are first
+ *    wrapped into it in FP64 (x - L floor(x / L)), and everything (cell ids,
+ *    distances by the minimum image) uses the wrapped position, rounded to FP32.
  */
 #ifndef SWIFT_GPU_H
 #define SWIFT_GPU_H
@@ -82,6 +83,9 @@ typedef struct {
   int threads_per_block; /* 64..1024, multiple of 32 */
   int max_lanes_per_particle; /* 1, 2, 4, 8, 16 or 32: lanes that share one particle's neighbour scan */
   int blocks_per_sm;     /* persistent blocks per SM (0 = occupancy maximum) */
+  int wait_limit_us;     /* limit of each bounded device-side wait (the density launch's grid barrier):
+                            0 = 5 s; negative = give up at once (fault injection: the call then reports
+                            ERR_TIMEOUT, its outputs are undefined, the context stays usable) */
 } swift_gpu_tuning;
 
 typedef struct {

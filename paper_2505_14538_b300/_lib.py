@@ -63,6 +63,7 @@ class Tuning(ctypes.Structure):
         ("threads_per_block", ctypes.c_int),
         ("max_lanes_per_particle", ctypes.c_int),
         ("blocks_per_sm", ctypes.c_int),
+        ("wait_limit_us", ctypes.c_int),
     ]
 
 

@@ -180,6 +180,20 @@ __device__ __forceinline__ double exact_H2(float kg, float h) {
   return __dmul_rn(H, H);
 }
 
+// A coordinate wrapped into the periodic box [0, L) with the same FP64
+// operations as the cell ids (x - L floor(x / L), each rounded once); a float
+// already in [0, L) is returned as is. The FP32 result may round up to L, which
+// still lies on the face of the cell the FP64 id gives it.
+__device__ __forceinline__ float wrap_coord(float x, float L) {
+  if (x >= 0.0f && x < L) return x;
+  const double Ld = (double)L;
+  return (float)__dsub_rn((double)x, __dmul_rn(Ld, floor(__ddiv_rn((double)x, Ld))));
+}
+
+__device__ __forceinline__ float4 wrap_pos(float4 p, const float L[3]) {
+  return make_float4(wrap_coord(p.x, L[0]), wrap_coord(p.y, L[1]), wrap_coord(p.z, L[2]), p.w);
+}
+
 // Warp-wide max of an int.
 __device__ __forceinline__ int warp_max(int v) { return __reduce_max_sync(0xffffffffu, v); }
 __device__ __forceinline__ unsigned warp_sum(unsigned v) { return __reduce_add_sync(0xffffffffu, v); }
@@ -192,7 +206,8 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 // Grid-wide barrier for cooperative (co-resident) launches. Bounded: gives up
-// after `limit_ns` and records SWIFT_GPU_ERR_TIMEOUT; returns false then.
+// after `limit_ns` (0: at once, without waiting) and records
+// SWIFT_GPU_ERR_TIMEOUT; returns false then.
 __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, Status* st,
                                              unsigned long long limit_ns) {
   __shared__ int ok;
@@ -208,6 +223,9 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, Sta
       atomicExch(count, 0u);
       __threadfence();
       atomicAdd(gen, 1u);
+    } else if (limit_ns == 0) {
+      set_error(st, SWIFT_GPU_ERR_TIMEOUT);
+      ok = 0;
     } else {
       unsigned long long t0 = global_ns();
       while (*vgen == g) {

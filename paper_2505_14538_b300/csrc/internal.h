@@ -135,6 +135,15 @@ inline bool kept_lists_usable(const Ctx* c) {
   return c->d_nlist && c->nl_lmax != 0 && c->nl_lmax == c->tuning.max_lanes_per_particle;
 }
 
+// Limit of each bounded device-side wait: tuning.wait_limit_us (0: 5 s;
+// negative: give up at once, the fault-injection setting).
+inline unsigned long long wait_limit_ns(const Ctx* c) {
+  const int us = c->tuning.wait_limit_us;
+  if (us < 0) return 0ull;
+  if (us == 0) return 5000000000ull;
+  return (unsigned long long)us * 1000ull;
+}
+
 // counters layout helpers
 constexpr int kCtrPerPass = 4;  // item_count, plist_count, ticket, spare
 __host__ __device__ inline int ctr_index(int pass, int which) { return pass * kCtrPerPass + which; }

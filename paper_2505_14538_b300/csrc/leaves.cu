@@ -46,11 +46,12 @@ constexpr int kDfsGap = 87;
 static_assert(kStack >= 27 + kDfsGap, "walk stack too small for its roots");
 
 __global__ void k_tree_gather(const float4* __restrict__ pos_h, const unsigned* __restrict__ perm,
-                              const unsigned* __restrict__ morton, int n, float4* __restrict__ pos,
-                              unsigned* __restrict__ mk) {
+                              const unsigned* __restrict__ morton, int n, const Grid* __restrict__ g,
+                              float4* __restrict__ pos, unsigned* __restrict__ mk) {
+  const float L[3] = {g->L[0], g->L[1], g->L[2]};
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     const unsigned src = perm[k];
-    pos[k] = pos_h[src];
+    pos[k] = wrap_pos(pos_h[src], L);
     mk[k] = morton[src];
   }
 }
@@ -399,7 +400,8 @@ int leaves_build(Ctx* c, const float4* pos_h, cudaStream_t s) {
   const int sm = c->num_sms;
   const unsigned* perm = c->d_vals[c->sorted_buf];
   unsigned* mk = c->d_keys[1 - c->sorted_buf];  // free after the sort
-  k_tree_gather<<<min((n + 255) / 256, sm * 8), 256, 0, s>>>(pos_h, perm, c->d_aux[1], n, c->d_pos, mk);
+  k_tree_gather<<<min((n + 255) / 256, sm * 8), 256, 0, s>>>(pos_h, perm, c->d_aux[1], n, c->d_grid, c->d_pos,
+                                                               mk);
   c->launches++;
   TreeArgs t;
   t.grid = c->d_grid;

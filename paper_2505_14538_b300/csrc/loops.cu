@@ -28,7 +28,6 @@ namespace sg {
 constexpr int kLoopThreads = 128;
 constexpr int kWarpsPerBlock = kLoopThreads / 32;
 constexpr size_t kLoopSmemBytes = sizeof(WarpSmem) * kWarpsPerBlock;
-constexpr unsigned long long kBarrierNs = 5000000000ull;  // 5 s
 
 __device__ __forceinline__ WarpSmem& warp_smem(unsigned char* smem) {
   return reinterpret_cast<WarpSmem*>(smem)[threadIdx.x >> 5];
@@ -83,6 +82,7 @@ struct DensArgs {
   int* plist[2];
   int* ctr;
   unsigned* barrier;  // [count, generation]
+  unsigned long long wait_ns;  // limit of each bounded grid barrier (0: give up at once)
   Status* st;
   unsigned long long* stats;
   // candidate lists kept for the gradient / force / adjoint loops (NULL: none)
@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(kLoopThreads, 5) k_density(DensArgs a) {
   // ---- prologue: gather into cell order, inputs of inactive particles
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < a.n; k += gridDim.x * blockDim.x) {
     const unsigned src = a.perm[k];
-    const float4 p = a.pos_in[src];
+    const float4 p = wrap_pos(a.pos_in[src], a.ph.L);
     a.pos[k] = p;
     a.vel[k] = a.vel_in[src];
     a.h[k] = p.w;
@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(kLoopThreads, 5) k_density(DensArgs a) {
       ibase += nit;
     }
   }
-  if (!grid_barrier(&a.barrier[0], &a.barrier[1], a.st, kBarrierNs)) return;
+  if (!grid_barrier(&a.barrier[0], &a.barrier[1], a.st, a.wait_ns)) return;
 
   DensOp op;
   op.pos = a.pos;
@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(kLoopThreads, 5) k_density(DensArgs a) {
       dens_item(a, op, g, w, it, plist, pass == 0 && !a.single_pass, last, items_next, plist_next, ctr_next,
                 Lmax, ninter, nhiter, ncand, pass == 0 ? t : -1);
     }
-    if (!grid_barrier(&a.barrier[0], &a.barrier[1], a.st, kBarrierNs)) return;
+    if (!grid_barrier(&a.barrier[0], &a.barrier[1], a.st, a.wait_ns)) return;
   }
   // ---- epilogue: h into the sorted positions, outputs to caller order
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < a.n; k += gridDim.x * blockDim.x) {
@@ -770,6 +770,7 @@ int density_impl(Ctx* c, const float4* pos_in, const float4* vel_in, const uint8
   a.plist[1] = c->d_plist[1];
   a.ctr = c->d_counters;
   a.barrier = reinterpret_cast<unsigned*>(c->d_counters + kCtrPerPass * (c->max_passes + 2));
+  a.wait_ns = wait_limit_ns(c);
   a.st = c->d_status;
   a.stats = c->d_stats;
   a.nlist = c->d_nlist;

@@ -120,7 +120,7 @@ struct PlainDensState {
 __global__ void k_plain_dens_prologue(PlainDensState s) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < s.n; k += gridDim.x * blockDim.x) {
     const unsigned src = s.perm[k];
-    const float4 p = s.pos_in[src];
+    const float4 p = wrap_pos(s.pos_in[src], s.ph.L);
     s.pos[k] = p;
     s.vel[k] = s.vel_in[src];
     s.h[k] = p.w;

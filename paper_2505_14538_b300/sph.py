@@ -216,10 +216,10 @@ class Context:
         t = _lib.Tuning()
         _check(self.lib.swift_gpu_get_tuning(self.handle, ctypes.byref(t)), "swift_gpu_get_tuning")
         return dict(threads_per_block=t.threads_per_block, max_lanes_per_particle=t.max_lanes_per_particle,
-                    blocks_per_sm=t.blocks_per_sm)
+                    blocks_per_sm=t.blocks_per_sm, wait_limit_us=t.wait_limit_us)
 
-    def set_tuning(self, threads_per_block=256, max_lanes_per_particle=32, blocks_per_sm=0):
-        t = _lib.Tuning(threads_per_block, max_lanes_per_particle, blocks_per_sm)
+    def set_tuning(self, threads_per_block=256, max_lanes_per_particle=32, blocks_per_sm=0, wait_limit_us=0):
+        t = _lib.Tuning(threads_per_block, max_lanes_per_particle, blocks_per_sm, wait_limit_us)
         _check(self.lib.swift_gpu_set_tuning(self.handle, ctypes.byref(t)), "swift_gpu_set_tuning")
 
     def autotune(self, loop: int, stream=None):

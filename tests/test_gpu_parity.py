@@ -315,3 +315,56 @@ def test_gradient_force_fused_equals_separate(sph, flags):
     assert abs(ra[3] - rb[3]) <= 1e-6 * rb[5] and abs(ra[6] - rb[6]) <= 1e-6 * rb[5]  # energy: against its abs sum
     assert np.all(np.abs(ra[[4, 5]] - rb[[4, 5]]) <= 1e-6 * rb[[4, 5]]) and ra[7] == rb[7]
     assert ia["interactions"][1:] == ib["interactions"][1:]
+
+
+def test_out_of_box_positions_are_wrapped(sph, O):
+    """Positions shifted by whole box lengths are wrapped into [0, L) (FP64) and give the oracle's answers there."""
+    d, vel, u = lattice_state(12, seed=21)
+    n = len(d["pos"])
+    rng = np.random.default_rng(21)
+    L = np.asarray(d["box"], np.float64)
+    shifted = (d["pos"].astype(np.float64) + L * rng.integers(-2, 3, size=(n, 3))).astype(np.float32)
+    wrapped = (shifted.astype(np.float64) - L * np.floor(shifted.astype(np.float64) / L)).astype(np.float32)
+    assert np.any(shifted != wrapped)
+    dg = dict(d)
+    dg["pos"] = shifted
+    g = run_gpu(sph, dg, vel, u, h_tol=1e-6)
+    assert g["status"][0] == 0, g["status"]
+    dw = dict(d)
+    dw["pos"] = wrapped
+    check_against_oracle(O, dw, vel, u, g, g["ctx"])
+
+
+def test_injected_faults_report_status(sph):
+    """Host-side fault injection: h <= 0, max_iter = 1, a grid barrier that gives up at once. No GPU fault."""
+    d, vel, u = lattice_state(12, seed=23)
+    n = len(d["pos"])
+    # h <= 0 on one particle: the build reports ERR_ARG
+    bad = dict(d)
+    bad["h"] = d["h"].copy()
+    bad["h"][7] = 0.0
+    ctx = sph.Context(n, box=d["box"])
+    pos_h, vel_m, ut = dev_arrays(bad, vel, u)
+    ctx.build_cells(pos_h)
+    assert ctx.sync_status()[0] == -1
+    # one Newton step only: the unconverged particles are counted
+    ctx = sph.Context(n, box=d["box"], max_iter=1, h_tol=1e-9)
+    pos_h, vel_m, ut = dev_arrays(d, vel, u)
+    ctx.build_cells(pos_h)
+    ctx.density(pos_h, vel_m)
+    code, detail = ctx.sync_status()
+    assert code == -4 and 0 < detail <= n
+    # the density launch's grid barrier gives up at once: ERR_TIMEOUT, and the context stays usable
+    ctx = sph.Context(n, box=d["box"], h_tol=1e-6)
+    ref = sph.Context(n, box=d["box"], h_tol=1e-6)
+    ctx.set_tuning(wait_limit_us=-1)
+    ctx.build_cells(pos_h)
+    ctx.density(pos_h, vel_m)
+    assert ctx.sync_status()[0] == -6
+    ctx.set_tuning(wait_limit_us=0)
+    out = ctx.step(pos_h, vel_m, ut)
+    exp = ref.step(pos_h, vel_m, ut)
+    torch.cuda.synchronize()
+    assert out["status"] == (0, 0)
+    for k in ("h", "rho4", "accel_dudt"):
+        assert torch.equal(out[k], exp[k]), k
