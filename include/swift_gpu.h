@@ -257,9 +257,14 @@ int swift_gpu_get_leaves(swift_gpu_ctx* ctx, int32_t* range, float* h_cap, int32
 int swift_gpu_get_tuning(swift_gpu_ctx* ctx, swift_gpu_tuning* t);
 int swift_gpu_set_tuning(swift_gpu_ctx* ctx, const swift_gpu_tuning* t);
 
-/* Time the given loop (0 density, 1 gradient, 2 force) on the data of the
- * last calls for each candidate tuning and keep the fastest. Requires force
- * to have run once. Blocking; leaves outputs of the last calls unchanged. */
+/* Time the given loop (0 density, 1 gradient, 2 force, 3 gradient + force)
+ * on the data of the last calls for each candidate tuning (lanes per
+ * particle 1..32, blocks per SM 0..2) and keep the fastest; the setting is
+ * shared by all loops. Requires force (or gradient + force) to have run once;
+ * loops 1 and 3 require a gradient output of a previous call. Blocking. The
+ * loop is run once more with the chosen setting, so its outputs (in the
+ * arrays of the last calls) are those of that setting: the same sums as
+ * before up to the FP32 summation order. */
 int swift_gpu_autotune(swift_gpu_ctx* ctx, int loop, void* stream);
 
 /* Largest particle count swift_gpu_density_static accepts. */

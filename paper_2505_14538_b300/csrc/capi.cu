@@ -420,7 +420,7 @@ int swift_gpu_set_tuning(swift_gpu_ctx* h, const swift_gpu_tuning* t) {
 
 int swift_gpu_autotune(swift_gpu_ctx* h, int loop, void* stream) {
   Ctx* c = from(h);
-  if (!c || loop < 0 || loop > 2 || (c->params.flags & SWIFT_GPU_PLAIN)) return SWIFT_GPU_ERR_ARG;
+  if (!c || loop < 0 || loop > 3 || (c->params.flags & SWIFT_GPU_PLAIN)) return SWIFT_GPU_ERR_ARG;
   if (!(c->state & 8)) return SWIFT_GPU_ERR_ORDER;
   cudaStream_t s = (cudaStream_t)stream;
   c->last_stream = s;

@@ -13,19 +13,20 @@ static int run_loop(Ctx* c, int loop, cudaStream_t s) {
     return density_impl(c, c->last_pos_in, c->last_vel_in, c->last_active, c->last_h_out, c->last_rho4, c->last_cd,
                         c->last_ngb, s);
   if (loop == 1) return gradient_impl(c, c->last_grad_out, s);
+  if (loop == 3) return grad_force_impl(c, c->last_grad_out, c->last_force_out, c->last_dhdt, nullptr, s);
   return force_impl(c, c->last_force_out, c->last_dhdt, nullptr, s);
 }
 
 int autotune_impl(Ctx* c, int loop, cudaStream_t s) {
-  if (loop == 1 && !c->last_grad_out) return SWIFT_GPU_ERR_ORDER;
+  if ((loop == 1 || loop == 3) && !c->last_grad_out) return SWIFT_GPU_ERR_ORDER;
   const int cand_l[6] = {1, 2, 4, 8, 16, 32};
   const int cand_b[3] = {0, 1, 2};
   swift_gpu_tuning best = c->tuning, orig = c->tuning;
   float best_ms = 1e30f;
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return SWIFT_GPU_ERR_CUDA;
-  // the force loop reads the ghost arrays of the force call; gradient those of the gradient call
-  if (loop == 2 || loop == 0) ghost_impl(c, c->last_u, c->last_alpha_v, c->last_alpha_c, s);
+  // the force loops read the ghost arrays of the force call; gradient those of the gradient call
+  if (loop != 1) ghost_impl(c, c->last_u, c->last_alpha_v, c->last_alpha_c, s);
   else ghost_impl(c, c->last_u, nullptr, nullptr, s);
   int rc = SWIFT_GPU_OK;
   for (int bi = 0; bi < 3 && rc == SWIFT_GPU_OK; ++bi) {
@@ -50,6 +51,8 @@ int autotune_impl(Ctx* c, int loop, cudaStream_t s) {
     }
   }
   c->tuning = rc == SWIFT_GPU_OK ? best : orig;
+  // the loop's outputs (and, for density, the kept candidate lists) from the chosen setting
+  if (rc == SWIFT_GPU_OK) rc = run_loop(c, loop, s);
   // leave the ghost arrays as the last force call left them
   ghost_impl(c, c->last_u, c->last_alpha_v, c->last_alpha_c, s);
   cudaEventDestroy(e0);

@@ -368,3 +368,24 @@ def test_injected_faults_report_status(sph):
     assert out["status"] == (0, 0)
     for k in ("h", "rho4", "accel_dudt"):
         assert torch.equal(out[k], exp[k]), k
+
+
+def test_autotune_picks_a_valid_setting_and_keeps_results(sph, O):
+    """The autotuner times the loops over its candidates, keeps a valid setting, and the step still matches."""
+    d, vel, u = lattice_state(16, seed=31)
+    n = len(d["pos"])
+    ctx = sph.Context(n, box=d["box"], h_tol=1e-6)
+    pos_h, vel_m, ut = dev_arrays(d, vel, u)
+    ref = ctx.step(pos_h, vel_m, ut)
+    ref = {k: v.clone() for k, v in ref.items() if torch.is_tensor(v)}
+    for loop in (0, 3):
+        t = ctx.autotune(loop)
+        assert t["max_lanes_per_particle"] in (1, 2, 4, 8, 16, 32) and 0 <= t["blocks_per_sm"] <= 2
+    assert ctx.sync_status() == (0, 0)
+    out = ctx.step(pos_h, vel_m, ut)
+    torch.cuda.synchronize()
+    assert torch.equal(out["ngb"], ref["ngb"])
+    for k in ("h", "rho4"):
+        assert torch.max(torch.abs(out[k] - ref[k]) / torch.abs(ref[k]).clamp_min(1e-30)).item() < 1e-5, k
+    sa = torch.abs(ref["accel_dudt"]).max().item()
+    assert torch.max(torch.abs(out["accel_dudt"] - ref["accel_dudt"])).item() < 1e-4 * sa
