@@ -280,9 +280,9 @@ def test_step_graph_replays_bit_identically(sph):
 
 @pytest.mark.parametrize("flags", [0, 8])
 def test_gradient_force_fused_equals_separate(sph, flags):
-    """swift_gpu_gradient_force evaluates the pairs of gradient() then force() in the same order: v_sig and the
-    Laplacian bitwise, a and du/dt to a few FP32 roundings (the compiler may fuse a multiply-add differently),
-    the FP64 sums to their own rounding (uniform grid and adaptive leaves)."""
+    """swift_gpu_gradient_force evaluates the pairs of gradient() then force(): v_sig bitwise (a max of the same
+    terms); the Laplacian, a and du/dt to a few FP32 roundings (the fused loop may sum the pairs in another
+    order); the FP64 sums to their own rounding (uniform grid and adaptive leaves)."""
     d, vel, u = lattice_state(16, seed=13, jitter=0.3)
     n = len(d["pos"])
     rng = np.random.default_rng(4)
@@ -303,7 +303,9 @@ def test_gradient_force_fused_equals_separate(sph, flags):
         assert ctx.sync_status() == (0, 0)
         outs.append((o, ctx.info()))
     (a, ia), (b, ib) = outs
-    assert torch.equal(a["vsig_lapu"], b["vsig_lapu"])
+    assert torch.equal(a["vsig_lapu"][:, 0], b["vsig_lapu"][:, 0])  # a max of identical terms
+    la, lb = a["vsig_lapu"][:, 1].cpu().numpy(), b["vsig_lapu"][:, 1].cpu().numpy()
+    assert np.max(np.abs(la - lb)) <= 1e-5 * np.abs(lb).max()
     ad_a, ad_b = a["accel_dudt"].cpu().numpy(), b["accel_dudt"].cpu().numpy()
     sc_a = np.abs(ad_b[:, :3]).max()
     assert np.max(np.abs(ad_a[:, :3] - ad_b[:, :3])) <= 1e-6 * sc_a
@@ -385,7 +387,12 @@ def test_autotune_picks_a_valid_setting_and_keeps_results(sph, O):
     out = ctx.step(pos_h, vel_m, ut)
     torch.cuda.synchronize()
     assert torch.equal(out["ngb"], ref["ngb"])
-    for k in ("h", "rho4"):
-        assert torch.max(torch.abs(out[k] - ref[k]) / torch.abs(ref[k]).clamp_min(1e-30)).item() < 1e-5, k
+    assert torch.max(torch.abs(out["h"] / ref["h"] - 1)).item() < 1e-5
+    r_out, r_ref = out["rho4"], ref["rho4"]
+    for c in (0, 2):  # rho and n: relative
+        assert torch.max(torch.abs(r_out[:, c] / r_ref[:, c] - 1)).item() < 1e-5, c
+    for c in (1, 3):  # h-derivatives (sums with cancellation): against the column's largest
+        sc = torch.abs(r_ref[:, c]).max().item()
+        assert torch.max(torch.abs(r_out[:, c] - r_ref[:, c])).item() < 1e-5 * sc, c
     sa = torch.abs(ref["accel_dudt"]).max().item()
     assert torch.max(torch.abs(out["accel_dudt"] - ref["accel_dudt"])).item() < 1e-4 * sa
