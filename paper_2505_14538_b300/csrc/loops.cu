@@ -323,61 +323,56 @@ __global__ void __launch_bounds__(kLoopThreads, 5) k_density(DensArgs a) {
     }
   }
   // ---- active work items (runs of <= kItemMax active particles of a cell or
-  // leaf). Each block takes a contiguous run of cells: its warps count the
-  // active particles first, one atomic per counter reserves the block's
-  // share, and the second sweep writes the items (two atomics per block, not
-  // per cell).
+  // leaf). In round r, warp w of block b takes cell r * 8G + 8b + w (G blocks,
+  // 8 warps a block); the block reserves its share of the round with one
+  // atomic per counter. Rounds run nearly in step across the grid, so the
+  // work queue comes out close to ascending cell order: the warps that later
+  // take neighbouring tickets work on neighbouring cells (or leaves) and share
+  // their neighbours in cache.
   {
     __shared__ int s_tot[kWarpsPerBlock], s_nit[kWarpsPerBlock], s_base[2];
     const int nunits = a.nb.adaptive ? *a.nb.n_leaves : g.ncells;
     const int wib = (int)(threadIdx.x >> 5);
-    const int per_block = (nunits + (int)gridDim.x - 1) / (int)gridDim.x;
-    const int c_lo = (int)blockIdx.x * per_block, c_hi = min(nunits, c_lo + per_block);
-    auto range = [&](int c, int& cs, int& ce) {
-      if (a.nb.adaptive) {
-        const int2 r = a.nb.leaf_range[c];
-        cs = r.x;
-        ce = r.y;
-      } else {
-        cs = a.nb.cell_start[c];
-        ce = a.nb.cell_start[c + 1];
+    const int stride = kWarpsPerBlock * (int)gridDim.x;
+    for (int r0 = 0; r0 < nunits; r0 += stride) {  // the same trip count for every warp of the block
+      const int c = r0 + (int)blockIdx.x * kWarpsPerBlock + wib;
+      int cs = 0, ce = 0;
+      if (c < nunits) {
+        if (a.nb.adaptive) {
+          const int2 r = a.nb.leaf_range[c];
+          cs = r.x;
+          ce = r.y;
+        } else {
+          cs = a.nb.cell_start[c];
+          ce = a.nb.cell_start[c + 1];
+        }
       }
-    };
-    int wtot = 0, wnit = 0;
-    for (int c = c_lo + wib; c < c_hi; c += kWarpsPerBlock) {
-      int cs, ce;
-      range(c, cs, ce);
       int total = 0;
       for (int b = cs; b < ce; b += 32) {
         const int k = b + (int)lane;
         const bool on = k < ce && (a.active ? a.active[a.perm[k]] != 0 : true);
         total += __popc(__ballot_sync(kFull, on));
       }
-      wtot += total;
-      wnit += (total + kItemMax - 1) / kItemMax;
-    }
-    if (lane == 0) {
-      s_tot[wib] = wtot;
-      s_nit[wib] = wnit;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      int pt = 0, it = 0;
-      for (int q = 0; q < kWarpsPerBlock; ++q) {
-        const int tq = s_tot[q], nq = s_nit[q];
-        s_tot[q] = pt;
-        s_nit[q] = it;
-        pt += tq;
-        it += nq;
+      const int nit = (total + kItemMax - 1) / kItemMax;
+      if (lane == 0) {
+        s_tot[wib] = total;
+        s_nit[wib] = nit;
       }
-      s_base[0] = pt ? atomicAdd(&a.ctr[ctr_index(0, 1)], pt) : 0;
-      s_base[1] = it ? atomicAdd(&a.ctr[ctr_index(0, 0)], it) : 0;
-    }
-    __syncthreads();
-    int pbase = s_base[0] + s_tot[wib], ibase = s_base[1] + s_nit[wib];
-    for (int c = c_lo + wib; c < c_hi; c += kWarpsPerBlock) {
-      int cs, ce;
-      range(c, cs, ce);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        int pt = 0, it = 0;
+        for (int q = 0; q < kWarpsPerBlock; ++q) {
+          const int tq = s_tot[q], nq = s_nit[q];
+          s_tot[q] = pt;
+          s_nit[q] = it;
+          pt += tq;
+          it += nq;
+        }
+        s_base[0] = pt ? atomicAdd(&a.ctr[ctr_index(0, 1)], pt) : 0;
+        s_base[1] = it ? atomicAdd(&a.ctr[ctr_index(0, 0)], it) : 0;
+      }
+      __syncthreads();
+      const int pbase = s_base[0] + s_tot[wib], ibase = s_base[1] + s_nit[wib];
       int wc = 0;
       for (int b = cs; b < ce; b += 32) {
         const int k = b + (int)lane;
@@ -386,11 +381,9 @@ __global__ void __launch_bounds__(kLoopThreads, 5) k_density(DensArgs a) {
         if (on) a.plist0[pbase + wc + __popc(m & ((1u << lane) - 1u))] = k;
         wc += __popc(m);
       }
-      const int nit = (wc + kItemMax - 1) / kItemMax;
       for (int t = (int)lane; t < nit; t += 32)
         a.items0[ibase + t] = Item{c, pbase + t * kItemMax, min(kItemMax, wc - t * kItemMax), 0};
-      pbase += wc;
-      ibase += nit;
+      __syncthreads();  // s_tot, s_nit and s_base are reused by the next round
     }
   }
   if (!grid_barrier(&a.barrier[0], &a.barrier[1], a.st, a.wait_ns)) return;
