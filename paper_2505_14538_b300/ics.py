@@ -19,6 +19,9 @@ not available, so the sets below stand in for it:
 * ``zeldovich`` - lattice displaced by a Gaussian random field with
                   P(k) ~ k^-2 (density contrast ~100), v proportional to the
                   displacement.
+* ``gresho``    - the Gresho-Chan vortex itself (Sec. 3.1, Eqs. 27-28) on a
+                  cubic lattice: rho = 1, gamma = 5/3, azimuthal velocity and
+                  pressure from the analytic steady state.
 
 Random streams: NumPy PCG64 seeded with ``SEED_BASE + config index``; the
 active flags use splitmix64(seed ^ i) mod 10 == 0.
@@ -237,10 +240,47 @@ def zeldovich(n_side: int = 256, index: int = 5, max_contrast: float = 100.0, sp
                    amplitude=A)
 
 
+def gresho_profile(r):
+    """Analytic Gresho-Chan vortex (Eqs. 27-28): azimuthal speed v_phi(r) and pressure p(r)."""
+    r = np.asarray(r, np.float64)
+    v = np.where(r < 0.2, 5.0 * r, np.where(r < 0.4, 2.0 - 5.0 * r, 0.0))
+    rs = np.maximum(r, 1e-300)
+    p_mid = 9.0 - 4.0 * np.log(0.2) + 12.5 * r * r - 20.0 * r + 4.0 * np.log(rs)
+    p = np.where(r < 0.2, 5.0 + 12.5 * r * r, np.where(r < 0.4, p_mid, 3.0 + 4.0 * np.log(2.0)))
+    return v, p
+
+
+def gresho(n_side: int = 64, jitter: float = 0.0, index: int = 6, rho0: float = 1.0):
+    """Gresho-Chan vortex on an n_side^3 cubic lattice (Sec. 3.1).
+
+    Axis along z through (0.5, 0.5); v = v_phi(r) (-(y - 0.5), x - 0.5, 0) / r
+    with r the distance from the axis in the x-y plane; rho = rho0 (m = rho0 /
+    N), u = p(r) / ((gamma - 1) rho0), h = eta / n_side.
+    """
+    rng = _rng(index)
+    dx = 1.0 / n_side
+    g = (np.arange(n_side) + 0.5) * dx
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    pos = np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1)
+    if jitter > 0:
+        pos = pos + rng.uniform(-jitter * dx, jitter * dx, size=pos.shape)
+    pos = _wrap(pos)
+    rx, ry = pos[:, 0] - 0.5, pos[:, 1] - 0.5
+    r = np.sqrt(rx * rx + ry * ry)
+    vphi, p = gresho_profile(r)
+    rs = np.where(r > 0, r, 1.0)
+    vel = np.stack([-vphi * ry / rs, vphi * rx / rs, np.zeros_like(r)], 1)
+    n = len(pos)
+    u = p / ((GAMMA_EOS - 1.0) * rho0)
+    return _finish(f"gresho{n_side}", pos, vel, np.full(n, rho0 / n), u, np.full(n, ETA * dx), spacing=dx)
+
+
 CONFIGS = {
     "lattice16": lambda: lattice(16),
     "sedov64": lambda: sedov(64),
     "plummer2M": lambda: plummer(),
     "kh32": lambda: kh(),
     "zeldovich256": lambda: zeldovich(256),
+    "gresho64": lambda: gresho(64),
+    "gresho128": lambda: gresho(128),
 }

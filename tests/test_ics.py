@@ -1,5 +1,6 @@
 """Seeded input generators (CPU): each workload has the shape it is documented to have."""
 import numpy as np
+import pytest
 
 from paper_2505_14538_b300 import ics
 
@@ -49,3 +50,32 @@ def test_zeldovich_contrast_matches_determinant():
                   for a in range(3)], -2)
     det = np.linalg.det(np.eye(3) + d["amplitude"] * J)
     assert abs(1.0 / det.min() - 20.0) < 1e-6 * 20.0
+
+
+def test_gresho_profile_balances_pressure_and_velocity():
+    """Eq. 28 must hold the vortex of Eq. 27 in equilibrium: dp/dr = rho v^2 / r, p continuous."""
+    for r in (0.05, 0.13, 0.19, 0.21, 0.3, 0.39, 0.41, 0.7):
+        e = 1e-6
+        _, pp = ics.gresho_profile(np.array([r - e, r + e]))
+        v, _ = ics.gresho_profile(np.array([r]))
+        assert (pp[1] - pp[0]) / (2 * e) == pytest.approx(v[0] ** 2 / r, rel=1e-6, abs=1e-8)
+    for r in (0.2, 0.4):
+        v, p = ics.gresho_profile(np.array([r - 1e-12, r]))
+        assert abs(p[1] - p[0]) < 1e-9 and abs(v[1] - v[0]) < 1e-9
+    assert ics.gresho_profile(np.array([0.2]))[0][0] == 1.0
+
+
+def test_gresho_initial_state():
+    d = ics.gresho(16)
+    n = len(d["pos"])
+    assert n == 16 ** 3 and abs(d["m"].astype(np.float64).sum() - 1.0) < 1e-6
+    x = d["pos"].astype(np.float64)
+    rx, ry = x[:, 0] - 0.5, x[:, 1] - 0.5
+    r = np.hypot(rx, ry)
+    v = d["vel"].astype(np.float64)
+    vf, p = ics.gresho_profile(r)
+    assert np.allclose(v[:, 0] * rx + v[:, 1] * ry, 0, atol=1e-6) and np.all(v[:, 2] == 0)
+    assert np.allclose(np.hypot(v[:, 0], v[:, 1]), vf, atol=1e-6)
+    assert np.allclose(d["u"], p / (ics.GAMMA_EOS - 1), rtol=1e-6)
+    # counter-clockwise about the z axis
+    assert np.all(rx * v[:, 1] - ry * v[:, 0] >= -1e-7)
