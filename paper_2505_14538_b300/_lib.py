@@ -1,4 +1,4 @@
-"""ctypes declarations of the C ABI in ``include/swift_gpu.h``.
+"""ctypes declarations of the C ABI in ``include/swift_gpu.h`` and ``include/swift_gpu_time.h``.
 
 Loading fails loudly (ImportError) when ``libswift_gpu.so`` has not been
 built: there is no fallback implementation.
@@ -34,7 +34,8 @@ EXPORTED = ("swift_gpu_default_params", "swift_gpu_create", "swift_gpu_destroy",
             "swift_gpu_build_cells", "swift_gpu_density", "swift_gpu_gradient", "swift_gpu_force",
             "swift_gpu_force_backward", "swift_gpu_sync_status", "swift_gpu_get_info", "swift_gpu_get_cells",
             "swift_gpu_get_tuning", "swift_gpu_set_tuning", "swift_gpu_autotune", "swift_gpu_density_static",
-            "swift_gpu_get_leaves", "swift_gpu_gradient_force")
+            "swift_gpu_get_leaves", "swift_gpu_gradient_force", "swift_gpu_default_time_params",
+            "swift_gpu_kick_drift", "swift_gpu_viscosity_switch", "swift_gpu_kick_finish")
 
 STATIC_MAX_PARTICLES = 32768
 
@@ -86,6 +87,31 @@ class Info(ctypes.Structure):
     ]
 
 
+class TimeParams(ctypes.Structure):
+    _fields_ = [
+        ("cfl", ctypes.c_float),
+        ("dt_max", ctypes.c_float),
+        ("alpha_v_max", ctypes.c_float),
+        ("alpha_v_min", ctypes.c_float),
+        ("visc_length", ctypes.c_float),
+        ("alpha_c_max", ctypes.c_float),
+        ("alpha_c_min", ctypes.c_float),
+        ("beta_c", ctypes.c_float),
+        ("u_min_frac", ctypes.c_float),
+    ]
+
+
+class Clock(ctypes.Structure):
+    """Host image of swift_gpu_clock (32 bytes; the library reads and writes a device copy)."""
+    _fields_ = [
+        ("t", ctypes.c_double),
+        ("t_end", ctypes.c_double),
+        ("dt", ctypes.c_float),
+        ("dt_next", ctypes.c_float),
+        ("step", ctypes.c_int64),
+    ]
+
+
 _VP = ctypes.c_void_p
 _I = ctypes.c_int
 _I64 = ctypes.c_int64
@@ -110,6 +136,13 @@ _SIGS = {
                                       _VP, _VP]),
     "swift_gpu_get_leaves": (_I, [_VP, _VP, _VP, _VP, _I64, _VP]),
     "swift_gpu_gradient_force": (_I, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "swift_gpu_default_time_params": (None, [ctypes.POINTER(TimeParams)]),
+    "swift_gpu_kick_drift": (_I, [_VP, ctypes.POINTER(TimeParams), _VP, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
+                                  _VP]),
+    "swift_gpu_viscosity_switch": (_I, [_VP, ctypes.POINTER(TimeParams), _VP, _I64, _VP, _VP, _VP, _VP, _VP, _VP,
+                                        _VP]),
+    "swift_gpu_kick_finish": (_I, [_VP, ctypes.POINTER(TimeParams), _VP, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
+                                   _VP, _VP]),
 }
 
 _lib = None
@@ -136,3 +169,9 @@ def default_params() -> Params:
     p = Params()
     load().swift_gpu_default_params(ctypes.byref(p))
     return p
+
+
+def default_time_params() -> TimeParams:
+    tp = TimeParams()
+    load().swift_gpu_default_time_params(ctypes.byref(tp))
+    return tp

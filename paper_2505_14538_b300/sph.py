@@ -227,48 +227,58 @@ class Context:
         return self.tuning()
 
     # ------------------------------------------------------- whole step
+    def density_checked(self, pos_h, vel_m, active=None, rho4=None, curl_div=None, min_cell_width: float = 0.0,
+                        check: bool = True, stream=None, **outs):
+        """build_cells -> density; with check=True the status word is read (a host synchronisation).
+
+        While the h iteration asks for a support wider than its cap, the
+        density call is repeated: on the uniform grid with cells twice as wide
+        (up to a third of the box) from the same starting h; with adaptive
+        leaves from the capped h, the leaves rebuilt around it (their caps grow
+        by 1 + leaf_margin), and with wider cells only when h reached the cell
+        cap. ``outs`` are optional output tensors of density() (h_out,
+        ngb_count). Raises SwiftGPUError on any status other than OK and
+        ERR_H_NOT_CONVERGED.
+        """
+        self.build_cells(pos_h, min_cell_width, stream)
+        d = self.density(pos_h, vel_m, active, rho4=rho4, curl_div=curl_div, stream=stream, **outs)
+        if not check:
+            return d
+        code, detail = self.sync_status()
+        box_third = min(float(b) for b in self.params.box) / 3.0
+        adaptive = bool(self.params.flags & _lib.FLAG_ADAPTIVE)
+        pos_cur = pos_h
+        for _ in range(32):
+            if code != _lib.ERR_H_EXCEEDS_CELL:
+                break
+            info = self.info()
+            width = max(info["cell_width"])
+            if not adaptive or float(d["h"].max()) >= 0.999 * info["h_cap"]:
+                if width >= 0.999 * box_third:
+                    break
+                min_w = max(min_cell_width, min(2.0 * width, box_third))
+            else:
+                min_w = min_cell_width  # only leaf caps were reached
+            if adaptive:
+                pos_cur = pos_cur.clone()
+                pos_cur[:, 3] = d["h"]
+            self.build_cells(pos_cur, min_w, stream)
+            d = self.density(pos_cur, vel_m, active, rho4=rho4, curl_div=curl_div, stream=stream, **outs)
+            code, detail = self.sync_status()
+        if code not in (_lib.OK, _lib.ERR_H_NOT_CONVERGED):
+            raise SwiftGPUError(code, "density", detail)
+        d["status"] = (code, detail)
+        return d
+
     def step(self, pos_h, vel_m, u, active=None, rho4=None, curl_div=None, alpha_v=None, alpha_c=None,
              min_cell_width: float = 0.0, check: bool = True, fused: bool = True, stream=None):
         """build_cells -> density (h iteration) -> gradient -> force on one stream.
 
         fused=True runs gradient and force as one call (swift_gpu_gradient_force,
-        the same outputs); fused=False as the two calls.
-
-        With check=True the status word is read after the density call (a
-        host synchronisation). While the h iteration asks for a support wider
-        than its cap, the density call is repeated: on the uniform grid with
-        cells twice as wide (up to a third of the box) from the same starting
-        h; with adaptive leaves from the capped h, the leaves rebuilt around
-        it (their caps grow by 1 + leaf_margin), and with wider cells only
-        when h reached the cell cap.
+        the same outputs); fused=False as the two calls. check as in
+        density_checked().
         """
-        self.build_cells(pos_h, min_cell_width, stream)
-        d = self.density(pos_h, vel_m, active, rho4=rho4, curl_div=curl_div, stream=stream)
-        if check:
-            code, detail = self.sync_status()
-            box_third = min(float(b) for b in self.params.box) / 3.0
-            adaptive = bool(self.params.flags & _lib.FLAG_ADAPTIVE)
-            pos_cur = pos_h
-            for _ in range(32):
-                if code != _lib.ERR_H_EXCEEDS_CELL:
-                    break
-                info = self.info()
-                width = max(info["cell_width"])
-                if not adaptive or float(d["h"].max()) >= 0.999 * info["h_cap"]:
-                    if width >= 0.999 * box_third:
-                        break
-                    min_w = max(min_cell_width, min(2.0 * width, box_third))
-                else:
-                    min_w = min_cell_width  # only leaf caps were reached
-                if adaptive:
-                    pos_cur = pos_cur.clone()
-                    pos_cur[:, 3] = d["h"]
-                self.build_cells(pos_cur, min_w, stream)
-                d = self.density(pos_cur, vel_m, active, rho4=rho4, curl_div=curl_div, stream=stream)
-                code, detail = self.sync_status()
-            if code not in (_lib.OK, _lib.ERR_H_NOT_CONVERGED):
-                raise SwiftGPUError(code, "density", detail)
-            d["status"] = (code, detail)
+        d = self.density_checked(pos_h, vel_m, active, rho4, curl_div, min_cell_width, check, stream)
         out = dict(d)
         if fused:
             out.update(self.gradient_force(u, alpha_v, alpha_c, stream=stream))
@@ -276,6 +286,58 @@ class Context:
             out["vsig_lapu"] = self.gradient(u, stream=stream)
             out.update(self.force(u, alpha_v, alpha_c, stream=stream))
         return out
+
+    # ------------------------------------------------ time integration (swift_gpu_time.h)
+    def kick_drift(self, tp, clock, pos_h, vel_m, u, accel_dudt, dh_dt, vel_pred, u_pred, stream=None):
+        n = pos_h.shape[0]
+        _check(self.lib.swift_gpu_kick_drift(
+            self.handle, ctypes.byref(tp), _ptr(clock, torch.float64, None, 4, "clock"), ctypes.c_int64(n),
+            _ptr(pos_h, _F32, 4, n, "pos_h"), _ptr(vel_m, _F32, 4, n, "vel_m"), _ptr(u, _F32, None, n, "u"),
+            _ptr(accel_dudt, _F32, 4, n, "accel_dudt"), _ptr(dh_dt, _F32, None, n, "dh_dt"),
+            _ptr(vel_pred, _F32, 4, n, "vel_pred"), _ptr(u_pred, _F32, None, n, "u_pred"), _stream(stream)),
+            "swift_gpu_kick_drift")
+
+    def viscosity_switch(self, tp, clock, h, u, curl_div, vsig_lapu, div_prev, alpha_v, stream=None):
+        n = h.shape[0]
+        _check(self.lib.swift_gpu_viscosity_switch(
+            self.handle, ctypes.byref(tp), _ptr(clock, torch.float64, None, 4, "clock"), ctypes.c_int64(n),
+            _ptr(h, _F32, None, n, "h"), _ptr(u, _F32, None, n, "u"), _ptr(curl_div, _F32, 4, n, "curl_div"),
+            _ptr(vsig_lapu, _F32, 2, n, "vsig_lapu"), _ptr(div_prev, _F32, None, n, "div_prev"),
+            _ptr(alpha_v, _F32, None, n, "alpha_v"), _stream(stream)), "swift_gpu_viscosity_switch")
+
+    def kick_finish(self, tp, clock, h, pos_h, vel_m, u, accel_dudt, vsig_lapu, alpha_v=None, alpha_c=None,
+                    stream=None):
+        n = pos_h.shape[0]
+        _check(self.lib.swift_gpu_kick_finish(
+            self.handle, ctypes.byref(tp), _ptr(clock, torch.float64, None, 4, "clock"), ctypes.c_int64(n),
+            _ptr(h, _F32, None, n, "h"), _ptr(pos_h, _F32, 4, n, "pos_h"), _ptr(vel_m, _F32, 4, n, "vel_m"),
+            _ptr(u, _F32, None, n, "u"), _ptr(accel_dudt, _F32, 4, n, "accel_dudt"),
+            _ptr(vsig_lapu, _F32, 2, n, "vsig_lapu"), _ptr(alpha_v, _F32, None, n, "alpha_v"),
+            _ptr(alpha_c, _F32, None, n, "alpha_c"), _stream(stream)), "swift_gpu_kick_finish")
+
+
+def make_time_params(**kw) -> _lib.TimeParams:
+    """Integration defaults (swift_gpu_default_time_params) with keyword overrides."""
+    tp = _lib.default_time_params()
+    for k, v in kw.items():
+        if not hasattr(tp, k):
+            raise KeyError(k)
+        setattr(tp, k, v)
+    return tp
+
+
+def new_clock(t_end: float = 0.0, device="cuda") -> torch.Tensor:
+    """A device swift_gpu_clock (32 bytes as four float64 words): t = 0, dt = dt_next = 0, step 0."""
+    c = _lib.Clock(0.0, float(t_end), 0.0, 0.0, 0)
+    raw = torch.frombuffer(bytearray(bytes(c)), dtype=torch.float64).clone()
+    return raw.to(device)
+
+
+def read_clock(clock: torch.Tensor) -> dict:
+    """Host copy of a device clock (synchronises its stream)."""
+    raw = clock.detach().cpu().numpy().tobytes()
+    c = _lib.Clock.from_buffer_copy(raw)
+    return dict(t=c.t, t_end=c.t_end, dt=c.dt, dt_next=c.dt_next, step=c.step)
 
 
 class SphForces(torch.autograd.Function):
