@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-clustered", action="store_true", help="skip the clustered (Plummer) active-step comparison")
+    ap.add_argument("--no-gresho", action="store_true", help="skip the integrated Gresho-Chan vortex steps")
     ap.add_argument("--autotune", action="store_true", help="run the library autotuner before timing")
     return ap.parse_args()
 
@@ -365,6 +366,8 @@ def run_ours(args, rank, world, pg):
         res["plain"] = run_plain(d, n, dev, min_width)
     if not args.no_clustered and rank == 0:
         res["clustered"] = run_clustered(dev)
+    if not args.no_gresho and rank == 0:
+        res["gresho"] = run_gresho(dev)
     if rank == 0 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(d, ctx)
     return res
@@ -503,6 +506,93 @@ def run_clustered(dev, steps=5):
         del ctx
     res["adaptive_speedup"] = res["uniform"]["ms_per_step"] / res["adaptive"]["ms_per_step"]
     return res
+
+
+# algorithmic HBM bytes per particle of the integration kernels (loads + stores of their arrays)
+INTEGRATION_BYTES = {"k_kick_drift": 56 + 56, "k_viscosity_switch": 40 + 8, "k_kick_finish": 72 + 40}
+
+
+def run_gresho(dev, n_side=128, steps=20, timed_direct=5):
+    """Whole integrated steps of the Gresho-Chan vortex (Sec. 3.1) at 128^3, the paper's Fig. 6 resolution.
+
+    One step = kick + drift, cells + density (h iteration), viscosity switch,
+    gradient + force, second kick + conduction switch + next step size,
+    captured once in a CUDA graph and replayed (the state advances in time).
+    The integration kernels are also timed alone (direct calls with events)
+    against the measured HBM copy bandwidth.
+    """
+    import numpy as np
+    import torch
+
+    from paper_2505_14538_b300 import ics, sph
+    from paper_2505_14538_b300.integrator import Integrator
+    d = ics.gresho(n_side)
+    n = len(d["pos"])
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev)
+    ctx = sph.Context(n)
+    it = Integrator(ctx, t(np.c_[d["pos"], d["h"]]), t(np.c_[d["vel"], d["m"]]), t(d["u"]))
+    it.prime()
+    for _ in range(3):
+        it.step(check=True)
+    stream = torch.cuda.current_stream()
+    # direct calls with events around every stage
+    names = ["k_kick_drift", "build_cells", "k_density", "k_viscosity_switch", "k_grad_force", "k_kick_finish"]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(timed_direct)]
+    c = it.ctx
+    for k in range(timed_direct):
+        e = ev[k]
+        e[0].record(stream)
+        c.kick_drift(it.tp, it.clock, it.pos_h, it.vel_m, it.u, it.accel_dudt, it.dh_dt, it.vel_pred, it.u_pred)
+        e[1].record(stream)
+        c.build_cells(it.pos_h, it.min_cell_width)
+        e[2].record(stream)
+        c.density(it.pos_h, it.vel_pred, None, h_out=it.h, rho4=it.rho4, curl_div=it.curl_div, ngb_count=it.ngb)
+        e[3].record(stream)
+        c.viscosity_switch(it.tp, it.clock, it.h, it.u_pred, it.curl_div, it.vsig_lapu, it.div_prev, it.alpha_v)
+        e[4].record(stream)
+        c.gradient_force(it.u_pred, it.alpha_v, it.alpha_c, vsig_lapu=it.vsig_lapu, accel_dudt=it.accel_dudt,
+                         dh_dt=it.dh_dt, reductions=it.reductions)
+        e[5].record(stream)
+        c.kick_finish(it.tp, it.clock, it.h, it.pos_h, it.vel_m, it.u, it.accel_dudt, it.vsig_lapu, it.alpha_v,
+                      it.alpha_c)
+        e[6].record(stream)
+    torch.cuda.synchronize()
+    it.check_status()
+    stage_ms = {names[j]: sum(ev[k][j].elapsed_time(ev[k][j + 1]) for k in range(timed_direct)) / timed_direct
+                for j in range(6)}
+    # graph replays
+    graph = it.capture(1)
+    gev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(steps)]
+    c0 = it.clock_state()
+    i0 = ctx.info()
+    torch.cuda.synchronize()
+    for k in range(steps):
+        gev[k][0].record(stream)
+        graph.replay()
+        gev[k][1].record(stream)
+    torch.cuda.synchronize()
+    it.check_status()
+    i1 = ctx.info()
+    c1 = it.clock_state()
+    ms = sum(gev[k][0].elapsed_time(gev[k][1]) for k in range(steps)) / steps
+    inter = sum(step_interactions(i0, i1)) / steps
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs")
+    kern = {}
+    for name, b in INTEGRATION_BYTES.items():
+        gbs = b * n / (stage_ms[name] * 1e-3) / 1e9
+        kern[name] = {"us": stage_ms[name] * 1e3, "bytes_per_particle": b, "achieved_gbs": gbs,
+                      "frac_of_measured_hbm": gbs / hbm if hbm else None}
+    return {"workload": f"gresho{n_side}: Gresho-Chan vortex (Eqs. 27-28) on a {n_side}^3 cubic lattice, rho=1, "
+                        "gamma=5/3, periodic unit box",
+            "particles": n, "steps": steps, "ms_per_step": ms, "steps_per_s": 1e3 / ms,
+            "particle_steps_per_s": n * 1e3 / ms, "interactions_per_step": inter,
+            "interactions_per_s": inter / (ms * 1e-3), "sim_time_advanced": c1["t"] - c0["t"],
+            "dt_last": c1["dt"], "launch": "one CUDA graph per step (kick/drift, build, density, switch, "
+                                           "gradient+force, kick/switch/dt)",
+            "stage_ms_direct": stage_ms, "integration_kernels": kern,
+            "integration_share": sum(stage_ms[k] for k in INTEGRATION_BYTES) / sum(stage_ms.values()),
+            "l2": "not flushed: the state (about 420 MB) is larger than the 126 MB L2"}
 
 
 # ------------------------------------------------------- CPU baseline leg
