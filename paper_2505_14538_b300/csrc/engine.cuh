@@ -145,6 +145,50 @@ __device__ __forceinline__ const unsigned* kept_list(const unsigned* nlist, cons
   return nlist + sp.x;
 }
 
+// Evens out the list lengths of the L = 2^lsh lanes that share one particle
+// (lanes slot + k A, A = 32 >> lsh, sub-lane k = lane / A): a particle with T
+// entries ends with T / L entries in each of its lanes, plus one in the first
+// T % L of them. Entries past a lane's new length move, in order, to the ends
+// of the lanes that are short. Which lane takes an entry changes a sum only by
+// rounding, and a phase over the lists then runs as many trips as the
+// particle's T / L needs instead of its longest lane. Every lane of the warp
+// calls it (lsh is the same for the whole item); returns the lane's new count.
+__device__ __forceinline__ int balance_lists(WarpSmem& w, int cnt, int lsh) {
+  if (lsh == 0) return cnt;
+  const unsigned lane = lane_id();
+  const int A = 32 >> lsh, L = 1 << lsh;
+  int T = cnt;
+  for (int o = A; o < 32; o <<= 1) T += __shfl_xor_sync(kFull, T, o);
+  const int sub = (int)lane >> (5 - lsh);
+  const int target = (T >> lsh) + (sub < (T & (L - 1)) ? 1 : 0);
+  const int sur = cnt > target ? cnt - target : 0;
+  const int def = target > cnt ? target - cnt : 0;
+  if (!__any_sync(kFull, sur > 0)) return cnt;
+  int ps = sur, pd = def;  // inclusive prefixes over the particle's sub-lanes
+  for (int o = A; o < 32; o <<= 1) {
+    const int ys = __shfl_up_sync(kFull, ps, o);
+    const int yd = __shfl_up_sync(kFull, pd, o);
+    if ((int)lane >= o) {
+      ps += ys;
+      pd += yd;
+    }
+  }
+  const int es = ps - sur, ed = pd - def;  // this lane's surplus units [es, ps), wanted units [ed, pd)
+  const int slot = (int)lane & (A - 1);
+  __syncwarp();
+  for (int k = 0; k < L; ++k) {
+    const int src = slot + k * A;
+    const int es_k = __shfl_sync(kFull, es, src);
+    const int ps_k = __shfl_sync(kFull, ps, src);
+    const int tg_k = __shfl_sync(kFull, target, src);
+    const int lo = max(ed, es_k), hi = min(pd, ps_k);
+    for (int u = lo; u < hi; ++u)
+      w.list[(cnt + (u - ed)) * 32 + (int)lane] = w.list[(tg_k + (u - es_k)) * 32 + src];
+  }
+  __syncwarp();
+  return target;
+}
+
 // Phase 2: each lane evaluates the interactions in its list.
 template <class Op>
 __device__ __forceinline__ void flush(const Op& op, typename Op::I& I, const WarpSmem& w, int cnt) {

@@ -10,7 +10,7 @@
 #include <cuda_runtime.h>
 
 #include "internal.h"
-#include "swift_gpu_time.h"
+#include "../../include/swift_gpu_time.h"
 
 namespace sg {
 namespace {

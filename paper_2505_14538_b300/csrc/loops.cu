@@ -196,8 +196,11 @@ __device__ __forceinline__ void dens_item(const DensArgs& a, const DensOp& op, c
     const float Hc = a.ph.kg * hcap;
     const float R2 = Hc * Hc + band_of(Hc, Lmax);
     bool ovf = false;
-    const int cnt = collect_item(g, a.nb, a.pos, it.cell, I.x, I.y, I.z, R2, lm.lsh, lm.s, lm.live, w, ncand, ovf);
+    int cnt = collect_item(g, a.nb, a.pos, it.cell, I.x, I.y, I.z, R2, lm.lsh, lm.s, lm.live, w, ncand, ovf);
     retry = lsum_u(ovf ? 1u : 0u, lm.lsh) != 0;
+    // even lists shorten the Newton walks and the final sums here, and the
+    // kept lists' width (the trips of the gradient and force loops)
+    cnt = balance_lists(w, cnt, lm.lsh);
     // kept only where every h (active or not) is within this item's cap: the
     // uniform grid with the cell-derived cap (leaves have caps of their own,
     // and a user h_max may lie below an inactive particle's h)
