@@ -27,6 +27,13 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 KERNEL_GAMMA = float(np.float32(1.825742))
 ETA = 1.2348
 
+# Kernel shapes (Sec. 2.1.1 names the cubic spline and the Wendland kernels):
+# 0 cubic spline, 1 Wendland C2, 2 Wendland C4, each with its own H/h from the
+# same definition (sqrt(30)/3, sqrt(15)/2, sqrt(78)/4), rounded to float32.
+CUBIC, WENDLAND_C2, WENDLAND_C4 = 0, 1, 2
+KERNEL_GAMMAS = {CUBIC: KERNEL_GAMMA, WENDLAND_C2: float(np.float32(np.sqrt(15.0) / 2.0)),
+                 WENDLAND_C4: float(np.float32(np.sqrt(78.0) / 4.0))}
+
 
 def build(force: bool = False) -> str:
     """Compile the oracle shared library next to its source; returns its path."""
@@ -54,6 +61,7 @@ class _CParams(ctypes.Structure):
         ("use_cells", ctypes.c_int),
         ("nthreads", ctypes.c_int),
         ("terms", ctypes.c_int),
+        ("kernel", ctypes.c_int),
     ]
 
 
@@ -73,6 +81,7 @@ class Params:
     use_cells: bool = True
     nthreads: int = 0
     terms: int = 7
+    kernel: int = CUBIC
 
     def c(self) -> _CParams:
         p = _CParams()
@@ -90,6 +99,7 @@ class Params:
         p.use_cells = int(self.use_cells)
         p.nthreads = int(self.nthreads)
         p.terms = int(self.terms)
+        p.kernel = int(self.kernel)
         return p
 
 
@@ -132,13 +142,14 @@ def cell_ids(x, box, nc):
     return out
 
 
-def kernel(r, h, kernel_gamma=KERNEL_GAMMA):
-    """W(r, h) and dW/dr of the cubic spline."""
+def kernel(r, h, kernel_gamma=KERNEL_GAMMA, kind=CUBIC):
+    """W(r, h) and dW/dr of the cubic spline (kind 0) or a Wendland kernel (1: C2, 2: C4)."""
     r = _d(r).ravel()
     W = np.zeros_like(r)
     dW = np.zeros_like(r)
-    lib().oracle_kernel(ctypes.c_int64(len(r)), _p(r), ctypes.c_double(h), ctypes.c_double(kernel_gamma),
-                        _p(W), _p(dW))
+    rc = lib().oracle_kernel(ctypes.c_int64(len(r)), _p(r), ctypes.c_double(h), ctypes.c_double(kernel_gamma),
+                             ctypes.c_int(kind), _p(W), _p(dW))
+    assert rc == 0
     return W, dW
 
 

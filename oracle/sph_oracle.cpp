@@ -17,6 +17,11 @@
  *  - Kernel: cubic spline (M4) in 3D with compact support H = kernel_gamma*h
  *    (Sec. 2.1.3, "H_i = gamma_k h_i"); W = (8/pi) H^-3 w(r/H),
  *    w(q) = 1-6q^2+6q^3 (q<1/2), 2(1-q)^3 (1/2<=q<1), 0 beyond.
+ *    Sec. 2.1.1 also names the Wendland kernels; with kernel = 1 or 2:
+ *    Wendland C2, W = (21/(2 pi)) H^-3 (1-q)^4 (1+4q), and Wendland C4,
+ *    W = (495/(32 pi)) H^-3 (1-q)^6 (1+6q+35q^2/3) (the 3-D normalisations;
+ *    their own H/h from the same second-moment definition as the cubic
+ *    spline's, sqrt(15)/2 and sqrt(78)/4, is passed as kernel_gamma).
  *  - Eq. 6: "grad_i W_ij" is the scalar dW/dr (it is multiplied by r_ij/h_i).
  *  - Eq. 3/4: differenced form. div v_i = (1/rho_i) sum_j m_j (v_j-v_i).grad_i W_ij;
  *    curl v_i = (1/rho_i) sum_j m_j (v_i-v_j) x grad_i W_ij. Eq. 4 as printed
@@ -82,6 +87,7 @@ typedef struct {
   int use_cells;        /* 0: all pairs (brute force); 1: cell list */
   int nthreads;         /* <= 0: OpenMP default */
   int terms;            /* force-loop terms: 1 pressure/energy, 2 viscosity, 4 conduction */
+  int kernel;           /* 0 cubic spline, 1 Wendland C2, 2 Wendland C4 */
 } oracle_params;
 
 }  // extern "C"
@@ -140,19 +146,45 @@ inline void spline(T q, T& w, T& dw) {
   }
 }
 
+/* Wendland C2 and C4 shapes w(q) and dw/dq on q in [0,1), zero beyond. */
+template <class T>
+inline void wendland(int kind, T q, T& w, T& dw) {
+  if (!(q < T(1.0))) {
+    w = T(0.0);
+    dw = T(0.0);
+    return;
+  }
+  T s = T(1.0) - q;
+  T s2 = s * s;
+  if (kind == 1) {
+    w = s2 * s2 * (T(1.0) + T(4.0) * q);
+    dw = T(-20.0) * q * s2 * s;
+  } else {
+    w = s2 * s2 * s2 * (T(1.0) + T(6.0) * q + T(35.0 / 3.0) * q * q);
+    dw = T(-56.0 / 3.0) * q * (T(1.0) + T(5.0) * q) * s2 * s2 * s;
+  }
+}
+
+/* 3-D normalisation C of W = C H^-3 w(r/H) (the integral of W is 1). */
+inline double kernel_norm(int kind) {
+  return kind == 1 ? 21.0 / (2.0 * kPi) : kind == 2 ? 495.0 / (32.0 * kPi) : 8.0 / kPi;
+}
+
 /* Per-particle kernel constants for support H: W = c3 w(q), dW/dr = c4 w'(q). */
 template <class T>
 struct KernelI {
   T H, invH, c3, c4;
+  int kind;
 };
 template <class T>
-inline KernelI<T> kernel_consts(double h, double kernel_gamma) {
+inline KernelI<T> kernel_consts(double h, double kernel_gamma, int kind) {
   KernelI<T> k;
   double H = kernel_gamma * h;
   k.H = T(H);
   k.invH = T(1.0 / H);
-  k.c3 = T((8.0 / kPi) / (H * H * H));
-  k.c4 = T((8.0 / kPi) / (H * H * H * H));
+  k.c3 = T(kernel_norm(kind) / (H * H * H));
+  k.c4 = T(kernel_norm(kind) / (H * H * H * H));
+  k.kind = kind;
   return k;
 }
 
@@ -160,7 +192,8 @@ inline KernelI<T> kernel_consts(double h, double kernel_gamma) {
 template <class T>
 inline void kernel_eval(const KernelI<T>& k, T r, T& W, T& dWdr) {
   T w, dw;
-  spline(r * k.invH, w, dw);
+  if (k.kind == 0) spline(r * k.invH, w, dw);
+  else wendland(k.kind, r * k.invH, w, dw);
   W = k.c3 * w;
   dWdr = k.c4 * dw;
 }
@@ -283,8 +316,8 @@ struct DensOut {
 
 /* Eq. 5 and Eq. 6 at h (self included in the sums, not in the count). */
 DensOut number_at(const Geo& g, const Cells& c, int64_t n, const double* x, int64_t i, double h,
-                  double kernel_gamma) {
-  KernelI<double> k = kernel_consts<double>(h, kernel_gamma);
+                  double kernel_gamma, int kind) {
+  KernelI<double> k = kernel_consts<double>(h, kernel_gamma, kind);
   double H2 = k.H * k.H;
   double s = 0.0, ds = 0.0;
   long long count = 0;
@@ -305,8 +338,8 @@ DensOut number_at(const Geo& g, const Cells& c, int64_t n, const double* x, int6
 }
 
 DensOut density_at(const Geo& g, const Cells& c, int64_t n, const double* x, const double* v,
-                   const double* m, int64_t i, double h, double kernel_gamma) {
-  KernelI<double> k = kernel_consts<double>(h, kernel_gamma);
+                   const double* m, int64_t i, double h, double kernel_gamma, int kind) {
+  KernelI<double> k = kernel_consts<double>(h, kernel_gamma, kind);
   double H2 = k.H * k.H;
   DensAcc<double> a{0, 0, 0, 0, 0, 0, 0, 0, 0};
   for_candidates(c, n, i, [&](int64_t j) {
@@ -352,7 +385,7 @@ SolveOut solve_h(const Geo& g, const Cells& c, int64_t n, const double* x, const
   s.converged = 0;
   s.pairs = 0;
   for (int it = 0; it < p.max_iter; ++it) {
-    DensOut d = number_at(g, c, n, x, i, h, p.kernel_gamma);
+    DensOut d = number_at(g, c, n, x, i, h, p.kernel_gamma, p.kernel);
     s.pairs += d.count;
     double target = eta3 / (h * h * h);
     double F = d.n - target;
@@ -376,7 +409,7 @@ SolveOut solve_h(const Geo& g, const Cells& c, int64_t n, const double* x, const
     }
     h = std::min(hn, hmax);
   }
-  s.d = density_at(g, c, n, x, v, m, i, s.h, p.kernel_gamma);
+  s.d = density_at(g, c, n, x, v, m, i, s.h, p.kernel_gamma, p.kernel);
   return s;
 }
 
@@ -496,8 +529,9 @@ int oracle_cell_ids(int64_t n, const double* x, const double* box, int nc, uint3
 }
 
 /* Kernel W(r,h) and dW/dr for a vector of r at one h (for the kernel pins). */
-int oracle_kernel(int64_t n, const double* r, double h, double kernel_gamma, double* W, double* dWdr) {
-  KernelI<double> k = kernel_consts<double>(h, kernel_gamma);
+int oracle_kernel(int64_t n, const double* r, double h, double kernel_gamma, int kind, double* W, double* dWdr) {
+  if (kind < 0 || kind > 2) return -1;
+  KernelI<double> k = kernel_consts<double>(h, kernel_gamma, kind);
   for (int64_t i = 0; i < n; ++i) kernel_eval(k, r[i], W[i], dWdr[i]);
   return 0;
 }
@@ -514,7 +548,7 @@ int oracle_density(const oracle_params* p, int64_t n, const double* x, const dou
 #pragma omp parallel for schedule(dynamic, 64) num_threads(nthreads_of(*p))
   for (int64_t i = 0; i < n; ++i) {
     if (active && !active[i]) continue;
-    DensOut d = density_at(g, c, n, x, v, m, i, h[i], p->kernel_gamma);
+    DensOut d = density_at(g, c, n, x, v, m, i, h[i], p->kernel_gamma, p->kernel);
     if (n_out) n_out[i] = d.n;
     if (dn_dh) dn_dh[i] = d.dn_dh;
     if (rho) rho[i] = d.rho;
@@ -587,7 +621,7 @@ int oracle_gradient(const oracle_params* p, int64_t n, const double* x, const do
 #pragma omp parallel for schedule(dynamic, 64) num_threads(nthreads_of(*p))
   for (int64_t i = 0; i < n; ++i) {
     if (active && !active[i]) continue;
-    KernelI<double> k = kernel_consts<double>(h[i], p->kernel_gamma);
+    KernelI<double> k = kernel_consts<double>(h[i], p->kernel_gamma, p->kernel);
     double H2 = k.H * k.H;
     GradAcc<double> a{2.0 * c[i], 0.0}; /* j = i: mu = 0 */
     for_candidates(cl, n, i, [&](int64_t j) {
@@ -619,7 +653,7 @@ int oracle_force(const oracle_params* p, int64_t n, const double* x, const doubl
   Cells cl = make_cells(g, n, x, p->kernel_gamma * max_of(n, h), p->use_cells);
   auto per = [&](int64_t i) {
     ForceI<double> I;
-    I.k = kernel_consts<double>(h[i], p->kernel_gamma);
+    I.k = kernel_consts<double>(h[i], p->kernel_gamma, p->kernel);
     I.f = f[i];
     I.rho = rho[i];
     I.P = P[i];
@@ -668,7 +702,7 @@ int oracle_interpolate(const oracle_params* p, int64_t n, const double* x, const
   Cells cl = make_cells(g, n, x, p->kernel_gamma * max_of(n, h), p->use_cells);
 #pragma omp parallel for schedule(dynamic, 64) num_threads(nthreads_of(*p))
   for (int64_t i = 0; i < n; ++i) {
-    KernelI<double> k = kernel_consts<double>(h[i], p->kernel_gamma);
+    KernelI<double> k = kernel_consts<double>(h[i], p->kernel_gamma, p->kernel);
     double H2 = k.H * k.H, s = 0.0;
     for_candidates(cl, n, i, [&](int64_t j) {
       double d[3] = {x[3 * i] - x[3 * j], x[3 * i + 1] - x[3 * j + 1], x[3 * i + 2] - x[3 * j + 2]};
@@ -696,7 +730,7 @@ int oracle_interpolate(const oracle_params* p, int64_t n, const double* x, const
 int oracle_count_flops(int loop, double q, int approaching, long long* out) {
   OpTally t{0, 0, 0, 0, 0};
   double h = 0.02, kg = 1.825742;
-  KernelI<Cnt> k = kernel_consts<Cnt>(h, kg);
+  KernelI<Cnt> k = kernel_consts<Cnt>(h, kg, 0);
   double r = q * kg * h;
   Cnt dx(r), dy(0.0), dz(0.0), r2(r * r);
   Cnt dvx(approaching ? -0.3 : 0.3), dvy(0.1), dvz(0.2);
@@ -714,7 +748,7 @@ int oracle_count_flops(int loop, double q, int approaching, long long* out) {
   } else {
     ForceI<Cnt> I, J;
     I.k = k;
-    J.k = kernel_consts<Cnt>(h * 1.05, kg);
+    J.k = kernel_consts<Cnt>(h * 1.05, kg, 0);
     I.f = J.f = Cnt(1.0);
     I.A = J.A = Cnt(1.0);
     I.rho = J.rho = Cnt(1.0);

@@ -39,14 +39,28 @@ def pair_list(x, h, box, kernel_gamma=KERNEL_GAMMA, block=512):
     return np.concatenate(I), np.concatenate(J)
 
 
-def _w(q):
+def _w(q, kernel=0):
+    """Kernel shape on the support (the caller masks q >= 1): cubic spline, Wendland C2 or C4."""
     s = torch.clamp(1.0 - q, min=0.0)
+    if kernel == 1:
+        return s ** 4 * (1.0 + 4.0 * q)
+    if kernel == 2:
+        return s ** 6 * (1.0 + 6.0 * q + (35.0 / 3.0) * q * q)
     return torch.where(q < 0.5, 1.0 - 6.0 * q * q + 6.0 * q * q * q, 2.0 * s * s * s)
 
 
-def _dw(q):
+def _dw(q, kernel=0):
     s = torch.clamp(1.0 - q, min=0.0)
+    if kernel == 1:
+        return -20.0 * q * s ** 3
+    if kernel == 2:
+        return (-56.0 / 3.0) * q * (1.0 + 5.0 * q) * s ** 5
     return torch.where(q < 0.5, -12.0 * q + 18.0 * q * q, -6.0 * s * s)
+
+
+def _norm(kernel=0):
+    """3-D normalisation of W = C H^-3 w(r/H)."""
+    return {0: 8.0 / math.pi, 1: 21.0 / (2.0 * math.pi), 2: 495.0 / (32.0 * math.pi)}[kernel]
 
 
 def _safe_sqrt(x):
@@ -54,7 +68,7 @@ def _safe_sqrt(x):
 
 
 def forward(x, v, u, m, h, pairs, box=(1.0, 1.0, 1.0), gamma=5.0 / 3.0, alpha_v=1.0, beta=3.0, alpha_c=1.0,
-            kernel_gamma=KERNEL_GAMMA):
+            kernel_gamma=KERNEL_GAMMA, kernel=0):
     """accel (n, 3) and du/dt (n,) at fixed h; x, v, u are torch float64 (may require grad)."""
     n = x.shape[0]
     i = torch.as_tensor(pairs[0], dtype=torch.long)
@@ -69,10 +83,10 @@ def forward(x, v, u, m, h, pairs, box=(1.0, 1.0, 1.0), gamma=5.0 / 3.0, alpha_v=
     e = d / r[:, None]
     Hi, Hj = H[i], H[j]
     qi, qj = r / Hi, r / Hj
-    c3 = (8.0 / math.pi) / H ** 3
-    Wi = c3[i] * _w(qi)
-    dWi = c3[i] / Hi * _dw(qi)
-    dWj = c3[j] / Hj * _dw(qj)
+    c3 = _norm(kernel) / H ** 3
+    Wi = c3[i] * _w(qi, kernel)
+    dWi = c3[i] / Hi * _dw(qi, kernel)
+    dWj = c3[j] / Hj * _dw(qj, kernel)
     in_i = (r < Hi).detach().to(torch.float64)  # pairs in i's density sums
     # density sums (self term: W(0) = c3, r dW/dr = 0)
     rho = m * c3 + torch.zeros(n, dtype=torch.float64).index_add(0, i, in_i * m[j] * Wi)
@@ -120,7 +134,7 @@ def loss_and_grad(x, v, u, m, h, w, cw, box=(1.0, 1.0, 1.0), pairs=None, **kw):
     v = torch.tensor(np.asarray(v, np.float64), requires_grad=True)
     u = torch.tensor(np.asarray(u, np.float64), requires_grad=True)
     if pairs is None:
-        pairs = pair_list(x.detach().numpy(), h, box)
+        pairs = pair_list(x.detach().numpy(), h, box, kw.get("kernel_gamma", KERNEL_GAMMA))
     a, du, _ = forward(x, v, u, m, h, pairs, box, **kw)
     Lv = (torch.as_tensor(np.asarray(w, np.float64)) * a).sum() + (torch.as_tensor(np.asarray(cw, np.float64)) * du).sum()
     gx, gv, gu = torch.autograd.grad(Lv, (x, v, u))

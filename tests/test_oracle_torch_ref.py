@@ -71,3 +71,15 @@ def test_torch_gradient_matches_oracle_finite_differences(O):
             assert abs(g - fd[0]) <= 1e-5 * scale[name], (name, k, comp, g, fd[0])
             checked += 1
     assert checked >= 18
+
+
+@pytest.mark.parametrize("kind", [1, 2])
+def test_torch_forward_matches_oracle_wendland(O, kind):
+    """The two restatements agree for the Wendland kernels too (same pair set, kernel's own H/h)."""
+    from oracle import torch_ref as T
+    x, v, u, m, h, w, cw = _state(seed=kind)
+    kg = O.KERNEL_GAMMAS[kind]
+    L, gx, gv, gu, a, du = T.loss_and_grad(x, v, u, m, h, w, cw, kernel_gamma=kg, kernel=kind)
+    s = O.step(O.Params(kernel=kind, kernel_gamma=kg), x, v, m, u, h, solve=False)
+    assert np.all(np.linalg.norm(a - s["accel"], axis=1) <= 1e-11 * s["s_a"])
+    assert np.all(np.abs(du - s["dudt"]) <= 1e-11 * s["s_u"])
