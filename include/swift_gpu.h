@@ -61,6 +61,14 @@ extern "C" {
                                      the particles of a leaf, only the leaves whose bounding boxes come within
                                      the larger of the two leaves' supports (not with PLAIN) */
 
+/* swift_gpu_params.kernel: the kernel shape W = C H^-3 w(r/H) (Sec. 2.1.1
+ * names the cubic spline and the Wendland kernels). kernel_gamma should be
+ * the shape's own H/h from the second-moment definition h = 2 sigma:
+ * sqrt(30)/3 = 1.825742, sqrt(15)/2 = 1.936492, sqrt(78)/4 = 2.207940. */
+#define SWIFT_GPU_KERNEL_CUBIC 0        /* cubic spline M4, C = 8/pi */
+#define SWIFT_GPU_KERNEL_WENDLAND_C2 1  /* w = (1-q)^4 (1+4q), C = 21/(2 pi) */
+#define SWIFT_GPU_KERNEL_WENDLAND_C4 2  /* w = (1-q)^6 (1+6q+35q^2/3), C = 495/(32 pi) */
+
 typedef struct {
   float box[3];        /* periodic box edge lengths L (the box is [0,L)^3) */
   float gamma_eos;     /* adiabatic index gamma (Sec. 3.1: 5/3) */
@@ -76,6 +84,7 @@ typedef struct {
   int flags;           /* SWIFT_GPU_* flags above */
   int leaf_max;        /* ADAPTIVE: a node with more particles is split into its 8 octants (8..1024) */
   float leaf_margin;   /* ADAPTIVE: the h cap of a leaf is (1 + leaf_margin) * its largest h at the build */
+  int kernel;          /* SWIFT_GPU_KERNEL_*: kernel shape (every loop and the adjoint) */
 } swift_gpu_params;
 
 /* Work-distribution knobs (chosen by swift_gpu_autotune, or set by hand). */
@@ -109,7 +118,7 @@ typedef struct swift_gpu_ctx swift_gpu_ctx;
 
 /* Fill *p with the defaults (unit box, gamma 5/3, eta 1.2348, kernel_gamma
  * 1.825742, alpha_v 1, beta_v 3, alpha_c 1, h_tol 1e-4, max_iter 30, h_max 0,
- * cell_margin 0.05, flags 0, leaf_max 32, leaf_margin 0.1). Host only; never fails. */
+ * cell_margin 0.05, flags 0, leaf_max 32, leaf_margin 0.1, kernel CUBIC). Host only; never fails. */
 void swift_gpu_default_params(swift_gpu_params* p);
 
 /* Create a context for up to n_max particles on the current CUDA device.

@@ -30,6 +30,12 @@ FLAG_NO_H_ITER = 2
 FLAG_NO_COMPENSATION = 4
 FLAG_ADAPTIVE = 8
 
+KERNEL_CUBIC = 0
+KERNEL_WENDLAND_C2 = 1
+KERNEL_WENDLAND_C4 = 2
+# H/h of each shape from the second-moment definition (sqrt(30)/3, sqrt(15)/2, sqrt(78)/4)
+KERNEL_GAMMAS = {KERNEL_CUBIC: 1.825742, KERNEL_WENDLAND_C2: 1.936492, KERNEL_WENDLAND_C4: 2.207940}
+
 EXPORTED = ("swift_gpu_default_params", "swift_gpu_create", "swift_gpu_destroy", "swift_gpu_set_params",
             "swift_gpu_build_cells", "swift_gpu_density", "swift_gpu_gradient", "swift_gpu_force",
             "swift_gpu_force_backward", "swift_gpu_sync_status", "swift_gpu_get_info", "swift_gpu_get_cells",
@@ -56,6 +62,7 @@ class Params(ctypes.Structure):
         ("flags", ctypes.c_int),
         ("leaf_max", ctypes.c_int),
         ("leaf_margin", ctypes.c_float),
+        ("kernel", ctypes.c_int),
     ]
 
 

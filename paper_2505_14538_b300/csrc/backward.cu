@@ -33,14 +33,6 @@ __device__ __forceinline__ WarpSmem& adj_smem(unsigned char* smem) {
   return reinterpret_cast<WarpSmem*>(smem)[threadIdx.x >> 5];
 }
 
-// First and second derivatives of the cubic-spline shape, dw/dq and d2w/dq2.
-__device__ __forceinline__ void spline_d12(float q, float& dw, float& d2w) {
-  const float s = fmaxf(1.0f - q, 0.0f);
-  const bool in = q < 0.5f;
-  dw = in ? q * fmaf(18.0f, q, -12.0f) : -6.0f * s * s;
-  d2w = in ? fmaf(36.0f, q, -12.0f) : 12.0f * s;
-}
-
 struct AdjArgs {
   Grid* grid;
   Nbr nb;
@@ -193,6 +185,8 @@ struct ForceAdjOp {
   const float4* __restrict__ g4;
   float L[3];
   float kg, beta, gm1, Lmax;
+  int kernel;
+  float knorm;
 
   __device__ __forceinline__ float stage_w(float hj) const {
     const float H = kg * hj;
@@ -223,10 +217,10 @@ struct ForceAdjOp {
     const float ir = 1.0f / r;
     const float e[3] = {d[0] * ir, d[1] * ir, d[2] * ir};
     float dwi, d2wi, dwj, d2wj;
-    spline_d12(r * i.invH, dwi, d2wi);
+    kshape_d12(kernel, r * i.invH, dwi, d2wi);
     const float invHj = 1.0f / Hj;
-    spline_d12(r * invHj, dwj, d2wj);
-    const float c4j = (8.0f / kPi) * invHj * invHj * invHj * invHj;
+    kshape_d12(kernel, r * invHj, dwj, d2wj);
+    const float c4j = knorm * invHj * invHj * invHj * invHj;
     const float dWk = i.c4 * dwi, d2Wk = i.c5 * d2wi;
     const float dWj = c4j * dwj, d2Wj = c4j * invHj * d2wj;
     Side sj;
@@ -273,7 +267,7 @@ __device__ __forceinline__ void force_adj_item(const AdjArgs& a, const ForceAdjO
   I.H2lo = H * H - b;
   I.H2hi = H * H + b;
   I.invH = 1.0f / H;
-  I.c4 = (8.0f / kPi) * I.invH * I.invH * I.invH * I.invH;
+  I.c4 = a.ph.knorm * I.invH * I.invH * I.invH * I.invH;
   I.c5 = I.c4 * I.invH;
   I.vx = v.x; I.vy = v.y; I.vz = v.z; I.m = v.w;
   I.s.A = gi.x; I.s.f = gi.y; I.s.rho = gi.z; I.s.c = gi.w;
@@ -358,6 +352,8 @@ __global__ void __launch_bounds__(kAdjThreads) k_force_adj(AdjArgs a) {
   op.L[0] = g.L[0]; op.L[1] = g.L[1]; op.L[2] = g.L[2];
   op.Lmax = fmaxf(g.L[0], fmaxf(g.L[1], g.L[2]));
   op.kg = a.ph.kg;
+  op.kernel = a.ph.kernel;
+  op.knorm = a.ph.knorm;
   op.beta = a.ph.beta_v;
   op.gm1 = a.ph.gamma_eos - 1.0f;
   const int n_items = a.ctr[0];
@@ -383,6 +379,8 @@ struct DensAdjOp {
   const float* __restrict__ cbz;
   float L[3];
   float kg, Lmax;
+  int kernel;
+  float knorm;
 
   __device__ __forceinline__ float stage_w(float hj) const {
     const float H = kg * hj;
@@ -398,7 +396,7 @@ struct DensAdjOp {
                                           float invH, float c4, float c5, float mass, float rb, float Db, float Sb,
                                           const float Cb[3], bool own) const {
     float dw, d2w;
-    spline_d12(r * invH, dw, d2w);
+    kshape_d12(kernel, r * invH, dw, d2w);
     const float W1 = c4 * dw, W2 = c5 * d2w;
     const float g = W1 / r;
     const float gp = (W2 - g) / r;
@@ -453,7 +451,7 @@ struct DensAdjOp {
       const float4 q = qb[j];
       const float Cj[3] = {q.w, cby[j], cbz[j]};
       const float invHj = 1.0f / Hj;
-      const float c4j = (8.0f / kPi) * invHj * invHj * invHj * invHj;
+      const float c4j = knorm * invHj * invHj * invHj * invHj;
       add_sum(i, r, e, d, vjk, invHj, c4j, c4j * invHj, i.m, q.x, q.y, q.z, Cj, false);
     }
   }
@@ -468,6 +466,8 @@ __global__ void __launch_bounds__(kAdjThreads) k_dens_adj(AdjArgs a) {
   op.L[0] = g.L[0]; op.L[1] = g.L[1]; op.L[2] = g.L[2];
   op.Lmax = fmaxf(g.L[0], fmaxf(g.L[1], g.L[2]));
   op.kg = a.ph.kg;
+  op.kernel = a.ph.kernel;
+  op.knorm = a.ph.knorm;
   const int n_items = a.ctr[0];
   const unsigned lane = lane_id();
   for (;;) {
@@ -488,7 +488,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_dens_adj(AdjArgs a) {
     I.H2lo = H * H - b;
     I.H2hi = H * H + b;
     I.invH = 1.0f / H;
-    I.c4 = (8.0f / kPi) * I.invH * I.invH * I.invH * I.invH;
+    I.c4 = a.ph.knorm * I.invH * I.invH * I.invH * I.invH;
     I.c5 = I.c4 * I.invH;
     I.vx = v.x; I.vy = v.y; I.vz = v.z; I.m = v.w;
     I.rb = q.x; I.Db = q.y; I.Sb = q.z;

@@ -29,6 +29,7 @@ int phys_from(const swift_gpu_params* p, Phys* ph) {
   if (!(p->kernel_gamma > 0.0f) || !(p->eta > 0.0f) || !(p->gamma_eos > 1.0f)) return SWIFT_GPU_ERR_ARG;
   if (p->max_iter < 1 || !(p->h_tol >= 0.0f) || p->h_max < 0.0f || p->cell_margin < 0.0f)
     return SWIFT_GPU_ERR_ARG;
+  if (p->kernel < SWIFT_GPU_KERNEL_CUBIC || p->kernel > SWIFT_GPU_KERNEL_WENDLAND_C4) return SWIFT_GPU_ERR_ARG;
   if ((p->flags & SWIFT_GPU_ADAPTIVE) &&
       ((p->flags & SWIFT_GPU_PLAIN) || p->leaf_max < 8 || p->leaf_max > 1024 || !(p->leaf_margin >= 0.0f) ||
        !isfinite(p->leaf_margin)))
@@ -44,6 +45,8 @@ int phys_from(const swift_gpu_params* p, Phys* ph) {
   ph->max_iter = p->max_iter < kMaxPasses ? p->max_iter : kMaxPasses;
   ph->h_max = p->h_max;
   ph->compensated = (p->flags & SWIFT_GPU_NO_COMPENSATION) ? 0 : 1;
+  ph->kernel = p->kernel;
+  ph->knorm = kernel_norm(p->kernel);
   return SWIFT_GPU_OK;
 }
 
@@ -90,6 +93,7 @@ void swift_gpu_default_params(swift_gpu_params* p) {
   p->flags = 0;
   p->leaf_max = 32;
   p->leaf_margin = 0.1f;
+  p->kernel = SWIFT_GPU_KERNEL_CUBIC;
 }
 
 int swift_gpu_create(swift_gpu_ctx** out, const swift_gpu_params* p, int64_t n_max) {

@@ -61,6 +61,8 @@ struct Phys {
   int max_iter;
   float h_max;       // user cap (0 = none)
   int compensated;
+  int kernel;        // kernel shape: 0 cubic spline, 1 Wendland C2, 2 Wendland C4
+  float knorm;       // its 3-D normalisation C (W = C H^-3 w(r/H))
 };
 
 // Where the candidate segments of a work item come from: the 27 neighbour
@@ -143,6 +145,62 @@ __device__ __forceinline__ float dspline(float q) {
   float dwo = -6.0f * s * s;
   float dwi = q * fmaf(18.0f, q, -12.0f);
   return q < 0.5f ? dwi : dwo;
+}
+
+// Kernel shapes (Sec. 2.1.1 names the cubic spline and the Wendland kernels):
+// 0 cubic spline, 1 Wendland C2 w = (1-q)^4 (1+4q), 2 Wendland C4
+// w = (1-q)^6 (1+6q+35q^2/3); W = C H^-3 w(r/H) with C the 3-D normalisation.
+constexpr int kKernelCubic = 0, kKernelWendlandC2 = 1, kKernelWendlandC4 = 2;
+
+__host__ __device__ __forceinline__ float kernel_norm(int kind) {
+  return kind == kKernelWendlandC2 ? 21.0f / (2.0f * kPi) : kind == kKernelWendlandC4 ? 495.0f / (32.0f * kPi)
+                                                                                       : 8.0f / kPi;
+}
+
+// Wendland C2 (kind 1) or C4 (kind 2) shape and dw/dq, zero beyond q = 1.
+__device__ __forceinline__ void wendland(int kind, float q, float& w, float& dw) {
+  const float s = fmaxf(1.0f - q, 0.0f);
+  const float s2 = s * s;
+  if (kind == kKernelWendlandC2) {
+    const float s3 = s2 * s;
+    w = s3 * s * fmaf(4.0f, q, 1.0f);
+    dw = -20.0f * q * s3;
+  } else {
+    const float s4 = s2 * s2;
+    w = s4 * s2 * fmaf(q, fmaf(35.0f / 3.0f, q, 6.0f), 1.0f);
+    dw = (-56.0f / 3.0f) * q * fmaf(5.0f, q, 1.0f) * s4 * s;
+  }
+}
+
+// w(q) and dw/dq of the selected shape (the branch is the same for a whole launch).
+__device__ __forceinline__ void kshape(int kind, float q, float& w, float& dw) {
+  if (kind == kKernelCubic) spline(q, w, dw);
+  else wendland(kind, q, w, dw);
+}
+
+__device__ __forceinline__ float dkshape(int kind, float q) {
+  if (kind == kKernelCubic) return dspline(q);
+  float w, dw;
+  wendland(kind, q, w, dw);
+  return dw;
+}
+
+// dw/dq and d2w/dq2 of the selected shape (the adjoint loops).
+__device__ __forceinline__ void kshape_d12(int kind, float q, float& dw, float& d2w) {
+  const float s = fmaxf(1.0f - q, 0.0f);
+  if (kind == kKernelCubic) {
+    const bool in = q < 0.5f;
+    dw = in ? q * fmaf(18.0f, q, -12.0f) : -6.0f * s * s;
+    d2w = in ? fmaf(36.0f, q, -12.0f) : 12.0f * s;
+  } else if (kind == kKernelWendlandC2) {
+    const float s2 = s * s;
+    dw = -20.0f * q * s2 * s;
+    d2w = 20.0f * s2 * fmaf(4.0f, q, -1.0f);
+  } else {
+    const float s4 = (s * s) * (s * s);
+    dw = (-56.0f / 3.0f) * q * fmaf(5.0f, q, 1.0f) * s4 * s;
+    d2w = (56.0f / 3.0f) * s4 * fmaf(q, fmaf(35.0f, q, -4.0f), -1.0f);
+  }
 }
 
 __device__ __forceinline__ float r2_of(float dx, float dy, float dz) {

@@ -96,7 +96,7 @@ __device__ __forceinline__ void dens_load(DensOp::I& I, const DensArgs& a, float
   const float4 p = a.pos[k];
   const float4 v = a.vel[k];
   I.x = p.x; I.y = p.y; I.z = p.z;
-  dens_set_h(I, a.h[k], a.ph.kg, Lmax);
+  dens_set_h(I, a.h[k], a.ph.kg, a.ph.knorm, Lmax);
   I.vx = v.x; I.vy = v.y; I.vz = v.z;
   I.ns = I.nc = I.rs = I.rc = I.dn = I.dr = I.div = I.cx = I.cy = I.cz = 0.0f;
   I.count = 0;
@@ -133,7 +133,7 @@ __device__ __forceinline__ void number_walk(const DensOp& op, const DensOp::I& I
           const float invr = r2 > 0.0f ? rsqrtf(r2) : 0.0f;
           const float r = r2 * invr;
           float wq, dwq;
-          spline(r * I.invH, wq, dwq);
+          kshape(op.kernel, r * I.invH, wq, dwq);
           const float W = I.c3 * wq;
           if (op.compensated) two_sum_acc(ns, nc, W);
           else ns += W;
@@ -224,7 +224,7 @@ __device__ __forceinline__ void dens_item(const DensArgs& a, const DensOp& op, c
         float h1;
         const float h0 = I.h;
         if (newton_step(h0, ns, nc, dn, lo, hi, hcap, cap_flag, a.ph, iter == a.ph.max_iter - 1, h1, flag)) {
-          dens_set_h(I, h1, a.ph.kg, Lmax);
+          dens_set_h(I, h1, a.ph.kg, a.ph.knorm, Lmax);
           if (fabsf(fmaf(ns + nc, h0 * h0 * h0, -e3)) < pred * e3 && iter + 2 < a.ph.max_iter) {
             done = true;
             prov = true;
@@ -300,11 +300,12 @@ __device__ __forceinline__ void dens_item(const DensArgs& a, const DensOp& op, c
   }
 }
 
+// The loop kernels are instantiated per kernel shape K (kKernelCubic,
+// kKernelWendlandC2, kKernelWendlandC4), so the shape is fixed at compile time.
+template <int K>
 __global__ void __launch_bounds__(kLoopThreads, 5) k_density(DensArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const unsigned lane = lane_id();
-  const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
   const Grid g = *a.grid;
   const float Lmax = fmaxf(g.L[0], fmaxf(g.L[1], g.L[2]));
   WarpSmem& w = warp_smem(smem);
@@ -396,6 +397,8 @@ __global__ void __launch_bounds__(kLoopThreads, 5) k_density(DensArgs a) {
   op.vel = a.vel;
   op.L[0] = g.L[0]; op.L[1] = g.L[1]; op.L[2] = g.L[2];
   op.kg = a.ph.kg;
+  op.kernel = K;
+  op.knorm = a.ph.knorm;
   op.compensated = a.ph.compensated;
   unsigned ninter = 0, nhiter = 0, ncand = 0;
   const int max_pass = a.single_pass ? 1 : a.ph.max_iter;
@@ -513,7 +516,7 @@ __device__ __forceinline__ void grad_item(const LoopArgs& a, const GradOp& op, c
   I.H2lo = H * H - b;
   I.H2hi = H * H + b;
   I.invH = 1.0f / H;
-  I.c4 = (8.0f / kPi) * I.invH * I.invH * I.invH * I.invH;
+  I.c4 = a.ph.knorm * I.invH * I.invH * I.invH * I.invH;
   I.vx = v.x; I.vy = v.y; I.vz = v.z;
   I.c = gi.w;
   I.u = a.gb[k].w;
@@ -533,6 +536,7 @@ __device__ __forceinline__ void grad_item(const LoopArgs& a, const GradOp& op, c
   }
 }
 
+template <int K>
 __global__ void __launch_bounds__(kLoopThreads, 5) k_gradient(LoopArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const unsigned lane = lane_id();
@@ -543,6 +547,8 @@ __global__ void __launch_bounds__(kLoopThreads, 5) k_gradient(LoopArgs a) {
   op.pos = a.pos; op.vel = a.vel; op.ga = a.ga; op.gb = a.gb;
   op.L[0] = g.L[0]; op.L[1] = g.L[1]; op.L[2] = g.L[2];
   op.kg = a.ph.kg;
+  op.kernel = K;
+  op.knorm = a.ph.knorm;
   op.beta = a.ph.beta_v;
   const int n_items = a.ctr[0];
   unsigned ninter = 0, ncand = 0;
@@ -581,7 +587,7 @@ __device__ __forceinline__ void force_item(const LoopArgs& a,
   I.H2lo = H * H - b;
   I.H2hi = H * H + b;
   I.invH = 1.0f / H;
-  I.c4 = (8.0f / kPi) * I.invH * I.invH * I.invH * I.invH;
+  I.c4 = a.ph.knorm * I.invH * I.invH * I.invH * I.invH;
   I.vx = v.x; I.vy = v.y; I.vz = v.z;
   I.A = gi.x; I.f = gi.y; I.rho = gi.z; I.c = gi.w;
   I.B = bi.x; I.av = bi.y; I.acP = bi.z; I.u = bi.w;
@@ -635,7 +641,7 @@ __device__ __forceinline__ void force_item(const LoopArgs& a,
   }
 }
 
-template <bool kGrad>
+template <bool kGrad, int K>
 __device__ __forceinline__ void force_kernel_body(const LoopArgs& a) {
   using Op = typename std::conditional<kGrad, GradForceOp, ForceOp>::type;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -648,6 +654,8 @@ __device__ __forceinline__ void force_kernel_body(const LoopArgs& a) {
   op.L[0] = g.L[0]; op.L[1] = g.L[1]; op.L[2] = g.L[2];
   op.Lmax = fmaxf(g.L[0], fmaxf(g.L[1], g.L[2]));
   op.kg = a.ph.kg;
+  op.kernel = K;
+  op.knorm = a.ph.knorm;
   op.beta = a.ph.beta_v;
   op.gm1 = a.ph.gamma_eos - 1.0f;
   op.compensated = a.ph.compensated;
@@ -690,10 +698,12 @@ __device__ __forceinline__ void force_kernel_body(const LoopArgs& a) {
   }
 }
 
-__global__ void __launch_bounds__(kLoopThreads, 4) k_force(LoopArgs a) { force_kernel_body<false>(a); }
+template <int K>
+__global__ void __launch_bounds__(kLoopThreads, 4) k_force(LoopArgs a) { force_kernel_body<false, K>(a); }
 
 // Gradient (Eqs. 10-11, Laplacian of u) and force in one pass over the pairs.
-__global__ void __launch_bounds__(kLoopThreads, 4) k_grad_force(LoopArgs a) { force_kernel_body<true>(a); }
+template <int K>
+__global__ void __launch_bounds__(kLoopThreads, 4) k_grad_force(LoopArgs a) { force_kernel_body<true, K>(a); }
 
 // One warp per quantity; lane l sums blocks l, l+32, ... and the warp then
 // combines the lanes in a fixed order, so the result does not depend on timing.
@@ -715,14 +725,40 @@ static int persistent_blocks(Ctx* c, const void* kern) {
   return nb < c->red_blocks ? nb : c->red_blocks;
 }
 
+// The instantiation of each loop kernel for kernel shape `kind`.
+static const void* density_kernel(int kind) {
+  return kind == kKernelWendlandC2 ? (const void*)k_density<kKernelWendlandC2>
+         : kind == kKernelWendlandC4 ? (const void*)k_density<kKernelWendlandC4>
+                                     : (const void*)k_density<kKernelCubic>;
+}
+static const void* gradient_kernel(int kind) {
+  return kind == kKernelWendlandC2 ? (const void*)k_gradient<kKernelWendlandC2>
+         : kind == kKernelWendlandC4 ? (const void*)k_gradient<kKernelWendlandC4>
+                                     : (const void*)k_gradient<kKernelCubic>;
+}
+static const void* force_kernel(int kind) {
+  return kind == kKernelWendlandC2 ? (const void*)k_force<kKernelWendlandC2>
+         : kind == kKernelWendlandC4 ? (const void*)k_force<kKernelWendlandC4>
+                                     : (const void*)k_force<kKernelCubic>;
+}
+static const void* grad_force_kernel(int kind) {
+  return kind == kKernelWendlandC2 ? (const void*)k_grad_force<kKernelWendlandC2>
+         : kind == kKernelWendlandC4 ? (const void*)k_grad_force<kKernelWendlandC4>
+                                     : (const void*)k_grad_force<kKernelCubic>;
+}
+
 static bool g_attr_done = false;
 static void ensure_attrs() {
   if (g_attr_done) return;
-  cudaFuncSetAttribute(k_density, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLoopSmemBytes);
-  cudaFuncSetAttribute(k_gradient, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLoopSmemBytes);
-  cudaFuncSetAttribute(k_force, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLoopSmemBytes);
-  cudaFuncSetAttribute(k_grad_force, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLoopSmemBytes);
+  for (int kind = kKernelCubic; kind <= kKernelWendlandC4; ++kind)
+    for (const void* f : {density_kernel(kind), gradient_kernel(kind), force_kernel(kind), grad_force_kernel(kind)})
+      cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLoopSmemBytes);
   g_attr_done = true;
+}
+
+static cudaError_t launch_loop(const void* f, int nblk, LoopArgs& a, cudaStream_t s) {
+  void* args[] = {&a};
+  return cudaLaunchKernel(f, dim3(nblk), dim3(kLoopThreads), args, kLoopSmemBytes, s);
 }
 
 void reduce_partials(Ctx* c, int nblocks, double* out, cudaStream_t s) {
@@ -733,7 +769,8 @@ void reduce_partials(Ctx* c, int nblocks, double* out, cudaStream_t s) {
 int density_impl(Ctx* c, const float4* pos_in, const float4* vel_in, const uint8_t* active, float* h_out,
                  float4* rho4, float4* cd, uint32_t* ngb, cudaStream_t s) {
   ensure_attrs();
-  const int nblk = persistent_blocks(c, (const void*)k_density);
+  const void* kern = density_kernel(c->phys.kernel);
+  const int nblk = persistent_blocks(c, kern);
   cudaMemsetAsync(c->d_counters, 0, sizeof(int) * (size_t)(kCtrPerPass * (c->max_passes + 2) + 2), s);
   DensArgs a;
   a.grid = c->d_grid;
@@ -775,8 +812,7 @@ int density_impl(Ctx* c, const float4* pos_in, const float4* vel_in, const uint8
   a.item_nl = c->d_nlist ? c->d_item_nl : nullptr;
   if (c->d_nl_ctr) cudaMemsetAsync(c->d_nl_ctr, 0, sizeof(unsigned long long), s);
   void* args[] = {&a};
-  cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_density, dim3(nblk), dim3(kLoopThreads), args,
-                                              kLoopSmemBytes, s);
+  cudaError_t e = cudaLaunchCooperativeKernel(kern, dim3(nblk), dim3(kLoopThreads), args, kLoopSmemBytes, s);
   c->launches += 2;
   c->all_active = active == nullptr;
   c->nl_lmax = a.item_nl ? c->tuning.max_lanes_per_particle : 0;  // lists follow this lane layout
@@ -821,23 +857,25 @@ static LoopArgs loop_args(Ctx* c, int* ticket, void* out) {
 
 int gradient_impl(Ctx* c, float2* out, cudaStream_t s) {
   ensure_attrs();
-  const int nblk = persistent_blocks(c, (const void*)k_gradient);
+  const void* kern = gradient_kernel(c->phys.kernel);
+  const int nblk = persistent_blocks(c, kern);
   int* ticket = c->d_counters + kCtrPerPass * (c->max_passes + 1) + 0;
   cudaMemsetAsync(ticket, 0, sizeof(int), s);
   LoopArgs a = loop_args(c, ticket, out);
-  k_gradient<<<nblk, kLoopThreads, kLoopSmemBytes, s>>>(a);
+  const cudaError_t e = launch_loop(kern, nblk, a, s);
   c->launches += 2;
-  return cudaGetLastError() == cudaSuccess ? SWIFT_GPU_OK : SWIFT_GPU_ERR_CUDA;
+  return e == cudaSuccess ? SWIFT_GPU_OK : SWIFT_GPU_ERR_CUDA;
 }
 
 int force_impl(Ctx* c, float4* out, float* dhdt, double* reductions, cudaStream_t s) {
   ensure_attrs();
-  const int nblk = persistent_blocks(c, (const void*)k_force);
+  const void* kern = force_kernel(c->phys.kernel);
+  const int nblk = persistent_blocks(c, kern);
   int* ticket = c->d_counters + kCtrPerPass * (c->max_passes + 1) + 1;
   cudaMemsetAsync(ticket, 0, sizeof(int), s);
   LoopArgs a = loop_args(c, ticket, out);
   a.dhdt = dhdt;
-  k_force<<<nblk, kLoopThreads, kLoopSmemBytes, s>>>(a);
+  if (launch_loop(kern, nblk, a, s) != cudaSuccess) return SWIFT_GPU_ERR_CUDA;
   c->launches += 2;
   if (reductions) {
     k_reduce_partials<<<1, 256, 0, s>>>(c->d_red_partial, nblk, reductions);
@@ -848,13 +886,14 @@ int force_impl(Ctx* c, float4* out, float* dhdt, double* reductions, cudaStream_
 
 int grad_force_impl(Ctx* c, float2* grad_out, float4* out, float* dhdt, double* reductions, cudaStream_t s) {
   ensure_attrs();
-  const int nblk = persistent_blocks(c, (const void*)k_grad_force);
+  const void* kern = grad_force_kernel(c->phys.kernel);
+  const int nblk = persistent_blocks(c, kern);
   int* ticket = c->d_counters + kCtrPerPass * (c->max_passes + 1) + 1;
   cudaMemsetAsync(ticket, 0, sizeof(int), s);
   LoopArgs a = loop_args(c, ticket, out);
   a.out2 = grad_out;
   a.dhdt = dhdt;
-  k_grad_force<<<nblk, kLoopThreads, kLoopSmemBytes, s>>>(a);
+  if (launch_loop(kern, nblk, a, s) != cudaSuccess) return SWIFT_GPU_ERR_CUDA;
   c->launches += 2;
   if (reductions) {
     k_reduce_partials<<<1, 256, 0, s>>>(c->d_red_partial, nblk, reductions);

@@ -27,6 +27,8 @@ struct DensOp {
   float L[3];
   float kg;
   int compensated;
+  int kernel;
+  float knorm;
 
   __device__ __forceinline__ float stage_w(float) const { return 0.0f; }
   __device__ __forceinline__ bool candidate(const I& i, float r2, float) const { return r2 < i.H2hi; }
@@ -44,7 +46,7 @@ struct DensOp {
     const float invr = r2 > 0.0f ? rsqrtf(r2) : 0.0f;
     const float r = r2 * invr;
     float w, dw;
-    spline(r * i.invH, w, dw);
+    kshape(kernel, r * i.invH, w, dw);
     const float W = i.c3 * w;
     const float dW = i.c4 * dw;
     const float mj = vj.w;
@@ -68,14 +70,14 @@ struct DensOp {
   }
 };
 
-__device__ __forceinline__ void dens_set_h(DensOp::I& I, float h, float kg, float Lmax) {
+__device__ __forceinline__ void dens_set_h(DensOp::I& I, float h, float kg, float knorm, float Lmax) {
   I.h = h;
   const float H = kg * h;
   const float b = band_of(H, Lmax);
   I.H2lo = H * H - b;
   I.H2hi = H * H + b;
   I.invH = 1.0f / H;
-  I.c3 = (8.0f / kPi) * I.invH * I.invH * I.invH;
+  I.c3 = knorm * I.invH * I.invH * I.invH;
   I.c4 = I.c3 * I.invH;
 }
 
@@ -155,6 +157,8 @@ struct GradOp {
   const float4* __restrict__ gb;
   float L[3];
   float kg, beta;
+  int kernel;
+  float knorm;
 
   __device__ __forceinline__ float stage_w(float) const { return 0.0f; }
   __device__ __forceinline__ bool candidate(const I& i, float r2, float) const { return r2 < i.H2hi; }
@@ -174,7 +178,7 @@ struct GradOp {
     const float uj = gb[j].w;
     const float invr = rsqrtf(r2);
     const float r = r2 * invr;
-    const float dW = i.c4 * dspline(r * i.invH);
+    const float dW = i.c4 * dkshape(kernel, r * i.invH);
     const float dvx = i.vx - vj.x, dvy = i.vy - vj.y, dvz = i.vz - vj.z;
     const float vr = fmaf(dvz, dz, fmaf(dvy, dy, dvx * dx)) * invr;
     const float mu = fminf(vr, 0.0f);
@@ -200,6 +204,8 @@ struct ForceOp {
   float L[3];
   float kg, beta, gm1, Lmax;
   int compensated;
+  int kernel;
+  float knorm;
 
   // staged w: the j support squared plus its guard band
   __device__ __forceinline__ float stage_w(float hj) const {
@@ -229,10 +235,10 @@ struct ForceOp {
     const float invr = rsqrtf(r2);
     const float r = r2 * invr;
     const float ex = dx * invr, ey = dy * invr, ez = dz * invr;
-    const float dWi = i.c4 * dspline(r * i.invH);
+    const float dWi = i.c4 * dkshape(kernel, r * i.invH);
     const float invHj = __fdividef(1.0f, Hj);
     const float ih2 = invHj * invHj;
-    const float dWj = ((8.0f / kPi) * ih2 * ih2) * dspline(r * invHj);
+    const float dWj = (knorm * ih2 * ih2) * dkshape(kernel, r * invHj);
     const float dvx = i.vx - vj.x, dvy = i.vy - vj.y, dvz = i.vz - vj.z;
     const float vr = fmaf(dvz, ez, fmaf(dvy, ey, dvx * ex));
     const float mj = vj.w;
@@ -328,7 +334,7 @@ struct GradForceOp : ForceOp {
     const float invr = rsqrtf(r2);
     const float r = r2 * invr;
     const float ex = dx * invr, ey = dy * invr, ez = dz * invr;
-    const float dWi = i.c4 * dspline(r * i.invH);
+    const float dWi = i.c4 * dkshape(kernel, r * i.invH);
     const float dvx = i.vx - vj.x, dvy = i.vy - vj.y, dvz = i.vz - vj.z;
     if (in_i) {  // gradient loop (as GradOp)
       const float vrg = fmaf(dvz, dz, fmaf(dvy, dy, dvx * dx)) * invr;
@@ -338,7 +344,7 @@ struct GradForceOp : ForceOp {
     }
     const float invHj = __fdividef(1.0f, Hj);
     const float ih2 = invHj * invHj;
-    const float dWj = ((8.0f / kPi) * ih2 * ih2) * dspline(r * invHj);
+    const float dWj = (knorm * ih2 * ih2) * dkshape(kernel, r * invHj);
     const float vr = fmaf(dvz, ez, fmaf(dvy, ey, dvx * ex));
     const float mj = vj.w;
     const float fsum = fmaf(i.f, dWi, aj.y * dWj);

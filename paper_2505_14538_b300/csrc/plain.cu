@@ -36,7 +36,8 @@ struct PlainArgs {
   const uint8_t* need;  // particles still computed in this pass
   Acc acc;
   float Lmax;
-  float kg;
+  float kg, knorm;
+  int kernel;
 };
 
 struct Task {
@@ -79,7 +80,7 @@ __global__ void k_plain_dens(PlainArgs a, DensOp op, Task t) {
     const float4 p = a.pos[k];
     const float4 v = a.vel[k];
     I.x = p.x; I.y = p.y; I.z = p.z;
-    dens_set_h(I, a.h[k], a.kg, a.Lmax);
+    dens_set_h(I, a.h[k], a.kg, a.knorm, a.Lmax);
     I.vx = v.x; I.vy = v.y; I.vz = v.z;
     I.k = k;
     dens_acc_load(I, a.acc, k);
@@ -197,7 +198,7 @@ __global__ void k_plain_grad(PlainArgs a, GradOp op, Task t) {
     I.H2lo = H * H - b;
     I.H2hi = H * H + b;
     I.invH = 1.0f / H;
-    I.c4 = (8.0f / kPi) * I.invH * I.invH * I.invH * I.invH;
+    I.c4 = a.knorm * I.invH * I.invH * I.invH * I.invH;
     I.vx = v.x; I.vy = v.y; I.vz = v.z;
     I.c = a.ga[k].w;
     I.u = a.gb[k].w;
@@ -231,7 +232,7 @@ __global__ void k_plain_force(PlainArgs a, ForceOp op, Task t) {
     I.H2lo = H * H - b;
     I.H2hi = H * H + b;
     I.invH = 1.0f / H;
-    I.c4 = (8.0f / kPi) * I.invH * I.invH * I.invH * I.invH;
+    I.c4 = a.knorm * I.invH * I.invH * I.invH * I.invH;
     I.vx = v.x; I.vy = v.y; I.vz = v.z;
     I.A = gi.x; I.f = gi.y; I.rho = gi.z; I.c = gi.w;
     I.B = bi.x; I.av = bi.y; I.acP = bi.z; I.u = bi.w;
@@ -364,6 +365,8 @@ static PlainArgs plain_args(Ctx* c, float Lmax) {
   a.acc = Acc{reinterpret_cast<float*>(c->d_scratch4[0]), (int)c->n_max};
   a.Lmax = Lmax;
   a.kg = c->phys.kg;
+  a.knorm = c->phys.knorm;
+  a.kernel = c->phys.kernel;
   return a;
 }
 
@@ -416,6 +419,8 @@ int plain_density_impl(Ctx* c, const float4* pos_in, const float4* vel_in, const
   op.vel = c->d_vel;
   op.L[0] = c->phys.L[0]; op.L[1] = c->phys.L[1]; op.L[2] = c->phys.L[2];
   op.kg = c->phys.kg;
+  op.kernel = c->phys.kernel;
+  op.knorm = c->phys.knorm;
   op.compensated = c->phys.compensated;
   PlainArgs a = plain_args(c, lmax_of(c->phys));
   a.acc = st.acc;
@@ -456,6 +461,8 @@ int plain_gradient_impl(Ctx* c, float2* out, cudaStream_t s) {
   op.pos = c->d_pos; op.vel = c->d_vel; op.ga = c->d_ga; op.gb = c->d_gb;
   op.L[0] = c->phys.L[0]; op.L[1] = c->phys.L[1]; op.L[2] = c->phys.L[2];
   op.kg = c->phys.kg;
+  op.kernel = c->phys.kernel;
+  op.knorm = c->phys.knorm;
   op.beta = c->phys.beta_v;
   PlainArgs a = plain_args(c, lmax_of(c->phys));
   a.acc = Acc{reinterpret_cast<float*>(c->d_scratch4[0]), (int)c->n_max};
@@ -477,6 +484,8 @@ int plain_force_impl(Ctx* c, float4* out, float* dhdt, double* reductions, cudaS
   op.L[0] = c->phys.L[0]; op.L[1] = c->phys.L[1]; op.L[2] = c->phys.L[2];
   op.Lmax = lmax_of(c->phys);
   op.kg = c->phys.kg;
+  op.kernel = c->phys.kernel;
+  op.knorm = c->phys.knorm;
   op.beta = c->phys.beta_v;
   op.gm1 = c->phys.gamma_eos - 1.0f;
   op.compensated = c->phys.compensated;

@@ -52,8 +52,14 @@ def _stream(stream=None):
 
 def make_params(**kw) -> _lib.Params:
     """Library defaults with keyword overrides (box, gamma_eos, eta, kernel_gamma, alpha_v,
-    beta_v, alpha_c, h_tol, max_iter, h_max, cell_margin, flags)."""
+    beta_v, alpha_c, h_tol, max_iter, h_max, cell_margin, flags, leaf_max, leaf_margin, kernel).
+
+    ``kernel`` (0 cubic spline, 1 Wendland C2, 2 Wendland C4) also sets
+    kernel_gamma to the shape's own H/h unless kernel_gamma is given.
+    """
     p = _lib.default_params()
+    if "kernel" in kw and "kernel_gamma" not in kw:  # (an unknown kernel is left to the library to refuse)
+        kw = dict(kw, kernel_gamma=_lib.KERNEL_GAMMAS.get(int(kw["kernel"]), p.kernel_gamma))
     for k, v in kw.items():
         if k == "box":
             p.box = (ctypes.c_float * 3)(*[float(b) for b in v])
@@ -95,7 +101,8 @@ class Context:
         p = self.params
         return dict(box=tuple(p.box), gamma_eos=p.gamma_eos, eta=p.eta, kernel_gamma=p.kernel_gamma,
                     alpha_v=p.alpha_v, beta_v=p.beta_v, alpha_c=p.alpha_c, h_tol=p.h_tol, max_iter=p.max_iter,
-                    h_max=p.h_max, cell_margin=p.cell_margin, flags=p.flags)
+                    h_max=p.h_max, cell_margin=p.cell_margin, flags=p.flags, leaf_max=p.leaf_max,
+                    leaf_margin=p.leaf_margin, kernel=p.kernel)
 
     # ------------------------------------------------------------ calls
     def build_cells(self, pos_h: torch.Tensor, min_cell_width: float = 0.0, stream=None):

@@ -38,7 +38,7 @@ def oracle_params(O, ctx_params, **kw):
     p = O.Params(box=tuple(float(b) for b in ctx_params.box), gamma_eos=float(ctx_params.gamma_eos),
                  eta=float(ctx_params.eta), kernel_gamma=float(ctx_params.kernel_gamma),
                  alpha_v=float(ctx_params.alpha_v), beta_v=float(ctx_params.beta_v),
-                 alpha_c=float(ctx_params.alpha_c))
+                 alpha_c=float(ctx_params.alpha_c), kernel=int(ctx_params.kernel))
     for k, v in kw.items():
         setattr(p, k, v)
     return p
