@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-clustered", action="store_true", help="skip the clustered (Plummer) active-step comparison")
     ap.add_argument("--no-gresho", action="store_true", help="skip the integrated Gresho-Chan vortex steps")
+    ap.add_argument("--no-kernel-shapes", action="store_true", help="skip the Wendland-kernel runs of the workload")
     ap.add_argument("--autotune", action="store_true", help="run the library autotuner before timing")
     return ap.parse_args()
 
@@ -368,6 +369,8 @@ def run_ours(args, rank, world, pg):
         res["clustered"] = run_clustered(dev)
     if not args.no_gresho and rank == 0:
         res["gresho"] = run_gresho(dev)
+    if not args.no_kernel_shapes and rank == 0:
+        res["kernel_shapes"] = run_kernel_shapes(dev, d, peak_max)
     if rank == 0 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(d, ctx)
     return res
@@ -506,6 +509,80 @@ def run_clustered(dev, steps=5):
         del ctx
     res["adaptive_speedup"] = res["uniform"]["ms_per_step"] / res["adaptive"]["ms_per_step"]
     return res
+
+
+def run_kernel_shapes(dev, d, peak_tflops, steps=30):
+    """The benchmark step on the same workload with each kernel shape (cubic spline, Wendland C2, C4).
+
+    Same eta, so the Wendland kernels (larger H/h) have about 57 and 85
+    neighbours against 48. Per shape: the graph-replayed step, the loop
+    kernels' times from direct calls, and their algorithmic FP32 rate from the
+    oracle's per-interaction flop counts of that shape.
+    """
+    import numpy as np
+    import torch
+
+    from paper_2505_14538_b300 import sph
+    with open(os.path.join(ROOT, "profiles", "flops_per_interaction.json")) as f:
+        fl = json.load(f)
+    counts = {0: [fl[k]["mean"] for k in ("density", "gradient", "force", "h_iteration")],
+              1: [fl["wendland_c2"][k] for k in ("density", "gradient", "force", "h_iteration")],
+              2: [fl["wendland_c4"][k] for k in ("density", "gradient", "force", "h_iteration")]}
+    n = len(d["pos"])
+    pos_h = torch.from_numpy(np.concatenate([d["pos"], d["h"][:, None]], 1).astype(np.float32)).to(dev)
+    vel_m = torch.from_numpy(np.concatenate([d["vel"], d["m"][:, None]], 1).astype(np.float32)).to(dev)
+    u = torch.from_numpy(d["u"].astype(np.float32)).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    out = {}
+    for kind, name in ((0, "cubic"), (1, "wendland_c2"), (2, "wendland_c4")):
+        ctx = sph.Context(n, kernel=kind)
+        first = ctx.step(pos_h, vel_m, u, check=True)
+        torch.cuda.synchronize()
+        width = max(ctx.info()["cell_width"]) if first["status"][0] != 0 else 0.0
+        graph = sph.StepGraph(ctx, pos_h, vel_m, u, width)
+        o = graph.out
+        for _ in range(3):
+            graph.replay()
+        torch.cuda.synchronize()
+        i0 = ctx.info()
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(steps)]
+        for k in range(steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            graph.replay()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        i1 = ctx.info()
+        ms = sum(e[0].elapsed_time(e[1]) for e in ev) / steps
+        inter = [x / steps for x in step_interactions(i0, i1)]
+        hiter = (i1["h_iteration_pairs"] - i0["h_iteration_pairs"]) / steps
+        dens_full = (i1["interactions"][0] - i0["interactions"][0]) / steps
+        lev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(10)]
+        for k in range(10):
+            flush.zero_()
+            ctx.build_cells(pos_h, width)
+            lev[k][0].record(stream)
+            ctx.density(pos_h, vel_m, h_out=o["h"], rho4=o["rho4"], curl_div=o["curl_div"], ngb_count=o["ngb"])
+            lev[k][1].record(stream)
+            ctx.gradient_force(u, vsig_lapu=o["vsig_lapu"], accel_dudt=o["accel_dudt"], dh_dt=o["dh_dt"],
+                               reductions=o["reductions"])
+            lev[k][2].record(stream)
+        torch.cuda.synchronize()
+        dms = sum(e[0].elapsed_time(e[1]) for e in lev) / 10
+        gms = sum(e[1].elapsed_time(e[2]) for e in lev) / 10
+        c = counts[kind]
+        fd = dens_full * c[0] + hiter * c[3]
+        fg = inter[1] * c[1] + inter[2] * c[2]
+        out[name] = {"ms_per_step": ms, "interactions_per_step": sum(inter), "value": sum(inter) / (ms * 1e-3),
+                     "mean_neighbours": float(o["ngb"].float().mean()), "nc": i1["nc"],
+                     "k_density_ms": dms, "k_grad_force_ms": gms,
+                     "k_density_frac": fd / (dms * 1e-3) / 1e12 / peak_tflops,
+                     "k_grad_force_frac": fg / (gms * 1e-3) / 1e12 / peak_tflops,
+                     "flops_per_interaction": dict(zip(("density", "gradient", "force", "h_iteration"), c)),
+                     "status": list(ctx.sync_status())}
+        del graph, ctx
+    return out
 
 
 # algorithmic HBM bytes per particle of the integration kernels (loads + stores of their arrays)

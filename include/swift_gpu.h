@@ -236,12 +236,14 @@ int swift_gpu_gradient_force(swift_gpu_ctx* ctx, const float* u, const float* al
 int swift_gpu_force_backward(swift_gpu_ctx* ctx, const float* grad_accel_dudt, float* grad_x, float* grad_v,
                              float* grad_u, int h_mode, void* stream);
 
-/* Wait for the stream of the last call and read the device status word:
+/* Wait for all work on the device (the calls may have been captured in a CUDA
+ * graph and replayed on any stream) and read the device status word:
  * *status = first device-side error code (0 = none), *detail = its count or
  * index. Clears the status word. Blocking. */
 int swift_gpu_sync_status(swift_gpu_ctx* ctx, int* status, int64_t* detail);
 
-/* Fill *info (blocking: synchronises the context's last stream). */
+/* Fill *info (blocking: waits for all work on the device first, as
+ * swift_gpu_sync_status does). */
 int swift_gpu_get_info(swift_gpu_ctx* ctx, swift_gpu_info* info);
 
 /* Copy the cell id of every particle (caller order) and the sort permutation

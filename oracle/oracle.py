@@ -253,10 +253,12 @@ def interpolate(p: Params, x, m, h, rho, Q):
     return out
 
 
-def count_flops(loop: int, q: float = 0.75, approaching: bool = True):
+def count_flops(loop: int, q: float = 0.75, approaching: bool = True, kind: int = CUBIC):
     """Ops of one interaction of loop 0 density / 1 gradient / 2 force / 3 h-iteration step (Eqs. 5-6)."""
     out = (ctypes.c_longlong * 5)()
-    lib().oracle_count_flops(ctypes.c_int(loop), ctypes.c_double(q), ctypes.c_int(int(approaching)), out)
+    rc = lib().oracle_count_flops(ctypes.c_int(loop), ctypes.c_double(q), ctypes.c_int(int(approaching)),
+                                  ctypes.c_int(kind), out)
+    assert rc == 0
     return dict(zip(("add", "mul", "div", "sqrt", "cmp"), list(out)))
 
 

@@ -727,10 +727,11 @@ int oracle_interpolate(const oracle_params* p, int64_t n, const double* x, const
  * mu < 0 branch. out[0..4] = add, mul, div, sqrt, cmp. The neighbour test
  * itself (3 sub, 3 mul, 2 add, 1 cmp) is not included.
  */
-int oracle_count_flops(int loop, double q, int approaching, long long* out) {
+int oracle_count_flops(int loop, double q, int approaching, int kind, long long* out) {
   OpTally t{0, 0, 0, 0, 0};
   double h = 0.02, kg = 1.825742;
-  KernelI<Cnt> k = kernel_consts<Cnt>(h, kg, 0);
+  if (kind < 0 || kind > 2) return -1;
+  KernelI<Cnt> k = kernel_consts<Cnt>(h, kg, kind);
   double r = q * kg * h;
   Cnt dx(r), dy(0.0), dz(0.0), r2(r * r);
   Cnt dvx(approaching ? -0.3 : 0.3), dvy(0.1), dvz(0.2);
@@ -748,7 +749,7 @@ int oracle_count_flops(int loop, double q, int approaching, long long* out) {
   } else {
     ForceI<Cnt> I, J;
     I.k = k;
-    J.k = kernel_consts<Cnt>(h * 1.05, kg, 0);
+    J.k = kernel_consts<Cnt>(h * 1.05, kg, kind);
     I.f = J.f = Cnt(1.0);
     I.A = J.A = Cnt(1.0);
     I.rho = J.rho = Cnt(1.0);

@@ -4,7 +4,9 @@ The counts come from the oracle's own pair functions instantiated on an
 op-counting scalar (add/sub/mul/div/sqrt = 1 flop each; comparisons are not
 flops). A hit falls in the inner spline branch (q < 1/2) with probability
 1/8 (hits are uniform in the support volume), so each loop's figure is
-1/8 inner + 7/8 outer. The neighbour test itself is not counted.
+1/8 inner + 7/8 outer. The Wendland kernels have one branch; their counts
+are written under "wendland_c2" and "wendland_c4". The neighbour test itself
+is not counted.
 """
 import json
 import os
@@ -24,7 +26,12 @@ def main():
             c = O.count_flops(loop, q, True)
             tot[q] = c["add"] + c["mul"] + c["div"] + c["sqrt"]
         out[name] = {"inner": tot[0.3], "outer": tot[0.75], "mean": 0.125 * tot[0.3] + 0.875 * tot[0.75]}
-    out["_how"] = ("oracle pair functions on an op-counting scalar; mean = 1/8 inner-branch + 7/8 "
+    for kind, key in ((O.WENDLAND_C2, "wendland_c2"), (O.WENDLAND_C4, "wendland_c4")):
+        out[key] = {}
+        for loop, name in ((0, "density"), (1, "gradient"), (2, "force"), (3, "h_iteration")):
+            c = O.count_flops(loop, 0.5, True, kind)
+            out[key][name] = c["add"] + c["mul"] + c["div"] + c["sqrt"]
+    out["_how"] = ("oracle pair functions on an op-counting scalar; cubic spline mean = 1/8 inner-branch + 7/8 "
                    "outer-branch count; written by oracle/write_flop_counts.py")
     path = os.path.join(os.path.dirname(HERE), "profiles", "flops_per_interaction.json")
     os.makedirs(os.path.dirname(path), exist_ok=True)

@@ -335,25 +335,25 @@ int swift_gpu_force_backward(swift_gpu_ctx* h, const float* grad_accel_dudt, flo
 int swift_gpu_sync_status(swift_gpu_ctx* h, int* status, int64_t* detail) {
   Ctx* c = from(h);
   if (!c) return SWIFT_GPU_ERR_ARG;
-  cudaStream_t s = c->last_stream;
-  cudaError_t e = cudaMemcpyAsync(c->h_status, c->d_status, sizeof(Status), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  // The whole device, not one stream: the calls may have been captured in a
+  // CUDA graph and replayed on a stream the library never saw.
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(c->h_status, c->d_status, sizeof(Status), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return SWIFT_GPU_ERR_CUDA;
   if (status) *status = c->h_status->code;
   if (detail) *detail = (int64_t)c->h_status->detail;
-  cudaMemsetAsync(c->d_status, 0, sizeof(Status), s);
-  return cudaStreamSynchronize(s) == cudaSuccess ? SWIFT_GPU_OK : SWIFT_GPU_ERR_CUDA;
+  return cudaMemset(c->d_status, 0, sizeof(Status)) == cudaSuccess && cudaDeviceSynchronize() == cudaSuccess
+             ? SWIFT_GPU_OK
+             : SWIFT_GPU_ERR_CUDA;
 }
 
 int swift_gpu_get_info(swift_gpu_ctx* h, swift_gpu_info* info) {
   Ctx* c = from(h);
   if (!c || !info) return SWIFT_GPU_ERR_ARG;
   Grid g;
-  cudaStream_t s = c->last_stream;
-  if (cudaMemcpyAsync(&g, c->d_grid, sizeof(Grid), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaMemcpyAsync(c->h_stats, c->d_stats, sizeof(unsigned long long) * kStatCount, cudaMemcpyDeviceToHost,
-                      s) != cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess)
+  if (cudaDeviceSynchronize() != cudaSuccess || cudaMemcpy(&g, c->d_grid, sizeof(Grid), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(c->h_stats, c->d_stats, sizeof(unsigned long long) * kStatCount, cudaMemcpyDeviceToHost) !=
+          cudaSuccess)
     return SWIFT_GPU_ERR_CUDA;
   memset(info, 0, sizeof(*info));
   info->n = c->n;

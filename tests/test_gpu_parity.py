@@ -278,6 +278,31 @@ def test_step_graph_replays_bit_identically(sph):
     assert g.launches_per_step > 5
 
 
+def test_info_and_status_wait_for_graph_replays(sph):
+    """After replays of a graph captured on another stream, info() and sync_status() see all of them."""
+    d = ics.sedov(32)
+    n = len(d["pos"])
+    pos_h, vel_m, ut = dev_arrays(d)
+    ctx = sph.Context(n)
+    g = sph.StepGraph(ctx, pos_h, vel_m, ut)
+    torch.cuda.synchronize()
+    i0 = ctx.info()
+    g.replay()
+    torch.cuda.synchronize()
+    i1 = ctx.info()
+    per = [i1["interactions"][j] - i0["interactions"][j] for j in range(3)]
+    assert per[1] > 0
+    for _ in range(5):
+        g.replay()
+    i2 = ctx.info()  # no host synchronisation before it
+    assert [i2["interactions"][j] - i1["interactions"][j] for j in range(3)] == [5 * x for x in per]
+    for _ in range(3):
+        g.replay()
+    assert ctx.sync_status() == (0, 0)
+    i3 = ctx.info()
+    assert i3["interactions"][1] - i2["interactions"][1] == 3 * per[1]
+
+
 @pytest.mark.parametrize("flags", [0, 8])
 def test_gradient_force_fused_equals_separate(sph, flags):
     """swift_gpu_gradient_force evaluates the pairs of gradient() then force(): v_sig bitwise (a max of the same
