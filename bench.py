@@ -618,6 +618,8 @@ def run_gresho(dev, n_side=128, steps=20, timed_direct=5):
     c = it.ctx
     for k in range(timed_direct):
         e = ev[k]
+        if k == timed_direct - 1:
+            torch.cuda.nvtx.range_push("gresho_step")  # marks one integrated step for profilers
         e[0].record(stream)
         c.kick_drift(it.tp, it.clock, it.pos_h, it.vel_m, it.u, it.accel_dudt, it.dh_dt, it.vel_pred, it.u_pred)
         e[1].record(stream)
@@ -633,6 +635,8 @@ def run_gresho(dev, n_side=128, steps=20, timed_direct=5):
         c.kick_finish(it.tp, it.clock, it.h, it.pos_h, it.vel_m, it.u, it.accel_dudt, it.vsig_lapu, it.alpha_v,
                       it.alpha_c)
         e[6].record(stream)
+        if k == timed_direct - 1:
+            torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     it.check_status()
     stage_ms = {names[j]: sum(ev[k][j].elapsed_time(ev[k][j + 1]) for k in range(timed_direct)) / timed_direct
