@@ -7,6 +7,12 @@ over an explicit list of interacting pairs, so that autograd gives the exact
 FP64 gradient of a loss of the outputs with respect to positions, velocities
 and internal energies at fixed smoothing lengths. The pair list is found by
 brute force over all pairs (O(N^2)), in FP64, with the oracle's predicate.
+
+``loss_and_grad_hsolved`` is the gradient when each h_i is the solution of
+the h iteration (Sec. 2.1.2), F_i(x, h_i) = n_i(x, h_i) - (eta/h_i)^3 = 0:
+by the implicit function theorem dh_i/dx = -(dF_i/dx) / (dF_i/dh_i), so
+dL/dx = dL/dx|_h - sum_i lambda_i dn_i/dx with lambda_i = (dL/dh_i|_x) / F'_i
+(n_i depends on h_i alone, so the Jacobian of F in h is diagonal).
 """
 from __future__ import annotations
 
@@ -139,3 +145,45 @@ def loss_and_grad(x, v, u, m, h, w, cw, box=(1.0, 1.0, 1.0), pairs=None, **kw):
     Lv = (torch.as_tensor(np.asarray(w, np.float64)) * a).sum() + (torch.as_tensor(np.asarray(cw, np.float64)) * du).sum()
     gx, gv, gu = torch.autograd.grad(Lv, (x, v, u))
     return float(Lv.detach()), gx.numpy(), gv.numpy(), gu.numpy(), a.detach().numpy(), du.detach().numpy()
+
+
+def number_density(x, h, pairs, box=(1.0, 1.0, 1.0), kernel_gamma=KERNEL_GAMMA, kernel=0):
+    """n_i = W(0, h_i) + sum over pairs with r < H_i of W(r_ij, h_i) (Eq. 5), differentiable in x and h."""
+    n = x.shape[0]
+    i = torch.as_tensor(pairs[0], dtype=torch.long)
+    j = torch.as_tensor(pairs[1], dtype=torch.long)
+    L = torch.as_tensor(box, dtype=torch.float64)
+    H = kernel_gamma * h
+    d = x[i] - x[j]
+    d = d - L * torch.round((d / L).detach())
+    r = torch.sqrt((d * d).sum(1))
+    q = r / H[i]
+    c3 = _norm(kernel) / H ** 3
+    inside = (q < 1.0).detach().to(torch.float64)
+    w = c3[i] * _w(q, kernel) * inside
+    return c3 * 1.0 + torch.zeros(n, dtype=torch.float64).index_add(0, i, w)
+
+
+def loss_and_grad_hsolved(x, v, u, m, h, w, cw, box=(1.0, 1.0, 1.0), eta=1.2348, **kw):
+    """(L, dL/dx, dL/dv, dL/du) with h = h(x) the root of the h iteration; h must be that root."""
+    kg = kw.get("kernel_gamma", KERNEL_GAMMA)
+    kernel = kw.get("kernel", 0)
+    xt = torch.tensor(np.asarray(x, np.float64), requires_grad=True)
+    vt = torch.tensor(np.asarray(v, np.float64), requires_grad=True)
+    ut = torch.tensor(np.asarray(u, np.float64), requires_grad=True)
+    ht = torch.tensor(np.asarray(h, np.float64), requires_grad=True)
+    pairs = pair_list(x, h, box, kg)
+    a, du, _ = forward(xt, vt, ut, m, ht, pairs, box, **kw)
+    Lv = (torch.as_tensor(np.asarray(w, np.float64)) * a).sum() + \
+        (torch.as_tensor(np.asarray(cw, np.float64)) * du).sum()
+    gx, gv, gu, gh = torch.autograd.grad(Lv, (xt, vt, ut, ht))
+    # F' = dn_i/dh_i + 3 eta^3 / h_i^4 (n_i depends on h_i only)
+    h2 = torch.tensor(np.asarray(h, np.float64), requires_grad=True)
+    nn = number_density(xt.detach(), h2, pairs, box, kg, kernel)
+    dn_dh = torch.autograd.grad(nn.sum(), h2)[0]
+    Fp = dn_dh + 3.0 * eta ** 3 / h2.detach() ** 4
+    lam = (gh / Fp).detach()
+    x2 = torch.tensor(np.asarray(x, np.float64), requires_grad=True)
+    nx = number_density(x2, torch.tensor(np.asarray(h, np.float64)), pairs, box, kg, kernel)
+    gx_ift = torch.autograd.grad((lam * nx).sum(), x2)[0]
+    return float(Lv.detach()), (gx - gx_ift).numpy(), gv.numpy(), gu.numpy(), gh.numpy(), lam.numpy()

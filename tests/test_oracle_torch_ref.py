@@ -83,3 +83,36 @@ def test_torch_forward_matches_oracle_wendland(O, kind):
     s = O.step(O.Params(kernel=kind, kernel_gamma=kg), x, v, m, u, h, solve=False)
     assert np.all(np.linalg.norm(a - s["accel"], axis=1) <= 1e-11 * s["s_a"])
     assert np.all(np.abs(du - s["dudt"]) <= 1e-11 * s["s_u"])
+
+
+def test_hsolved_gradient_matches_oracle_finite_differences(O):
+    """h = h(x) (the root of the h iteration): the IFT gradient against central differences of the C++
+    oracle's loss with h re-solved at every perturbed position (to 1e-13)."""
+    from oracle import torch_ref as T
+    x, v, u, m, h0, w, cw = _state(seed=3, n_side=7, jitter=0.3)
+    p = O.Params(h_tol=1e-14, max_iter=80, h_max=0.4)
+    h = O.solve_h(p, x, v, m, h0)["h"]
+    L, gx, gv, gu, gh, lam = T.loss_and_grad_hsolved(x, v, u, m, h, w, cw)
+    assert np.abs(gh).max() > 0 and np.abs(lam).max() > 0
+
+    def loss(xx, vv, uu):
+        s = O.step(p, xx, vv, m, uu, h)  # solve=True: h re-solved from h as the start
+        return float((w * s["accel"]).sum() + (cw * s["dudt"]).sum())
+
+    assert abs(loss(x, v, u) - L) < 1e-9 * abs(L) + 1e-12
+    rng = np.random.default_rng(9)
+    scale = np.abs(gx).max()
+    fixed_h = T.loss_and_grad(x, v, u, m, h, w, cw)[1]
+    moved = 0
+    for k in rng.choice(len(x), 6, replace=False):
+        for c in range(3):
+            fds = []
+            for delta in (2e-6, 1e-6):
+                xp, xm = x.copy(), x.copy()
+                xp[k, c] += delta
+                xm[k, c] -= delta
+                fds.append((loss(xp, v, u) - loss(xm, v, u)) / (2 * delta))
+            assert abs(fds[0] - fds[1]) < 1e-4 * scale  # smooth here (no support edge crossed)
+            assert abs(gx[k, c] - fds[1]) < 1e-5 * scale, (k, c, gx[k, c], fds[1])
+            moved += abs(gx[k, c] - fixed_h[k, c]) > 1e-3 * scale
+    assert moved > 0  # the h term matters at this tolerance
