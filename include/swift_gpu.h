@@ -224,8 +224,14 @@ int swift_gpu_gradient_force(swift_gpu_ctx* ctx, const float* u, const float* al
  * grad_accel_dudt[n] = float4 (dL/da_x, dL/da_y, dL/da_z, dL/d(du/dt)) for a
  * scalar loss L of the outputs of the last swift_gpu_force call, write
  * grad_x[n] (float4, w unused), grad_v[n] (float4, w unused), grad_u[n].
- * h_mode 0: h held at the values of the last density call (the only mode
- * built; 1, h = h(x) through the converged h equation, returns ERR_ARG).
+ * h_mode 0: h held at the values of the last density call.
+ * h_mode 1: each h_i is the root of the h iteration, F_i = n_i(x, h_i) -
+ * (eta/h_i)^3 = 0 (Sec. 2.1.2), so h moves with x: by the implicit function
+ * theorem grad_x gains -sum_i lambda_i dn_i/dx with lambda_i = (dL/dh_i at
+ * fixed x) / (dn_i/dh_i + 3 eta^3 / h_i^4); dL/dh comes from the same two
+ * passes and a third gather adds the term. Exact at the root: the density
+ * call should have converged (a tighter h_tol makes it closer); ERR_ARG with
+ * SWIFT_GPU_NO_H_ITER (h is then an input, not a root).
  * Two gather passes over the same neighbour scan as the forward loops: the
  * force pair terms are reversed in both orientations of every pair, the
  * ghost step is reversed per particle, and the adjoints of each particle's

@@ -1,6 +1,7 @@
 // backward.cu -- adjoint of the density + ghost + force loops (not in the
 // paper): for a loss L = sum_i w_i . a_i + c_i du_i/dt of the last force call,
-// the gradients dL/dx, dL/dv, dL/du at fixed smoothing lengths.
+// the gradients dL/dx, dL/dv, dL/du at fixed smoothing lengths (h_mode 0), or
+// with each h_i the root of the h iteration (h_mode 1, Sec. 2.1.2).
 //
 // Two gather passes over the same neighbour scan as the forward loops (no
 // atomics, no stored pair lists; the per-particle density sums of the
@@ -17,6 +18,14 @@
 //   k_dens_adj   for particle k and every pair in k's or j's density sums,
 //                the adjoints of rho, D, S, C of both particles are carried to
 //                dL/dx_k and dL/dv_k, and the totals go to caller order.
+// With h_mode 1 the same two passes also collect dL/dh_k at fixed x: through
+// dW(r, h_k) in the force pairs (both orientations), the 1/h_k of the
+// Balsara switch, and the h-derivatives of k's own sums rho, D, S, C. Since
+// F_k = n_k(x, h_k) - (eta/h_k)^3 = 0 defines h_k and n_k depends on h_k
+// alone, the implicit function theorem gives the extra term
+//   dL/dx_k -= sum_j (lambda_k dW(r,h_k)/dr + lambda_j dW(r,h_j)/dr) e_kj,
+//   lambda = (dL/dh) / F',  F' = dn/dh + 3 eta^3 / h^4,
+// gathered by a third pass, k_ift_adj.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -34,6 +43,7 @@ __device__ __forceinline__ WarpSmem& adj_smem(unsigned char* smem) {
 }
 
 struct AdjArgs {
+  int hmode;           // 1: h = h(x), collect dL/dh and lambda
   Grid* grid;
   Nbr nb;
   const unsigned* perm;
@@ -50,6 +60,7 @@ struct AdjArgs {
   float4* vb;          // sorted: dL/dv direct
   float4* qb;          // sorted: adjoints of (rho, D, S, C_x)
   float* cby;          // sorted: adjoint of C_y
+  float* lam;          // sorted: lambda = (dL/dh) / F' (h_mode 1)
   float* cbz;          // sorted: adjoint of C_z
   const Item* items;
   const int* plist;
@@ -78,7 +89,7 @@ struct SideBar {
 __device__ __forceinline__ void pair_reverse(const Side& I, const Side& J, float mj, float r, const float e[3],
                                              float dWi, float dWj, float d2Wi, float d2Wj, const float v[3],
                                              const float lw[3], float lc, float beta, float dbar[3], float vbar[3],
-                                             SideBar& Ib, SideBar& Jb) {
+                                             SideBar& Ib, SideBar& Jb, float& dWib_out, float& dWjb_out) {
   // forward values needed by the reverse sweep
   const float vr = fmaf(v[2], e[2], fmaf(v[1], e[1], v[0] * e[0]));
   const float fsum = fmaf(I.f, dWi, J.f * dWj);
@@ -159,6 +170,8 @@ __device__ __forceinline__ void pair_reverse(const Side& I, const Side& J, float
   eb[0] = fmaf(vrb, v[0], eb[0]);
   eb[1] = fmaf(vrb, v[1], eb[1]);
   eb[2] = fmaf(vrb, v[2], eb[2]);
+  dWib_out = dWib;
+  dWjb_out = dWjb;
   const float rb = fmaf(dWib, d2Wi, dWjb * d2Wj);
   const float ebe = fmaf(eb[2], e[2], fmaf(eb[1], e[1], eb[0] * e[0]));
   const float ir = 1.0f / r;
@@ -176,6 +189,7 @@ struct ForceAdjOp {
     float lw[3], lc;
     float xb[3], vb[3];
     SideBar sb;
+    float hb, ih;  // dL/dh_k through dW(r, h_k) in the force pairs; 1/h_k
     int k;
   };
   const float4* __restrict__ pos;
@@ -230,8 +244,9 @@ struct ForceAdjOp {
     const float vkj[3] = {i.vx - vj.x, i.vy - vj.y, i.vz - vj.z};
     float db[3], vbv[3];
     SideBar Ib, Jb;
+    float dWkb1, dWjb1, dWjb2, dWkb2;
     // k first: k's own sum, weights of k
-    pair_reverse(i.s, sj, vj.w, r, e, dWk, dWj, d2Wk, d2Wj, vkj, i.lw, i.lc, beta, db, vbv, Ib, Jb);
+    pair_reverse(i.s, sj, vj.w, r, e, dWk, dWj, d2Wk, d2Wj, vkj, i.lw, i.lc, beta, db, vbv, Ib, Jb, dWkb1, dWjb1);
     i.xb[0] += db[0]; i.xb[1] += db[1]; i.xb[2] += db[2];
     i.vb[0] += vbv[0]; i.vb[1] += vbv[1]; i.vb[2] += vbv[2];
     i.sb.A += Ib.A; i.sb.f += Ib.f; i.sb.rho += Ib.rho; i.sb.c += Ib.c; i.sb.B += Ib.B;
@@ -240,11 +255,13 @@ struct ForceAdjOp {
     const float en[3] = {-e[0], -e[1], -e[2]};
     const float vjk[3] = {-vkj[0], -vkj[1], -vkj[2]};
     const float lwj[3] = {wj.x, wj.y, wj.z};
-    pair_reverse(sj, i.s, i.m, r, en, dWj, dWk, d2Wj, d2Wk, vjk, lwj, wj.w, beta, db, vbv, Jb, Ib);
+    pair_reverse(sj, i.s, i.m, r, en, dWj, dWk, d2Wj, d2Wk, vjk, lwj, wj.w, beta, db, vbv, Jb, Ib, dWjb2, dWkb2);
     i.xb[0] -= db[0]; i.xb[1] -= db[1]; i.xb[2] -= db[2];
     i.vb[0] -= vbv[0]; i.vb[1] -= vbv[1]; i.vb[2] -= vbv[2];
     i.sb.A += Ib.A; i.sb.f += Ib.f; i.sb.rho += Ib.rho; i.sb.c += Ib.c; i.sb.B += Ib.B;
     i.sb.acP += Ib.acP; i.sb.u += Ib.u; i.sb.P += Ib.P;
+    // dW(r, h)/dh = -(4 dW/dr + r d2W/dr2) / h, for both terms that hold dW(r, h_k)
+    i.hb = fmaf(-(dWkb1 + dWkb2) * i.ih, fmaf(r, d2Wk, 4.0f * dWk), i.hb);
   }
 };
 
@@ -276,6 +293,8 @@ __device__ __forceinline__ void force_adj_item(const AdjArgs& a, const ForceAdjO
   I.lw[0] = wk.x; I.lw[1] = wk.y; I.lw[2] = wk.z; I.lc = wk.w;
   I.xb[0] = I.xb[1] = I.xb[2] = I.vb[0] = I.vb[1] = I.vb[2] = 0.0f;
   I.sb = SideBar{0, 0, 0, 0, 0, 0, 0, 0};
+  I.hb = 0.0f;
+  I.ih = 1.0f / p.w;
   I.k = k;
   unsigned ncand = 0;
   int sm;
@@ -293,6 +312,7 @@ __device__ __forceinline__ void force_adj_item(const AdjArgs& a, const ForceAdjO
   I.sb.acP = lsum(I.sb.acP, lsh);
   I.sb.u = lsum(I.sb.u, lsh);
   I.sb.P = lsum(I.sb.P, lsh);
+  I.hb = lsum(I.hb, lsh);
   if (!(live && s == 0)) return;
   // reverse of the ghost step of particle k
   const float gam = a.ph.gamma_eos, gm1 = gam - 1.0f;
@@ -327,6 +347,7 @@ __device__ __forceinline__ void force_adj_item(const AdjArgs& a, const ForceAdjO
       curlb[2] = acb * cz / acurl;
     }
     cb += epsb * 1e-4f / h;
+    I.hb -= epsb * 1e-4f * c / (h * h);  // eps = 1e-4 c / h
   }
   if (c > 0.0f) ub += cb * gam * gm1 / (2.0f * c);  // c = sqrt(gamma (gamma-1) u)
   // f = 1/Omega, Omega = 1 - D / (3 rho)
@@ -340,7 +361,7 @@ __device__ __forceinline__ void force_adj_item(const AdjArgs& a, const ForceAdjO
   a.cby[k] = curlb[1] * ir;
   a.cbz[k] = curlb[2] * ir;
   a.xb[k] = make_float4(I.xb[0], I.xb[1], I.xb[2], ub);
-  a.vb[k] = make_float4(I.vb[0], I.vb[1], I.vb[2], 0.0f);
+  a.vb[k] = make_float4(I.vb[0], I.vb[1], I.vb[2], I.hb);  // .w: dL/dh_k so far (h_mode 1)
 }
 
 __global__ void __launch_bounds__(kAdjThreads) k_force_adj(AdjArgs a) {
@@ -371,6 +392,7 @@ struct DensAdjOp {
     float vx, vy, vz, m;
     float rb, Db, Sb, Cb[3];
     float xb[3], vb[3];
+    float hE, hS, hC[3];  // h_mode 1: sums of k's own pairs for dD/dh, dS/dh, dC/dh
   };
   const float4* __restrict__ pos;
   const float4* __restrict__ vel;
@@ -381,6 +403,7 @@ struct DensAdjOp {
   float kg, Lmax;
   int kernel;
   float knorm;
+  int hmode;
 
   __device__ __forceinline__ float stage_w(float hj) const {
     const float H = kg * hj;
@@ -420,6 +443,19 @@ struct DensAdjOp {
       i.xb[q] = fmaf(es, e[q], i.xb[q]);
       i.xb[q] = fmaf(so * mass * g, Sb * va[q] - Cxv[q], i.xb[q]);
       i.vb[q] = fmaf(mass * g, -Sb * d[q] + dxC[q], i.vb[q]);
+    }
+    if (own && hmode) {
+      // h-derivatives of k's own sums (times -h or h): D: 9W + 7 r W' + r^2 W'';
+      // S and C: (4 W' + r W'') / r times the pair's (v_j - v_k).d and (v_j - v_k) x d
+      float w0, dw0;
+      kshape(kernel, r * invH, w0, dw0);
+      const float W0 = c4 * w0 / invH;
+      i.hE = fmaf(mass, fmaf(r, fmaf(r, W2, 7.0f * W1), 9.0f * W0), i.hE);
+      const float gh = mass * fmaf(r, W2, 4.0f * W1) / r;
+      i.hS = fmaf(gh, sd, i.hS);
+      i.hC[0] = fmaf(gh, vxd[0], i.hC[0]);
+      i.hC[1] = fmaf(gh, vxd[1], i.hC[1]);
+      i.hC[2] = fmaf(gh, vxd[2], i.hC[2]);
     }
   }
   __device__ __forceinline__ void interact(I& i, int j, unsigned code) const {
@@ -468,6 +504,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_dens_adj(AdjArgs a) {
   op.kg = a.ph.kg;
   op.kernel = a.ph.kernel;
   op.knorm = a.ph.knorm;
+  op.hmode = a.hmode;
   const int n_items = a.ctr[0];
   const unsigned lane = lane_id();
   for (;;) {
@@ -494,6 +531,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_dens_adj(AdjArgs a) {
     I.rb = q.x; I.Db = q.y; I.Sb = q.z;
     I.Cb[0] = q.w; I.Cb[1] = a.cby[k]; I.Cb[2] = a.cbz[k];
     I.xb[0] = I.xb[1] = I.xb[2] = I.vb[0] = I.vb[1] = I.vb[2] = 0.0f;
+    I.hE = I.hS = I.hC[0] = I.hC[1] = I.hC[2] = 0.0f;
     unsigned ncand = 0;
     int sm;
     const unsigned* sl = kept_list(a.nlist, a.item_nl, t, sm);
@@ -502,13 +540,134 @@ __global__ void __launch_bounds__(kAdjThreads) k_dens_adj(AdjArgs a) {
       I.xb[c] = lsum(I.xb[c], lsh);
       I.vb[c] = lsum(I.vb[c], lsh);
     }
+    if (a.hmode) {
+      I.hE = lsum(I.hE, lsh);
+      I.hS = lsum(I.hS, lsh);
+      for (int c = 0; c < 3; ++c) I.hC[c] = lsum(I.hC[c], lsh);
+    }
     if (live && s == 0) {
       const float4 xd = a.xb[k];
       const float4 vd = a.vb[k];
       const unsigned dst = a.perm[k];
+      if (a.hmode) {
+        // dL/dh_k = (force and Balsara part) + rho_b drho/dh + D_b dD/dh + S_b dS/dh + C_b . dC/dh,
+        // then lambda_k = (dL/dh_k) / F'_k
+        const float4 r4 = a.rho4[k];
+        const float h = p.w, ih = 1.0f / h;
+        const float D = -h * r4.y;
+        const float W00 = I.c4 / I.invH;  // W(0, h_k): every shape has w(0) = 1
+        const float dD = -(I.hE + 9.0f * I.m * W00) * ih;
+        float hb = vd.w - I.rb * D * ih + I.Db * dD - I.Sb * I.hS * ih;
+        hb += (I.Cb[0] * I.hC[0] + I.Cb[1] * I.hC[1] + I.Cb[2] * I.hC[2]) * ih;
+        const float Fp = r4.w + (float)(3.0 * a.ph.eta3) * ih * ih * ih * ih;
+        a.lam[k] = hb / Fp;
+      }
       a.grad_x[dst] = make_float4(xd.x + I.xb[0], xd.y + I.xb[1], xd.z + I.xb[2], 0.0f);
       a.grad_v[dst] = make_float4(vd.x + I.vb[0], vd.y + I.vb[1], vd.z + I.vb[2], 0.0f);
       a.grad_u[dst] = xd.w;
+    }
+  }
+}
+
+// ------------------------------------------------ implicit-function term
+struct IftAdjOp {
+  struct I {
+    float x, y, z, h, H2lo, H2hi, invH, c4, lam;
+    float xb[3];
+  };
+  const float4* __restrict__ pos;
+  const float* __restrict__ lam;
+  float L[3];
+  float kg, Lmax;
+  int kernel;
+  float knorm;
+
+  __device__ __forceinline__ float stage_w(float hj) const {
+    const float H = kg * hj;
+    return H * H + band_of(H, Lmax);
+  }
+  __device__ __forceinline__ bool candidate(const I& i, float r2, float H2j_hi) const {
+    return r2 < fmaxf(i.H2hi, H2j_hi);
+  }
+  // -(lambda_k dW(r,h_k)/dr + lambda_j dW(r,h_j)/dr) e_kj: the x-derivative of
+  // lambda_k n_k and of lambda_j n_j for the pair (each zero beyond its support)
+  __device__ __forceinline__ void interact(I& i, int j, unsigned code) const {
+    const float4 pj = pos[j];
+    float xj = pj.x, yj = pj.y, zj = pj.z;
+    shift_j(code, L, xj, yj, zj);
+    const float d[3] = {i.x - xj, i.y - yj, i.z - zj};
+    const float r2 = r2_of(d[0], d[1], d[2]);
+    if (!(r2 > 0.0f)) return;
+    const float Hj = kg * pj.w;
+    const float H2j = Hj * Hj;
+    const float bj_band = band_of(Hj, Lmax);
+    if (r2 >= fmaxf(i.H2hi, H2j + bj_band)) return;  // outside both supports
+    bool in_k = r2 < i.H2lo;
+    bool in_j = r2 < H2j - bj_band;
+    if (!in_k || !in_j) {
+      const double ex = exact_r2(i.x, i.y, i.z, pj.x, pj.y, pj.z, L[0], L[1], L[2]);
+      in_k = ex < exact_H2(kg, i.h);
+      in_j = ex < exact_H2(kg, pj.w);
+      if (!in_k && !in_j) return;
+    }
+    const float r = sqrtf(r2);
+    float t = 0.0f;
+    if (in_k) t = i.lam * i.c4 * dkshape(kernel, r * i.invH);
+    if (in_j) {
+      const float invHj = 1.0f / Hj;
+      t = fmaf(lam[j] * knorm * (invHj * invHj) * (invHj * invHj), dkshape(kernel, r * invHj), t);
+    }
+    const float tr = t / r;
+    i.xb[0] = fmaf(-tr, d[0], i.xb[0]);
+    i.xb[1] = fmaf(-tr, d[1], i.xb[1]);
+    i.xb[2] = fmaf(-tr, d[2], i.xb[2]);
+  }
+};
+
+__global__ void __launch_bounds__(kAdjThreads) k_ift_adj(AdjArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const Grid g = *a.grid;
+  WarpSmem& w = adj_smem(smem);
+  IftAdjOp op;
+  op.pos = a.pos; op.lam = a.lam;
+  op.L[0] = g.L[0]; op.L[1] = g.L[1]; op.L[2] = g.L[2];
+  op.Lmax = fmaxf(g.L[0], fmaxf(g.L[1], g.L[2]));
+  op.kg = a.ph.kg;
+  op.kernel = a.ph.kernel;
+  op.knorm = a.ph.knorm;
+  const int n_items = a.ctr[0];
+  const unsigned lane = lane_id();
+  for (;;) {
+    const int t = take_ticket(a.ticket);
+    if (t >= n_items) break;
+    const Item it = a.items[t];
+    const int lsh = lanes_shift(it.cnt, a.lmax);
+    const int slot = (int)(lane & ((32u >> lsh) - 1u)), s = (int)(lane >> (5 - lsh));
+    const bool live = slot < it.cnt;
+    const int k = a.plist[it.off + (live ? slot : 0)];
+    IftAdjOp::I I;
+    const float4 p = a.pos[k];
+    I.x = p.x; I.y = p.y; I.z = p.z; I.h = p.w;
+    const float H = a.ph.kg * p.w;
+    const float b = band_of(H, op.Lmax);
+    I.H2lo = H * H - b;
+    I.H2hi = H * H + b;
+    I.invH = 1.0f / H;
+    I.c4 = a.ph.knorm * (I.invH * I.invH) * (I.invH * I.invH);
+    I.lam = a.lam[k];
+    I.xb[0] = I.xb[1] = I.xb[2] = 0.0f;
+    unsigned ncand = 0;
+    int sm;
+    const unsigned* sl = kept_list(a.nlist, a.item_nl, t, sm);
+    scan_item(op, I, g, a.nb, a.pos, it.cell, lsh, s, live, w, ncand, sl, sm);
+    for (int c = 0; c < 3; ++c) I.xb[c] = lsum(I.xb[c], lsh);
+    if (live && s == 0) {
+      const unsigned dst = a.perm[k];
+      float4 gx = a.grad_x[dst];
+      gx.x += I.xb[0];
+      gx.y += I.xb[1];
+      gx.z += I.xb[2];
+      a.grad_x[dst] = gx;
     }
   }
 }
@@ -520,12 +679,14 @@ __global__ void k_gather_weights(int n, const unsigned* __restrict__ perm, const
 
 int backward_impl(Ctx* c, const float4* grad_ad, float4* grad_x, float4* grad_v, float* grad_u, int h_mode,
                   cudaStream_t s) {
-  if (h_mode != 0) return SWIFT_GPU_ERR_ARG;  // the implicit-function term for h(x) is not built
+  // h = h(x) needs the h iteration's root: not with a density call at fixed h
+  if (h_mode == 1 && (c->params.flags & SWIFT_GPU_NO_H_ITER)) return SWIFT_GPU_ERR_ARG;
   if (c->n == 0) return SWIFT_GPU_OK;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_force_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjSmemBytes);
     cudaFuncSetAttribute(k_dens_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjSmemBytes);
+    cudaFuncSetAttribute(k_ift_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjSmemBytes);
     attr = true;
   }
   int per_sm = 0;
@@ -539,6 +700,7 @@ int backward_impl(Ctx* c, const float4* grad_ad, float4* grad_x, float4* grad_v,
   const int nbg = min((c->n + 255) / 256, c->num_sms * 8);
   k_gather_weights<<<nbg, 256, 0, s>>>(c->n, c->d_vals[c->sorted_buf], grad_ad, c->d_scratch4[0]);
   AdjArgs a;
+  a.hmode = h_mode;
   a.grid = c->d_grid;
   a.nb = nbr_of(c);
   const bool lists = kept_lists_usable(c);
@@ -559,6 +721,8 @@ int backward_impl(Ctx* c, const float4* grad_ad, float4* grad_x, float4* grad_v,
   a.qb = c->d_scratch4[3];
   a.cby = c->d_scratch1[0];
   a.cbz = c->d_scratch1[1];
+  // lambda reuses the loss weights' array: only k_force_adj reads those
+  a.lam = reinterpret_cast<float*>(c->d_scratch4[0]);
   a.items = c->d_items0;
   a.plist = c->d_plist0;
   a.ctr = c->d_counters;
@@ -570,6 +734,12 @@ int backward_impl(Ctx* c, const float4* grad_ad, float4* grad_x, float4* grad_v,
   a.ticket = tickets + 1;
   k_dens_adj<<<nb2, kAdjThreads, kAdjSmemBytes, s>>>(a);
   c->launches += 4;
+  if (h_mode == 1) {
+    cudaMemsetAsync(tickets, 0, sizeof(int), s);  // k_force_adj's ticket, free again
+    a.ticket = tickets;
+    k_ift_adj<<<nb2, kAdjThreads, kAdjSmemBytes, s>>>(a);
+    c->launches += 2;
+  }
   return cudaGetLastError() == cudaSuccess ? SWIFT_GPU_OK : SWIFT_GPU_ERR_CUDA;
 }
 

@@ -383,6 +383,44 @@ class SphForces(torch.autograd.Function):
         return gx[:, :3], gv[:, :3], gu, None, None, None
 
 
+class SphForcesSolvedH(torch.autograd.Function):
+    """(a, du/dt, h) = F(x, v, u) with h solved by the h iteration (Sec. 2.1.2), differentiable in x, v, u.
+
+    ``forward(x, v, u, m, h0, lib_ctx)``: h0 (n,) is only the starting guess;
+    ``lib_ctx`` a :class:`Context` with the h iteration (no FLAG_NO_H_ITER),
+    whose h_tol sets how close h is to the root. Runs build_cells, density,
+    force; h is returned as a non-differentiable output. The backward pass calls
+    swift_gpu_force_backward with h_mode 1: h moves with x through the implicit
+    function theorem. Run backward before the context is used again.
+    """
+
+    @staticmethod
+    def forward(ctx, x, v, u, m, h0, lib_ctx):
+        from . import _lib
+        if lib_ctx.params.flags & _lib.FLAG_NO_H_ITER:
+            raise ValueError("SphForcesSolvedH needs the h iteration (a context without FLAG_NO_H_ITER)")
+        pos_h = torch.cat([x, h0[:, None]], 1).float().contiguous()
+        vel_m = torch.cat([v, m[:, None]], 1).float().contiguous()
+        uu = u.float().contiguous()
+        d = lib_ctx.density_checked(pos_h, vel_m)
+        out = lib_ctx.force(uu, want_dh=False, want_reductions=False)
+        ctx.lib_ctx = lib_ctx
+        ad = out["accel_dudt"]
+        h = d["h"].clone()
+        ctx.mark_non_differentiable(h)
+        return ad[:, :3].clone(), ad[:, 3].clone(), h
+
+    @staticmethod
+    def backward(ctx, grad_a, grad_du, grad_h):
+        n = ctx.lib_ctx.n
+        dev = grad_a.device if grad_a is not None else grad_du.device
+        ga = grad_a if grad_a is not None else torch.zeros(n, 3, dtype=torch.float32, device=dev)
+        gd = grad_du if grad_du is not None else torch.zeros(n, dtype=torch.float32, device=dev)
+        g4 = torch.cat([ga.float(), gd.float()[:, None]], 1).contiguous()
+        gx, gv, gu = ctx.lib_ctx.force_backward(g4, h_mode=1)
+        return gx[:, :3], gv[:, :3], gu, None, None, None
+
+
 class StepGraph:
     """One hot-path step (build_cells, density, gradient + force) captured once in a CUDA graph.
 

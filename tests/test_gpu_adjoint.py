@@ -193,3 +193,75 @@ def test_adjoint_kh32_full_size_finite_differences(O):
             assert abs(g - fds[0]) <= 1e-4 * scale[nm], (nm, k, comp, g, fds[0])
             checked += 1
     assert checked >= 30
+
+
+def _run_gpu_hsolved(d, vel, u, w, cw, **params):
+    from paper_2505_14538_b300 import sph
+    n = len(d["pos"])
+    ctx = sph.Context(n, box=d["box"], h_tol=1e-7, max_iter=60, **params)
+    x = torch.from_numpy(d["pos"].astype(np.float32)).cuda().requires_grad_(True)
+    v = torch.from_numpy(vel.astype(np.float32)).cuda().requires_grad_(True)
+    uu = torch.from_numpy(u.astype(np.float32)).cuda().requires_grad_(True)
+    m = torch.from_numpy(d["m"].astype(np.float32)).cuda()
+    h0 = torch.from_numpy(d["h"].astype(np.float32)).cuda()
+    a, du, h = sph.SphForcesSolvedH.apply(x, v, uu, m, h0, ctx)
+    L = (torch.from_numpy(w.astype(np.float32)).cuda() * a).sum() + \
+        (torch.from_numpy(cw.astype(np.float32)).cuda() * du).sum()
+    L.backward()
+    torch.cuda.synchronize()
+    assert ctx.sync_status()[0] == 0
+    return x.grad.cpu().numpy(), v.grad.cpu().numpy(), uu.grad.cpu().numpy(), h.cpu().numpy()
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_adjoint_hsolved_matches_torch_fp64(O, kind):
+    """h_mode 1 (h = h(x), implicit function theorem) against the FP64 torch reference at the oracle's own root."""
+    from oracle import torch_ref as T
+    d = ics.lattice(10, jitter=0.3, index=14)
+    n = len(d["pos"])
+    rng = np.random.default_rng(60 + kind)
+    vel = rng.normal(0, 0.3, (n, 3)).astype(np.float32)
+    u = (d["u"] * rng.uniform(0.5, 1.5, n)).astype(np.float32)
+    w = rng.normal(size=(n, 3))
+    cw = rng.normal(size=n)
+    kg = O.KERNEL_GAMMAS[kind]
+    gx, gv, gu, h_gpu = _run_gpu_hsolved(d, vel, u, w, cw, kernel=kind)
+    p = O.Params(kernel=kind, kernel_gamma=kg, h_tol=1e-14, max_iter=80, h_max=0.4)
+    root = O.solve_h(p, d["pos"], vel, d["m"], d["h"])
+    assert root["converged"].all()
+    h = root["h"]
+    assert np.max(np.abs(h_gpu / h - 1)) < 1e-5
+    _, rx, rv, ru, rh, lam = T.loss_and_grad_hsolved(d["pos"], vel, u, d["m"], h, w, cw, box=d["box"],
+                                                     kernel_gamma=kg, kernel=kind)
+    # the sqrt kink of Eq. 22 (pairs with equal pressures and different u), as for h_mode 0
+    pairs = T.pair_list(d["pos"], h, d["box"], kg)
+    _, _, ex = T.forward(torch.tensor(d["pos"].astype(np.float64)), torch.tensor(vel.astype(np.float64)),
+                         torch.tensor(u.astype(np.float64)), d["m"], h, pairs, d["box"], kernel_gamma=kg, kernel=kind)
+    P = ex["P"].numpy()
+    i, j = pairs
+    bad = (np.abs(P[i] - P[j]) < 1e-5 * (P[i] + P[j])) & (u[i] != u[j])
+    mask = np.zeros(n, bool)
+    mask[i[bad]] = True
+    mask[i[mask[j]]] = True
+    keep = ~mask
+    assert keep.mean() > {0: 0.8, 1: 0.7}[kind]  # Wendland C2: more neighbours reach the kink
+    for got, ref, nm in ((gx, rx, "x"), (gv, rv, "v"), (gu, ru, "u")):
+        err = np.abs(got[keep] - ref[keep]).max()
+        assert err <= 1e-4 * np.abs(ref).max(), (kind, nm, err, np.abs(ref).max())
+    # the h term is not negligible here: the fixed-h gradient differs from it
+    fixed = T.loss_and_grad(d["pos"], vel, u, d["m"], h, w, cw, box=d["box"], kernel_gamma=kg, kernel=kind)[1]
+    assert np.abs(fixed - rx).max() > 1e-2 * np.abs(rx).max()
+
+
+def test_hsolved_adjoint_refused_at_fixed_h():
+    from paper_2505_14538_b300 import _lib, sph
+    d = ics.lattice(8, jitter=0.2)
+    n = len(d["pos"])
+    ctx = sph.Context(n, flags=_lib.FLAG_NO_H_ITER)
+    pos_h = torch.from_numpy(np.concatenate([d["pos"], d["h"][:, None]], 1).astype(np.float32)).cuda()
+    vel_m = torch.from_numpy(np.concatenate([d["vel"], d["m"][:, None]], 1).astype(np.float32)).cuda()
+    ctx.build_cells(pos_h)
+    ctx.density(pos_h, vel_m)
+    ctx.force(torch.from_numpy(d["u"].astype(np.float32)).cuda())
+    with pytest.raises(sph.SwiftGPUError):
+        ctx.force_backward(torch.zeros(n, 4, device="cuda"), h_mode=1)
