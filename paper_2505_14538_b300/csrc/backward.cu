@@ -71,6 +71,8 @@ struct AdjArgs {
   float* grad_u;
   const unsigned* nlist;  // candidate lists kept by the density call (NULL: scan)
   const int2* item_nl;
+  const unsigned long long* nl_ctr;  // space the items asked for (above nl_cap: the lists are not used)
+  long long nl_cap;
 };
 
 // One side of a force pair: the per-particle inputs and, after the reverse
@@ -298,7 +300,7 @@ __device__ __forceinline__ void force_adj_item(const AdjArgs& a, const ForceAdjO
   I.k = k;
   unsigned ncand = 0;
   int sm;
-  const unsigned* sl = kept_list(a.nlist, a.item_nl, t, sm);
+  const unsigned* sl = kept_list(a.nlist, a.item_nl, t, sm, a.nl_ctr, a.nl_cap);
   scan_item(op, I, g, a.nb, a.pos, it.cell, lsh, s, live, w, ncand, sl, sm);
   for (int q = 0; q < 3; ++q) {
     I.xb[q] = lsum(I.xb[q], lsh);
@@ -534,7 +536,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_dens_adj(AdjArgs a) {
     I.hE = I.hS = I.hC[0] = I.hC[1] = I.hC[2] = 0.0f;
     unsigned ncand = 0;
     int sm;
-    const unsigned* sl = kept_list(a.nlist, a.item_nl, t, sm);
+    const unsigned* sl = kept_list(a.nlist, a.item_nl, t, sm, a.nl_ctr, a.nl_cap);
     scan_item(op, I, g, a.nb, a.pos, it.cell, lsh, s, live, w, ncand, sl, sm);
     for (int c = 0; c < 3; ++c) {
       I.xb[c] = lsum(I.xb[c], lsh);
@@ -658,7 +660,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_ift_adj(AdjArgs a) {
     I.xb[0] = I.xb[1] = I.xb[2] = 0.0f;
     unsigned ncand = 0;
     int sm;
-    const unsigned* sl = kept_list(a.nlist, a.item_nl, t, sm);
+    const unsigned* sl = kept_list(a.nlist, a.item_nl, t, sm, a.nl_ctr, a.nl_cap);
     scan_item(op, I, g, a.nb, a.pos, it.cell, lsh, s, live, w, ncand, sl, sm);
     for (int c = 0; c < 3; ++c) I.xb[c] = lsum(I.xb[c], lsh);
     if (live && s == 0) {
@@ -706,6 +708,8 @@ int backward_impl(Ctx* c, const float4* grad_ad, float4* grad_x, float4* grad_v,
   const bool lists = kept_lists_usable(c);
   a.nlist = lists ? c->d_nlist : nullptr;
   a.item_nl = lists ? c->d_item_nl : nullptr;
+  a.nl_ctr = c->d_nl_ctr;
+  a.nl_cap = c->nl_cap;
   a.perm = c->d_vals[c->sorted_buf];
   a.ph = c->phys;
   a.lmax = c->tuning.max_lanes_per_particle;

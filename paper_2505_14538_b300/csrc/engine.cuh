@@ -135,10 +135,14 @@ __device__ __forceinline__ void stage_candidate(const Grid& g, const float4* __r
   entry = (unsigned)j | (code << kIndexBits);
 }
 
-// The candidate list the density call kept for pass-0 item t, if any.
-__device__ __forceinline__ const unsigned* kept_list(const unsigned* nlist, const int2* item_nl, int t, int& m) {
+// The candidate list the density call kept for pass-0 item t, if any. When
+// the store ran out (nl_ctr, the space all items asked for, above nl_cap),
+// which items got a list depends on timing, so then no item uses one: the
+// sums of every particle are then taken in the same order on every run.
+__device__ __forceinline__ const unsigned* kept_list(const unsigned* nlist, const int2* item_nl, int t, int& m,
+                                                     const unsigned long long* nl_ctr, long long nl_cap) {
   m = 0;
-  if (!nlist) return nullptr;
+  if (!nlist || *nl_ctr > (unsigned long long)nl_cap) return nullptr;
   const int2 sp = item_nl[t];
   if (sp.x < 0) return nullptr;
   m = sp.y;

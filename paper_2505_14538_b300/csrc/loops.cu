@@ -499,6 +499,8 @@ struct LoopArgs {
   unsigned long long* stats;
   const unsigned* nlist;  // candidate lists kept by the density call (NULL: scan)
   const int2* item_nl;
+  const unsigned long long* nl_ctr;  // space the items asked for (above nl_cap: the lists are not used)
+  long long nl_cap;
 };
 
 
@@ -525,7 +527,7 @@ __device__ __forceinline__ void grad_item(const LoopArgs& a, const GradOp& op, c
   I.count = 0;
   I.k = k;
   int sm;
-  const unsigned* sl = kept_list(a.nlist, a.item_nl, t, sm);
+  const unsigned* sl = kept_list(a.nlist, a.item_nl, t, sm, a.nl_ctr, a.nl_cap);
   scan_item(op, I, g, a.nb, a.pos, it.cell, lm.lsh, lm.s, lm.live, w, ncand, sl, sm);
   I.vsig = lmax(I.vsig, lm.lsh);
   I.lap = lsum(I.lap, lm.lsh);
@@ -601,7 +603,7 @@ __device__ __forceinline__ void force_item(const LoopArgs& a,
     I.gcount = 0;
   }
   int sm;
-  const unsigned* sl = kept_list(a.nlist, a.item_nl, t, sm);
+  const unsigned* sl = kept_list(a.nlist, a.item_nl, t, sm, a.nl_ctr, a.nl_cap);
   scan_item(op, I, g, a.nb, a.pos, it.cell, lm.lsh, lm.s, lm.live, w, ncand, sl, sm);
   lsum2(I.axs, I.axc, lm.lsh);
   lsum2(I.ays, I.ayc, lm.lsh);
@@ -852,6 +854,8 @@ static LoopArgs loop_args(Ctx* c, int* ticket, void* out) {
   const bool lists = kept_lists_usable(c);
   a.nlist = lists ? c->d_nlist : nullptr;
   a.item_nl = lists ? c->d_item_nl : nullptr;
+  a.nl_ctr = c->d_nl_ctr;
+  a.nl_cap = c->nl_cap;
   return a;
 }
 

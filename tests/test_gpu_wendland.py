@@ -137,3 +137,22 @@ def test_wendland_static_entry_point(sph):
 def test_kernel_argument_checked(sph):
     with pytest.raises(sph.SwiftGPUError):
         sph.Context(16, kernel=3)
+
+
+def test_wendland_c4_repeats_bit_for_bit(sph):
+    """With ~85 neighbours the kept candidate lists can fill their store; the loops then scan instead,
+    for every item, so a repeated step gives bitwise the same outputs."""
+    d = ics.lattice(24, jitter=0.2)
+    n = len(d["pos"])
+    pos_h = torch.from_numpy(np.concatenate([d["pos"], d["h"][:, None]], 1).astype(np.float32)).cuda()
+    vel_m = torch.from_numpy(np.concatenate([d["vel"], d["m"][:, None]], 1).astype(np.float32)).cuda()
+    u = torch.from_numpy(d["u"].astype(np.float32)).cuda()
+    outs = []
+    for _ in range(3):
+        ctx = sph.Context(n, max_iter=40, kernel=2)
+        o = ctx.step(pos_h, vel_m, u)
+        torch.cuda.synchronize()
+        outs.append({k: o[k].cpu().numpy() for k in ("h", "rho4", "ngb", "vsig_lapu", "accel_dudt", "dh_dt")})
+    for o in outs[1:]:
+        for k in o:
+            assert np.array_equal(o[k], outs[0][k]), k
