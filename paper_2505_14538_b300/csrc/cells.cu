@@ -148,7 +148,7 @@ __global__ void k_scan_h(const float4* __restrict__ pos_h, int n, float L0, floa
 }
 
 __global__ void k_grid_setup(const unsigned* __restrict__ hmax_bits, Grid* g, Phys ph, float margin,
-                             float min_width, int nc_cap, Status* st) {
+                             float min_width, int nc_cap, int host_passes, Status* st) {
   float hmax = __uint_as_float(*hmax_bits);
   float want = fmaxf(min_width, (1.0f + margin) * ph.kg * hmax);
   int nct = 1;
@@ -178,7 +178,14 @@ __global__ void k_grid_setup(const unsigned* __restrict__ hmax_bits, Grid* g, Ph
   int bits = 0;
   while ((1 << bits) < nct) ++bits;
   g->key_bits = bits;
-  for (int q = 0; q < kMaxKeyPasses; ++q) g->pass_live[q] = 8 * q < bits ? 1 : 0;
+  int live = 0;
+  for (int q = 0; q < kMaxKeyPasses; ++q) {
+    g->pass_live[q] = 8 * q < bits ? 1 : 0;
+    live += g->pass_live[q];
+  }
+  // the host runs host_passes passes and reads the sort from buffer host_passes % 2; the
+  // passes past the live ones do nothing, so the keys start where live passes end there
+  g->sort_start = (host_passes & 1) ^ (live & 1);
 }
 
 // Spread the 10 low bits of v to every third bit (bit b -> bit 3b).
@@ -195,9 +202,12 @@ __device__ __forceinline__ unsigned spread3(unsigned v) {
 // is instead the 30-bit Morton code of the position inside the cell (10 bits
 // per axis, x in the lowest bit of each 3-bit digit) and the cell id goes to
 // cell_out, morton_out keeping a copy of the code.
-__global__ void k_cell_ids(const float4* __restrict__ pos_h, int n, const Grid* __restrict__ g,
-                           unsigned* __restrict__ keys, unsigned* __restrict__ vals, unsigned* __restrict__ cell_out,
-                           unsigned* __restrict__ morton_out) {
+__global__ void k_cell_ids(const float4* __restrict__ pos_h, int n, const Grid* __restrict__ g, KeyBufs kb,
+                           unsigned* __restrict__ cell_out, unsigned* __restrict__ morton_out) {
+  // uniform grid: buffer g->sort_start; adaptive leaves: buffer 0 (their passes are all live)
+  const int b = cell_out ? 0 : g->sort_start;
+  unsigned* __restrict__ keys = kb.k[b];
+  unsigned* __restrict__ vals = kb.v[b];
   const int nx = g->nc[0], ny = g->nc[1], nz = g->nc[2];
   const double Lx = g->L[0], Ly = g->L[1], Lz = g->L[2];
   const float ncf[3] = {(float)nx, (float)ny, (float)nz};
@@ -259,51 +269,58 @@ __global__ void k_cell_ids(const float4* __restrict__ pos_h, int n, const Grid* 
 }
 
 // keys[k] = src[idx[k]]
-__global__ void k_gather_keys(unsigned* __restrict__ keys, const unsigned* __restrict__ src,
-                              const unsigned* __restrict__ idx, int n) {
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) keys[k] = src[idx[k]];
+// Adaptive leaves: after the Morton passes (in buffer 0), the cell ids of the
+// Morton-ordered particles become the keys of the cell-id passes, in buffer
+// g->sort_start (with their values) like the uniform grid's keys.
+__global__ void k_gather_keys(KeyBufs kb, const unsigned* __restrict__ cell_of, int n, const Grid* __restrict__ g) {
+  const int b = g->sort_start;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const unsigned v = kb.v[0][k];
+    kb.k[b][k] = cell_of[v];
+    if (b != 0) kb.v[b][k] = v;
+  }
 }
 
 // ------------------------------------------------------------ radix sort
-// Pass over digit `shift..shift+8`. Histogram layout: hist[d * nblocks + b].
-__global__ void k_radix_count(const unsigned* __restrict__ keys, int n, int shift, const Grid* __restrict__ g,
+// Histogram layout: hist[d * nblocks + b].
+// Radix pass `pass` over 8-bit digit `shift`. With bits >= 0 (the Morton keys of
+// adaptive leaves) every pass is live and src is the host's buffer. With bits
+// < 0 (cell ids) a pass over bits no cell uses does nothing, and the live
+// passes read buffer g->sort_start ^ (pass & 1): they end in the buffer the
+// host reads.
+__device__ __forceinline__ int pass_src(const Grid* g, int bits, int pass, int host_src) {
+  return bits >= 0 ? host_src : (g->sort_start ^ (pass & 1));
+}
+
+__global__ void k_radix_count(KeyBufs kb, int host_src, int pass, int n, int shift, const Grid* __restrict__ g,
                               int bits, unsigned* __restrict__ hist) {
   __shared__ unsigned h[256];
+  const bool live = shift < (bits >= 0 ? bits : g->key_bits);
+  if (!live) return;  // its scan and scatter are skipped too
+  const unsigned* __restrict__ keys = kb.k[pass_src(g, bits, pass, host_src)];
   h[threadIdx.x] = 0;
   __syncthreads();
-  const bool live = shift < (bits >= 0 ? bits : g->key_bits);
   const int base = blockIdx.x * kRadixTile;
-  if (live) {
-    for (int k = 0; k < kRadixItems; ++k) {
-      int i = base + k * kRadixThreads + threadIdx.x;
-      if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
-    }
-  } else if (threadIdx.x == 0) {
-    int cnt = min(kRadixTile, n - base);
-    h[0] = cnt > 0 ? cnt : 0;
+  for (int k = 0; k < kRadixItems; ++k) {
+    int i = base + k * kRadixThreads + threadIdx.x;
+    if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
   }
   __syncthreads();
   hist[threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
 }
 
-__global__ void k_radix_scatter(const unsigned* __restrict__ kin, const unsigned* __restrict__ vin, int n,
-                                int shift, const Grid* __restrict__ g, int bits, const unsigned* __restrict__ offs,
-                                unsigned* __restrict__ kout, unsigned* __restrict__ vout) {
+__global__ void k_radix_scatter(KeyBufs kb, int host_src, int pass, int n, int shift, const Grid* __restrict__ g,
+                                int bits, const unsigned* __restrict__ offs) {
   __shared__ unsigned run[256];
   __shared__ unsigned wcnt[kRadixThreads / 32][256];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool live = shift < (bits >= 0 ? bits : g->key_bits);
-  if (!live) {  // the digit is 0 for every key: the stable order is the input order
-    const int base = blockIdx.x * kRadixTile;
-    for (int k = threadIdx.x; k < kRadixTile; k += kRadixThreads) {
-      const int i = base + k;
-      if (i < n) {
-        kout[i] = kin[i];
-        vout[i] = vin[i];
-      }
-    }
-    return;
-  }
+  if (!live) return;
+  const int src = pass_src(g, bits, pass, host_src);
+  const unsigned* __restrict__ kin = kb.k[src];
+  const unsigned* __restrict__ vin = kb.v[src];
+  unsigned* __restrict__ kout = kb.k[1 - src];
+  unsigned* __restrict__ vout = kb.v[1 - src];
   run[threadIdx.x] = offs[threadIdx.x * gridDim.x + blockIdx.x];
   for (int ww = 0; ww < kRadixThreads / 32; ++ww) wcnt[ww][threadIdx.x] = 0;
   __syncthreads();
@@ -314,7 +331,7 @@ __global__ void k_radix_scatter(const unsigned* __restrict__ kin, const unsigned
     bool valid = i < n;
     unsigned key = valid ? kin[i] : 0u;
     unsigned val = valid ? vin[i] : 0u;
-    unsigned d = live ? ((key >> shift) & 255u) : 0u;
+    unsigned d = (key >> shift) & 255u;
     unsigned vmask = __ballot_sync(0xffffffffu, valid);
     unsigned peers = __match_any_sync(0xffffffffu, valid ? d : 0xffffffffu) & vmask;
     unsigned rank = __popc(peers & lt);
@@ -359,33 +376,36 @@ int build_cells_impl(Ctx* c, const float4* pos_h, int n, float min_width, cudaSt
   }
   const bool adaptive = (c->params.flags & SWIFT_GPU_ADAPTIVE) != 0;
   const int nc_cap = adaptive && c->nc_cap > kAdaptiveNcCap ? kAdaptiveNcCap : c->nc_cap;
+  const int host_passes = (c->max_key_bits + 7) / 8;
   k_grid_setup<<<1, 1, 0, s>>>(c->d_hmax_bits, c->d_grid, c->phys, c->params.cell_margin, min_width, nc_cap,
-                               c->d_status);
+                               host_passes, c->d_status);
   c->launches++;
   if (n > 0) {
     int gb = min((n + 255) / 256, sm * 8);
-    k_cell_ids<<<gb, 256, 0, s>>>(pos_h, n, c->d_grid, c->d_keys[0], c->d_vals[0], adaptive ? c->d_aux[0] : nullptr,
+    const KeyBufs kb{{c->d_keys[0], c->d_keys[1]}, {c->d_vals[0], c->d_vals[1]}};
+    k_cell_ids<<<gb, 256, 0, s>>>(pos_h, n, c->d_grid, kb, adaptive ? c->d_aux[0] : nullptr,
                                   adaptive ? c->d_aux[1] : nullptr);
     c->launches++;
     const int nb = (n + kRadixTile - 1) / kRadixTile;
-    int src = 0;
-    auto pass = [&](int shift, int bits) {
-      k_radix_count<<<nb, kRadixThreads, 0, s>>>(c->d_keys[src], n, shift, c->d_grid, bits, c->d_hist);
+    int src = 0;  // host's view of the buffer a pass reads (as if every pass ran)
+    auto pass = [&](int p, int shift, int bits) {
+      k_radix_count<<<nb, kRadixThreads, 0, s>>>(kb, src, p, n, shift, c->d_grid, bits, c->d_hist);
       const int* gate = bits >= 0 ? nullptr : &c->d_grid->pass_live[shift / 8];
       exclusive_scan(c, c->d_hist, c->d_hist, 256 * nb, c->d_scan_tmp, s, gate);
-      k_radix_scatter<<<nb, kRadixThreads, 0, s>>>(c->d_keys[src], c->d_vals[src], n, shift, c->d_grid, bits,
-                                                    c->d_hist, c->d_keys[1 - src], c->d_vals[1 - src]);
+      k_radix_scatter<<<nb, kRadixThreads, 0, s>>>(kb, src, p, n, shift, c->d_grid, bits, c->d_hist);
       c->launches += 2;
       src = 1 - src;
     };
     if (adaptive) {
-      // least significant key first: the Morton code inside the cell, then the cell id
-      for (int shift = 0; shift < 30; shift += 8) pass(shift, 30);
-      k_gather_keys<<<gb, 256, 0, s>>>(c->d_keys[src], c->d_aux[0], c->d_vals[src], n);
+      // least significant key first: the Morton code inside the cell (four passes, ending in
+      // buffer 0), then the cell id
+      for (int shift = 0, p = 0; shift < 30; shift += 8, ++p) pass(p, shift, 30);
+      k_gather_keys<<<gb, 256, 0, s>>>(kb, c->d_aux[0], n, c->d_grid);
       c->launches++;
     }
-    for (int shift = 0; shift < c->max_key_bits; shift += 8) pass(shift, -1);
-    c->sorted_buf = src;  // keys/vals of this buffer are sorted by cell id
+    for (int shift = 0, p = 0; shift < c->max_key_bits; shift += 8, ++p) pass(p, shift, -1);
+    // the live cell-id passes end in buffer host_passes % 2 (their start buffer was chosen for it)
+    c->sorted_buf = host_passes & 1;
   }
   {
     int gb = min((n + 1 + 255) / 256, sm * 8);

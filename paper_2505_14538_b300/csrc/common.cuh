@@ -42,6 +42,14 @@ struct Grid {
   int key_bits;
   float width[3];
   int pass_live[kMaxKeyPasses];  // radix pass q sorts bits 8q.. of the cell id (0: all zero)
+  int sort_start;    // uniform grid: key buffer the cell ids are written to, so that the live
+                     // passes alone end in the buffer the host expects
+};
+
+// The two key/value buffers of the cell sort.
+struct KeyBufs {
+  unsigned* k[2];
+  unsigned* v[2];
 };
 
 // Status a particle capped at the cell's h raises: a wider cell would help

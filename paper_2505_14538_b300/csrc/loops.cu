@@ -705,7 +705,7 @@ __global__ void __launch_bounds__(kLoopThreads, 4) k_force(LoopArgs a) { force_k
 
 // Gradient (Eqs. 10-11, Laplacian of u) and force in one pass over the pairs.
 template <int K>
-__global__ void __launch_bounds__(kLoopThreads, 4) k_grad_force(LoopArgs a) { force_kernel_body<true, K>(a); }
+__global__ void __launch_bounds__(kLoopThreads, 5) k_grad_force(LoopArgs a) { force_kernel_body<true, K>(a); }
 
 // One warp per quantity; lane l sums blocks l, l+32, ... and the warp then
 // combines the lanes in a fixed order, so the result does not depend on timing.
