@@ -126,7 +126,7 @@ int swift_gpu_create(swift_gpu_ctx** out, const swift_gpu_params* p, int64_t n_m
   c->max_key_bits = bits;
   c->max_passes = kMaxPasses;
   const int64_t n = n_max;
-  const int64_t nb = (n + 4095) / 4096;
+  const int64_t nb = (n + kRadixTile - 1) / kRadixTile;  // radix tiles: 256 histogram entries each
   int64_t scan_m = 256 * nb > ncells_max + 1 ? 256 * nb : ncells_max + 1;
   // adaptive tree: cells (at most kAdaptiveNcCap^3 of them) plus 2 nodes per
   // particle, all addressable with kIndexBits; leaves are disjoint and non-empty

@@ -20,9 +20,6 @@ namespace sg {
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;  // 2048
-constexpr int kRadixThreads = 256;
-constexpr int kRadixItems = 16;
-constexpr int kRadixTile = kRadixThreads * kRadixItems;  // 4096
 
 // ------------------------------------------------------------------ scans
 // Exclusive scan of uint32, three phases: per-tile sums, scan of the sums in

@@ -144,6 +144,12 @@ inline unsigned long long wait_limit_ns(const Ctx* c) {
   return (unsigned long long)us * 1000ull;
 }
 
+// Radix sort of the cell ids: one block sorts a tile of kRadixTile keys, and
+// the histogram holds 256 digits per tile (every allocation derives from these).
+constexpr int kRadixThreads = 256;
+constexpr int kRadixItems = 16;
+constexpr int kRadixTile = kRadixThreads * kRadixItems;  // 4096
+
 // counters layout helpers
 constexpr int kCtrPerPass = 4;  // item_count, plist_count, ticket, spare
 __host__ __device__ inline int ctr_index(int pass, int which) { return pass * kCtrPerPass + which; }

@@ -27,7 +27,7 @@ constexpr int static_nc_cap() {
   return c;
 }
 constexpr int64_t kStaticCells = (int64_t)static_nc_cap() * static_nc_cap() * static_nc_cap();
-constexpr int64_t kStaticRadixBlocks = (kStaticN + 4095) / 4096;
+constexpr int64_t kStaticRadixBlocks = (kStaticN + kRadixTile - 1) / kRadixTile;
 constexpr int64_t kStaticScanM = 256 * kStaticRadixBlocks > kStaticCells + 1 ? 256 * kStaticRadixBlocks
                                                                              : kStaticCells + 1;
 
