@@ -147,8 +147,8 @@ inline unsigned long long wait_limit_ns(const Ctx* c) {
 // Radix sort of the cell ids: one block sorts a tile of kRadixTile keys, and
 // the histogram holds 256 digits per tile (every allocation derives from these).
 constexpr int kRadixThreads = 256;
-constexpr int kRadixItems = 16;
-constexpr int kRadixTile = kRadixThreads * kRadixItems;  // 4096
+constexpr int kRadixItems = 8;
+constexpr int kRadixTile = kRadixThreads * kRadixItems;  // 2048
 
 // counters layout helpers
 constexpr int kCtrPerPass = 4;  // item_count, plist_count, ticket, spare
