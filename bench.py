@@ -168,18 +168,24 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def measured_traffic(kernel):
-    """DRAM bytes per launch from the committed ncu summary, if it matches the current kernel source."""
+def measured_counters(kernel):
+    """The committed ncu record of a loop kernel (DRAM bytes per launch, FMA-pipe and issue activity),
+    if it was taken from the current kernel source; else {}."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             t = json.load(f)
     except OSError:
-        return None
+        return {}
     e = t.get(kernel)
     if not e or e.get("source_hash") != kernel_source_hash():
-        return None
-    return e.get("bytes_per_launch")
+        return {}
+    return e
+
+
+def measured_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the current kernel source."""
+    return measured_counters(kernel).get("bytes_per_launch")
 
 
 def measured_peaks():
@@ -335,8 +341,13 @@ def run_ours(args, rank, world, pg):
             "flops_per_launch": flops[dom],
             "flops_per_interaction": {"density": fpi[0], "h_iteration": fpi[3], "gradient": fpi[1], "force": fpi[2]},
             "per_loop": {names[j]: {"ms": kernel_ms[j], "tflops": flops[j] / (kernel_ms[j] * 1e-3) / 1e12,
-                                    "frac": flops[j] / (kernel_ms[j] * 1e-3) / 1e12 / peak_max}
+                                    "frac": flops[j] / (kernel_ms[j] * 1e-3) / 1e12 / peak_max,
+                                    "hw_fma_pipe_frac": (measured_counters(names[j]).get("fma_pipe_active_pct", 0) / 100
+                                                         or None)}
                          for j in range(2)},
+            "frac_note": "frac counts the algorithmic flops of the interacting pairs only (oracle op counts); "
+                         "hw_fma_pipe_frac is the FMA pipe's busy fraction counted by ncu (all FP32 work: "
+                         "candidate tests, compensated sums, misses), from profiles/traffic.json",
             "interactions": {"density": inter[0], "gradient": inter[1], "force": inter[2],
                              "density_full_sums_all_passes": dens_full},
             "candidates": {"density": cand[0], "gradient": cand[1], "force": cand[2]},
