@@ -122,8 +122,12 @@ typedef struct swift_gpu_ctx swift_gpu_ctx;
 void swift_gpu_default_params(swift_gpu_params* p);
 
 /* Create a context for up to n_max particles on the current CUDA device.
- * Allocates every device buffer the calls need (about 600 bytes per particle
- * plus the cell arrays, the adaptive tree and leaf lists included), so no later call allocates. *ctx is owned by the
+ * Allocates every device buffer the calls need, so no later call allocates:
+ * about 0.6 KB per particle, plus the cell arrays, the adaptive tree and leaf
+ * lists (about 0.3 KB per particle), and on the uniform grid (a context
+ * created without ADAPTIVE) the store of the candidate lists the density call
+ * keeps for the later loops: 512 bytes per particle for the cubic spline,
+ * scaled by (kernel_gamma / 1.825742)^3 up to 1 KB for the Wendland shapes. *ctx is owned by the
  * caller and freed with swift_gpu_destroy. Errors: ERR_ARG (null/invalid
  * params, n_max < 1 or > 2^26), ERR_NOMEM, ERR_CUDA. */
 int swift_gpu_create(swift_gpu_ctx** ctx, const swift_gpu_params* p, int64_t n_max);

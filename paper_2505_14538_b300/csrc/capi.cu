@@ -138,7 +138,17 @@ int swift_gpu_create(swift_gpu_ctx** out, const swift_gpu_params* p, int64_t n_m
   c->leaf_cap = (int)n;
   if (scan_m < node_cap + 1) scan_m = node_cap + 1;  // leaf flags of the tree nodes
   // kept candidate lists: 128 entries per particle (a list that does not fit leaves its item to scan)
-  c->nl_cap = 128 * n < ((int64_t)1 << 31) - 64 ? 128 * n : ((int64_t)1 << 31) - 64;
+  // Kept candidate lists (uniform grid only; adaptive leaves never keep them): the candidates within
+  // the cell cap's support, padded to the longest lane of each item. 128 entries a particle hold the
+  // cubic spline's (about 56 neighbours); the other shapes scale with their neighbour count, (H/h)^3.
+  int64_t per = 128;
+  if (p->kernel_gamma > 1.825742f) {
+    const double s = (double)p->kernel_gamma / 1.825742;
+    per = (int64_t)(16.0 * ceil(128.0 * s * s * s / 16.0));
+    if (per > 256) per = 256;
+  }
+  const bool keep_lists = (p->flags & SWIFT_GPU_ADAPTIVE) == 0;
+  c->nl_cap = !keep_lists ? 0 : per * n < ((int64_t)1 << 31) - 64 ? per * n : ((int64_t)1 << 31) - 64;
   int64_t nbr_cap = 48 * n > ((int64_t)1 << 22) ? 48 * n : ((int64_t)1 << 22);  // at least 16 MB of lists
   c->nbr_cap = (int)(nbr_cap < (int64_t)INT32_MAX ? nbr_cap : (int64_t)INT32_MAX);
   c->red_blocks = c->num_sms * 32;
@@ -159,7 +169,7 @@ int swift_gpu_create(swift_gpu_ctx** out, const swift_gpu_params* p, int64_t n_m
             dalloc(&c->d_node_done, node_cap) && dalloc(&c->d_node_flag, node_cap + 1) &&
             dalloc(&c->d_leaf_range, n) && dalloc(&c->d_leaf_hcap, n) && dalloc(&c->d_leaf_node, n) &&
             dalloc(&c->d_nbr_span, n) && dalloc(&c->d_nbr, (size_t)c->nbr_cap) &&
-            dalloc(&c->d_tree_ctr, kTreeCtrCount) && dalloc(&c->d_nlist, (size_t)c->nl_cap) &&
+            dalloc(&c->d_tree_ctr, kTreeCtrCount) && (c->nl_cap == 0 || dalloc(&c->d_nlist, (size_t)c->nl_cap)) &&
             dalloc(&c->d_item_nl, n) && dalloc(&c->d_nl_ctr, 1) &&
             cudaMallocHost((void**)&c->h_status, sizeof(Status)) == cudaSuccess &&
             cudaMallocHost((void**)&c->h_stats, sizeof(unsigned long long) * kStatCount) == cudaSuccess;
