@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-clustered", action="store_true", help="skip the clustered (Plummer) active-step comparison")
     ap.add_argument("--no-gresho", action="store_true", help="skip the integrated Gresho-Chan vortex steps")
     ap.add_argument("--no-kernel-shapes", action="store_true", help="skip the Wendland-kernel runs of the workload")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint (force backward) timing")
     ap.add_argument("--autotune", action="store_true", help="run the library autotuner before timing")
     return ap.parse_args()
 
@@ -382,6 +383,8 @@ def run_ours(args, rank, world, pg):
         res["gresho"] = run_gresho(dev)
     if not args.no_kernel_shapes and rank == 0:
         res["kernel_shapes"] = run_kernel_shapes(dev, d, peak_max)
+    if not args.no_adjoint and rank == 0:
+        res["adjoint"] = run_adjoint(dev)
     if rank == 0 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(d, ctx)
         res["errors_vs_fp64_oracle"] = errors_vs_oracle(d, graph.out, ctx)
@@ -641,6 +644,54 @@ def run_kernel_shapes(dev, d, peak_tflops, steps=30):
                      "status": list(ctx.sync_status())}
         del graph, ctx
     return out
+
+
+def run_adjoint(dev, steps=20):
+    """The adjoint of density + ghost + force (swift_gpu_force_backward) on the Kelvin-Helmholtz set.
+
+    kh(): 32 x (21 + 11) x 32 layers (32768 particles), vx = +-0.5, P = 2.5,
+    with a seeded random loss L = sum w.a + c du/dt. Per step: the forward
+    loops (build, density, force) and the backward passes, with h fixed
+    (h_mode 0: two gathers) and with h = h(x) solved by the h iteration
+    (h_mode 1: the h-adjoint and a third gather for the implicit-function term).
+    """
+    import numpy as np
+    import torch
+
+    from paper_2505_14538_b300 import _lib, ics, sph
+    d = ics.kh()
+    n = len(d["pos"])
+    rng = np.random.default_rng(2505)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev)
+    pos_h, vel_m, u = t(np.c_[d["pos"], d["h"]]), t(np.c_[d["vel"], d["m"]]), t(d["u"])
+    g4 = t(np.c_[rng.normal(size=(n, 3)), rng.normal(size=n)])
+    res = {"workload": f"kh32: Kelvin-Helmholtz slab, {n} particles (32 x (21 + 11) x 32 layers), vx = +-0.5, "
+                       "P = 2.5; loss weights N(0, 1)", "particles": n, "steps": steps}
+    for mode, flags in ((0, _lib.FLAG_NO_H_ITER), (1, 0)):
+        ctx = sph.Context(n, flags=flags, h_tol=1e-6, max_iter=40)
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps + 2)]
+        for k in range(steps + 2):  # the first two are warm-ups
+            e = ev[k]
+            e[0].record()
+            ctx.build_cells(pos_h)
+            ctx.density(pos_h, vel_m)
+            ctx.force(u)
+            e[1].record()
+            ctx.force_backward(g4, h_mode=mode)
+            e[2].record()
+            if k == 1:
+                torch.cuda.synchronize()
+                i0 = ctx.info()
+        torch.cuda.synchronize()
+        i1 = ctx.info()
+        code = ctx.sync_status()
+        fw = sum(ev[k][0].elapsed_time(ev[k][1]) for k in range(2, steps + 2)) / steps
+        bw = sum(ev[k][1].elapsed_time(ev[k][2]) for k in range(2, steps + 2)) / steps
+        pairs = (i1["interactions"][2] - i0["interactions"][2]) / steps  # force pairs of the forward call
+        res[f"h_mode_{mode}"] = {"forward_ms": fw, "backward_ms": bw, "force_pairs": pairs,
+                                 "backward_pairs_per_s": pairs / (bw * 1e-3), "status": list(code)}
+        del ctx
+    return res
 
 
 # algorithmic HBM bytes per particle of the integration kernels (loads + stores of their arrays)
