@@ -195,6 +195,15 @@ __device__ __forceinline__ unsigned spread3(unsigned v) {
   return v;
 }
 
+// 30-bit Morton code of a position inside its cell, from the fractions of
+// the cell width along each axis, in units of 1/1024 of the width.
+__device__ __forceinline__ unsigned morton_of(float fx, float fy, float fz) {
+  const unsigned qx = (unsigned)fminf(fmaxf(fx * 1024.0f, 0.0f), 1023.0f);
+  const unsigned qy = (unsigned)fminf(fmaxf(fy * 1024.0f, 0.0f), 1023.0f);
+  const unsigned qz = (unsigned)fminf(fmaxf(fz * 1024.0f, 0.0f), 1023.0f);
+  return spread3(qx) | (spread3(qy) << 1) | (spread3(qz) << 2);
+}
+
 // Cell id of every particle; with `cell_out` (adaptive leaves) the sort key
 // is instead the 30-bit Morton code of the position inside the cell (10 bits
 // per axis, x in the lowest bit of each 3-bit digit) and the cell id goes to
@@ -212,12 +221,14 @@ __global__ void k_cell_ids(const float4* __restrict__ pos_h, int n, const Grid* 
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     float4 p = pos_h[i];
     vals[i] = (unsigned)i;
-    if (!cell_out) {
+    {
       // FP32 first: t = x nc / L carries at most 3 roundings (< 2^-22 t), so
       // a fraction of t farther than 8 ulps from an integer floors as the FP64
-      // value does; closer ones (and positions outside [0, L)) take FP64.
+      // value does; closer ones, positions outside [0, L) and, for Morton
+      // codes, box sides other than 1 take FP64.
       const float xs[3] = {p.x, p.y, p.z};
       int cf[3];
+      float frs[3];
       bool ok = true;
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
@@ -227,9 +238,22 @@ __global__ void k_cell_ids(const float4* __restrict__ pos_h, int n, const Grid* 
         const float eta = 4.76837158203125e-7f * fmaxf(t, 1.0f);  // 8 * 2^-24
         ok = ok && xs[q] >= 0.0f && xs[q] < Lf[q] && fr > eta && fr < 1.0f - eta;
         cf[q] = min(max((int)fl, 0), (q == 0 ? nx : q == 1 ? ny : nz) - 1);
+        // Morton fraction (L = 1): x nc = t + lo exactly, and t - fl is
+        // exact, so one rounding gives the float of the exact fraction,
+        // as the FP64 path's float(x nc - c)
+        frs[q] = fr + fmaf(xs[q], ncf[q], -t);
+        ok = ok && (cell_out == nullptr || Lf[q] == 1.0f);
       }
       if (ok) {
-        keys[i] = (unsigned)(cf[0] + nx * (cf[1] + ny * cf[2]));
+        const unsigned cell = (unsigned)(cf[0] + nx * (cf[1] + ny * cf[2]));
+        if (cell_out) {
+          const unsigned m = morton_of(frs[0], frs[1], frs[2]);
+          keys[i] = m;
+          morton_out[i] = m;
+          cell_out[i] = cell;
+        } else {
+          keys[i] = cell;
+        }
         continue;
       }
     }
@@ -250,12 +274,8 @@ __global__ void k_cell_ids(const float4* __restrict__ pos_h, int n, const Grid* 
     cz = min(max(cz, 0), nz - 1);
     const unsigned cell = (unsigned)(cx + nx * (cy + ny * cz));
     if (cell_out) {
-      // position inside the cell in units of 1/1024 of its width
-      // (the fraction is exact in FP64; its FP32 rounding only orders particles)
-      const unsigned qx = (unsigned)fminf(fmaxf((float)(tx - cx) * 1024.0f, 0.0f), 1023.0f);
-      const unsigned qy = (unsigned)fminf(fmaxf((float)(ty - cy) * 1024.0f, 0.0f), 1023.0f);
-      const unsigned qz = (unsigned)fminf(fmaxf((float)(tz - cz) * 1024.0f, 0.0f), 1023.0f);
-      const unsigned m = spread3(qx) | (spread3(qy) << 1) | (spread3(qz) << 2);
+      // the fraction is exact in FP64; its FP32 rounding only orders particles
+      const unsigned m = morton_of((float)(tx - cx), (float)(ty - cy), (float)(tz - cz));
       keys[i] = m;
       morton_out[i] = m;
       cell_out[i] = cell;

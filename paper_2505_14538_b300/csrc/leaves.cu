@@ -10,14 +10,15 @@
 //                  search of the level's Morton digit inside the node's
 //                  range), any other node is a leaf
 //   k_leaf_number  leaf indices from a scan of the leaf flags
-//   k_leaf_finish  one warp per leaf reduces its particles' bounding box and
+//   k_leaf_finish  8 lanes per leaf reduce its particles' bounding box and
 //                  largest h; the boxes and reaches of the inner nodes follow
 //                  bottom-up (the last child to finish completes its parent)
-//   k_leaf_walk    one warp per leaf walks the trees of the 27 neighbour
-//                  cells (periodic images included) with a shared-memory
-//                  stack, descends into nodes whose bounding box comes within
-//                  the larger reach (kernel_gamma * h_cap) of the two sides,
-//                  and writes its neighbour leaves as one contiguous list
+//   k_leaf_walk    one warp per parent of leaves walks the trees of the 27
+//                  neighbour cells (periodic images included) with a
+//                  shared-memory stack, descends into nodes whose bounding box
+//                  comes within the larger reach (kernel_gamma * h_cap) of the
+//                  two sides, and filters that list for each of its leaves,
+//                  which get their neighbour leaves as one contiguous list
 //
 // Every pair that any loop may need is covered: a pair (i, j) is a candidate
 // only when its FP32 r^2 is below max(H_i, H_j)^2 plus the guard band, and
@@ -178,38 +179,44 @@ __global__ void k_leaf_number(const unsigned* __restrict__ scan, int node_cap, i
   if (blockIdx.x == 0 && threadIdx.x == 0) tctr[kTreeLeaves] = (int)scan[node_cap];
 }
 
-// One warp per leaf: bounding box and largest h of its particles; then up
-// the tree, the last child to finish writes its parent's box (the union of
-// the children's) and reach (the largest of theirs), and carries on.
+// A group of 8 lanes per leaf (leaves hold about leaf_max / 4 particles on
+// average, so a warp works on four at once): bounding box and largest h of
+// its particles; then up the tree, the last child to finish writes its
+// parent's box (the union of the children's, at most 8) and reach (the
+// largest of theirs), and carries on. The groups of a warp run their loops
+// independently; every shuffle names only its group's lanes.
+constexpr int kFinishLanes = 8;
 __global__ void __launch_bounds__(kTreeThreads) k_leaf_finish(TreeArgs a) {
   const unsigned lane = lane_id();
-  const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const unsigned gl = lane & (kFinishLanes - 1);
+  const unsigned gmask = 0xffu << (lane & ~(unsigned)(kFinishLanes - 1));
+  const int group = (int)((blockIdx.x * blockDim.x + threadIdx.x) / kFinishLanes);
+  const int ngroups = (int)((gridDim.x * blockDim.x) / kFinishLanes);
   const float hcap_cell = a.grid->hcap;
   const float inf = __int_as_float(0x7f800000);
   const int nleaves = a.tctr[kTreeLeaves];
-  for (int li = gwarp; li < nleaves; li += nwarps) {
+  for (int li = group; li < nleaves; li += ngroups) {
     int v = a.leaf_node[li];
     const int2 r = a.node_range[v];
     float lx = inf, ly = inf, lz = inf, hx = -inf, hy = -inf, hz = -inf, hm = 0.0f;
-    for (int k = r.x + (int)lane; k < r.y; k += 32) {
+    for (int k = r.x + (int)gl; k < r.y; k += kFinishLanes) {
       const float4 p = a.pos[k];
       lx = fminf(lx, p.x); ly = fminf(ly, p.y); lz = fminf(lz, p.z);
       hx = fmaxf(hx, p.x); hy = fmaxf(hy, p.y); hz = fmaxf(hz, p.z);
       hm = fmaxf(hm, p.w);
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      lx = fminf(lx, __shfl_xor_sync(kFull, lx, o));
-      ly = fminf(ly, __shfl_xor_sync(kFull, ly, o));
-      lz = fminf(lz, __shfl_xor_sync(kFull, lz, o));
-      hx = fmaxf(hx, __shfl_xor_sync(kFull, hx, o));
-      hy = fmaxf(hy, __shfl_xor_sync(kFull, hy, o));
-      hz = fmaxf(hz, __shfl_xor_sync(kFull, hz, o));
-      hm = fmaxf(hm, __shfl_xor_sync(kFull, hm, o));
+    for (int o = kFinishLanes / 2; o > 0; o >>= 1) {
+      lx = fminf(lx, __shfl_xor_sync(gmask, lx, o, kFinishLanes));
+      ly = fminf(ly, __shfl_xor_sync(gmask, ly, o, kFinishLanes));
+      lz = fminf(lz, __shfl_xor_sync(gmask, lz, o, kFinishLanes));
+      hx = fmaxf(hx, __shfl_xor_sync(gmask, hx, o, kFinishLanes));
+      hy = fmaxf(hy, __shfl_xor_sync(gmask, hy, o, kFinishLanes));
+      hz = fmaxf(hz, __shfl_xor_sync(gmask, hz, o, kFinishLanes));
+      hm = fmaxf(hm, __shfl_xor_sync(gmask, hm, o, kFinishLanes));
     }
     const float hcap = fminf(hcap_cell, (1.0f + a.margin) * hm);
-    if (lane == 0) {
+    if (gl == 0) {
       a.leaf_range[li] = r;
       a.leaf_hcap[li] = hcap;
       a.node[2 * v] = make_float4(lx, ly, lz, a.kg * hcap);
@@ -217,7 +224,7 @@ __global__ void __launch_bounds__(kTreeThreads) k_leaf_finish(TreeArgs a) {
     }
     for (;;) {
       int p = -1, done = 0, link = 0;
-      if (lane == 0) {
+      if (gl == 0) {
         p = a.node_parent[v];
         if (p >= 0) {
           __threadfence();  // this node's record before the count
@@ -225,29 +232,29 @@ __global__ void __launch_bounds__(kTreeThreads) k_leaf_finish(TreeArgs a) {
           link = a.node_link[p];
         }
       }
-      p = __shfl_sync(kFull, p, 0);
-      done = __shfl_sync(kFull, done, 0);
-      link = __shfl_sync(kFull, link, 0);
+      p = __shfl_sync(gmask, p, 0, kFinishLanes);
+      done = __shfl_sync(gmask, done, 0, kFinishLanes);
+      link = __shfl_sync(gmask, link, 0, kFinishLanes);
       const int nch = link >> kLinkShift;
       if (p < 0 || done != nch - 1) break;  // a sibling is still running: it finishes the parent
       __threadfence();
       const int first = link & kLinkMask;
       float4 cl = make_float4(inf, inf, inf, 0.0f), ch = make_float4(-inf, -inf, -inf, 0.0f);
-      if ((int)lane < nch) {
-        cl = __ldcg(&a.node[2 * (first + (int)lane)]);  // from L2: written by other warps
-        ch = __ldcg(&a.node[2 * (first + (int)lane) + 1]);
+      if ((int)gl < nch) {
+        cl = __ldcg(&a.node[2 * (first + (int)gl)]);  // from L2: written by other warps
+        ch = __ldcg(&a.node[2 * (first + (int)gl) + 1]);
       }
 #pragma unroll
-      for (int o = 4; o > 0; o >>= 1) {
-        cl.x = fminf(cl.x, __shfl_xor_sync(kFull, cl.x, o));
-        cl.y = fminf(cl.y, __shfl_xor_sync(kFull, cl.y, o));
-        cl.z = fminf(cl.z, __shfl_xor_sync(kFull, cl.z, o));
-        cl.w = fmaxf(cl.w, __shfl_xor_sync(kFull, cl.w, o));
-        ch.x = fmaxf(ch.x, __shfl_xor_sync(kFull, ch.x, o));
-        ch.y = fmaxf(ch.y, __shfl_xor_sync(kFull, ch.y, o));
-        ch.z = fmaxf(ch.z, __shfl_xor_sync(kFull, ch.z, o));
+      for (int o = kFinishLanes / 2; o > 0; o >>= 1) {
+        cl.x = fminf(cl.x, __shfl_xor_sync(gmask, cl.x, o, kFinishLanes));
+        cl.y = fminf(cl.y, __shfl_xor_sync(gmask, cl.y, o, kFinishLanes));
+        cl.z = fminf(cl.z, __shfl_xor_sync(gmask, cl.z, o, kFinishLanes));
+        cl.w = fmaxf(cl.w, __shfl_xor_sync(gmask, cl.w, o, kFinishLanes));
+        ch.x = fmaxf(ch.x, __shfl_xor_sync(gmask, ch.x, o, kFinishLanes));
+        ch.y = fmaxf(ch.y, __shfl_xor_sync(gmask, ch.y, o, kFinishLanes));
+        ch.z = fmaxf(ch.z, __shfl_xor_sync(gmask, ch.z, o, kFinishLanes));
       }
-      if (lane == 0) {
+      if (gl == 0) {
         a.node[2 * p] = cl;
         a.node[2 * p + 1] = make_float4(ch.x, ch.y, ch.z, __int_as_float(link));
       }
@@ -262,6 +269,7 @@ struct WalkArgs {
   const float4* node;
   const int2* leaf_range;
   const int* leaf_node;
+  const int* node_parent;
   int* tctr;               // list entries reserved so far at kTreeEntries, tickets at kTreeTicket
   int2* nbr_span;          // per leaf: (first entry, length)
   unsigned* nbr;
@@ -271,19 +279,37 @@ struct WalkArgs {
 constexpr int kOutBuf = 512;      // list entries a warp keeps in shared memory before reserving
 constexpr int kWalkChunk = 8;     // leaves per ticket
 constexpr size_t kWalkSmemBytes = sizeof(unsigned) * kWalkWarps * (kStack + kOutBuf);
+static_assert(kOutBuf / 32 * 8 + 16 * 4 <= kStack, "the stack holds the masks and boxes of a shared walk");
+static_assert((kOutBuf / 32 * 8) % 4 == 0, "the siblings' boxes start 16-byte aligned");
 
-// Walk of the trees around leaf li: every leaf (with periodic image) whose
-// box comes within the larger reach; entry t of the list goes to out[t] when
-// t < out_cap. Returns the list length; `overflow` when the stack ran out.
-__device__ __forceinline__ int walk_leaf(const WalkArgs& a, const Grid& g, int li, unsigned* st, unsigned* out,
-                                         int out_cap, bool& overflow) {
+// Whether node b's box (shifted by the periodic image `code`) comes within
+// the larger reach of the box (la, ha) and b's own: the particle test is
+// r2 < H^2 + band(H) with H <= reach, evaluated with the same rounded
+// operations, and 2^-12 extra slack. The test is monotone: a box inside
+// another, with no larger reach, never passes where the larger one fails.
+__device__ __forceinline__ bool box_near(const float4& la, const float4& ha, float4 lb, float4 hb, unsigned code,
+                                         const float* L, float Lmax) {
+  shift_j(code, L, lb.x, lb.y, lb.z);
+  shift_j(code, L, hb.x, hb.y, hb.z);
+  const float gx = fmaxf(fmaxf(lb.x - ha.x, la.x - hb.x), 0.0f);
+  const float gy = fmaxf(fmaxf(lb.y - ha.y, la.y - hb.y), 0.0f);
+  const float gz = fmaxf(fmaxf(lb.z - ha.z, la.z - hb.z), 0.0f);
+  const float R = fmaxf(la.w, lb.w);
+  return r2_of(gx, gy, gz) < (R * R + band_of(R, Lmax)) * 1.000244140625f;
+}
+
+// Walk of the trees of the 27 cells around `cell` for the box (la, ha):
+// every leaf (with periodic image) that passes box_near, and whose
+// ancestors do; entry t of the list goes to out[t] when t < out_cap, as
+// leaf index | code << kIndexBits, or with `as_node` as its node index
+// instead. Returns the list length; `overflow` when the stack ran out.
+__device__ __forceinline__ int walk_box(const WalkArgs& a, const Grid& g, int cell, const float4& la,
+                                        const float4& ha, unsigned* st, unsigned* out, int out_cap, bool as_node,
+                                        bool& overflow) {
   const unsigned lane = lane_id();
   const float L[3] = {g.L[0], g.L[1], g.L[2]};
   const float Lmax = fmaxf(L[0], fmaxf(L[1], L[2]));
   const int nx = g.nc[0], ny = g.nc[1], nz = g.nc[2];
-  const int va = a.leaf_node[li];
-  const float4 la = a.node[2 * va], ha = a.node[2 * va + 1];
-  const int cell = (int)a.skeys[a.leaf_range[li].x];
   __syncwarp();
   if (lane < 27) {
     const int cx = cell % nx, cy = (cell / nx) % ny, cz = cell / (nx * ny);
@@ -308,25 +334,18 @@ __device__ __forceinline__ int walk_leaf(const WalkArgs& a, const Grid& g, int l
     bool pass = false;
     int link = 0;
     const unsigned code = e >> kIndexBits;
+    const int b = (int)(e & kIndexMask);
     if ((int)lane < take) {
-      const int b = (int)(e & kIndexMask);
-      float4 lb = a.node[2 * b], hb = a.node[2 * b + 1];
+      const float4 lb = a.node[2 * b], hb = a.node[2 * b + 1];
       link = __float_as_int(hb.w);
-      shift_j(code, L, lb.x, lb.y, lb.z);
-      shift_j(code, L, hb.x, hb.y, hb.z);
-      const float gx = fmaxf(fmaxf(lb.x - ha.x, la.x - hb.x), 0.0f);
-      const float gy = fmaxf(fmaxf(lb.y - ha.y, la.y - hb.y), 0.0f);
-      const float gz = fmaxf(fmaxf(lb.z - ha.z, la.z - hb.z), 0.0f);
-      const float R = fmaxf(la.w, lb.w);
-      // the particle test is r2 < H^2 + band(H) with H <= R; 2^-12 extra slack
-      pass = r2_of(gx, gy, gz) < (R * R + band_of(R, Lmax)) * 1.000244140625f;
+      pass = box_near(la, ha, lb, hb, code, L, Lmax);
     }
     const int nch = link >> kLinkShift;  // empty cells never pass
     const bool is_leaf = pass && nch == 0;
     const unsigned lm = __ballot_sync(kFull, is_leaf);
     if (is_leaf) {
       const int t = count + __popc(lm & ((1u << lane) - 1u));
-      if (t < out_cap) out[t] = (unsigned)(link & kLinkMask) | (code << kIndexBits);
+      if (t < out_cap) out[t] = (unsigned)(as_node ? b : (link & kLinkMask)) | (code << kIndexBits);
     }
     count += __popc(lm);
     const int nk = pass ? nch : 0;
@@ -349,17 +368,48 @@ __device__ __forceinline__ int walk_leaf(const WalkArgs& a, const Grid& g, int l
   return count;
 }
 
-// Warps take kWalkChunk leaves per ticket; per leaf: walk once into shared
-// memory, reserve the list's place with one atomic and copy it out (a list
-// longer than the buffer is walked a second time straight into its place).
-// Each list is contiguous and in walk order; where the lists lie does not
-// change any result. A leaf whose walk ran out of stack gets no list.
+// One leaf's own walk; the list is reserved with one atomic and copied out
+// (a list longer than the buffer is walked a second time straight into its
+// place). A leaf whose walk ran out of stack gets no list.
+__device__ __forceinline__ void walk_one_leaf(const WalkArgs& a, const Grid& g, int li, int cell, unsigned* st,
+                                              unsigned* buf) {
+  const unsigned lane = lane_id();
+  const int va = a.leaf_node[li];
+  const float4 la = a.node[2 * va], ha = a.node[2 * va + 1];
+  bool overflow = false;
+  const int count = walk_box(a, g, cell, la, ha, st, buf, kOutBuf, false, overflow);
+  int base = 0;
+  if (lane == 0 && !overflow) base = atomicAdd(&a.tctr[kTreeEntries], count);
+  base = __shfl_sync(kFull, base, 0);
+  const int room = a.nbr_cap - base;  // entries of this list that fit (a list past the cap is unused)
+  if (!overflow) {
+    if (count <= kOutBuf) {
+      for (int t = (int)lane; t < count && t < room; t += 32) a.nbr[base + t] = buf[t];
+    } else if (room > 0) {
+      walk_box(a, g, cell, la, ha, st, a.nbr + base, room, false, overflow);
+    }
+  }
+  if (lane == 0) a.nbr_span[li] = overflow ? make_int2(0, 0x7fffffff) : make_int2(base, count);
+}
+
+// Warps take kWalkChunk leaves per ticket. The leaves of one parent node
+// have consecutive indices (leaves are numbered in node order, and a node's
+// children are consecutive nodes), and the first of them walks for all: one
+// walk with the parent's box and reach, whose list (in shared memory) holds
+// every leaf any sibling's own walk would find, since the parent's box
+// contains theirs and its reach is no smaller, and box_near is monotone.
+// Each sibling's list is that list filtered by box_near against its own box:
+// the same set its own walk gives, in the parent walk's order. A parent list
+// longer than the buffer falls back to a walk per leaf. Each list is
+// contiguous; where the lists lie does not change any result.
 __global__ void __launch_bounds__(kWalkThreads) k_leaf_walk(WalkArgs a) {
   extern __shared__ __align__(16) unsigned wsmem[];
   unsigned* st = wsmem + (threadIdx.x >> 5) * (kStack + kOutBuf);
   unsigned* buf = st + kStack;
   const unsigned lane = lane_id();
   const Grid& g = *a.grid;
+  const float L[3] = {g.L[0], g.L[1], g.L[2]};
+  const float Lmax = fmaxf(L[0], fmaxf(L[1], L[2]));
   const int nleaves = a.tctr[kTreeLeaves];
   for (;;) {
     int l0 = 0;
@@ -367,20 +417,86 @@ __global__ void __launch_bounds__(kWalkThreads) k_leaf_walk(WalkArgs a) {
     l0 = __shfl_sync(kFull, l0, 0);
     if (l0 >= nleaves) break;
     for (int li = l0; li < min(l0 + kWalkChunk, nleaves); ++li) {
+      const int p = a.node_parent[a.leaf_node[li]];
+      if (p >= 0 && li > 0 && a.node_parent[a.leaf_node[li - 1]] == p) continue;  // a sibling walks for it
+      const int cell = (int)a.skeys[a.leaf_range[li].x];
+      // siblings: the leaves li, li + 1, ... with parent p (at most 8)
+      int m = 1;
+      if (p >= 0) {
+        const int lj = li + (int)lane;
+        const bool sib = lane < 8 && lj < nleaves && a.node_parent[a.leaf_node[lj]] == p;
+        m = __ffs(~__ballot_sync(kFull, sib)) - 1;
+      }
+      if (m == 1) {
+        walk_one_leaf(a, g, li, cell, st, buf);
+        continue;
+      }
       bool overflow = false;
-      const int count = walk_leaf(a, g, li, st, buf, kOutBuf, overflow);
+      const float4 lp = a.node[2 * p], hp = a.node[2 * p + 1];
+      const int count = walk_box(a, g, cell, lp, hp, st, buf, kOutBuf, true, overflow);
+      if (overflow || count > kOutBuf) {
+        for (int c = 0; c < m; ++c) walk_one_leaf(a, g, li + c, cell, st, buf);
+        continue;
+      }
+      // one pass over the parent's list: lane t tests entry t against every
+      // sibling's box; the ballot of sibling c for chunk q goes to
+      // st[q * 8 + c] (the stack is empty now), and entry t becomes the
+      // leaf index | code it is written out as
+      const int nq = (count + 31) / 32;
+      float4* sib_box = reinterpret_cast<float4*>(st + kOutBuf / 32 * 8);  // the siblings' boxes
+      if ((int)lane < 2 * m) sib_box[lane] = a.node[2 * a.leaf_node[li + (int)(lane >> 1)] + (int)(lane & 1u)];
+      __syncwarp();
+      for (int q = 0; q < nq; ++q) {
+        const int t = q * 32 + (int)lane;
+        unsigned outv = 0;
+        float4 lb = make_float4(0.0f, 0.0f, 0.0f, 0.0f), hb = lb;
+        unsigned code = 0;
+        const bool on = t < count;
+        if (on) {
+          const unsigned e = buf[t];
+          const int b = (int)(e & kIndexMask);
+          code = e >> kIndexBits;
+          lb = a.node[2 * b];
+          hb = a.node[2 * b + 1];
+          outv = (unsigned)(__float_as_int(hb.w) & kLinkMask) | (code << kIndexBits);
+        }
+        for (int c = 0; c < m; ++c) {
+          const unsigned pm = __ballot_sync(kFull, on && box_near(sib_box[2 * c], sib_box[2 * c + 1], lb, hb, code,
+                                                                  L, Lmax));
+          if (lane == 0) st[q * 8 + c] = pm;
+        }
+        __syncwarp();
+        if (on) buf[t] = outv;
+      }
+      __syncwarp();
+      // list lengths, one reservation for the family, then the lists
+      int len = 0;
+      if ((int)lane < m)
+        for (int q = 0; q < nq; ++q) len += __popc(st[q * 8 + (int)lane]);
+      int incl = len;
+#pragma unroll
+      for (int o = 1; o < 8; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, incl, o);
+        if ((int)lane >= o) incl += y;
+      }
+      const int total = __shfl_sync(kFull, incl, 7);
       int base = 0;
-      if (lane == 0 && !overflow) base = atomicAdd(&a.tctr[kTreeEntries], count);
+      if (lane == 0) base = atomicAdd(&a.tctr[kTreeEntries], total);
       base = __shfl_sync(kFull, base, 0);
-      const int room = a.nbr_cap - base;  // entries of this list that fit (a list past the cap is unused)
-      if (!overflow) {
-        if (count <= kOutBuf) {
-          for (int t = (int)lane; t < count && t < room; t += 32) a.nbr[base + t] = buf[t];
-        } else if (room > 0) {
-          walk_leaf(a, g, li, st, a.nbr + base, room, overflow);
+      if ((int)lane < m) a.nbr_span[li + (int)lane] = make_int2(base + incl - len, len);
+      const unsigned lt = (1u << lane) - 1u;
+      for (int c = 0; c < m; ++c) {
+        int o = base + __shfl_sync(kFull, incl - len, c);
+        for (int q = 0; q < nq; ++q) {
+          const unsigned pm = st[q * 8 + c];
+          if ((pm >> lane) & 1u) {
+            const int dst = o + __popc(pm & lt);
+            if (dst < a.nbr_cap) a.nbr[dst] = buf[q * 32 + (int)lane];
+          }
+          o += __popc(pm);
         }
       }
-      if (lane == 0) a.nbr_span[li] = overflow ? make_int2(0, 0x7fffffff) : make_int2(base, count);
+      __syncwarp();
     }
   }
 }
@@ -438,6 +554,7 @@ int leaves_build(Ctx* c, const float4* pos_h, cudaStream_t s) {
   w.node = c->d_node;
   w.leaf_range = c->d_leaf_range;
   w.leaf_node = c->d_leaf_node;
+  w.node_parent = c->d_node_parent;
   w.tctr = c->d_tree_ctr;
   w.nbr_span = c->d_nbr_span;
   w.nbr = c->d_nbr;

@@ -207,11 +207,14 @@ __device__ __forceinline__ void dens_item(const DensArgs& a, const DensOp& op, c
     if (a.item_nl && item_idx >= 0)
       keep_list(a, w, item_idx, !retry && !a.nb.adaptive && g.hcap_from_cells, cnt, lm.live);
     bool done = !lm.live || retry;
-    // a step whose relative residual |n h^3 - eta^3| / eta^3 is below this
-    // leaves, by Newton's quadratic convergence, a residual well inside
-    // h_tol: the walk that would only confirm it is skipped
+    // a step whose relative residual G = |n h^3 - eta^3| / eta^3 is below
+    // this leaves, by Newton's quadratic convergence, a residual well inside
+    // h_tol: the walk that would only confirm it is skipped. With n nearly
+    // constant in h the next residual is about (2/3) G^2 (0.72-0.84 G^2 on a
+    // jittered lattice), so 0.6 sqrt(h_tol) leaves at most 0.36 c h_tol; a
+    // miss only costs the particle another pass, the final sums verify it
     const float e3 = (float)a.ph.eta3;
-    const float pred = 0.3f * sqrtf((float)a.ph.h_tol);
+    const float pred = 0.6f * sqrtf((float)a.ph.h_tol);
     for (int iter = 0;; ++iter) {
       float ns = 0.0f, nc = 0.0f, dn = 0.0f;
       unsigned np = 0;
@@ -327,8 +330,8 @@ __global__ void __launch_bounds__(kLoopThreads, 5) k_density(DensArgs a) {
     }
   }
   // ---- active work items (runs of <= kItemMax active particles of a cell or
-  // leaf). In round r, warp w of block b takes cell r * 8G + 8b + w (G blocks,
-  // 8 warps a block); the block reserves its share of the round with one
+  // leaf). In round r, warp w of block b takes cell r * 4G + 4b + w (G blocks,
+  // 4 warps a block); the block reserves its share of the round with one
   // atomic per counter. Rounds run nearly in step across the grid, so the
   // work queue comes out close to ascending cell order: the warps that later
   // take neighbouring tickets work on neighbouring cells (or leaves) and share
