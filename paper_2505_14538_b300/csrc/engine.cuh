@@ -33,7 +33,9 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr unsigned kNoEntry = 0xffffffffu;  // padding of a stored candidate list
 
 struct WarpSmem {
-  unsigned list[kCap * 32];  // lane-private lists, entry t of lane l at [t * 32 + l]
+  // lane-private lists, entry t of lane l at [t * 32 + l]; row kCap takes the
+  // stores of collect_item's tests that miss once a list is full
+  unsigned list[(kCap + 1) * 32];
   float4 stage[32];          // current chunk: shifted position + per-loop w
   unsigned stage_idx[32];    // current chunk: j | shift code << kIndexBits
   int seg_start[32];
@@ -351,16 +353,15 @@ __device__ __forceinline__ int collect_item(const Grid& g, const Nbr& nb, const 
 #pragma unroll 4
       for (int kk = 0; kk < nk; ++kk) {
         const int k = (kk << lsh) + s;
+        // branch-free: every test stores its entry at the list's end, and
+        // a hit keeps it (a miss is overwritten by the next store)
         const float4 c = w.stage[k];
+        const unsigned ix = w.stage_idx[k];
         const float dx = xi - c.x, dy = yi - c.y, dz = zi - c.z;
-        if (r2_of(dx, dy, dz) < R2) {
-          if (cnt < kCap) {
-            w.list[cnt * 32 + lane] = w.stage_idx[k];
-            ++cnt;
-          } else {
-            ovf = true;
-          }
-        }
+        const bool hit = r2_of(dx, dy, dz) < R2;
+        w.list[min(cnt, kCap) * 32 + lane] = ix;
+        ovf = ovf || (hit && cnt >= kCap);
+        cnt += (hit && cnt < kCap) ? 1 : 0;
       }
       ncand += (unsigned)nk;
     }

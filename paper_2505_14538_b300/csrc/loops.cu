@@ -123,24 +123,24 @@ __device__ __forceinline__ void number_walk(const DensOp& op, const DensOp::I& I
     for (int q = 0; q < 4; ++q) pj[q] = op.pos[e[q] & kIndexMask];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      if (t0 + q < cnt) {
-        const int j = (int)(e[q] & kIndexMask);
-        float xj = pj[q].x, yj = pj[q].y, zj = pj[q].z;
-        shift_j(e[q] >> kIndexBits, op.L, xj, yj, zj);
-        const float dx = I.x - xj, dy = I.y - yj, dz = I.z - zj;
-        const float r2 = r2_of(dx, dy, dz);
-        if (r2 < I.H2hi) {
-          const float invr = r2 > 0.0f ? rsqrtf(r2) : 0.0f;
-          const float r = r2 * invr;
-          float wq, dwq;
-          kshape(op.kernel, r * I.invH, wq, dwq);
-          const float W = I.c3 * wq;
-          if (op.compensated) two_sum_acc(ns, nc, W);
-          else ns += W;
-          dn += fmaf(r, I.c4 * dwq, 3.0f * W);
-          npairs += (j != I.k) ? 1u : 0u;
-        }
-      }
+      // branch-free: W and dW/dr vanish beyond the support (so entries of
+      // the list outside H add exact zeros), and padding is masked
+      const bool valid = t0 + q < cnt;
+      const int j = (int)(e[q] & kIndexMask);
+      float xj = pj[q].x, yj = pj[q].y, zj = pj[q].z;
+      shift_j(e[q] >> kIndexBits, op.L, xj, yj, zj);
+      const float dx = I.x - xj, dy = I.y - yj, dz = I.z - zj;
+      const float r2 = r2_of(dx, dy, dz);
+      const float invr = r2 > 0.0f ? rsqrtf(r2) : 0.0f;
+      const float r = r2 * invr;
+      float wq, dwq;
+      kshape(op.kernel, r * I.invH, wq, dwq);
+      const float W = valid ? I.c3 * wq : 0.0f;
+      const float D = valid ? fmaf(r, I.c4 * dwq, 3.0f * W) : 0.0f;
+      if (op.compensated) two_sum_acc(ns, nc, W);
+      else ns += W;
+      dn += D;
+      npairs += (valid && r2 < I.H2hi && j != I.k) ? 1u : 0u;
     }
   }
 }

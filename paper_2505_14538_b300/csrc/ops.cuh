@@ -39,16 +39,17 @@ struct DensOp {
     shift_j(code, L, xj, yj, zj);
     const float dx = i.x - xj, dy = i.y - yj, dz = i.z - zj;
     const float r2 = r2_of(dx, dy, dz);
-    if (r2 >= i.H2lo) {
-      if (r2 >= i.H2hi) return;
-      if (!(exact_r2(i.x, i.y, i.z, pj.x, pj.y, pj.z, L[0], L[1], L[2]) < exact_H2(kg, i.h))) return;
-    }
+    // j is in N_i: below the guard band in FP32, or by the exact FP64
+    // decision inside it; out-of-set pairs add exact zeros (W = dW = 0)
+    bool in = r2 < i.H2lo;
+    if (!in && r2 < i.H2hi)
+      in = exact_r2(i.x, i.y, i.z, pj.x, pj.y, pj.z, L[0], L[1], L[2]) < exact_H2(kg, i.h);
     const float invr = r2 > 0.0f ? rsqrtf(r2) : 0.0f;
     const float r = r2 * invr;
     float w, dw;
     kshape(kernel, r * i.invH, w, dw);
-    const float W = i.c3 * w;
-    const float dW = i.c4 * dw;
+    const float W = in ? i.c3 * w : 0.0f;
+    const float dW = in ? i.c4 * dw : 0.0f;
     const float mj = vj.w;
     if (compensated) {
       two_sum_acc(i.ns, i.nc, W);
@@ -66,7 +67,7 @@ struct DensOp {
     i.cx = fmaf(-g, fmaf(dvy, dz, -dvz * dy), i.cx);
     i.cy = fmaf(-g, fmaf(dvz, dx, -dvx * dz), i.cy);
     i.cz = fmaf(-g, fmaf(dvx, dy, -dvy * dx), i.cz);
-    i.count += (j != i.k) ? 1u : 0u;
+    i.count += (in && j != i.k) ? 1u : 0u;
   }
 };
 
