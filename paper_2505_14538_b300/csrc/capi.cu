@@ -152,7 +152,7 @@ int swift_gpu_create(swift_gpu_ctx** out, const swift_gpu_params* p, int64_t n_m
   int64_t nbr_cap = 48 * n > ((int64_t)1 << 22) ? 48 * n : ((int64_t)1 << 22);  // at least 16 MB of lists
   c->nbr_cap = (int)(nbr_cap < (int64_t)INT32_MAX ? nbr_cap : (int64_t)INT32_MAX);
   c->red_blocks = c->num_sms * 32;
-  bool ok = dalloc(&c->d_status, 1) && dalloc(&c->d_grid, 1) && dalloc(&c->d_hmax_bits, 1) &&
+  bool ok = dalloc(&c->d_status, 1) && dalloc(&c->d_grid, 1) && dalloc(&c->d_hmax_bits, kHmaxWords) &&
             dalloc(&c->d_keys[0], n) && dalloc(&c->d_keys[1], n) && dalloc(&c->d_vals[0], n) &&
             dalloc(&c->d_vals[1], n) && dalloc(&c->d_hist, 256 * nb) &&
             dalloc(&c->d_scan_tmp, scan_tiles_needed(scan_m) + 1) && dalloc(&c->d_cell_start, ncells_max + 1) &&

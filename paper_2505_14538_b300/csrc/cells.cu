@@ -2,11 +2,12 @@
 // (Sec. 2.2, Fig. 3: cubic cells, self and pair interactions) and the stable
 // sort of particles by cell id, all without host synchronisation.
 //
-//   k_scan_h       max of h, NaN / h <= 0 checks
-//   k_grid_setup   nc, widths, h cap, key bits (one thread)
+//   k_scan_h       max of h, NaN / h <= 0 checks; its last block sets up the
+//                  grid: nc, widths, h cap, key bits
 //   k_cell_ids     FP64 cell id per particle (wrap, floor(x nc / L), clamp);
 //                  with adaptive leaves also the Morton code inside the cell,
-//                  sorted on first so that each cell ends in Morton order
+//                  sorted on first so that each cell ends in Morton order;
+//                  per radix tile, the counts of the first pass
 //   radix passes   LSD radix sort of (cell id, original index), 8-bit digits,
 //                  stable, so ties keep the input order
 //   k_cell_start   start offset of every cell (empty cells included)
@@ -131,22 +132,11 @@ void exclusive_scan(Ctx* c, const unsigned* in, unsigned* out, int m, unsigned* 
 }
 
 // ------------------------------------------------------------- grid setup
-__global__ void k_scan_h(const float4* __restrict__ pos_h, int n, float L0, float L1, float L2,
-                         unsigned* __restrict__ hmax_bits, Status* st) {
-  float hm = 0.0f;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    float4 p = pos_h[i];
-    bool bad = !(isfinite(p.x) && isfinite(p.y) && isfinite(p.z) && isfinite(p.w)) || !(p.w > 0.0f);
-    if (bad) set_error(st, SWIFT_GPU_ERR_ARG);
-    else hm = fmaxf(hm, p.w);
-  }
-  for (int o = 16; o > 0; o >>= 1) hm = fmaxf(hm, __shfl_xor_sync(0xffffffffu, hm, o));
-  if ((threadIdx.x & 31) == 0) atomicMax(hmax_bits, __float_as_uint(hm));  // h > 0: bits order like values
-}
-
-__global__ void k_grid_setup(const unsigned* __restrict__ hmax_bits, Grid* g, Phys ph, float margin,
-                             float min_width, int nc_cap, int host_passes, Status* st) {
-  float hmax = __uint_as_float(*hmax_bits);
+// Grid of the build from the largest h: nc per axis (cells no narrower than
+// the support of the largest h, at least 3, at most nc_cap), widths, the h
+// cap the cells allow, and the radix passes the cell ids need.
+__device__ void grid_setup(float hmax, Grid* g, const Phys& ph, float margin, float min_width, int nc_cap,
+                           int host_passes, Status* st) {
   float want = fmaxf(min_width, (1.0f + margin) * ph.kg * hmax);
   int nct = 1;
   for (int a = 0; a < 3; ++a) {
@@ -185,6 +175,38 @@ __global__ void k_grid_setup(const unsigned* __restrict__ hmax_bits, Grid* g, Ph
   g->sort_start = (host_passes & 1) ^ (live & 1);
 }
 
+// Largest h (NaN / h <= 0 rejected) into hm[0]; the last block to finish
+// (counted in hm[1]) sets up the grid from it. hm starts zeroed.
+__global__ void k_scan_h(const float4* __restrict__ pos_h, int n, unsigned* hm_words, Grid* g, Phys ph, float margin,
+                         float min_width, int nc_cap, int host_passes, Status* st) {
+  __shared__ bool s_last;
+  float hm = 0.0f;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    float4 p = pos_h[i];
+    bool bad = !(isfinite(p.x) && isfinite(p.y) && isfinite(p.z) && isfinite(p.w)) || !(p.w > 0.0f);
+    if (bad) set_error(st, SWIFT_GPU_ERR_ARG);
+    else hm = fmaxf(hm, p.w);
+  }
+  for (int o = 16; o > 0; o >>= 1) hm = fmaxf(hm, __shfl_xor_sync(0xffffffffu, hm, o));
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&hm_words[0], __float_as_uint(hm));  // h > 0: bits order like values
+    __threadfence();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&hm_words[1], 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (s_last && threadIdx.x == 0) {
+    __threadfence();
+    grid_setup(__uint_as_float(atomicOr(&hm_words[0], 0u)), g, ph, margin, min_width, nc_cap, host_passes, st);
+  }
+}
+
+// The grid alone (no particles).
+__global__ void k_grid_setup(Grid* g, Phys ph, float margin, float min_width, int nc_cap, int host_passes,
+                             Status* st) {
+  grid_setup(0.0f, g, ph, margin, min_width, nc_cap, host_passes, st);
+}
+
 // Spread the 10 low bits of v to every third bit (bit b -> bit 3b).
 __device__ __forceinline__ unsigned spread3(unsigned v) {
   v &= 0x3ffu;
@@ -207,9 +229,15 @@ __device__ __forceinline__ unsigned morton_of(float fx, float fy, float fz) {
 // Cell id of every particle; with `cell_out` (adaptive leaves) the sort key
 // is instead the 30-bit Morton code of the position inside the cell (10 bits
 // per axis, x in the lowest bit of each 3-bit digit) and the cell id goes to
-// cell_out, morton_out keeping a copy of the code.
-__global__ void k_cell_ids(const float4* __restrict__ pos_h, int n, const Grid* __restrict__ g, KeyBufs kb,
-                           unsigned* __restrict__ cell_out, unsigned* __restrict__ morton_out) {
+// cell_out, morton_out keeping a copy of the code. Blocks take the radix
+// tiles, so each also writes its tile's histogram of the keys' lowest digit:
+// the counts of the first radix pass.
+__global__ void __launch_bounds__(kRadixThreads) k_cell_ids(const float4* __restrict__ pos_h, int n,
+                                                            const Grid* __restrict__ g, KeyBufs kb,
+                                                            unsigned* __restrict__ cell_out,
+                                                            unsigned* __restrict__ morton_out,
+                                                            unsigned* __restrict__ hist) {
+  __shared__ unsigned hcount[256];
   // uniform grid: buffer g->sort_start; adaptive leaves: buffer 0 (their passes are all live)
   const int b = cell_out ? 0 : g->sort_start;
   unsigned* __restrict__ keys = kb.k[b];
@@ -218,8 +246,20 @@ __global__ void k_cell_ids(const float4* __restrict__ pos_h, int n, const Grid* 
   const double Lx = g->L[0], Ly = g->L[1], Lz = g->L[2];
   const float ncf[3] = {(float)nx, (float)ny, (float)nz};
   const float Lf[3] = {g->L[0], g->L[1], g->L[2]};
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    float4 p = pos_h[i];
+  hcount[threadIdx.x] = 0;
+  float4 pt[kRadixItems];  // the tile's positions, all loads issued first
+#pragma unroll
+  for (int it = 0; it < kRadixItems; ++it) {
+    const int i = blockIdx.x * kRadixTile + it * kRadixThreads + (int)threadIdx.x;
+    pt[it] = i < n ? pos_h[i] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < kRadixItems; ++it) {
+    const int i = blockIdx.x * kRadixTile + it * kRadixThreads + (int)threadIdx.x;
+    if (i >= n) continue;
+    unsigned key;
+    const float4 p = pt[it];
     vals[i] = (unsigned)i;
     {
       // FP32 first: t = x nc / L carries at most 3 roundings (< 2^-22 t), so
@@ -248,12 +288,13 @@ __global__ void k_cell_ids(const float4* __restrict__ pos_h, int n, const Grid* 
         const unsigned cell = (unsigned)(cf[0] + nx * (cf[1] + ny * cf[2]));
         if (cell_out) {
           const unsigned m = morton_of(frs[0], frs[1], frs[2]);
-          keys[i] = m;
+          keys[i] = key = m;
           morton_out[i] = m;
           cell_out[i] = cell;
         } else {
-          keys[i] = cell;
+          keys[i] = key = cell;
         }
+        atomicAdd(&hcount[key & 255u], 1u);
         continue;
       }
     }
@@ -276,13 +317,16 @@ __global__ void k_cell_ids(const float4* __restrict__ pos_h, int n, const Grid* 
     if (cell_out) {
       // the fraction is exact in FP64; its FP32 rounding only orders particles
       const unsigned m = morton_of((float)(tx - cx), (float)(ty - cy), (float)(tz - cz));
-      keys[i] = m;
+      keys[i] = key = m;
       morton_out[i] = m;
       cell_out[i] = cell;
     } else {
-      keys[i] = cell;
+      keys[i] = key = cell;
     }
+    atomicAdd(&hcount[key & 255u], 1u);
   }
+  __syncthreads();
+  hist[threadIdx.x * gridDim.x + blockIdx.x] = hcount[threadIdx.x];
 }
 
 // keys[k] = src[idx[k]]
@@ -340,14 +384,22 @@ __global__ void k_radix_scatter(KeyBufs kb, int host_src, int pass, int n, int s
   unsigned* __restrict__ vout = kb.v[1 - src];
   run[threadIdx.x] = offs[threadIdx.x * gridDim.x + blockIdx.x];
   for (int ww = 0; ww < kRadixThreads / 32; ++ww) wcnt[ww][threadIdx.x] = 0;
-  __syncthreads();
   const int base = blockIdx.x * kRadixTile;
+  unsigned keys[kRadixItems], vals[kRadixItems];  // the tile's keys, all loads issued first
+#pragma unroll
+  for (int k = 0; k < kRadixItems; ++k) {
+    const int i = base + k * kRadixThreads + threadIdx.x;
+    keys[k] = i < n ? kin[i] : 0u;
+    vals[k] = i < n ? vin[i] : 0u;
+  }
+  __syncthreads();
   const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
   for (int k = 0; k < kRadixItems; ++k) {
     int i = base + k * kRadixThreads + threadIdx.x;
     bool valid = i < n;
-    unsigned key = valid ? kin[i] : 0u;
-    unsigned val = valid ? vin[i] : 0u;
+    unsigned key = keys[k];
+    unsigned val = vals[k];
     unsigned d = (key >> shift) & 255u;
     unsigned vmask = __ballot_sync(0xffffffffu, valid);
     unsigned peers = __match_any_sync(0xffffffffu, valid ? d : 0xffffffffu) & vmask;
@@ -384,33 +436,40 @@ __global__ void k_cell_start(const unsigned* __restrict__ skeys, int n, const Gr
 int build_cells_impl(Ctx* c, const float4* pos_h, int n, float min_width, cudaStream_t s) {
   c->n = n;
   c->nl_lmax = 0;  // kept candidate lists belong to the previous build
-  cudaMemsetAsync(c->d_hmax_bits, 0, sizeof(unsigned), s);
   int sm = c->num_sms;
-  if (n > 0) {
-    k_scan_h<<<min((n + 255) / 256, sm * 8), 256, 0, s>>>(pos_h, n, c->phys.L[0], c->phys.L[1], c->phys.L[2],
-                                                         c->d_hmax_bits, c->d_status);
-    c->launches++;
-  }
   const bool adaptive = (c->params.flags & SWIFT_GPU_ADAPTIVE) != 0;
   const int nc_cap = adaptive && c->nc_cap > kAdaptiveNcCap ? kAdaptiveNcCap : c->nc_cap;
   const int host_passes = (c->max_key_bits + 7) / 8;
-  k_grid_setup<<<1, 1, 0, s>>>(c->d_hmax_bits, c->d_grid, c->phys, c->params.cell_margin, min_width, nc_cap,
-                               host_passes, c->d_status);
+  if (n > 0) {
+    cudaMemsetAsync(c->d_hmax_bits, 0, sizeof(unsigned) * kHmaxWords, s);
+    k_scan_h<<<min((n + 255) / 256, sm * 8), 256, 0, s>>>(pos_h, n, c->d_hmax_bits, c->d_grid, c->phys,
+                                                         c->params.cell_margin, min_width, nc_cap, host_passes,
+                                                         c->d_status);
+  } else {
+    k_grid_setup<<<1, 1, 0, s>>>(c->d_grid, c->phys, c->params.cell_margin, min_width, nc_cap, host_passes,
+                                 c->d_status);
+  }
   c->launches++;
   if (n > 0) {
     int gb = min((n + 255) / 256, sm * 8);
     const KeyBufs kb{{c->d_keys[0], c->d_keys[1]}, {c->d_vals[0], c->d_vals[1]}};
-    k_cell_ids<<<gb, 256, 0, s>>>(pos_h, n, c->d_grid, kb, adaptive ? c->d_aux[0] : nullptr,
-                                  adaptive ? c->d_aux[1] : nullptr);
-    c->launches++;
     const int nb = (n + kRadixTile - 1) / kRadixTile;
+    // the keys, and the counts of the first pass (its digit 0 is always live)
+    k_cell_ids<<<nb, kRadixThreads, 0, s>>>(pos_h, n, c->d_grid, kb, adaptive ? c->d_aux[0] : nullptr,
+                                            adaptive ? c->d_aux[1] : nullptr, c->d_hist);
+    c->launches++;
     int src = 0;  // host's view of the buffer a pass reads (as if every pass ran)
+    bool counted = true;
     auto pass = [&](int p, int shift, int bits) {
-      k_radix_count<<<nb, kRadixThreads, 0, s>>>(kb, src, p, n, shift, c->d_grid, bits, c->d_hist);
+      if (!counted) {
+        k_radix_count<<<nb, kRadixThreads, 0, s>>>(kb, src, p, n, shift, c->d_grid, bits, c->d_hist);
+        c->launches++;
+      }
+      counted = false;
       const int* gate = bits >= 0 ? nullptr : &c->d_grid->pass_live[shift / 8];
       exclusive_scan(c, c->d_hist, c->d_hist, 256 * nb, c->d_scan_tmp, s, gate);
       k_radix_scatter<<<nb, kRadixThreads, 0, s>>>(kb, src, p, n, shift, c->d_grid, bits, c->d_hist);
-      c->launches += 2;
+      c->launches++;
       src = 1 - src;
     };
     if (adaptive) {

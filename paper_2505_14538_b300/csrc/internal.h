@@ -149,6 +149,9 @@ inline unsigned long long wait_limit_ns(const Ctx* c) {
 constexpr int kRadixThreads = 256;
 constexpr int kRadixItems = 8;
 constexpr int kRadixTile = kRadixThreads * kRadixItems;  // 2048
+// The max-h buffer of the cell build: the bits of the largest h, and the
+// count of k_scan_h blocks done (the last one sets up the grid).
+constexpr int kHmaxWords = 2;
 
 // counters layout helpers
 constexpr int kCtrPerPass = 4;  // item_count, plist_count, ticket, spare

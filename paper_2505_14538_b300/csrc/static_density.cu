@@ -48,7 +48,7 @@ constexpr StaticLayout static_layout() {
   const size_t n = (size_t)kStaticN;
   L.status = take(sizeof(Status));
   L.grid = take(sizeof(Grid));
-  L.hmax = take(sizeof(unsigned));
+  L.hmax = take(sizeof(unsigned) * kHmaxWords);
   L.keys0 = take(4 * n);
   L.keys1 = take(4 * n);
   L.vals0 = take(4 * n);
