@@ -646,27 +646,18 @@ def run_kernel_shapes(dev, d, peak_tflops, steps=30):
     return out
 
 
-def run_adjoint(dev, steps=20):
-    """The adjoint of density + ghost + force (swift_gpu_force_backward) on the Kelvin-Helmholtz set.
-
-    kh(): 32 x (21 + 11) x 32 layers (32768 particles), vx = +-0.5, P = 2.5,
-    with a seeded random loss L = sum w.a + c du/dt. Per step: the forward
-    loops (build, density, force) and the backward passes, with h fixed
-    (h_mode 0: two gathers) and with h = h(x) solved by the h iteration
-    (h_mode 1: the h-adjoint and a third gather for the implicit-function term).
-    """
+def _adjoint_case(dev, d, steps):
+    """Forward loops (build, density, force) and swift_gpu_force_backward on one set, h fixed and h = h(x)."""
     import numpy as np
     import torch
 
-    from paper_2505_14538_b300 import _lib, ics, sph
-    d = ics.kh()
+    from paper_2505_14538_b300 import _lib, sph
     n = len(d["pos"])
     rng = np.random.default_rng(2505)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev)
     pos_h, vel_m, u = t(np.c_[d["pos"], d["h"]]), t(np.c_[d["vel"], d["m"]]), t(d["u"])
     g4 = t(np.c_[rng.normal(size=(n, 3)), rng.normal(size=n)])
-    res = {"workload": f"kh32: Kelvin-Helmholtz slab, {n} particles (32 x (21 + 11) x 32 layers), vx = +-0.5, "
-                       "P = 2.5; loss weights N(0, 1)", "particles": n, "steps": steps}
+    res = {}
     for mode, flags in ((0, _lib.FLAG_NO_H_ITER), (1, 0)):
         ctx = sph.Context(n, flags=flags, h_tol=1e-6, max_iter=40)
         ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps + 2)]
@@ -691,6 +682,29 @@ def run_adjoint(dev, steps=20):
         res[f"h_mode_{mode}"] = {"forward_ms": fw, "backward_ms": bw, "force_pairs": pairs,
                                  "backward_pairs_per_s": pairs / (bw * 1e-3), "status": list(code)}
         del ctx
+    return res
+
+
+def run_adjoint(dev, steps=20):
+    """The adjoint of density + ghost + force (swift_gpu_force_backward) on two sets.
+
+    kh(): 32 x (21 + 11) x 32 layers (32768 particles), vx = +-0.5, P = 2.5 (the
+    configuration the adjoint tests use), and the benchmark's own sedov64 set
+    (262144 particles), each with a seeded random loss L = sum w.a + c du/dt.
+    Per step: the forward loops (build, density, force) and the backward
+    passes, with h fixed (h_mode 0: two gathers) and with h = h(x) solved by
+    the h iteration (h_mode 1: the h-adjoint and a third gather for the
+    implicit-function term).
+    """
+    from paper_2505_14538_b300 import ics
+    d = ics.kh()
+    res = {"workload": f"kh32: Kelvin-Helmholtz slab, {len(d['pos'])} particles (32 x (21 + 11) x 32 layers), "
+                       "vx = +-0.5, P = 2.5; loss weights N(0, 1)", "particles": len(d["pos"]), "steps": steps}
+    res.update(_adjoint_case(dev, d, steps))
+    d = workload()
+    res["sedov64"] = {"workload": f"sedov64 ({len(d['pos'])} particles, the benchmark step's set); "
+                                  "loss weights N(0, 1)", "particles": len(d["pos"]), "steps": steps}
+    res["sedov64"].update(_adjoint_case(dev, d, steps))
     return res
 
 

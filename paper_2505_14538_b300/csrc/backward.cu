@@ -471,14 +471,18 @@ struct DensAdjOp {
     const float H2j = Hj * Hj;
     const float bj_band = band_of(Hj, Lmax);
     if (r2 >= fmaxf(i.H2hi, H2j + bj_band)) return;  // outside both supports
+    // membership in each support: in FP32 outside its guard band, in FP64
+    // (from the same floats) only inside it
     bool in_k = r2 < i.H2lo;
     bool in_j = r2 < H2j - bj_band;
-    if (!in_k || !in_j) {
+    const bool band_k = !in_k && r2 < i.H2hi;
+    const bool band_j = !in_j && r2 < H2j + bj_band;
+    if (band_k || band_j) {
       const double ex = exact_r2(i.x, i.y, i.z, pj.x, pj.y, pj.z, L[0], L[1], L[2]);
-      in_k = ex < exact_H2(kg, i.h);
-      in_j = ex < exact_H2(kg, pj.w);
-      if (!in_k && !in_j) return;
+      if (band_k) in_k = ex < exact_H2(kg, i.h);
+      if (band_j) in_j = ex < exact_H2(kg, pj.w);
     }
+    if (!in_k && !in_j) return;
     const float4 vj = vel[j];
     const float r = sqrtf(r2);
     const float ir = 1.0f / r;
@@ -604,14 +608,18 @@ struct IftAdjOp {
     const float H2j = Hj * Hj;
     const float bj_band = band_of(Hj, Lmax);
     if (r2 >= fmaxf(i.H2hi, H2j + bj_band)) return;  // outside both supports
+    // membership in each support: in FP32 outside its guard band, in FP64
+    // (from the same floats) only inside it
     bool in_k = r2 < i.H2lo;
     bool in_j = r2 < H2j - bj_band;
-    if (!in_k || !in_j) {
+    const bool band_k = !in_k && r2 < i.H2hi;
+    const bool band_j = !in_j && r2 < H2j + bj_band;
+    if (band_k || band_j) {
       const double ex = exact_r2(i.x, i.y, i.z, pj.x, pj.y, pj.z, L[0], L[1], L[2]);
-      in_k = ex < exact_H2(kg, i.h);
-      in_j = ex < exact_H2(kg, pj.w);
-      if (!in_k && !in_j) return;
+      if (band_k) in_k = ex < exact_H2(kg, i.h);
+      if (band_j) in_j = ex < exact_H2(kg, pj.w);
     }
+    if (!in_k && !in_j) return;
     const float r = sqrtf(r2);
     float t = 0.0f;
     if (in_k) t = i.lam * i.c4 * dkshape(kernel, r * i.invH);
