@@ -168,6 +168,9 @@ __device__ __forceinline__ void keep_list(const DensArgs& a, const WarpSmem& w, 
   if (lane == 0) a.item_nl[item_idx] = span;
 }
 
+// kFixedH: the density at the given h (no h iteration), a kernel of its own
+// so that the iterating one carries none of its branches.
+template <bool kFixedH>
 __device__ __forceinline__ void dens_item(const DensArgs& a, const DensOp& op, const Grid& g, WarpSmem& w,
                                           const Item& it, const int* __restrict__ plist, bool list_mode,
                                           bool last, Item* items_next, int* plist_next, int* ctr_next, float Lmax,
@@ -192,6 +195,7 @@ __device__ __forceinline__ void dens_item(const DensArgs& a, const DensOp& op, c
   // the prediction that it converges: the final sums then verify it
   float lo = 0.0f, hi = __int_as_float(0x7f800000);
   bool prov = false;
+  bool scan = false;  // fixed h: the item's sums from a scan of the cells instead of its lists
   if (list_mode) {
     const float Hc = a.ph.kg * hcap;
     const float R2 = Hc * Hc + band_of(Hc, Lmax);
@@ -206,7 +210,14 @@ __device__ __forceinline__ void dens_item(const DensArgs& a, const DensOp& op, c
     // and a user h_max may lie below an inactive particle's h)
     if (a.item_nl && item_idx >= 0)
       keep_list(a, w, item_idx, !retry && !a.nb.adaptive && g.hcap_from_cells, cnt, lm.live);
-    bool done = !lm.live || retry;
+    // at fixed h (no h iteration) there is no later pass: an item with a
+    // list that overflowed scans the cells below, all its particles (the
+    // scan and the flush are warp-wide, so the choice is the whole warp's)
+    if constexpr (kFixedH) {
+      scan = __any_sync(kFull, retry);
+      if (scan) retry = false;
+    }
+    bool done = !lm.live || retry || kFixedH;
     // a step whose relative residual G = |n h^3 - eta^3| / eta^3 is below
     // this leaves, by Newton's quadratic convergence, a residual well inside
     // h_tol: the walk that would only confirm it is skipped. With n nearly
@@ -238,10 +249,16 @@ __device__ __forceinline__ void dens_item(const DensArgs& a, const DensOp& op, c
       }
       if (!__any_sync(kFull, !done)) break;
     }
-    flush(op, I, w, (lm.live && !retry) ? cnt : 0);  // full sums at the final h
+    if (!scan) flush(op, I, w, (lm.live && !retry) ? cnt : 0);  // full sums at the final h
   } else {
     if (a.item_nl && item_idx >= 0 && lane == 0) a.item_nl[item_idx] = make_int2(-1, 0);
     scan_item(op, I, g, a.nb, a.pos, it.cell, lm.lsh, lm.s, lm.live, w, ncand);
+  }
+  if constexpr (kFixedH) {
+    if (list_mode && scan) {
+      if (a.item_nl && item_idx >= 0 && lane == 0) a.item_nl[item_idx] = make_int2(-1, 0);
+      scan_item(op, I, g, a.nb, a.pos, it.cell, lm.lsh, lm.s, lm.live, w, ncand);
+    }
   }
   lsum2(I.ns, I.nc, lm.lsh);
   lsum2(I.rs, I.rc, lm.lsh);
@@ -305,7 +322,7 @@ __device__ __forceinline__ void dens_item(const DensArgs& a, const DensOp& op, c
 
 // The loop kernels are instantiated per kernel shape K (kKernelCubic,
 // kKernelWendlandC2, kKernelWendlandC4), so the shape is fixed at compile time.
-template <int K>
+template <int K, bool kFixedH>
 __global__ void __launch_bounds__(kLoopThreads, 5) k_density(DensArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const unsigned lane = lane_id();
@@ -419,7 +436,8 @@ __global__ void __launch_bounds__(kLoopThreads, 5) k_density(DensArgs a) {
       const int t = take_ticket(&a.ctr[ctr_index(pass, 2)]);
       if (t >= n_items) break;
       const Item it = items[t];
-      dens_item(a, op, g, w, it, plist, pass == 0 && !a.single_pass, last, items_next, plist_next, ctr_next,
+      dens_item<kFixedH>(a, op, g, w, it, plist, pass == 0 && (kFixedH || !a.single_pass), last, items_next,
+                         plist_next, ctr_next,
                 Lmax, ninter, nhiter, ncand, pass == 0 ? t : -1);
     }
     if (!grid_barrier(&a.barrier[0], &a.barrier[1], a.st, a.wait_ns)) return;
@@ -731,10 +749,14 @@ static int persistent_blocks(Ctx* c, const void* kern) {
 }
 
 // The instantiation of each loop kernel for kernel shape `kind`.
-static const void* density_kernel(int kind) {
-  return kind == kKernelWendlandC2 ? (const void*)k_density<kKernelWendlandC2>
-         : kind == kKernelWendlandC4 ? (const void*)k_density<kKernelWendlandC4>
-                                     : (const void*)k_density<kKernelCubic>;
+static const void* density_kernel(int kind, bool fixed_h) {
+  if (fixed_h)
+    return kind == kKernelWendlandC2 ? (const void*)k_density<kKernelWendlandC2, true>
+           : kind == kKernelWendlandC4 ? (const void*)k_density<kKernelWendlandC4, true>
+                                       : (const void*)k_density<kKernelCubic, true>;
+  return kind == kKernelWendlandC2 ? (const void*)k_density<kKernelWendlandC2, false>
+         : kind == kKernelWendlandC4 ? (const void*)k_density<kKernelWendlandC4, false>
+                                     : (const void*)k_density<kKernelCubic, false>;
 }
 static const void* gradient_kernel(int kind) {
   return kind == kKernelWendlandC2 ? (const void*)k_gradient<kKernelWendlandC2>
@@ -756,7 +778,8 @@ static bool g_attr_done = false;
 static void ensure_attrs() {
   if (g_attr_done) return;
   for (int kind = kKernelCubic; kind <= kKernelWendlandC4; ++kind)
-    for (const void* f : {density_kernel(kind), gradient_kernel(kind), force_kernel(kind), grad_force_kernel(kind)})
+    for (const void* f : {density_kernel(kind, false), density_kernel(kind, true), gradient_kernel(kind),
+                          force_kernel(kind), grad_force_kernel(kind)})
       cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLoopSmemBytes);
   g_attr_done = true;
 }
@@ -774,7 +797,7 @@ void reduce_partials(Ctx* c, int nblocks, double* out, cudaStream_t s) {
 int density_impl(Ctx* c, const float4* pos_in, const float4* vel_in, const uint8_t* active, float* h_out,
                  float4* rho4, float4* cd, uint32_t* ngb, cudaStream_t s) {
   ensure_attrs();
-  const void* kern = density_kernel(c->phys.kernel);
+  const void* kern = density_kernel(c->phys.kernel, (c->params.flags & SWIFT_GPU_NO_H_ITER) != 0);
   const int nblk = persistent_blocks(c, kern);
   cudaMemsetAsync(c->d_counters, 0, sizeof(int) * (size_t)(kCtrPerPass * (c->max_passes + 2) + 2), s);
   DensArgs a;
