@@ -366,7 +366,7 @@ __device__ __forceinline__ void force_adj_item(const AdjArgs& a, const ForceAdjO
   a.vb[k] = make_float4(I.vb[0], I.vb[1], I.vb[2], I.hb);  // .w: dL/dh_k so far (h_mode 1)
 }
 
-__global__ void __launch_bounds__(kAdjThreads) k_force_adj(AdjArgs a) {
+__global__ void __launch_bounds__(kAdjThreads, 5) k_force_adj(AdjArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const Grid g = *a.grid;
   WarpSmem& w = adj_smem(smem);
@@ -499,7 +499,7 @@ struct DensAdjOp {
   }
 };
 
-__global__ void __launch_bounds__(kAdjThreads) k_dens_adj(AdjArgs a) {
+__global__ void __launch_bounds__(kAdjThreads, 5) k_dens_adj(AdjArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const Grid g = *a.grid;
   WarpSmem& w = adj_smem(smem);
