@@ -181,6 +181,45 @@ def test_fixed_h_counts_at_input_h(sph, O):
     assert np.max(np.abs(g["rho4"][:, 0] / st["rho"] - 1)) < 1e-5
 
 
+def test_fixed_h_kept_lists_with_overflow(sph, O):
+    """NO_H_ITER keeps the density call's candidate lists for the gradient and force loops. On the
+    Kelvin-Helmholtz slab (density ratio 2.2, the cells sized by the light layer's h) some lanes of
+    the dense layer collect more candidates than a list holds: their items take the 27-cell scan as
+    a whole warp. Every output against the oracle at the input h."""
+    d = ics.kh(16, 11, 5)
+    rng = np.random.default_rng(4)
+    n = len(d["pos"])
+    vel = d["vel"] + rng.normal(0, 0.05, (n, 3)).astype(np.float32)
+    u = d["u"]
+    g = run_gpu(sph, d, vel, u, flags=2)
+    assert g["status"] == (0, 0) and g["status2"] == (0, 0)
+    assert np.array_equal(g["h"], d["h"])
+    pf = oracle_params(O, g["ctx"].params)
+    st = O.step(pf, d["pos"], vel, d["m"], u, d["h"], solve=False)
+    assert np.array_equal(g["ngb"].astype(np.int64), st["ngb"])
+    assert np.max(np.abs(g["rho4"][:, 0] / st["rho"] - 1)) < 1e-5
+    vs = g["vsig_lapu"]
+    assert np.max(np.abs(vs[:, 0] / st["vsig"] - 1)) < 1e-5
+    assert np.max(np.abs(vs[:, 1] - st["lapu"])) < 1e-4 * max(np.abs(st["lapu"]).max(), 1e-30)
+    a = g["accel_dudt"]
+    assert np.all(np.linalg.norm(a[:, :3] - st["accel"], axis=1) <= 1e-4 * st["s_a"] + 1e-30)
+    assert np.all(np.abs(a[:, 3] - st["dudt"]) <= 1e-4 * st["s_u"] + 1e-30)
+    # the overflowing items scanned in the density call and again in the gradient and force
+    # loops; the others read their kept lists
+    cand = g["info"]["candidates"]
+    assert cand[1] == cand[2] < cand[0], cand
+    # on a lattice no list overflows: the loops read kept lists only, far fewer candidates than
+    # the density call's 27-cell tests, with the same outputs as the iterating path's loops at that h
+    d, vel, u = lattice_state(12, jitter=0.3)
+    g = run_gpu(sph, d, vel, u, flags=2)
+    cand = g["info"]["candidates"]
+    assert cand[2] < cand[0] / 3, cand
+    st = O.step(oracle_params(O, g["ctx"].params), d["pos"], vel, d["m"], u, d["h"], solve=False)
+    a = g["accel_dudt"]
+    assert np.all(np.linalg.norm(a[:, :3] - st["accel"], axis=1) <= 1e-4 * st["s_a"] + 1e-30)
+    assert np.all(np.abs(a[:, 3] - st["dudt"]) <= 1e-4 * st["s_u"] + 1e-30)
+
+
 def test_deterministic(sph):
     d, vel, u = lattice_state(16, seed=3)
     a = run_gpu(sph, d, vel, u, h_tol=1e-6)
