@@ -145,10 +145,12 @@ def workload():
 
 
 def flops_per_interaction():
-    """Algorithmic flops of one pair: density (full sums), gradient, force, h-iteration step."""
+    """Algorithmic flops of one pair: density (full sums), gradient, force, h-iteration step; and of one
+    neighbour test (a candidate's squared distance)."""
     with open(os.path.join(ROOT, "profiles", "flops_per_interaction.json")) as f:
         fl = json.load(f)
-    return [fl["density"]["mean"], fl["gradient"]["mean"], fl["force"]["mean"], fl["h_iteration"]["mean"]]
+    return [fl["density"]["mean"], fl["gradient"]["mean"], fl["force"]["mean"], fl["h_iteration"]["mean"],
+            fl["neighbour_test"]]
 
 
 def step_interactions(i0, i1):
@@ -332,6 +334,8 @@ def run_ours(args, rank, world, pg):
     # density: full-sum pairs at the density count, h-iteration pairs at the Eqs. 5-6 count;
     # gradient + force: the gradient pairs at the gradient count plus the force pairs at the force count
     flops = [dens_full * fpi[0] + hiter * fpi[3], inter[1] * fpi[1] + inter[2] * fpi[2]]
+    # the same with every candidate's neighbour test counted (the fused loop tests each kept entry once)
+    flops_tests = [flops[0] + cand[0] * fpi[4], flops[1] + cand[2] * fpi[4]]
     achieved = flops[dom] / (kernel_ms[dom] * 1e-3) / 1e12
     traffic = measured_traffic(names[dom])
     roof = {"bound": "alu", "kernel": names[dom], "achieved": achieved, "peak": peak_max, "unit": "TFLOP/s",
@@ -340,13 +344,17 @@ def run_ours(args, rank, world, pg):
             "frac_at_measured_clock": (achieved / (sms * 256 * clocks["sm_mhz"] * 1e6 / 1e12)
                                        if clocks.get("sm_mhz") else None),
             "flops_per_launch": flops[dom],
-            "flops_per_interaction": {"density": fpi[0], "h_iteration": fpi[3], "gradient": fpi[1], "force": fpi[2]},
+            "flops_per_interaction": {"density": fpi[0], "h_iteration": fpi[3], "gradient": fpi[1], "force": fpi[2],
+                                      "neighbour_test": fpi[4]},
             "per_loop": {names[j]: {"ms": kernel_ms[j], "tflops": flops[j] / (kernel_ms[j] * 1e-3) / 1e12,
                                     "frac": flops[j] / (kernel_ms[j] * 1e-3) / 1e12 / peak_max,
+                                    "frac_with_neighbour_tests": flops_tests[j] / (kernel_ms[j] * 1e-3) / 1e12
+                                    / peak_max,
                                     "hw_fma_pipe_frac": (measured_counters(names[j]).get("fma_pipe_active_pct", 0) / 100
                                                          or None)}
                          for j in range(2)},
             "frac_note": "frac counts the algorithmic flops of the interacting pairs only (oracle op counts); "
+                         "frac_with_neighbour_tests adds every candidate's squared distance (8 flops); "
                          "hw_fma_pipe_frac is the FMA pipe's busy fraction counted by ncu (all FP32 work: "
                          "candidate tests, compensated sums, misses), from profiles/traffic.json",
             "interactions": {"density": inter[0], "gradient": inter[1], "force": inter[2],
@@ -377,6 +385,11 @@ def run_ours(args, rank, world, pg):
         res["e2e"] = run_e2e(ctx, pos_h_host, vel_m_host, u_host, min_width, n, dev, pg, world, K=min(K, 100))
     if not args.no_plain and rank == 0:
         res["plain"] = run_plain(d, n, dev, min_width)
+        if "value" in res["plain"]:
+            # the same interactions per step and flops per interaction as the persistent step
+            fl_step = (flops[0] + flops[1]) / inter_step
+            res["plain"]["frac_fp32_peak"] = res["plain"]["value"] * fl_step / 1e12 / peak_max
+            res["plain"]["persistent_frac_fp32_peak"] = value / world * fl_step / 1e12 / peak_max
     if not args.no_clustered and rank == 0:
         res["clustered"] = run_clustered(dev)
     if not args.no_gresho and rank == 0:

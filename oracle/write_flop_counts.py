@@ -5,8 +5,11 @@ op-counting scalar (add/sub/mul/div/sqrt = 1 flop each; comparisons are not
 flops). A hit falls in the inner spline branch (q < 1/2) with probability
 1/8 (hits are uniform in the support volume), so each loop's figure is
 1/8 inner + 7/8 outer. The Wendland kernels have one branch; their counts
-are written under "wendland_c2" and "wendland_c4". The neighbour test itself
-is not counted.
+are written under "wendland_c2" and "wendland_c4". The neighbour test is not
+part of those counts; its own cost, the distance of the predicate
+(r^2 = dx^2 + dy^2 + dz^2 from the three coordinate differences: 3 sub, 3 mul,
+2 add; the comparison is not a flop, and the periodic image is applied once
+per cell, not per pair), is written under "neighbour_test".
 """
 import json
 import os
@@ -31,8 +34,10 @@ def main():
         for loop, name in ((0, "density"), (1, "gradient"), (2, "force"), (3, "h_iteration")):
             c = O.count_flops(loop, 0.5, True, kind)
             out[key][name] = c["add"] + c["mul"] + c["div"] + c["sqrt"]
+    out["neighbour_test"] = 3 + 3 + 2
     out["_how"] = ("oracle pair functions on an op-counting scalar; cubic spline mean = 1/8 inner-branch + 7/8 "
-                   "outer-branch count; written by oracle/write_flop_counts.py")
+                   "outer-branch count; neighbour_test: the predicate's squared distance (3 sub, 3 mul, 2 add); "
+                   "written by oracle/write_flop_counts.py")
     path = os.path.join(os.path.dirname(HERE), "profiles", "flops_per_interaction.json")
     os.makedirs(os.path.dirname(path), exist_ok=True)
     with open(path, "w") as f:
