@@ -153,6 +153,17 @@ def flops_per_interaction():
             fl["neighbour_test"]]
 
 
+def occupancy(counts):
+    """Occupancy summary of a count per cell (or leaf): percentiles and a histogram in powers of 2."""
+    import numpy as np
+    c = np.asarray(counts, dtype=np.int64)
+    bins = [0] + [1 << k for k in range(0, 21)]
+    hist = np.histogram(c, bins=bins + [1 << 40])[0]
+    return {"n": int(c.size), "max": int(c.max()) if c.size else 0, "mean": float(c.mean()) if c.size else 0.0,
+            "p50": float(np.percentile(c, 50)) if c.size else 0.0, "p99": float(np.percentile(c, 99)) if c.size else 0.0,
+            "hist_pow2": {f"[{lo},{hi})": int(h) for lo, hi, h in zip(bins, bins[1:] + [1 << 40], hist) if h}}
+
+
 def step_interactions(i0, i1):
     """Pair interactions between two info snapshots, a fixed count of the workload, whatever the iteration:
     [density: the pairs of the final density sums (j != i, r_ij < H_i at the final h), which is the gradient
@@ -579,6 +590,15 @@ def run_clustered(dev, steps=5):
         if flags:
             r.update({"leaves": i1["n_leaves"], "leaf_pairs": i1["leaf_pairs"], "tree_depth": i1["tree_depth"],
                       "leaf_max": int(ctx.params.leaf_max), "leaf_margin": float(ctx.params.leaf_margin)})
+            rng, _, nbr = ctx.leaves()
+            size = (rng[:, 1] - rng[:, 0]).cpu().numpy()
+            r["leaf_size"] = occupancy(size)
+            r["leaf_list_length"] = occupancy(nbr.cpu().numpy())
+        else:
+            cid, _ = ctx.cells()
+            r["cell_occupancy"] = occupancy(np.bincount(cid.cpu().numpy(), minlength=int(np.prod(i1["nc"]))))
+        per_loop = [x / steps for x in step_interactions(i0, i1)]
+        r["hit_rate"] = [p / c if c else None for p, c in zip(per_loop, r["candidates_per_step"])]
         res[name] = r
         del ctx
     res["adaptive_speedup"] = res["uniform"]["ms_per_step"] / res["adaptive"]["ms_per_step"]
