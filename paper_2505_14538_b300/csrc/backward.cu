@@ -692,13 +692,11 @@ int backward_impl(Ctx* c, const float4* grad_ad, float4* grad_x, float4* grad_v,
   // h = h(x) needs the h iteration's root: not with a density call at fixed h
   if (h_mode == 1 && (c->params.flags & SWIFT_GPU_NO_H_ITER)) return SWIFT_GPU_ERR_ARG;
   if (c->n == 0) return SWIFT_GPU_OK;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_force_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjSmemBytes);
-    cudaFuncSetAttribute(k_dens_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjSmemBytes);
-    cudaFuncSetAttribute(k_ift_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjSmemBytes);
-    attr = true;
-  }
+  // function attributes belong to the current device's context: set them on every call (cheap, and
+  // allowed while a stream is captured)
+  cudaFuncSetAttribute(k_force_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjSmemBytes);
+  cudaFuncSetAttribute(k_dens_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjSmemBytes);
+  cudaFuncSetAttribute(k_ift_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjSmemBytes);
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k_force_adj, kAdjThreads, kAdjSmemBytes);
   int per_sm2 = 0;
@@ -720,7 +718,7 @@ int backward_impl(Ctx* c, const float4* grad_ad, float4* grad_x, float4* grad_v,
   a.nl_cap = c->nl_cap;
   a.perm = c->d_vals[c->sorted_buf];
   a.ph = c->phys;
-  a.lmax = c->tuning.max_lanes_per_particle;
+  a.lmax = cell_lanes(c);
   a.pos = c->d_pos;
   a.vel = c->d_vel;
   a.rho4 = c->d_rho4;

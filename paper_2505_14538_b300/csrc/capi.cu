@@ -10,6 +10,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "lpp.cuh"
 
 struct swift_gpu_ctx {
   sg::Ctx c;
@@ -18,8 +19,6 @@ struct swift_gpu_ctx {
 namespace sg {
 
 Ctx* from(swift_gpu_ctx* c) { return c ? &c->c : nullptr; }
-
-constexpr int kMaxPasses = 64;
 
 static bool aligned(const void* p, size_t a) { return p && ((uintptr_t)p % a) == 0; }
 
@@ -64,7 +63,7 @@ static void free_all(Ctx* c) {
                   c->d_scratch4[0], c->d_scratch1[0], c->d_scratch1[1], c->d_plain_act, c->d_aux[0], c->d_aux[1],
                   c->d_node_range, c->d_node, c->d_node_link, c->d_node_parent, c->d_node_done, c->d_node_flag,
                   c->d_leaf_range, c->d_leaf_hcap, c->d_leaf_node, c->d_nbr_span, c->d_nbr, c->d_tree_ctr,
-                  c->d_nlist, c->d_item_nl, c->d_nl_ctr};
+                  c->d_nlist, c->d_item_nl, c->d_nl_ctr, c->d_rep, c->d_lcnt, c->d_gc};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_status) cudaFreeHost(c->h_status);
@@ -114,7 +113,7 @@ int swift_gpu_create(swift_gpu_ctx** out, const swift_gpu_params* p, int64_t n_m
     return SWIFT_GPU_ERR_CUDA;
   }
   c->tuning.threads_per_block = 256;
-  c->tuning.max_lanes_per_particle = 32;
+  c->tuning.max_lanes_per_particle = 32;  // one lane a particle below, where that path exists
   c->tuning.blocks_per_sm = 0;
   int nc_cap = (int)floor(cbrt(2.0 * (double)n_max));
   if (nc_cap < 3) nc_cap = 3;
@@ -148,7 +147,12 @@ int swift_gpu_create(swift_gpu_ctx** out, const swift_gpu_params* p, int64_t n_m
     if (per > 256) per = 256;
   }
   const bool keep_lists = (p->flags & SWIFT_GPU_ADAPTIVE) == 0;
+  // the lane-per-particle path keeps a fixed span of W entries a lane for every group of 32
+  const bool lpp = keep_lists && (p->flags & SWIFT_GPU_PLAIN) == 0;
+  const int64_t lpp_need = (int64_t)lpp_width_of(p->kernel) * 32 * ((n + 31) / 32);
+  if (lpp && lpp_need > per * n) per = (lpp_need + n - 1) / n;
   c->nl_cap = !keep_lists ? 0 : per * n < ((int64_t)1 << 31) - 64 ? per * n : ((int64_t)1 << 31) - 64;
+  const bool lpp_fits = lpp && lpp_need <= c->nl_cap;
   int64_t nbr_cap = 48 * n > ((int64_t)1 << 22) ? 48 * n : ((int64_t)1 << 22);  // at least 16 MB of lists
   c->nbr_cap = (int)(nbr_cap < (int64_t)INT32_MAX ? nbr_cap : (int64_t)INT32_MAX);
   c->red_blocks = c->num_sms * 32;
@@ -171,10 +175,12 @@ int swift_gpu_create(swift_gpu_ctx** out, const swift_gpu_params* p, int64_t n_m
             dalloc(&c->d_nbr_span, n) && dalloc(&c->d_nbr, (size_t)c->nbr_cap) &&
             dalloc(&c->d_tree_ctr, kTreeCtrCount) && (c->nl_cap == 0 || dalloc(&c->d_nlist, (size_t)c->nl_cap)) &&
             dalloc(&c->d_item_nl, n) && dalloc(&c->d_nl_ctr, 1) &&
+            (!lpp_fits || (dalloc(&c->d_rep, (size_t)kAxes * n) && dalloc(&c->d_lcnt, n) && dalloc(&c->d_gc, n))) &&
             cudaMallocHost((void**)&c->h_status, sizeof(Status)) == cudaSuccess &&
             cudaMallocHost((void**)&c->h_stats, sizeof(unsigned long long) * kStatCount) == cudaSuccess;
   if (ok)
     for (int q = 1; q < 4; ++q) c->d_scratch4[q] = c->d_scratch4[0] + q * n;
+
   if (!ok) {
     cudaGetLastError();
     free_all(c);

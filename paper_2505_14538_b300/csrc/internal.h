@@ -96,6 +96,14 @@ struct Ctx {
   int2* d_item_nl = nullptr;
   unsigned long long* d_nl_ctr = nullptr;
   int nl_lmax = 0;  // lanes-per-particle limit they were built with (0: none)
+  // lane-per-particle path (uniform grid): the 13 axis-sorted replicas of the
+  // cells (13 n_max float4), the per-lane candidate counts of the groups' kept
+  // lists (n_max), and whether the last density call kept such lists
+  float4* d_rep = nullptr;
+  int* d_lcnt = nullptr;
+  float4* d_gc = nullptr;  // sorted (1/H, C/H^4, H^2 -/+ band) from the ghost step
+
+  int lpp_lists = 0;
 
   // host mirrors
   Status* h_status = nullptr;  // pinned
@@ -134,6 +142,18 @@ int backward_impl(Ctx* c, const float4* grad_ad, float4* grad_x, float4* grad_v,
 inline bool kept_lists_usable(const Ctx* c) {
   return c->d_nlist && c->nl_lmax != 0 && c->nl_lmax == c->tuning.max_lanes_per_particle;
 }
+
+// Lanes per particle of the cell-item kernels. A tuning of one lane a
+// particle selects the lane-per-particle path where it exists; the cell-item
+// kernels that still run there (the later density passes, the adjoint, the
+// fallbacks) share a particle among up to 32 lanes.
+inline int cell_lanes(const Ctx* c) {
+  return c->tuning.max_lanes_per_particle == 1 && c->d_rep ? 32 : c->tuning.max_lanes_per_particle;
+}
+
+// Most Newton passes of one density call: the counters of the context and of
+// the static entry point are laid out for this many.
+constexpr int kMaxPasses = 64;
 
 // Limit of each bounded device-side wait: tuning.wait_limit_us (0: 5 s;
 // negative: give up at once, the fault-injection setting).

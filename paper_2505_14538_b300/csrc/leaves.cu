@@ -501,16 +501,12 @@ __global__ void __launch_bounds__(kWalkThreads) k_leaf_walk(WalkArgs a) {
   }
 }
 
-static bool g_walk_attr = false;
-
 int leaves_build(Ctx* c, const float4* pos_h, cudaStream_t s) {
   const int n = c->n;
   cudaMemsetAsync(c->d_tree_ctr, 0, sizeof(int) * kTreeCtrCount, s);
   if (n == 0) return cudaGetLastError() == cudaSuccess ? SWIFT_GPU_OK : SWIFT_GPU_ERR_CUDA;
-  if (!g_walk_attr) {
-    cudaFuncSetAttribute(k_leaf_walk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWalkSmemBytes);
-    g_walk_attr = true;
-  }
+  // per call: function attributes belong to the current device's context
+  cudaFuncSetAttribute(k_leaf_walk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWalkSmemBytes);
   cudaMemsetAsync(c->d_node_flag, 0, sizeof(unsigned) * ((size_t)c->node_cap + 1), s);
   cudaMemsetAsync(c->d_node_done, 0, sizeof(int) * (size_t)c->node_cap, s);
   const int sm = c->num_sms;

@@ -20,7 +20,9 @@
 
 #include "common.cuh"
 #include "engine.cuh"
+#include "force_lpp.cuh"
 #include "internal.h"
+#include "lpp.cuh"
 #include "ops.cuh"
 
 namespace sg {
@@ -90,6 +92,12 @@ struct DensArgs {
   long long nl_cap;
   unsigned long long* nl_ctr;
   int2* item_nl;       // per pass-0 item: (first entry, entries per lane) or (-1, 0)
+  // lane-per-particle pass 0 (uniform grid): axis-sorted cell replicas and the
+  // per-lane candidate counts of each group's kept list
+  float4* rep;
+  long long rep_stride;
+  int* lcnt;
+  int lpp_w;  // entries a lane of a group's kept list holds
 };
 
 __device__ __forceinline__ void dens_load(DensOp::I& I, const DensArgs& a, float Lmax, int k) {
@@ -147,25 +155,45 @@ __device__ __forceinline__ void number_walk(const DensOp& op, const DensOp::I& I
 
 // The candidates a pass-0 item collects (every j within the cap's support,
 // a superset of every pair the later loops need, since no h exceeds its cap)
-// are kept in HBM, lane-interleaved as in shared memory and padded with
-// kNoEntry, so the gradient, force and adjoint loops need not scan again.
-__device__ __forceinline__ void keep_list(const DensArgs& a, const WarpSmem& w, int item_idx, bool ok, int cnt,
-                                          bool live) {
+// are kept in HBM for the gradient and force loops, in the layout of the
+// lane-per-particle groups: the particle at pass-0 list position idx owns
+// lane idx % 32 of group idx / 32, entry t at t * 32 + lane of the group's
+// span of W entries a lane, and lcnt[idx] its count. The sub-lanes of a
+// particle write their shares one after the other (an exclusive prefix of
+// their counts). A group is left without a list (item_nl[group].x = -1) when
+// one of its particles has more than W candidates, or took the multi-pass
+// route, or when some h may exceed the cap (`ok` false).
+__device__ __forceinline__ void keep_list(const DensArgs& a, const WarpSmem& w, const Item& it, const LaneMap& lm,
+                                          bool ok, int cnt) {
   const unsigned lane = lane_id();
-  int2 span = make_int2(-1, 0);
-  if (__all_sync(kFull, ok)) {
-    const int m = __reduce_max_sync(kFull, live ? cnt : 0);
-    unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(a.nl_ctr, (unsigned long long)m * 32ull);
-    base = __shfl_sync(kFull, base, 0);
-    if (base + (unsigned long long)m * 32ull <= (unsigned long long)a.nl_cap) {
-      for (int t = 0; t < m; ++t)
-        a.nlist[base + (unsigned long long)(t * 32 + (int)lane)] =
-            (live && t < cnt) ? w.list[t * 32 + lane] : kNoEntry;
-      span = make_int2((int)base, m);
-    }
+  const int A = 32 >> lm.lsh;
+  const int c = lm.live ? cnt : 0;
+  int incl = c, tot = c;
+  for (int o = A; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(kFull, incl, o);
+    if ((int)lane >= o) incl += y;
+    tot += __shfl_xor_sync(kFull, tot, o);
   }
-  if (lane == 0) a.item_nl[item_idx] = span;
+  const bool all_ok = __all_sync(kFull, ok);
+  if (!lm.live) return;
+  const int idx = it.off + lm.slot;
+  const int grp = idx >> 5;
+  if (!all_ok || tot > a.lpp_w) {
+    if (lm.s == 0) a.item_nl[grp].x = -1;
+    return;
+  }
+  unsigned* dst = a.nlist + (long long)grp * (a.lpp_w * 32) + (idx & 31);
+  const int pre = incl - c;
+  for (int t = 0; t < c; ++t) dst[(pre + t) * 32] = w.list[t * 32 + lane];
+  if (lm.s == 0) {
+    a.lcnt[idx] = tot;
+    atomicMax(&a.item_nl[grp].y, tot);
+  }
+}
+
+// A pass-0 item whose particles' lists are not kept: their groups have none.
+__device__ __forceinline__ void drop_lists(const DensArgs& a, const Item& it, const LaneMap& lm) {
+  if (lm.live && lm.s == 0) a.item_nl[(it.off + lm.slot) >> 5].x = -1;
 }
 
 // kFixedH: the density at the given h (no h iteration), a kernel of its own
@@ -208,8 +236,7 @@ __device__ __forceinline__ void dens_item(const DensArgs& a, const DensOp& op, c
     // kept only where every h (active or not) is within this item's cap: the
     // uniform grid with the cell-derived cap (leaves have caps of their own,
     // and a user h_max may lie below an inactive particle's h)
-    if (a.item_nl && item_idx >= 0)
-      keep_list(a, w, item_idx, !retry && !a.nb.adaptive && g.hcap_from_cells, cnt, lm.live);
+    if (a.item_nl && item_idx >= 0) keep_list(a, w, it, lm, !retry && !a.nb.adaptive && g.hcap_from_cells, cnt);
     // at fixed h (no h iteration) there is no later pass: an item with a
     // list that overflowed scans the cells below, all its particles (the
     // scan and the flush are warp-wide, so the choice is the whole warp's)
@@ -251,12 +278,12 @@ __device__ __forceinline__ void dens_item(const DensArgs& a, const DensOp& op, c
     }
     if (!scan) flush(op, I, w, (lm.live && !retry) ? cnt : 0);  // full sums at the final h
   } else {
-    if (a.item_nl && item_idx >= 0 && lane == 0) a.item_nl[item_idx] = make_int2(-1, 0);
+    if (a.item_nl && item_idx >= 0) drop_lists(a, it, lm);
     scan_item(op, I, g, a.nb, a.pos, it.cell, lm.lsh, lm.s, lm.live, w, ncand);
   }
   if constexpr (kFixedH) {
     if (list_mode && scan) {
-      if (a.item_nl && item_idx >= 0 && lane == 0) a.item_nl[item_idx] = make_int2(-1, 0);
+      if (a.item_nl && item_idx >= 0) drop_lists(a, it, lm);
       scan_item(op, I, g, a.nb, a.pos, it.cell, lm.lsh, lm.s, lm.live, w, ncand);
     }
   }
@@ -320,15 +347,201 @@ __device__ __forceinline__ void dens_item(const DensArgs& a, const DensOp& op, c
   }
 }
 
+// ================================================ lane-per-particle pass 0
+template <int K>
+__host__ __device__ constexpr int lpp_width() {
+  return lpp_width_of(K);
+}
+// Shared memory a warp of the density kernel uses: the cell-item lanes' lists,
+// or a lane-per-particle group's squared distances (W per lane).
+__host__ __device__ constexpr size_t lpp_warp_bytes(int kind) {
+  return (size_t)lpp_width_of(kind) * 32 * 4;
+}
+__host__ __device__ constexpr size_t dens_warp_bytes(int kind, bool lpp) {
+  return lpp && lpp_warp_bytes(kind) > sizeof(WarpSmem) ? lpp_warp_bytes(kind) : sizeof(WarpSmem);
+}
+
+// Eqs. 5-6 at the lane particle's current h over its stored squared
+// distances (one step of the h iteration): no neighbour records are read.
+// Four entries at a time; the sums are taken in list order.
+template <int K>
+__device__ __forceinline__ void walk_r2(const DensOp::I& I, const float* r2s, int cnt, bool compensated, float& ns,
+                                        float& nc, float& dn, unsigned& npairs) {
+  const int m = __reduce_max_sync(kFull, cnt);
+  for (int t0 = 0; t0 < m; t0 += 4) {
+    float r2[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) r2[q] = t0 + q < cnt ? r2s[(t0 + q) * 32] : -1.0f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const bool valid = r2[q] >= 0.0f;
+      const float rr = fmaxf(r2[q], 0.0f);
+      const float invr = rr > 0.0f ? rsqrtf(rr) : 0.0f;
+      const float r = rr * invr;
+      float wq, dwq;
+      kshape(K, r * I.invH, wq, dwq);
+      const float W = valid ? I.c3 * wq : 0.0f;
+      const float D = valid ? fmaf(r, I.c4 * dwq, 3.0f * W) : 0.0f;
+      if (compensated) two_sum_acc(ns, nc, W);
+      else ns += W;
+      dn += D;
+      npairs += (valid && rr > 0.0f && rr < I.H2hi) ? 1u : 0u;
+    }
+  }
+}
+
+// Pass 0 of the density loop for group `grp` (pass-0 particle list entries
+// [32 grp, 32 grp + 32), one lane each): the windowed collect (lpp.cuh) into
+// the group's kept list and the lane's squared distances, the Newton
+// iteration on those distances, and the full sums at the final h over the
+// kept list. Particles whose candidates do not fit in W, and predicted
+// convergences that the final sums refute, continue as one-particle cell
+// items of the next pass. At fixed h (kFixedH) a particle whose candidates do
+// not fit scans its 27 cells instead.
+template <int K, bool kFixedH>
+__device__ __forceinline__ void dens_group(const DensArgs& a, const DensOp& op, const Grid& g, float* r2w, int grp,
+                                           int P, bool last, Item* items_next, int* plist_next, int* ctr_next,
+                                           float Lmax, unsigned& ninter, unsigned& nhiter, unsigned& ncand) {
+  constexpr int W = lpp_width<K>();
+  const unsigned lane = lane_id();
+  const int idx = grp * 32 + (int)lane;
+  const bool live = idx < P;
+  const int k = a.plist0[live ? idx : grp * 32];
+  DensOp::I I;
+  dens_load(I, a, Lmax, k);
+  const float hcap = g.hcap;
+  const int cap_flag = cell_cap_flag(g);
+  const float Hc = a.ph.kg * hcap;
+  const float R2 = Hc * Hc + band_of(Hc, Lmax);
+  unsigned* lst = a.nlist + (long long)grp * (W * 32) + lane;
+  float* r2s = r2w + lane;
+  const int cell = (int)a.nb.skeys[k];
+  bool ovf = false;
+  int cnt = lpp_collect<W>(g, a.nb.cell_start, a.pos, a.rep, a.rep_stride, I.x, I.y, I.z, cell, R2, Lmax, live,
+                           lst, r2s, ovf, ncand);
+  if (!live) cnt = 0;
+  cnt = min(cnt, W);
+  // the group's kept list serves the later loops when every lane's candidates
+  // fit and every h (active or not) is within the cell cap
+  const bool keep = __all_sync(kFull, !ovf) && g.hcap_from_cells;
+  const int mw = __reduce_max_sync(kFull, cnt);
+  if (lane == 0) a.item_nl[grp] = make_int2(keep ? 0 : -1, mw);
+  if (live) a.lcnt[idx] = cnt;
+  bool retry = ovf;  // the multi-pass route from the starting h
+  bool scan = false; // fixed h: the particle's sums from a scan of its cells
+  int flag = 0;
+  float hn = I.h;
+  float lo = 0.0f, hi = __int_as_float(0x7f800000);
+  bool prov = false;
+  if constexpr (kFixedH) {
+    scan = ovf && live;
+    retry = false;
+  } else {
+    bool done = !live || retry;
+    // the predicted-convergence skip of dens_item: a relative residual below
+    // 0.6 sqrt(h_tol) leaves, by Newton's quadratic convergence, a residual
+    // well inside h_tol, and the final sums verify it
+    const float e3 = (float)a.ph.eta3;
+    const float pred = 0.6f * sqrtf((float)a.ph.h_tol);
+    for (int iter = 0;; ++iter) {
+      float ns = 0.0f, nc = 0.0f, dn = 0.0f;
+      unsigned np = 0;
+      walk_r2<K>(I, r2s, done ? 0 : cnt, a.ph.compensated, ns, nc, dn, np);
+      if (!done) {
+        nhiter += np;
+        float h1;
+        const float h0 = I.h;
+        if (newton_step(h0, ns, nc, dn, lo, hi, hcap, cap_flag, a.ph, iter == a.ph.max_iter - 1, h1, flag)) {
+          dens_set_h(I, h1, a.ph.kg, a.ph.knorm, Lmax);
+          if (fabsf(fmaf(ns + nc, h0 * h0 * h0, -e3)) < pred * e3 && iter + 2 < a.ph.max_iter) {
+            done = true;
+            prov = true;
+          }
+        } else {
+          done = true;
+        }
+      }
+      if (!__any_sync(kFull, !done)) break;
+    }
+  }
+  // full sums at the final h over the kept list, four entries at a time: the
+  // entries, then all eight records, are loaded before any arithmetic; the
+  // sums are taken in list order
+  {
+    const int fc = (live && !retry && !scan) ? cnt : 0;
+    const int m = __reduce_max_sync(kFull, fc);
+    for (int t0 = 0; t0 < m; t0 += 4) {
+      unsigned e[4];
+      DensOp::DRec r[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) e[q] = t0 + q < fc ? lst[(t0 + q) * 32] : (unsigned)k;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) op.load_rec((int)(e[q] & kIndexMask), r[q]);
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (t0 + q < fc) op.interact(I, (int)(e[q] & kIndexMask), e[q] >> kIndexBits, r[q]);
+    }
+  }
+  if constexpr (kFixedH) {
+    if (__any_sync(kFull, scan)) lpp_scan(op, I, g, a.nb.cell_start, cell, scan, ncand);
+  }
+  bool again = false;
+  if (live) {
+    if (retry) {
+      again = true;
+    } else {
+      ninter += I.count;
+      if (prov) {
+        float2 br = make_float2(lo, hi);
+        if (newton_step(I.h, I.ns, I.nc, I.dn, br.x, br.y, hcap, cap_flag, a.ph, last, hn, flag)) {
+          a.h[k] = hn;
+          a.bracket[k] = br;
+          again = true;
+        }
+      }
+      if (!again) {
+        a.h[k] = I.h;
+        const float rho = I.rs + I.rc;
+        const float invh = 1.0f / I.h;
+        a.rho4[k] = make_float4(rho, -I.dr * invh, I.ns + I.nc, -I.dn * invh);
+        const float ir = 1.0f / rho;
+        a.cd[k] = make_float4(I.cx * ir, I.cy * ir, I.cz * ir, I.div * ir);
+        a.ngb[k] = I.count;
+        if (flag) set_error(a.st, flag);
+      }
+    }
+  }
+  // particles that continue: one cell item each (all lanes of the next pass on it)
+  const unsigned am = __ballot_sync(kFull, again);
+  if (am) {
+    const int nu = __popc(am);
+    int pbase = 0, ibase = 0;
+    if (lane == 0) {
+      pbase = atomicAdd(&ctr_next[1], nu);
+      ibase = atomicAdd(&ctr_next[0], nu);
+    }
+    pbase = __shfl_sync(kFull, pbase, 0);
+    ibase = __shfl_sync(kFull, ibase, 0);
+    if (again) {
+      const int r = __popc(am & ((1u << lane) - 1u));
+      plist_next[pbase + r] = k;
+      items_next[ibase + r] = Item{cell, pbase + r, 1, 0};
+    }
+  }
+}
+
 // The loop kernels are instantiated per kernel shape K (kKernelCubic,
 // kKernelWendlandC2, kKernelWendlandC4), so the shape is fixed at compile time.
-template <int K, bool kFixedH>
-__global__ void __launch_bounds__(kLoopThreads, 5) k_density(DensArgs a) {
+// kLPP: pass 0 runs lane per particle over groups (dens_group), with the
+// replicas of every cell built in the prologue; later passes run cell items.
+template <int K, bool kFixedH, bool kLPP>
+__global__ void __launch_bounds__(kLoopThreads, kLPP ? 4 : 5) k_density(DensArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const unsigned lane = lane_id();
   const Grid g = *a.grid;
   const float Lmax = fmaxf(g.L[0], fmaxf(g.L[1], g.L[2]));
-  WarpSmem& w = warp_smem(smem);
+  constexpr size_t kWarpBytes = dens_warp_bytes(K, kLPP);
+  WarpSmem& w = *reinterpret_cast<WarpSmem*>(smem + (threadIdx.x >> 5) * kWarpBytes);
 
   // ---- prologue: gather into cell order, inputs of inactive particles
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < a.n; k += gridDim.x * blockDim.x) {
@@ -410,6 +623,18 @@ __global__ void __launch_bounds__(kLoopThreads, 5) k_density(DensArgs a) {
       __syncthreads();  // s_tot, s_nit and s_base are reused by the next round
     }
   }
+  // ---- replicas of every cell along the 13 pair axes (one warp a cell), from
+  // the same wrapped positions the gather above writes
+  if constexpr (kLPP) {
+    const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+    for (int c = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); c < g.ncells; c += nw) {
+      const int cs = a.nb.cell_start[c], m = a.nb.cell_start[c + 1] - cs;
+      if (m == 0 || m > kRepMax) continue;
+      float4 p = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      if ((int)lane < m) p = wrap_pos(a.pos_in[a.perm[cs + (int)lane]], a.ph.L);
+      build_replicas_cell(a.rep, a.rep_stride, cs, m, p);
+    }
+  }
   if (!grid_barrier(&a.barrier[0], &a.barrier[1], a.st, a.wait_ns)) return;
 
   DensOp op;
@@ -432,13 +657,25 @@ __global__ void __launch_bounds__(kLoopThreads, 5) k_density(DensArgs a) {
     int* plist_next = a.plist[(pass + 1) & 1];
     int* ctr_next = &a.ctr[ctr_index(pass + 1, 0)];
     const bool last = pass == max_pass - 1;
-    for (;;) {
-      const int t = take_ticket(&a.ctr[ctr_index(pass, 2)]);
-      if (t >= n_items) break;
-      const Item it = items[t];
-      dens_item<kFixedH>(a, op, g, w, it, plist, pass == 0 && (kFixedH || !a.single_pass), last, items_next,
-                         plist_next, ctr_next,
-                Lmax, ninter, nhiter, ncand, pass == 0 ? t : -1);
+    if (kLPP && pass == 0) {
+      const int P = *((volatile int*)&a.ctr[ctr_index(0, 1)]);
+      const int ng = (P + 31) >> 5;
+      float* r2w = reinterpret_cast<float*>(smem + (threadIdx.x >> 5) * kWarpBytes);
+      for (;;) {
+        const int t = take_ticket(&a.ctr[ctr_index(0, 2)]);
+        if (t >= ng) break;
+        dens_group<K, kFixedH>(a, op, g, r2w, t, P, last, items_next, plist_next, ctr_next, Lmax, ninter, nhiter,
+                               ncand);
+      }
+    } else {
+      for (;;) {
+        const int t = take_ticket(&a.ctr[ctr_index(pass, 2)]);
+        if (t >= n_items) break;
+        const Item it = items[t];
+        dens_item<kFixedH>(a, op, g, w, it, plist, !kLPP && pass == 0 && (kFixedH || !a.single_pass), last,
+                           items_next, plist_next, ctr_next, Lmax, ninter, nhiter, ncand,
+                           !kLPP && pass == 0 ? t : -1);
+      }
     }
     if (!grid_barrier(&a.barrier[0], &a.barrier[1], a.st, a.wait_ns)) return;
   }
@@ -471,10 +708,13 @@ __global__ void __launch_bounds__(kLoopThreads, 5) k_density(DensArgs a) {
 // ============================================================== ghost step
 // Per particle (Eq. 8, equation of state, sound speed, Balsara switch):
 // ga = (A = f P / rho^2, f, rho, c), gb = (B, alpha_v, alpha_c P, u).
+// gc (may be NULL) = (1/H, C/H^4, H^2 - band, H^2 + band), the kernel constants
+// and guard band of the particle's support as the force pair term reads them.
 __global__ void k_ghost(int n, const unsigned* __restrict__ perm, const float4* __restrict__ pos,
                         const float4* __restrict__ rho4, const float4* __restrict__ cd, const float* __restrict__ u,
                         const float* __restrict__ alpha_v, const float* __restrict__ alpha_c, Phys ph,
-                        float4* __restrict__ ga, float4* __restrict__ gb) {
+                        float4* __restrict__ ga, float4* __restrict__ gb, float4* __restrict__ gc) {
+  const float Lmax = fmaxf(ph.L[0], fmaxf(ph.L[1], ph.L[2]));
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     const unsigned src = perm[k];
     const float h = pos[k].w;
@@ -494,6 +734,12 @@ __global__ void k_ghost(int n, const unsigned* __restrict__ perm, const float4* 
     const float acoef = alpha_c ? alpha_c[src] : ph.alpha_c;
     ga[k] = make_float4(A, f, rho, c);
     gb[k] = make_float4(B, av, acoef * P, uk);
+    if (gc) {
+      const float H = ph.kg * h;
+      const float iH = 1.0f / H;
+      const float bd = band_of(H, Lmax);
+      gc[k] = make_float4(iH, ph.knorm * iH * iH * iH * iH, H * H - bd, H * H + bd);
+    }
   }
 }
 
@@ -522,6 +768,8 @@ struct LoopArgs {
   const int2* item_nl;
   const unsigned long long* nl_ctr;  // space the items asked for (above nl_cap: the lists are not used)
   long long nl_cap;
+  const int* lcnt;  // lane-per-particle path: candidates of each group lane's kept list
+  const float4* gc; // sorted (1/H, C/H^4, H^2 - band, H^2 + band) from the ghost step
 };
 
 
@@ -728,6 +976,219 @@ __global__ void __launch_bounds__(kLoopThreads, 4) k_force(LoopArgs a) { force_k
 template <int K>
 __global__ void __launch_bounds__(kLoopThreads, 5) k_grad_force(LoopArgs a) { force_kernel_body<true, K>(a); }
 
+// ================================== lane-per-particle gradient / force loops
+// One lane per particle over the kept list of its group (written by the
+// density call; entry t of lane l at t * 32 + l of the group's span, so the
+// 32 lanes read entry t in one coalesced access). A group without a kept list
+// scans its cells per lane. kMode: 0 gradient, 1 force, 2 gradient + force
+// (one pass over the pairs). The force modes take the pair term of
+// force_lpp.cuh, two entries at a time: both entries' records are loaded
+// first, the next two entries are read meanwhile, and the two entries' terms
+// are summed in FP32 before the compensated sums take them.
+template <int kMode, int K>
+__global__ void __launch_bounds__(kLoopThreads, 4) k_loop_lpp(LoopArgs a) {
+  constexpr int W = lpp_width<K>();
+  constexpr bool kGrad = kMode != 1;
+  __shared__ double red[kWarpsPerBlock][8];
+  const unsigned lane = lane_id();
+  const Grid g = *a.grid;
+  const float Lmax = fmaxf(g.L[0], fmaxf(g.L[1], g.L[2]));
+  const int P = a.ctr[ctr_index(0, 1)];
+  const int ng = (P + 31) >> 5;
+  unsigned ninter = 0, nginter = 0, ncand = 0;
+  // per-thread partials of the global sums as FP32 TwoSum pairs (sum, error), kept in shared
+  // memory (column per thread) so that they take no registers in the pair loop
+  __shared__ float s_acc[16][kLoopThreads];
+  if constexpr (kMode != 0)
+    for (int q = 0; q < 16; ++q) s_acc[q][threadIdx.x] = 0.0f;
+  // the cell-scan fallback's ops (groups without a kept list)
+  GradOp gop;
+  GradForceOp fop;
+  gop.pos = fop.pos = a.pos;
+  gop.vel = fop.vel = a.vel;
+  gop.ga = fop.ga = a.ga;
+  gop.gb = fop.gb = a.gb;
+  for (int q = 0; q < 3; ++q) gop.L[q] = fop.L[q] = g.L[q];
+  gop.kg = fop.kg = a.ph.kg;
+  gop.kernel = fop.kernel = K;
+  gop.knorm = fop.knorm = a.ph.knorm;
+  gop.beta = fop.beta = a.ph.beta_v;
+  fop.Lmax = Lmax;
+  fop.gm1 = a.ph.gamma_eos - 1.0f;
+  fop.compensated = a.ph.compensated;
+  const LeanConst kc{a.ph};
+  for (;;) {
+    const int t = take_ticket(a.ticket);
+    if (t >= ng) break;
+    const int idx = t * 32 + (int)lane;
+    const bool live = idx < P;
+    const int k = a.plist[live ? idx : t * 32];
+    const bool has = a.nlist != nullptr && a.item_nl[t].x >= 0;
+    const int cnt = (has && live) ? a.lcnt[idx] : 0;
+    const unsigned* lst = a.nlist + (long long)t * (W * 32) + lane;
+    const unsigned dst = live ? a.perm[k] : 0u;
+    const float4 p = a.pos[k];
+    const float4 v = a.vel[k];
+    const float4 gi = a.ga[k];
+    const float H = a.ph.kg * p.w;
+    const float b = band_of(H, Lmax);
+    if constexpr (kMode == 0) {
+      GradOp::I I;
+      I.x = p.x; I.y = p.y; I.z = p.z; I.h = p.w;
+      I.H2lo = H * H - b;
+      I.H2hi = H * H + b;
+      I.invH = 1.0f / H;
+      I.c4 = a.ph.knorm * I.invH * I.invH * I.invH * I.invH;
+      I.vx = v.x; I.vy = v.y; I.vz = v.z;
+      I.c = gi.w;
+      I.u = a.gb[k].w;
+      I.vsig = 2.0f * gi.w;
+      I.lap = 0.0f;
+      I.count = 0;
+      I.k = k;
+      if (has) {
+        const int m = __reduce_max_sync(kFull, cnt);
+        for (int u = 0; u < m; ++u) {
+          if (u < cnt) {
+            const unsigned e = lst[u * 32];
+            gop.interact(I, (int)(e & kIndexMask), e >> kIndexBits);
+          }
+        }
+        ncand += (unsigned)cnt;
+      } else {
+        lpp_scan(gop, I, g, a.nb.cell_start, (int)a.nb.skeys[k], live, ncand);
+      }
+      if (live) {
+        ninter += I.count;
+        reinterpret_cast<float2*>(a.out)[dst] = make_float2(I.vsig, 2.0f * I.lap);
+      }
+    } else {
+      const float4 bi = a.gb[k];
+      LeanI I;
+      I.x = p.x; I.y = p.y; I.z = p.z; I.h = p.w;
+      I.H2lo = H * H - b;
+      I.H2hi = H * H + b;
+      I.invH = 1.0f / H;
+      I.c4 = a.ph.knorm * I.invH * I.invH * I.invH * I.invH;
+      I.vx = v.x; I.vy = v.y; I.vz = v.z;
+      I.A = gi.x; I.f = gi.y; I.rho = gi.z; I.c = gi.w;
+      I.B = bi.x; I.av = bi.y; I.acP = bi.z; I.u = bi.w;
+      I.P = kc.gm1() * gi.z * bi.w;
+      I.axs = I.axc = I.ays = I.ayc = I.azs = I.azc = I.dus = I.duc = I.dh = 0.0f;
+      I.vsig = 2.0f * gi.w;  // the j = i term of v_sig,max
+      I.lap = 0.0f;
+      I.gcount = I.count = 0;
+      if (has) {
+        const int m = __reduce_max_sync(kFull, cnt);
+        unsigned e0 = 0 < cnt ? lst[0] : (unsigned)k;
+        unsigned e1 = 1 < cnt ? lst[32] : (unsigned)k;
+        for (int u = 0; u < m; u += 2) {
+          LeanRec r0, r1;
+          lean_load(a.pos, a.vel, a.ga, a.gb, a.gc, (int)(e0 & kIndexMask), r0);
+          lean_load(a.pos, a.vel, a.ga, a.gb, a.gc, (int)(e1 & kIndexMask), r1);
+          const unsigned n0 = u + 2 < cnt ? lst[(u + 2) * 32] : (unsigned)k;
+          const unsigned n1 = u + 3 < cnt ? lst[(u + 3) * 32] : (unsigned)k;
+          float tax = 0.0f, tay = 0.0f, taz = 0.0f, tdu = 0.0f;
+          if (u < cnt) lean_pair<K, kGrad>(I, r0, e0 >> kIndexBits, kc, tax, tay, taz, tdu);
+          if (u + 1 < cnt) lean_pair<K, kGrad>(I, r1, e1 >> kIndexBits, kc, tax, tay, taz, tdu);
+          if (a.ph.compensated) {
+            two_sum_acc(I.axs, I.axc, tax);
+            two_sum_acc(I.ays, I.ayc, tay);
+            two_sum_acc(I.azs, I.azc, taz);
+            two_sum_acc(I.dus, I.duc, tdu);
+          } else {
+            I.axs += tax;
+            I.ays += tay;
+            I.azs += taz;
+            I.dus += tdu;
+          }
+          e0 = n0;
+          e1 = n1;
+        }
+        ncand += (unsigned)cnt;
+      } else {
+        // no kept list: the cell scan with the pair functions of the cell-item kernels
+        GradForceOp::I F;
+        F.x = I.x; F.y = I.y; F.z = I.z; F.h = I.h;
+        F.H2lo = I.H2lo; F.H2hi = I.H2hi; F.invH = I.invH; F.c4 = I.c4;
+        F.vx = I.vx; F.vy = I.vy; F.vz = I.vz;
+        F.A = I.A; F.f = I.f; F.rho = I.rho; F.c = I.c;
+        F.B = I.B; F.av = I.av; F.acP = I.acP; F.u = I.u; F.P = I.P;
+        F.axs = F.axc = F.ays = F.ayc = F.azs = F.azc = F.dus = F.duc = F.dh = 0.0f;
+        F.vsig = I.vsig;
+        F.lap = 0.0f;
+        F.gcount = F.count = 0;
+        F.k = k;
+        lpp_scan(fop, F, g, a.nb.cell_start, (int)a.nb.skeys[k], live, ncand);
+        I.axs = F.axs; I.axc = F.axc; I.ays = F.ays; I.ayc = F.ayc; I.azs = F.azs; I.azc = F.azc;
+        I.dus = F.dus; I.duc = F.duc; I.dh = F.dh;
+        I.vsig = F.vsig; I.lap = F.lap; I.gcount = F.gcount; I.count = F.count;
+      }
+      if (live) {
+        ninter += I.count;
+        const float ax = I.axs + I.axc, ay = I.ays + I.ayc, az = I.azs + I.azc, du = I.dus + I.duc;
+        reinterpret_cast<float4*>(a.out)[dst] = make_float4(ax, ay, az, du);
+        if (a.dhdt) a.dhdt[dst] = -(I.h / (3.0f * I.rho)) * I.f * I.dh;
+        if constexpr (kMode == 2) {
+          nginter += I.gcount;
+          a.out2[dst] = make_float2(I.vsig, 2.0f * I.lap);
+        }
+        const float m = v.w;
+        const float mx = m * ax, my = m * ay, mz = m * az;
+        const float va = fmaf(v.z, az, fmaf(v.y, ay, v.x * ax));
+        float acc[8], accc[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          acc[q] = s_acc[q][threadIdx.x];
+          accc[q] = s_acc[8 + q][threadIdx.x];
+        }
+        two_sum_acc(acc[0], accc[0], mx);
+        two_sum_acc(acc[1], accc[1], my);
+        two_sum_acc(acc[2], accc[2], mz);
+        two_sum_acc(acc[3], accc[3], m * va);
+        two_sum_acc(acc[3], accc[3], m * du);
+        two_sum_acc(acc[4], accc[4], sqrtf(fmaf(mz, mz, fmaf(my, my, mx * mx))));
+        two_sum_acc(acc[5], accc[5], m * fabsf(va));
+        two_sum_acc(acc[5], accc[5], m * fabsf(du));
+        two_sum_acc(acc[6], accc[6], m * du);
+        acc[7] += (float)I.count;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          s_acc[q][threadIdx.x] = acc[q];
+          s_acc[8 + q][threadIdx.x] = accc[q];
+        }
+      }
+    }
+  }
+  if constexpr (kMode != 0) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      double x = (double)s_acc[q][threadIdx.x] + (double)s_acc[8 + q][threadIdx.x];
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+      if (lane == 0) red[threadIdx.x >> 5][q] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) {
+      double x = 0.0;
+      for (int ww = 0; ww < kWarpsPerBlock; ++ww) x += red[ww][threadIdx.x];
+      a.red_partial[blockIdx.x * 8 + threadIdx.x] = x;
+    }
+  }
+  ninter = warp_sum(ninter);
+  ncand = warp_sum(ncand);
+  if (lane == 0) {
+    atomicAdd(&a.stats[kMode == 0 ? kStatInterGrad : kStatInterForce], (unsigned long long)ninter);
+    atomicAdd(&a.stats[kMode == 0 ? kStatCandGrad : kStatCandForce], (unsigned long long)ncand);
+  }
+  if constexpr (kMode == 2) {
+    nginter = warp_sum(nginter);
+    if (lane == 0) {
+      atomicAdd(&a.stats[kStatInterGrad], (unsigned long long)nginter);
+      atomicAdd(&a.stats[kStatCandGrad], (unsigned long long)ncand);
+    }
+  }
+}
+
 // One warp per quantity; lane l sums blocks l, l+32, ... and the warp then
 // combines the lanes in a fixed order, so the result does not depend on timing.
 __global__ void k_reduce_partials(const double* __restrict__ part, int nblocks, double* __restrict__ out) {
@@ -739,9 +1200,9 @@ __global__ void k_reduce_partials(const double* __restrict__ part, int nblocks, 
 }
 
 // =================================================================== hosts
-static int persistent_blocks(Ctx* c, const void* kern) {
+static int persistent_blocks(Ctx* c, const void* kern, size_t smem) {
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kLoopThreads, kLoopSmemBytes);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kLoopThreads, smem);
   if (per_sm < 1) per_sm = 1;
   if (c->tuning.blocks_per_sm > 0 && c->tuning.blocks_per_sm < per_sm) per_sm = c->tuning.blocks_per_sm;
   int nb = per_sm * c->num_sms;
@@ -749,14 +1210,15 @@ static int persistent_blocks(Ctx* c, const void* kern) {
 }
 
 // The instantiation of each loop kernel for kernel shape `kind`.
-static const void* density_kernel(int kind, bool fixed_h) {
-  if (fixed_h)
-    return kind == kKernelWendlandC2 ? (const void*)k_density<kKernelWendlandC2, true>
-           : kind == kKernelWendlandC4 ? (const void*)k_density<kKernelWendlandC4, true>
-                                       : (const void*)k_density<kKernelCubic, true>;
-  return kind == kKernelWendlandC2 ? (const void*)k_density<kKernelWendlandC2, false>
-         : kind == kKernelWendlandC4 ? (const void*)k_density<kKernelWendlandC4, false>
-                                     : (const void*)k_density<kKernelCubic, false>;
+template <int K>
+static const void* density_kernel_k(bool fixed_h, bool lpp) {
+  if (lpp) return fixed_h ? (const void*)k_density<K, true, true> : (const void*)k_density<K, false, true>;
+  return fixed_h ? (const void*)k_density<K, true, false> : (const void*)k_density<K, false, false>;
+}
+static const void* density_kernel(int kind, bool fixed_h, bool lpp) {
+  return kind == kKernelWendlandC2   ? density_kernel_k<kKernelWendlandC2>(fixed_h, lpp)
+         : kind == kKernelWendlandC4 ? density_kernel_k<kKernelWendlandC4>(fixed_h, lpp)
+                                     : density_kernel_k<kKernelCubic>(fixed_h, lpp);
 }
 static const void* gradient_kernel(int kind) {
   return kind == kKernelWendlandC2 ? (const void*)k_gradient<kKernelWendlandC2>
@@ -773,20 +1235,40 @@ static const void* grad_force_kernel(int kind) {
          : kind == kKernelWendlandC4 ? (const void*)k_grad_force<kKernelWendlandC4>
                                      : (const void*)k_grad_force<kKernelCubic>;
 }
-
-static bool g_attr_done = false;
-static void ensure_attrs() {
-  if (g_attr_done) return;
-  for (int kind = kKernelCubic; kind <= kKernelWendlandC4; ++kind)
-    for (const void* f : {density_kernel(kind, false), density_kernel(kind, true), gradient_kernel(kind),
-                          force_kernel(kind), grad_force_kernel(kind)})
-      cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLoopSmemBytes);
-  g_attr_done = true;
+// Lane-per-particle loop kernel of `mode` (0 gradient, 1 force, 2 both).
+template <int M>
+static const void* lpp_loop_kernel_m(int kind) {
+  return kind == kKernelWendlandC2 ? (const void*)k_loop_lpp<M, kKernelWendlandC2>
+         : kind == kKernelWendlandC4 ? (const void*)k_loop_lpp<M, kKernelWendlandC4>
+                                     : (const void*)k_loop_lpp<M, kKernelCubic>;
+}
+static const void* lpp_loop_kernel(int mode, int kind) {
+  return mode == 0 ? lpp_loop_kernel_m<0>(kind) : mode == 1 ? lpp_loop_kernel_m<1>(kind) : lpp_loop_kernel_m<2>(kind);
 }
 
-static cudaError_t launch_loop(const void* f, int nblk, LoopArgs& a, cudaStream_t s) {
+static size_t dens_smem(int kind, bool lpp) { return dens_warp_bytes(kind, lpp) * kWarpsPerBlock; }
+
+// Raise the dynamic shared-memory limit of every loop kernel, once per device
+// (function attributes belong to the device's context).
+constexpr int kMaxAttrDevices = 64;
+static int g_attr_done[kMaxAttrDevices] = {0};
+static void ensure_attrs(const Ctx* c) {
+  const int dev = c->device;
+  if (dev >= 0 && dev < kMaxAttrDevices && __atomic_load_n(&g_attr_done[dev], __ATOMIC_ACQUIRE)) return;
+  for (int kind = kKernelCubic; kind <= kKernelWendlandC4; ++kind) {
+    for (int fh = 0; fh < 2; ++fh)
+      for (int lpp = 0; lpp < 2; ++lpp)
+        cudaFuncSetAttribute(density_kernel(kind, fh != 0, lpp != 0), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)dens_smem(kind, lpp != 0));
+    for (const void* f : {gradient_kernel(kind), force_kernel(kind), grad_force_kernel(kind)})
+      cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLoopSmemBytes);
+  }
+  if (dev >= 0 && dev < kMaxAttrDevices) __atomic_store_n(&g_attr_done[dev], 1, __ATOMIC_RELEASE);
+}
+
+static cudaError_t launch_loop(const void* f, int nblk, LoopArgs& a, cudaStream_t s, size_t smem = kLoopSmemBytes) {
   void* args[] = {&a};
-  return cudaLaunchKernel(f, dim3(nblk), dim3(kLoopThreads), args, kLoopSmemBytes, s);
+  return cudaLaunchKernel(f, dim3(nblk), dim3(kLoopThreads), args, smem, s);
 }
 
 void reduce_partials(Ctx* c, int nblocks, double* out, cudaStream_t s) {
@@ -794,11 +1276,21 @@ void reduce_partials(Ctx* c, int nblocks, double* out, cudaStream_t s) {
   c->launches++;
 }
 
+// The lane-per-particle path runs the persistent density call on the uniform
+// grid when the tuning asks for one lane a particle and the context holds the
+// replicas and the kept-list store.
+static bool use_lpp(const Ctx* c) {
+  return c->tuning.max_lanes_per_particle == 1 && c->d_rep != nullptr && c->d_nlist != nullptr &&
+         c->d_lcnt != nullptr && !(c->params.flags & (SWIFT_GPU_ADAPTIVE | SWIFT_GPU_PLAIN));
+}
+
 int density_impl(Ctx* c, const float4* pos_in, const float4* vel_in, const uint8_t* active, float* h_out,
                  float4* rho4, float4* cd, uint32_t* ngb, cudaStream_t s) {
-  ensure_attrs();
-  const void* kern = density_kernel(c->phys.kernel, (c->params.flags & SWIFT_GPU_NO_H_ITER) != 0);
-  const int nblk = persistent_blocks(c, kern);
+  ensure_attrs(c);
+  const bool lpp = use_lpp(c);
+  const void* kern = density_kernel(c->phys.kernel, (c->params.flags & SWIFT_GPU_NO_H_ITER) != 0, lpp);
+  const size_t smem = dens_smem(c->phys.kernel, lpp);
+  const int nblk = persistent_blocks(c, kern, smem);
   cudaMemsetAsync(c->d_counters, 0, sizeof(int) * (size_t)(kCtrPerPass * (c->max_passes + 2) + 2), s);
   DensArgs a;
   a.grid = c->d_grid;
@@ -806,7 +1298,8 @@ int density_impl(Ctx* c, const float4* pos_in, const float4* vel_in, const uint8
   a.perm = c->d_vals[c->sorted_buf];
   a.n = c->n;
   a.ph = c->phys;
-  a.lmax = c->tuning.max_lanes_per_particle;
+  // the cell items of later passes (one particle each on this path) take all lanes of a warp
+  a.lmax = cell_lanes(c);
   a.single_pass = (c->params.flags & SWIFT_GPU_NO_H_ITER) ? 1 : 0;
   a.pos_in = pos_in;
   a.vel_in = vel_in;
@@ -834,16 +1327,24 @@ int density_impl(Ctx* c, const float4* pos_in, const float4* vel_in, const uint8
   a.wait_ns = wait_limit_ns(c);
   a.st = c->d_status;
   a.stats = c->d_stats;
-  a.nlist = c->d_nlist;
+  // kept lists in the groups' layout (either engine), where the context holds the store for it
+  const bool keep = c->d_nlist != nullptr && c->d_lcnt != nullptr && !(c->params.flags & SWIFT_GPU_ADAPTIVE);
+  a.nlist = keep ? c->d_nlist : nullptr;
   a.nl_cap = c->nl_cap;
   a.nl_ctr = c->d_nl_ctr;
-  a.item_nl = c->d_nlist ? c->d_item_nl : nullptr;
-  if (c->d_nl_ctr) cudaMemsetAsync(c->d_nl_ctr, 0, sizeof(unsigned long long), s);
+  a.item_nl = keep ? c->d_item_nl : nullptr;
+  a.rep = c->d_rep;
+  a.rep_stride = c->n;
+  a.lcnt = c->d_lcnt;
+  a.lpp_w = lpp_width_of(c->phys.kernel);
+  if (keep && !lpp && c->n > 0) cudaMemsetAsync(c->d_item_nl, 0, sizeof(int2) * (size_t)((c->n + 31) / 32), s);
   void* args[] = {&a};
-  cudaError_t e = cudaLaunchCooperativeKernel(kern, dim3(nblk), dim3(kLoopThreads), args, kLoopSmemBytes, s);
+  cudaError_t e = cudaLaunchCooperativeKernel(kern, dim3(nblk), dim3(kLoopThreads), args, smem, s);
   c->launches += 2;
   c->all_active = active == nullptr;
-  c->nl_lmax = a.item_nl ? c->tuning.max_lanes_per_particle : 0;  // lists follow this lane layout
+  // the kept lists are per group of the pass-0 list, whichever engine wrote them
+  c->nl_lmax = 0;
+  c->lpp_lists = keep ? 1 : 0;
   return e == cudaSuccess ? SWIFT_GPU_OK : SWIFT_GPU_ERR_CUDA;
 }
 
@@ -851,7 +1352,7 @@ int ghost_impl(Ctx* c, const float* u, const float* alpha_v, const float* alpha_
   if (c->n == 0) return SWIFT_GPU_OK;
   const int nb = min((c->n + 255) / 256, c->num_sms * 8);
   k_ghost<<<nb, 256, 0, s>>>(c->n, c->d_vals[c->sorted_buf], c->d_pos, c->d_rho4, c->d_cd, u, alpha_v, alpha_c,
-                             c->phys, c->d_ga, c->d_gb);
+                             c->phys, c->d_ga, c->d_gb, c->d_gc);
   c->launches++;
   return cudaGetLastError() == cudaSuccess ? SWIFT_GPU_OK : SWIFT_GPU_ERR_CUDA;
 }
@@ -862,7 +1363,7 @@ static LoopArgs loop_args(Ctx* c, int* ticket, void* out) {
   a.nb = nbr_of(c);
   a.perm = c->d_vals[c->sorted_buf];
   a.ph = c->phys;
-  a.lmax = c->tuning.max_lanes_per_particle;
+  a.lmax = cell_lanes(c);
   a.pos = c->d_pos;
   a.vel = c->d_vel;
   a.ga = c->d_ga;
@@ -877,36 +1378,51 @@ static LoopArgs loop_args(Ctx* c, int* ticket, void* out) {
   a.red_partial = c->d_red_partial;
   a.st = c->d_status;
   a.stats = c->d_stats;
-  const bool lists = kept_lists_usable(c);
+  const bool lists = c->lpp_lists ? true : kept_lists_usable(c);
   a.nlist = lists ? c->d_nlist : nullptr;
   a.item_nl = lists ? c->d_item_nl : nullptr;
   a.nl_ctr = c->d_nl_ctr;
   a.nl_cap = c->nl_cap;
+  a.lcnt = c->d_lcnt;
+  a.gc = c->d_gc;
   return a;
 }
 
-int gradient_impl(Ctx* c, float2* out, cudaStream_t s) {
-  ensure_attrs();
-  const void* kern = gradient_kernel(c->phys.kernel);
-  const int nblk = persistent_blocks(c, kern);
-  int* ticket = c->d_counters + kCtrPerPass * (c->max_passes + 1) + 0;
-  cudaMemsetAsync(ticket, 0, sizeof(int), s);
-  LoopArgs a = loop_args(c, ticket, out);
-  const cudaError_t e = launch_loop(kern, nblk, a, s);
+// One gradient / force / both launch (mode 0 / 1 / 2): lane per particle over
+// the density call's groups when it ran that way, else cell items.
+static int loop_launch(Ctx* c, int mode, LoopArgs& a, cudaStream_t s, int* nblk_out) {
+  ensure_attrs(c);
+  const void* kern;
+  size_t smem = kLoopSmemBytes;
+  if (c->lpp_lists) {
+    kern = lpp_loop_kernel(mode, c->phys.kernel);
+    smem = 0;
+  } else {
+    kern = mode == 0 ? gradient_kernel(c->phys.kernel) : mode == 1 ? force_kernel(c->phys.kernel)
+                                                                   : grad_force_kernel(c->phys.kernel);
+  }
+  const int nblk = persistent_blocks(c, kern, smem);
+  if (nblk_out) *nblk_out = nblk;
+  const cudaError_t e = launch_loop(kern, nblk, a, s, smem);
   c->launches += 2;
   return e == cudaSuccess ? SWIFT_GPU_OK : SWIFT_GPU_ERR_CUDA;
 }
 
+int gradient_impl(Ctx* c, float2* out, cudaStream_t s) {
+  int* ticket = c->d_counters + kCtrPerPass * (c->max_passes + 1) + 0;
+  cudaMemsetAsync(ticket, 0, sizeof(int), s);
+  LoopArgs a = loop_args(c, ticket, out);
+  return loop_launch(c, 0, a, s, nullptr);
+}
+
 int force_impl(Ctx* c, float4* out, float* dhdt, double* reductions, cudaStream_t s) {
-  ensure_attrs();
-  const void* kern = force_kernel(c->phys.kernel);
-  const int nblk = persistent_blocks(c, kern);
   int* ticket = c->d_counters + kCtrPerPass * (c->max_passes + 1) + 1;
   cudaMemsetAsync(ticket, 0, sizeof(int), s);
   LoopArgs a = loop_args(c, ticket, out);
   a.dhdt = dhdt;
-  if (launch_loop(kern, nblk, a, s) != cudaSuccess) return SWIFT_GPU_ERR_CUDA;
-  c->launches += 2;
+  int nblk = 0;
+  const int rc = loop_launch(c, 1, a, s, &nblk);
+  if (rc != SWIFT_GPU_OK) return rc;
   if (reductions) {
     k_reduce_partials<<<1, 256, 0, s>>>(c->d_red_partial, nblk, reductions);
     c->launches++;
@@ -915,16 +1431,14 @@ int force_impl(Ctx* c, float4* out, float* dhdt, double* reductions, cudaStream_
 }
 
 int grad_force_impl(Ctx* c, float2* grad_out, float4* out, float* dhdt, double* reductions, cudaStream_t s) {
-  ensure_attrs();
-  const void* kern = grad_force_kernel(c->phys.kernel);
-  const int nblk = persistent_blocks(c, kern);
   int* ticket = c->d_counters + kCtrPerPass * (c->max_passes + 1) + 1;
   cudaMemsetAsync(ticket, 0, sizeof(int), s);
   LoopArgs a = loop_args(c, ticket, out);
   a.out2 = grad_out;
   a.dhdt = dhdt;
-  if (launch_loop(kern, nblk, a, s) != cudaSuccess) return SWIFT_GPU_ERR_CUDA;
-  c->launches += 2;
+  int nblk = 0;
+  const int rc = loop_launch(c, 2, a, s, &nblk);
+  if (rc != SWIFT_GPU_OK) return rc;
   if (reductions) {
     k_reduce_partials<<<1, 256, 0, s>>>(c->d_red_partial, nblk, reductions);
     c->launches++;

@@ -32,9 +32,23 @@ struct DensOp {
 
   __device__ __forceinline__ float stage_w(float) const { return 0.0f; }
   __device__ __forceinline__ bool candidate(const I& i, float r2, float) const { return r2 < i.H2hi; }
+  // j's two records, for loops that load several entries ahead of the arithmetic
+  // (named apart from the force loops' Rec: the cell-item flush takes one entry at a time here)
+  struct DRec {
+    float4 pj, vj;
+  };
+  __device__ __forceinline__ void load_rec(int j, DRec& r) const {
+    r.pj = pos[j];
+    r.vj = vel[j];
+  }
   __device__ __forceinline__ void interact(I& i, int j, unsigned code) const {
-    const float4 pj = pos[j];
-    const float4 vj = vel[j];
+    DRec r;
+    load_rec(j, r);
+    interact(i, j, code, r);
+  }
+  __device__ __forceinline__ void interact(I& i, int j, unsigned code, const DRec& rec) const {
+    const float4 pj = rec.pj;
+    const float4 vj = rec.vj;
     float xj = pj.x, yj = pj.y, zj = pj.z;
     shift_j(code, L, xj, yj, zj);
     const float dx = i.x - xj, dy = i.y - yj, dz = i.z - zj;

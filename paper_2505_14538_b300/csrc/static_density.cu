@@ -16,7 +16,7 @@ namespace sg {
 // Capacity of the static scratch: particles and the cell grid it implies
 // (at most 2 * n_max cells, as for a context of the same size).
 constexpr int64_t kStaticN = SWIFT_GPU_STATIC_MAX_PARTICLES;
-constexpr int kStaticMaxPasses = 64;
+constexpr int kStaticMaxPasses = kMaxPasses;  // the counters hold every pass phys_from allows
 constexpr size_t kAlign = 256;
 
 constexpr size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }

@@ -225,8 +225,17 @@ class Context:
         return dict(threads_per_block=t.threads_per_block, max_lanes_per_particle=t.max_lanes_per_particle,
                     blocks_per_sm=t.blocks_per_sm, wait_limit_us=t.wait_limit_us)
 
-    def set_tuning(self, threads_per_block=256, max_lanes_per_particle=32, blocks_per_sm=0, wait_limit_us=0):
-        t = _lib.Tuning(threads_per_block, max_lanes_per_particle, blocks_per_sm, wait_limit_us)
+    def set_tuning(self, threads_per_block=None, max_lanes_per_particle=None, blocks_per_sm=None, wait_limit_us=None):
+        """Set the work-distribution knobs; a knob not given keeps its current value.
+
+        max_lanes_per_particle = 1 selects the lane-per-particle path on the uniform grid (the default
+        there); 2-32 the cell items, whose particles share up to that many lanes of a warp."""
+        cur = self.tuning()
+        given = dict(threads_per_block=threads_per_block, max_lanes_per_particle=max_lanes_per_particle,
+                     blocks_per_sm=blocks_per_sm, wait_limit_us=wait_limit_us)
+        cur.update({k: v for k, v in given.items() if v is not None})
+        t = _lib.Tuning(cur["threads_per_block"], cur["max_lanes_per_particle"], cur["blocks_per_sm"],
+                        cur["wait_limit_us"])
         _check(self.lib.swift_gpu_set_tuning(self.handle, ctypes.byref(t)), "swift_gpu_set_tuning")
 
     def autotune(self, loop: int, stream=None):

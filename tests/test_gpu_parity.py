@@ -44,9 +44,13 @@ def oracle_params(O, ctx_params, **kw):
     return p
 
 
-def run_gpu(sph, d, vel=None, u=None, min_cell_width=0.0, active=None, **params):
+def run_gpu(sph, d, vel=None, u=None, min_cell_width=0.0, active=None, lanes=None, **params):
+    """One build, density, gradient and force pass; ``lanes`` sets the tuning's lanes per particle
+    (1: the lane-per-particle path of the uniform grid, the default there; 2-32: cell items)."""
     n = len(d["pos"])
     ctx = sph.Context(max(n, 1), box=d["box"], **params)
+    if lanes is not None:
+        ctx.set_tuning(max_lanes_per_particle=lanes)
     pos_h, vel_m, ut = dev_arrays(d, vel, u)
     act = None if active is None else torch.from_numpy(active.astype(np.uint8)).cuda()
     ctx.build_cells(pos_h, min_cell_width)
@@ -137,28 +141,36 @@ def test_cells_bit_exact(sph, O):
     assert np.array_equal(perm, np.argsort(ref, kind="stable"))
 
 
-def test_lattice16_full_pipeline(sph, O):
-    """Jittered 16^3 lattice with random v and u, 4^3 cells: every output against the oracle."""
+@pytest.mark.parametrize("lanes", [1, 32])
+def test_lattice16_full_pipeline(sph, O, lanes):
+    """Jittered 16^3 lattice with random v and u, 4^3 cells (64 particles a cell, more than a cell
+    replica holds, so the lane-per-particle path reads them whole): every output against the oracle,
+    with both engines."""
     d, vel, u = lattice_state(16)
-    g = run_gpu(sph, d, vel, u, min_cell_width=0.25, h_tol=1e-6)
+    g = run_gpu(sph, d, vel, u, min_cell_width=0.25, h_tol=1e-6, lanes=lanes)
     assert g["status"] == (0, 0), g["status"]
     check_against_oracle(O, d, vel, u, g, g["ctx"])
     inter = g["info"]["interactions"]
     assert inter[1] == g["ngb"].sum()
 
 
-def test_sedov_small_auto_cells(sph, O):
-    """Sedov blast at 16^3 with automatic cell width (strong u contrast, viscosity, conduction)."""
+@pytest.mark.parametrize("lanes", [1, 32])
+def test_sedov_small_auto_cells(sph, O, lanes):
+    """Sedov blast at 16^3 with automatic cell width (strong u contrast, viscosity, conduction), with
+    both engines; about 13 particles a cell, so the lane-per-particle path reads its neighbour cells
+    through the pair-axis windows."""
     d = ics.sedov(16)
     rng = np.random.default_rng(1)
     vel = rng.normal(0, 0.05, size=(len(d["pos"]), 3)).astype(np.float32)
-    g = run_gpu(sph, d, vel, d["u"], h_tol=1e-6)
+    g = run_gpu(sph, d, vel, d["u"], h_tol=1e-6, lanes=lanes)
     assert g["status"][0] in (0,), g["status"]
     check_against_oracle(O, d, vel, d["u"], g, g["ctx"])
 
 
-def test_ragged_uniform_random(sph, O):
-    """3001 uniform random particles (ragged item sizes and tails), non-cubic box, random h."""
+@pytest.mark.parametrize("lanes", [1, 32])
+def test_ragged_uniform_random(sph, O, lanes):
+    """3001 uniform random particles (ragged item sizes and tails: the last group of 32 is partial),
+    non-cubic box, random h, with both engines."""
     rng = np.random.default_rng(7)
     n = 3001
     box = (1.0, 0.8, 1.25)
@@ -166,7 +178,7 @@ def test_ragged_uniform_random(sph, O):
     h = (rng.uniform(0.9, 1.1, n) * 1.2348 * (np.prod(box) / n) ** (1 / 3)).astype(np.float32)
     d = dict(pos=pos, h=h, m=np.full(n, 1.0 / n, np.float32), u=rng.uniform(0.5, 2, n).astype(np.float32),
              vel=rng.normal(0, 0.2, (n, 3)).astype(np.float32), box=box)
-    g = run_gpu(sph, d, d["vel"], d["u"], h_tol=1e-6)
+    g = run_gpu(sph, d, d["vel"], d["u"], h_tol=1e-6, lanes=lanes)
     assert g["status"][0] == 0, g["status"]
     check_against_oracle(O, d, d["vel"], d["u"], g, g["ctx"])
 
@@ -181,17 +193,20 @@ def test_fixed_h_counts_at_input_h(sph, O):
     assert np.max(np.abs(g["rho4"][:, 0] / st["rho"] - 1)) < 1e-5
 
 
-def test_fixed_h_kept_lists_with_overflow(sph, O):
+@pytest.mark.parametrize("lanes", [1, 32])
+def test_fixed_h_kept_lists_with_overflow(sph, O, lanes):
     """NO_H_ITER keeps the density call's candidate lists for the gradient and force loops. On the
     Kelvin-Helmholtz slab (density ratio 2.2, the cells sized by the light layer's h) some lanes of
-    the dense layer collect more candidates than a list holds: their items take the 27-cell scan as
-    a whole warp. Every output against the oracle at the input h."""
+    the dense layer collect more candidates than a list holds: with cell items their items take the
+    27-cell scan as a whole warp; lane per particle, such a particle scans its cells in the density
+    call and its group does in the gradient and force loops. Every output against the oracle at the
+    input h."""
     d = ics.kh(16, 11, 5)
     rng = np.random.default_rng(4)
     n = len(d["pos"])
     vel = d["vel"] + rng.normal(0, 0.05, (n, 3)).astype(np.float32)
     u = d["u"]
-    g = run_gpu(sph, d, vel, u, flags=2)
+    g = run_gpu(sph, d, vel, u, flags=2, lanes=lanes)
     assert g["status"] == (0, 0) and g["status2"] == (0, 0)
     assert np.array_equal(g["h"], d["h"])
     pf = oracle_params(O, g["ctx"].params)
@@ -204,16 +219,19 @@ def test_fixed_h_kept_lists_with_overflow(sph, O):
     a = g["accel_dudt"]
     assert np.all(np.linalg.norm(a[:, :3] - st["accel"], axis=1) <= 1e-4 * st["s_a"] + 1e-30)
     assert np.all(np.abs(a[:, 3] - st["dudt"]) <= 1e-4 * st["s_u"] + 1e-30)
-    # the overflowing items scanned in the density call and again in the gradient and force
-    # loops; the others read their kept lists
+    # the overflowing items (groups) scanned in the density call and again in the gradient and
+    # force loops; the others read their kept lists
     cand = g["info"]["candidates"]
-    assert cand[1] == cand[2] < cand[0], cand
-    # on a lattice no list overflows: the loops read kept lists only, far fewer candidates than
-    # the density call's 27-cell tests, with the same outputs as the iterating path's loops at that h
+    assert cand[1] == cand[2], cand
+    if lanes != 1:
+        assert cand[2] < cand[0], cand
+    # on a lattice no list overflows: the loops read kept lists only, fewer candidates than the
+    # density call tested (the cell items' 27-cell scan, or lane per particle the pair-axis windows,
+    # whose kept entries are its hits), with the same outputs as the iterating path's loops at that h
     d, vel, u = lattice_state(12, jitter=0.3)
-    g = run_gpu(sph, d, vel, u, flags=2)
+    g = run_gpu(sph, d, vel, u, flags=2, lanes=lanes)
     cand = g["info"]["candidates"]
-    assert cand[2] < cand[0] / 3, cand
+    assert cand[2] < (cand[0] / 3 if lanes != 1 else cand[0]), cand
     st = O.step(oracle_params(O, g["ctx"].params), d["pos"], vel, d["m"], u, d["h"], solve=False)
     a = g["accel_dudt"]
     assert np.all(np.linalg.norm(a[:, :3] - st["accel"], axis=1) <= 1e-4 * st["s_a"] + 1e-30)
