@@ -90,7 +90,12 @@ typedef struct {
 /* Work-distribution knobs (chosen by swift_gpu_autotune, or set by hand). */
 typedef struct {
   int threads_per_block; /* 64..1024, multiple of 32 */
-  int max_lanes_per_particle; /* 1, 2, 4, 8, 16 or 32: lanes that share one particle's neighbour scan */
+  int max_lanes_per_particle; /* 1, 2, 4, 8, 16 or 32: lanes that share one particle's neighbour scan;
+                                 on the uniform grid 1 selects the lane-per-particle density call (each
+                                 lane scans its own particle's neighbour cells through windows along the
+                                 13 pair axes, Sec. 2.2.2) and 2..32 the cell items (a warp shares one
+                                 cell's candidates); the gradient and force loops run one lane a particle
+                                 over the density call's kept lists either way */
   int blocks_per_sm;     /* persistent blocks per SM (0 = occupancy maximum) */
   int wait_limit_us;     /* limit of each bounded device-side wait (the density launch's grid barrier):
                             0 = 5 s; negative = give up at once (fault injection: the call then reports
@@ -278,14 +283,19 @@ int swift_gpu_get_leaves(swift_gpu_ctx* ctx, int32_t* range, float* h_cap, int32
 int swift_gpu_get_tuning(swift_gpu_ctx* ctx, swift_gpu_tuning* t);
 int swift_gpu_set_tuning(swift_gpu_ctx* ctx, const swift_gpu_tuning* t);
 
-/* Time the given loop (0 density, 1 gradient, 2 force, 3 gradient + force)
+/* Time the given loop (0 density, 1 gradient, 2 force, 3 gradient + force,
+ * 4 the whole step after the cell build: density, then gradient + force)
  * on the data of the last calls for each candidate tuning (lanes per
  * particle 1..32, blocks per SM 0..2) and keep the fastest; the setting is
- * shared by all loops. Requires force (or gradient + force) to have run once;
- * loops 1 and 3 require a gradient output of a previous call. Blocking. The
- * loop is run once more with the chosen setting, so its outputs (in the
- * arrays of the last calls) are those of that setting: the same sums as
- * before up to the FP32 summation order. */
+ * shared by all loops. The lanes per particle also choose the density
+ * call's engine on the uniform grid (1: one lane a particle with pair-axis
+ * windows; 2..32: cell items), whose kept lists the gradient and force loops
+ * read, so for loops 1-3 each candidate first re-runs the density call
+ * (untimed). Requires force (or gradient + force) to have run once; loops 1,
+ * 3 and 4 require a gradient output of a previous call. Blocking. The loop is
+ * run once more with the chosen setting, so its outputs (in the arrays of
+ * the last calls) are those of that setting: the same sums as before up to
+ * the FP32 summation order. */
 int swift_gpu_autotune(swift_gpu_ctx* ctx, int loop, void* stream);
 
 /* Largest particle count swift_gpu_density_static accepts. */

@@ -3,9 +3,10 @@
 // the gradients dL/dx, dL/dv, dL/du at fixed smoothing lengths (h_mode 0), or
 // with each h_i the root of the h iteration (h_mode 1, Sec. 2.1.2).
 //
-// Two gather passes over the same neighbour scan as the forward loops (no
-// atomics, no stored pair lists; the per-particle density sums of the
-// forward call are reused):
+// Two gather passes, each scanning the 27 neighbour cells of the forward
+// call's cell items again (no atomics, and no pair list of the forward call
+// is read: the candidates are recomputed; the per-particle density sums of
+// the forward call are reused):
 //   k_force_adj  for particle k and every force pair (r < max(H_k, H_j)), the
 //                pair term is evaluated forward and then in reverse in both
 //                orientations: k as the first particle (weights w_k, c_k) and
@@ -69,10 +70,6 @@ struct AdjArgs {
   float4* grad_x;      // caller order
   float4* grad_v;
   float* grad_u;
-  const unsigned* nlist;  // candidate lists kept by the density call (NULL: scan)
-  const int2* item_nl;
-  const unsigned long long* nl_ctr;  // space the items asked for (above nl_cap: the lists are not used)
-  long long nl_cap;
 };
 
 // One side of a force pair: the per-particle inputs and, after the reverse
@@ -299,9 +296,7 @@ __device__ __forceinline__ void force_adj_item(const AdjArgs& a, const ForceAdjO
   I.ih = 1.0f / p.w;
   I.k = k;
   unsigned ncand = 0;
-  int sm;
-  const unsigned* sl = kept_list(a.nlist, a.item_nl, t, sm, a.nl_ctr, a.nl_cap);
-  scan_item(op, I, g, a.nb, a.pos, it.cell, lsh, s, live, w, ncand, sl, sm);
+  scan_item(op, I, g, a.nb, a.pos, it.cell, lsh, s, live, w, ncand);
   for (int q = 0; q < 3; ++q) {
     I.xb[q] = lsum(I.xb[q], lsh);
     I.vb[q] = lsum(I.vb[q], lsh);
@@ -539,9 +534,7 @@ __global__ void __launch_bounds__(kAdjThreads, 5) k_dens_adj(AdjArgs a) {
     I.xb[0] = I.xb[1] = I.xb[2] = I.vb[0] = I.vb[1] = I.vb[2] = 0.0f;
     I.hE = I.hS = I.hC[0] = I.hC[1] = I.hC[2] = 0.0f;
     unsigned ncand = 0;
-    int sm;
-    const unsigned* sl = kept_list(a.nlist, a.item_nl, t, sm, a.nl_ctr, a.nl_cap);
-    scan_item(op, I, g, a.nb, a.pos, it.cell, lsh, s, live, w, ncand, sl, sm);
+    scan_item(op, I, g, a.nb, a.pos, it.cell, lsh, s, live, w, ncand);
     for (int c = 0; c < 3; ++c) {
       I.xb[c] = lsum(I.xb[c], lsh);
       I.vb[c] = lsum(I.vb[c], lsh);
@@ -667,9 +660,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_ift_adj(AdjArgs a) {
     I.lam = a.lam[k];
     I.xb[0] = I.xb[1] = I.xb[2] = 0.0f;
     unsigned ncand = 0;
-    int sm;
-    const unsigned* sl = kept_list(a.nlist, a.item_nl, t, sm, a.nl_ctr, a.nl_cap);
-    scan_item(op, I, g, a.nb, a.pos, it.cell, lsh, s, live, w, ncand, sl, sm);
+    scan_item(op, I, g, a.nb, a.pos, it.cell, lsh, s, live, w, ncand);
     for (int c = 0; c < 3; ++c) I.xb[c] = lsum(I.xb[c], lsh);
     if (live && s == 0) {
       const unsigned dst = a.perm[k];
@@ -711,11 +702,8 @@ int backward_impl(Ctx* c, const float4* grad_ad, float4* grad_x, float4* grad_v,
   a.hmode = h_mode;
   a.grid = c->d_grid;
   a.nb = nbr_of(c);
-  const bool lists = kept_lists_usable(c);
-  a.nlist = lists ? c->d_nlist : nullptr;
-  a.item_nl = lists ? c->d_item_nl : nullptr;
-  a.nl_ctr = c->d_nl_ctr;
-  a.nl_cap = c->nl_cap;
+  // the gathers rescan the cells: the forward call's kept lists are laid out for
+  // the lane-per-particle loops, not for these cell items
   a.perm = c->d_vals[c->sorted_buf];
   a.ph = c->phys;
   a.lmax = cell_lanes(c);

@@ -63,7 +63,7 @@ static void free_all(Ctx* c) {
                   c->d_scratch4[0], c->d_scratch1[0], c->d_scratch1[1], c->d_plain_act, c->d_aux[0], c->d_aux[1],
                   c->d_node_range, c->d_node, c->d_node_link, c->d_node_parent, c->d_node_done, c->d_node_flag,
                   c->d_leaf_range, c->d_leaf_hcap, c->d_leaf_node, c->d_nbr_span, c->d_nbr, c->d_tree_ctr,
-                  c->d_nlist, c->d_item_nl, c->d_nl_ctr, c->d_rep, c->d_lcnt, c->d_gc};
+                  c->d_nlist, c->d_item_nl, c->d_rep, c->d_lcnt, c->d_gc};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_status) cudaFreeHost(c->h_status);
@@ -164,7 +164,7 @@ int swift_gpu_create(swift_gpu_ctx** out, const swift_gpu_params* p, int64_t n_m
             dalloc(&c->d_h, n) && dalloc(&c->d_bracket, n) && dalloc(&c->d_ngb, n) && dalloc(&c->d_ga, n) &&
             dalloc(&c->d_gb, n) && dalloc(&c->d_act, n) && dalloc(&c->d_items0, n) && dalloc(&c->d_plist0, n) &&
             dalloc(&c->d_items[0], n) && dalloc(&c->d_items[1], n) && dalloc(&c->d_plist[0], n) &&
-            dalloc(&c->d_plist[1], n) && dalloc(&c->d_counters, kCtrPerPass * (kMaxPasses + 2) + 2) &&
+            dalloc(&c->d_plist[1], n) && dalloc(&c->d_counters, kCtrCount(kMaxPasses)) &&
             dalloc(&c->d_stats, kStatCount) && dalloc(&c->d_red_partial, 8 * (size_t)c->red_blocks) &&
             dalloc(&c->d_scratch4[0], 4 * n) && dalloc(&c->d_scratch1[0], n) && dalloc(&c->d_scratch1[1], n) &&
             dalloc(&c->d_plain_act, n) && dalloc(&c->d_aux[0], n) && dalloc(&c->d_aux[1], n) &&
@@ -174,7 +174,7 @@ int swift_gpu_create(swift_gpu_ctx** out, const swift_gpu_params* p, int64_t n_m
             dalloc(&c->d_leaf_range, n) && dalloc(&c->d_leaf_hcap, n) && dalloc(&c->d_leaf_node, n) &&
             dalloc(&c->d_nbr_span, n) && dalloc(&c->d_nbr, (size_t)c->nbr_cap) &&
             dalloc(&c->d_tree_ctr, kTreeCtrCount) && (c->nl_cap == 0 || dalloc(&c->d_nlist, (size_t)c->nl_cap)) &&
-            dalloc(&c->d_item_nl, n) && dalloc(&c->d_nl_ctr, 1) &&
+            dalloc(&c->d_item_nl, n) &&
             (!lpp_fits || (dalloc(&c->d_rep, (size_t)kAxes * n) && dalloc(&c->d_lcnt, n) && dalloc(&c->d_gc, n))) &&
             cudaMallocHost((void**)&c->h_status, sizeof(Status)) == cudaSuccess &&
             cudaMallocHost((void**)&c->h_stats, sizeof(unsigned long long) * kStatCount) == cudaSuccess;
@@ -189,7 +189,7 @@ int swift_gpu_create(swift_gpu_ctx** out, const swift_gpu_params* p, int64_t n_m
   }
   cudaMemset(c->d_status, 0, sizeof(Status));
   cudaMemset(c->d_stats, 0, sizeof(unsigned long long) * kStatCount);
-  cudaMemset(c->d_counters, 0, sizeof(int) * (kCtrPerPass * (kMaxPasses + 2) + 2));
+  cudaMemset(c->d_counters, 0, sizeof(int) * kCtrCount(kMaxPasses));
   cudaMemset(c->d_tree_ctr, 0, sizeof(int) * kTreeCtrCount);
   if (cudaDeviceSynchronize() != cudaSuccess) {
     free_all(c);
@@ -440,7 +440,7 @@ int swift_gpu_set_tuning(swift_gpu_ctx* h, const swift_gpu_tuning* t) {
 
 int swift_gpu_autotune(swift_gpu_ctx* h, int loop, void* stream) {
   Ctx* c = from(h);
-  if (!c || loop < 0 || loop > 3 || (c->params.flags & SWIFT_GPU_PLAIN)) return SWIFT_GPU_ERR_ARG;
+  if (!c || loop < 0 || loop > 4 || (c->params.flags & SWIFT_GPU_PLAIN)) return SWIFT_GPU_ERR_ARG;
   if (!(c->state & 8)) return SWIFT_GPU_ERR_ORDER;
   cudaStream_t s = (cudaStream_t)stream;
   c->last_stream = s;

@@ -435,8 +435,7 @@ __global__ void k_cell_start(const unsigned* __restrict__ skeys, int n, const Gr
 
 int build_cells_impl(Ctx* c, const float4* pos_h, int n, float min_width, cudaStream_t s) {
   c->n = n;
-  c->nl_lmax = 0;  // kept candidate lists belong to the previous build
-  c->lpp_lists = 0;
+  c->lpp_lists = 0;  // kept candidate lists belong to the previous build
   int sm = c->num_sms;
   const bool adaptive = (c->params.flags & SWIFT_GPU_ADAPTIVE) != 0;
   const int nc_cap = adaptive && c->nc_cap > kAdaptiveNcCap ? kAdaptiveNcCap : c->nc_cap;

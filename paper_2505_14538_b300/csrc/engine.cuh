@@ -30,7 +30,6 @@ namespace sg {
 
 constexpr int kCap = 64;  // list entries per lane before a flush
 constexpr unsigned kFull = 0xffffffffu;
-constexpr unsigned kNoEntry = 0xffffffffu;  // padding of a stored candidate list
 
 struct WarpSmem {
   // lane-private lists, entry t of lane l at [t * 32 + l]; row kCap takes the
@@ -135,20 +134,6 @@ __device__ __forceinline__ void stage_candidate(const Grid& g, const float4* __r
   pj = pos[j];
   shift_j(code, g.L, pj.x, pj.y, pj.z);
   entry = (unsigned)j | (code << kIndexBits);
-}
-
-// The candidate list the density call kept for pass-0 item t, if any. When
-// the store ran out (nl_ctr, the space all items asked for, above nl_cap),
-// which items got a list depends on timing, so then no item uses one: the
-// sums of every particle are then taken in the same order on every run.
-__device__ __forceinline__ const unsigned* kept_list(const unsigned* nlist, const int2* item_nl, int t, int& m,
-                                                     const unsigned long long* nl_ctr, long long nl_cap) {
-  m = 0;
-  if (!nlist || *nl_ctr > (unsigned long long)nl_cap) return nullptr;
-  const int2 sp = item_nl[t];
-  if (sp.x < 0) return nullptr;
-  m = sp.y;
-  return nlist + sp.x;
 }
 
 // Evens out the list lengths of the L = 2^lsh lanes that share one particle
@@ -257,34 +242,16 @@ __device__ __forceinline__ int next_chunk(const Grid& g, const Nbr& nb, const Se
 // next chunk are issued before the current one is tested (software
 // pipelining: the test hides their latency). One flush site keeps the
 // inlined interaction code in a single copy.
-//
-// With a stored list (`sl`: the item's lane-interleaved candidate list kept
-// by the density call, entry t of lane l at sl[t * 32 + l], kNoEntry after
-// the lane's last) the scan is skipped: the lane's entries go straight into
-// its shared-memory list for the one flush.
 template <class Op>
 __device__ __forceinline__ void scan_item(const Op& op, typename Op::I& I, const Grid& g, const Nbr& nb,
                                           const float4* __restrict__ pos, int cell, int lsh, int s, bool live,
-                                          WarpSmem& w, unsigned& ncand, const unsigned* __restrict__ sl = nullptr,
-                                          int sm = 0) {
+                                          WarpSmem& w, unsigned& ncand) {
   const unsigned lane = lane_id();
   int cnt = 0;
-  int bn = 0, sb = 0, base = -32, total = 0, len = 0;
-  Segs q;
-  q.nseg = 0;
-  if (sl) {
-    for (int t = 0; t < sm; ++t) {
-      const unsigned e = sl[t * 32 + (int)lane];
-      w.list[t * 32 + (int)lane] = e;
-      cnt += e != kNoEntry ? 1 : 0;  // the lane's entries come first
-    }
-    if (!live) cnt = 0;
-    ncand += (unsigned)cnt;
-  } else {
-    q = item_segments(nb, cell);
-    if (q.nseg > 0) total = setup_segments(g, nb, q, 0, w, bn);
-    len = next_chunk(g, nb, q, w, sb, bn, total, base);
-  }
+  int bn = 0, sb = 0, base = -32, total = 0;
+  const Segs q = item_segments(nb, cell);
+  if (q.nseg > 0) total = setup_segments(g, nb, q, 0, w, bn);
+  int len = next_chunk(g, nb, q, w, sb, bn, total, base);
   float4 pj = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   unsigned ej = 0;
   if ((int)lane < len) stage_candidate(g, pos, w, bn, base + (int)lane, pj, ej);

@@ -94,8 +94,6 @@ struct Ctx {
   unsigned* d_nlist = nullptr;
   long long nl_cap = 0;
   int2* d_item_nl = nullptr;
-  unsigned long long* d_nl_ctr = nullptr;
-  int nl_lmax = 0;  // lanes-per-particle limit they were built with (0: none)
   // lane-per-particle path (uniform grid): the 13 axis-sorted replicas of the
   // cells (13 n_max float4), the per-lane candidate counts of the groups' kept
   // lists (n_max), and whether the last density call kept such lists
@@ -137,12 +135,6 @@ int autotune_impl(Ctx* c, int loop, cudaStream_t s);
 int backward_impl(Ctx* c, const float4* grad_ad, float4* grad_x, float4* grad_v, float* grad_u, int h_mode,
                   cudaStream_t s);
 
-// The kept candidate lists match the current lane layout (the persistent
-// density call of the last build made them).
-inline bool kept_lists_usable(const Ctx* c) {
-  return c->d_nlist && c->nl_lmax != 0 && c->nl_lmax == c->tuning.max_lanes_per_particle;
-}
-
 // Lanes per particle of the cell-item kernels. A tuning of one lane a
 // particle selects the lane-per-particle path where it exists; the cell-item
 // kernels that still run there (the later density passes, the adjoint, the
@@ -176,5 +168,11 @@ constexpr int kHmaxWords = 2;
 // counters layout helpers
 constexpr int kCtrPerPass = 4;  // item_count, plist_count, ticket, spare
 __host__ __device__ inline int ctr_index(int pass, int which) { return pass * kCtrPerPass + which; }
+// After the passes' counters: the later loops' tickets (pass slot passes + 1: gradient, force, and the
+// adjoint's two), the density launch's grid barrier (2), the ticket of the cell-item launch that follows
+// a lane-per-particle one, and the flag the density call sets when a group has no kept list.
+__host__ __device__ constexpr int kCtrUnlistedTicket(int passes) { return kCtrPerPass * (passes + 2) + 2; }
+__host__ __device__ constexpr int kCtrMissing(int passes) { return kCtrPerPass * (passes + 2) + 3; }
+__host__ __device__ constexpr int kCtrCount(int passes) { return kCtrPerPass * (passes + 2) + 4; }
 
 }  // namespace sg

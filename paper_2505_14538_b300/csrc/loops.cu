@@ -87,17 +87,17 @@ struct DensArgs {
   unsigned long long wait_ns;  // limit of each bounded grid barrier (0: give up at once)
   Status* st;
   unsigned long long* stats;
-  // candidate lists kept for the gradient / force / adjoint loops (NULL: none)
+  // candidate lists kept for the gradient and force loops (NULL: none), per group of
+  // 32 pass-0 particles: W entries a lane, item_nl[group] = (0 or -1 without a list, longest list)
   unsigned* nlist;
-  long long nl_cap;
-  unsigned long long* nl_ctr;
-  int2* item_nl;       // per pass-0 item: (first entry, entries per lane) or (-1, 0)
+  int2* item_nl;
   // lane-per-particle pass 0 (uniform grid): axis-sorted cell replicas and the
   // per-lane candidate counts of each group's kept list
   float4* rep;
   long long rep_stride;
   int* lcnt;
   int lpp_w;  // entries a lane of a group's kept list holds
+  int* missing;  // set when a group is left without a kept list
 };
 
 __device__ __forceinline__ void dens_load(DensOp::I& I, const DensArgs& a, float Lmax, int k) {
@@ -179,7 +179,10 @@ __device__ __forceinline__ void keep_list(const DensArgs& a, const WarpSmem& w, 
   const int idx = it.off + lm.slot;
   const int grp = idx >> 5;
   if (!all_ok || tot > a.lpp_w) {
-    if (lm.s == 0) a.item_nl[grp].x = -1;
+    if (lm.s == 0) {
+      a.item_nl[grp].x = -1;
+      *a.missing = 1;
+    }
     return;
   }
   unsigned* dst = a.nlist + (long long)grp * (a.lpp_w * 32) + (idx & 31);
@@ -193,7 +196,10 @@ __device__ __forceinline__ void keep_list(const DensArgs& a, const WarpSmem& w, 
 
 // A pass-0 item whose particles' lists are not kept: their groups have none.
 __device__ __forceinline__ void drop_lists(const DensArgs& a, const Item& it, const LaneMap& lm) {
-  if (lm.live && lm.s == 0) a.item_nl[(it.off + lm.slot) >> 5].x = -1;
+  if (lm.live && lm.s == 0) {
+    a.item_nl[(it.off + lm.slot) >> 5].x = -1;
+    *a.missing = 1;
+  }
 }
 
 // kFixedH: the density at the given h (no h iteration), a kernel of its own
@@ -425,7 +431,10 @@ __device__ __forceinline__ void dens_group(const DensArgs& a, const DensOp& op, 
   // fit and every h (active or not) is within the cell cap
   const bool keep = __all_sync(kFull, !ovf) && g.hcap_from_cells;
   const int mw = __reduce_max_sync(kFull, cnt);
-  if (lane == 0) a.item_nl[grp] = make_int2(keep ? 0 : -1, mw);
+  if (lane == 0) {
+    a.item_nl[grp] = make_int2(keep ? 0 : -1, mw);
+    if (!keep) *a.missing = 1;
+  }
   if (live) a.lcnt[idx] = cnt;
   bool retry = ovf;  // the multi-pass route from the starting h
   bool scan = false; // fixed h: the particle's sums from a scan of its cells
@@ -764,19 +773,21 @@ struct LoopArgs {
   double* red_partial;  // force: [gridDim.x][8]
   Status* st;
   unsigned long long* stats;
-  const unsigned* nlist;  // candidate lists kept by the density call (NULL: scan)
-  const int2* item_nl;
-  const unsigned long long* nl_ctr;  // space the items asked for (above nl_cap: the lists are not used)
-  long long nl_cap;
+  const unsigned* nlist;  // candidate lists kept by the density call, per group (NULL: scan)
+  const int2* item_nl;    // per group: (0 or -1 without a list, longest list)
   const int* lcnt;  // lane-per-particle path: candidates of each group lane's kept list
+  const int* missing;    // set by the density call when some group has no kept list
+  int only_unlisted;     // cell-item kernels: only particles whose group has no kept list
+  int red_offset;        // first block slot of this launch's partial sums
   const float4* gc; // sorted (1/H, C/H^4, H^2 - band, H^2 + band) from the ghost step
 };
 
 
 __device__ __forceinline__ void grad_item(const LoopArgs& a, const GradOp& op, const Grid& g, WarpSmem& w,
                                           const Item& it, int t, float Lmax, unsigned& ninter, unsigned& ncand) {
-  const LaneMap lm = lane_map(it.cnt, a.lmax);
+  LaneMap lm = lane_map(it.cnt, a.lmax);
   const int k = a.plist[it.off + (lm.live ? lm.slot : 0)];
+  if (a.only_unlisted) lm.live = lm.live && a.item_nl[(it.off + lm.slot) >> 5].x < 0;
   GradOp::I I;
   const float4 p = a.pos[k];
   const float4 v = a.vel[k];
@@ -795,9 +806,7 @@ __device__ __forceinline__ void grad_item(const LoopArgs& a, const GradOp& op, c
   I.lap = 0.0f;
   I.count = 0;
   I.k = k;
-  int sm;
-  const unsigned* sl = kept_list(a.nlist, a.item_nl, t, sm, a.nl_ctr, a.nl_cap);
-  scan_item(op, I, g, a.nb, a.pos, it.cell, lm.lsh, lm.s, lm.live, w, ncand, sl, sm);
+  scan_item(op, I, g, a.nb, a.pos, it.cell, lm.lsh, lm.s, lm.live, w, ncand);
   I.vsig = lmax(I.vsig, lm.lsh);
   I.lap = lsum(I.lap, lm.lsh);
   I.count = lsum_u(I.count, lm.lsh);
@@ -821,12 +830,16 @@ __global__ void __launch_bounds__(kLoopThreads, 5) k_gradient(LoopArgs a) {
   op.kernel = K;
   op.knorm = a.ph.knorm;
   op.beta = a.ph.beta_v;
+  // after a lane-per-particle launch, only the particles whose group has no kept list (none: no work)
+  if (a.only_unlisted && *a.missing == 0) return;
   const int n_items = a.ctr[0];
   unsigned ninter = 0, ncand = 0;
   for (;;) {
     const int t = take_ticket(a.ticket);
     if (t >= n_items) break;
     const Item it = a.items[t];
+    if (a.only_unlisted && !__any_sync(kFull, (int)lane < it.cnt && a.item_nl[(it.off + (int)lane) >> 5].x < 0))
+      continue;
     grad_item(a, op, g, w, it, t, Lmax, ninter, ncand);
   }
   ninter = warp_sum(ninter);
@@ -845,8 +858,9 @@ __device__ __forceinline__ void force_item(const LoopArgs& a,
                                            const Grid& g, WarpSmem& w, const Item& it, int t, unsigned& ninter,
                                            unsigned& nginter, unsigned& ncand, float* acc, float* accc) {
   using Op = typename std::conditional<kGrad, GradForceOp, ForceOp>::type;
-  const LaneMap lm = lane_map(it.cnt, a.lmax);
+  LaneMap lm = lane_map(it.cnt, a.lmax);
   const int k = a.plist[it.off + (lm.live ? lm.slot : 0)];
+  if (a.only_unlisted) lm.live = lm.live && a.item_nl[(it.off + lm.slot) >> 5].x < 0;
   typename Op::I I;
   const float4 p = a.pos[k];
   const float4 v = a.vel[k];
@@ -871,9 +885,7 @@ __device__ __forceinline__ void force_item(const LoopArgs& a,
     I.lap = 0.0f;
     I.gcount = 0;
   }
-  int sm;
-  const unsigned* sl = kept_list(a.nlist, a.item_nl, t, sm, a.nl_ctr, a.nl_cap);
-  scan_item(op, I, g, a.nb, a.pos, it.cell, lm.lsh, lm.s, lm.live, w, ncand, sl, sm);
+  scan_item(op, I, g, a.nb, a.pos, it.cell, lm.lsh, lm.s, lm.live, w, ncand);
   lsum2(I.axs, I.axc, lm.lsh);
   lsum2(I.ays, I.ayc, lm.lsh);
   lsum2(I.azs, I.azc, lm.lsh);
@@ -930,6 +942,12 @@ __device__ __forceinline__ void force_kernel_body(const LoopArgs& a) {
   op.beta = a.ph.beta_v;
   op.gm1 = a.ph.gamma_eos - 1.0f;
   op.compensated = a.ph.compensated;
+  // after a lane-per-particle launch, only the particles whose group has no kept list; none: the
+  // block's slots of the global sums are zero and there is nothing else to do
+  if (a.only_unlisted && *a.missing == 0) {
+    if (threadIdx.x < 8) a.red_partial[(a.red_offset + blockIdx.x) * 8 + threadIdx.x] = 0.0;
+    return;
+  }
   const int n_items = a.ctr[0];
   unsigned ninter = 0, nginter = 0, ncand = 0;
   // per-thread partials of the global sums: FP32 TwoSum pairs (sum, error),
@@ -939,6 +957,8 @@ __device__ __forceinline__ void force_kernel_body(const LoopArgs& a) {
     const int t = take_ticket(a.ticket);
     if (t >= n_items) break;
     const Item it = a.items[t];
+    if (a.only_unlisted && !__any_sync(kFull, (int)lane < it.cnt && a.item_nl[(it.off + (int)lane) >> 5].x < 0))
+      continue;
     force_item<kGrad>(a, op, g, w, it, t, ninter, nginter, ncand, acc, accc);
   }
   // block partial of the FP64 sums (summed in block order by k_reduce_partials)
@@ -952,7 +972,7 @@ __device__ __forceinline__ void force_kernel_body(const LoopArgs& a) {
   if (threadIdx.x < 8) {
     double x = 0.0;
     for (int ww = 0; ww < kWarpsPerBlock; ++ww) x += red[ww][threadIdx.x];
-    a.red_partial[blockIdx.x * 8 + threadIdx.x] = x;
+    a.red_partial[(a.red_offset + blockIdx.x) * 8 + threadIdx.x] = x;
   }
   ninter = warp_sum(ninter);
   ncand = warp_sum(ncand);
@@ -980,13 +1000,15 @@ __global__ void __launch_bounds__(kLoopThreads, 5) k_grad_force(LoopArgs a) { fo
 // One lane per particle over the kept list of its group (written by the
 // density call; entry t of lane l at t * 32 + l of the group's span, so the
 // 32 lanes read entry t in one coalesced access). A group without a kept list
-// scans its cells per lane. kMode: 0 gradient, 1 force, 2 gradient + force
+// (a particle with more candidates than a list holds: clustered sets on the
+// uniform grid) is left to the cell-item kernel launched after this one,
+// which scans the cells of those particles only (LoopArgs::only_unlisted). kMode: 0 gradient, 1 force, 2 gradient + force
 // (one pass over the pairs). The force modes take the pair term of
 // force_lpp.cuh, two entries at a time: both entries' records are loaded
 // first, the next two entries are read meanwhile, and the two entries' terms
 // are summed in FP32 before the compensated sums take them.
 template <int kMode, int K>
-__global__ void __launch_bounds__(kLoopThreads, 4) k_loop_lpp(LoopArgs a) {
+__global__ void __launch_bounds__(kLoopThreads, 4) k_loop_lpp(const __grid_constant__ LoopArgs a) {
   constexpr int W = lpp_width<K>();
   constexpr bool kGrad = kMode != 1;
   __shared__ double red[kWarpsPerBlock][8];
@@ -1001,21 +1023,17 @@ __global__ void __launch_bounds__(kLoopThreads, 4) k_loop_lpp(LoopArgs a) {
   __shared__ float s_acc[16][kLoopThreads];
   if constexpr (kMode != 0)
     for (int q = 0; q < 16; ++q) s_acc[q][threadIdx.x] = 0.0f;
-  // the cell-scan fallback's ops (groups without a kept list)
+  // the gradient loop's pair function (gradient alone)
   GradOp gop;
-  GradForceOp fop;
-  gop.pos = fop.pos = a.pos;
-  gop.vel = fop.vel = a.vel;
-  gop.ga = fop.ga = a.ga;
-  gop.gb = fop.gb = a.gb;
-  for (int q = 0; q < 3; ++q) gop.L[q] = fop.L[q] = g.L[q];
-  gop.kg = fop.kg = a.ph.kg;
-  gop.kernel = fop.kernel = K;
-  gop.knorm = fop.knorm = a.ph.knorm;
-  gop.beta = fop.beta = a.ph.beta_v;
-  fop.Lmax = Lmax;
-  fop.gm1 = a.ph.gamma_eos - 1.0f;
-  fop.compensated = a.ph.compensated;
+  gop.pos = a.pos;
+  gop.vel = a.vel;
+  gop.ga = a.ga;
+  gop.gb = a.gb;
+  for (int q = 0; q < 3; ++q) gop.L[q] = g.L[q];
+  gop.kg = a.ph.kg;
+  gop.kernel = K;
+  gop.knorm = a.ph.knorm;
+  gop.beta = a.ph.beta_v;
   const LeanConst kc{a.ph};
   for (;;) {
     const int t = take_ticket(a.ticket);
@@ -1024,7 +1042,8 @@ __global__ void __launch_bounds__(kLoopThreads, 4) k_loop_lpp(LoopArgs a) {
     const bool live = idx < P;
     const int k = a.plist[live ? idx : t * 32];
     const bool has = a.nlist != nullptr && a.item_nl[t].x >= 0;
-    const int cnt = (has && live) ? a.lcnt[idx] : 0;
+    if (!has) continue;  // the cell-item launch that follows takes this group's particles
+    const int cnt = live ? a.lcnt[idx] : 0;
     const unsigned* lst = a.nlist + (long long)t * (W * 32) + lane;
     const unsigned dst = live ? a.perm[k] : 0u;
     const float4 p = a.pos[k];
@@ -1046,18 +1065,14 @@ __global__ void __launch_bounds__(kLoopThreads, 4) k_loop_lpp(LoopArgs a) {
       I.lap = 0.0f;
       I.count = 0;
       I.k = k;
-      if (has) {
-        const int m = __reduce_max_sync(kFull, cnt);
-        for (int u = 0; u < m; ++u) {
-          if (u < cnt) {
-            const unsigned e = lst[u * 32];
-            gop.interact(I, (int)(e & kIndexMask), e >> kIndexBits);
-          }
+      const int m = __reduce_max_sync(kFull, cnt);
+      for (int u = 0; u < m; ++u) {
+        if (u < cnt) {
+          const unsigned e = lst[u * 32];
+          gop.interact(I, (int)(e & kIndexMask), e >> kIndexBits);
         }
-        ncand += (unsigned)cnt;
-      } else {
-        lpp_scan(gop, I, g, a.nb.cell_start, (int)a.nb.skeys[k], live, ncand);
       }
+      ncand += (unsigned)cnt;
       if (live) {
         ninter += I.count;
         reinterpret_cast<float2*>(a.out)[dst] = make_float2(I.vsig, 2.0f * I.lap);
@@ -1078,52 +1093,33 @@ __global__ void __launch_bounds__(kLoopThreads, 4) k_loop_lpp(LoopArgs a) {
       I.vsig = 2.0f * gi.w;  // the j = i term of v_sig,max
       I.lap = 0.0f;
       I.gcount = I.count = 0;
-      if (has) {
-        const int m = __reduce_max_sync(kFull, cnt);
-        unsigned e0 = 0 < cnt ? lst[0] : (unsigned)k;
-        unsigned e1 = 1 < cnt ? lst[32] : (unsigned)k;
-        for (int u = 0; u < m; u += 2) {
-          LeanRec r0, r1;
-          lean_load(a.pos, a.vel, a.ga, a.gb, a.gc, (int)(e0 & kIndexMask), r0);
-          lean_load(a.pos, a.vel, a.ga, a.gb, a.gc, (int)(e1 & kIndexMask), r1);
-          const unsigned n0 = u + 2 < cnt ? lst[(u + 2) * 32] : (unsigned)k;
-          const unsigned n1 = u + 3 < cnt ? lst[(u + 3) * 32] : (unsigned)k;
-          float tax = 0.0f, tay = 0.0f, taz = 0.0f, tdu = 0.0f;
-          if (u < cnt) lean_pair<K, kGrad>(I, r0, e0 >> kIndexBits, kc, tax, tay, taz, tdu);
-          if (u + 1 < cnt) lean_pair<K, kGrad>(I, r1, e1 >> kIndexBits, kc, tax, tay, taz, tdu);
-          if (a.ph.compensated) {
-            two_sum_acc(I.axs, I.axc, tax);
-            two_sum_acc(I.ays, I.ayc, tay);
-            two_sum_acc(I.azs, I.azc, taz);
-            two_sum_acc(I.dus, I.duc, tdu);
-          } else {
-            I.axs += tax;
-            I.ays += tay;
-            I.azs += taz;
-            I.dus += tdu;
-          }
-          e0 = n0;
-          e1 = n1;
+      const int m = __reduce_max_sync(kFull, cnt);
+      unsigned e0 = 0 < cnt ? lst[0] : (unsigned)k;
+      unsigned e1 = 1 < cnt ? lst[32] : (unsigned)k;
+      for (int u = 0; u < m; u += 2) {
+        LeanRec r0, r1;
+        lean_load(a.pos, a.vel, a.ga, a.gb, a.gc, (int)(e0 & kIndexMask), r0);
+        lean_load(a.pos, a.vel, a.ga, a.gb, a.gc, (int)(e1 & kIndexMask), r1);
+        const unsigned n0 = u + 2 < cnt ? lst[(u + 2) * 32] : (unsigned)k;
+        const unsigned n1 = u + 3 < cnt ? lst[(u + 3) * 32] : (unsigned)k;
+        float tax = 0.0f, tay = 0.0f, taz = 0.0f, tdu = 0.0f;
+        if (u < cnt) lean_pair<K, kGrad>(I, r0, e0 >> kIndexBits, kc, tax, tay, taz, tdu);
+        if (u + 1 < cnt) lean_pair<K, kGrad>(I, r1, e1 >> kIndexBits, kc, tax, tay, taz, tdu);
+        if (a.ph.compensated) {
+          two_sum_acc(I.axs, I.axc, tax);
+          two_sum_acc(I.ays, I.ayc, tay);
+          two_sum_acc(I.azs, I.azc, taz);
+          two_sum_acc(I.dus, I.duc, tdu);
+        } else {
+          I.axs += tax;
+          I.ays += tay;
+          I.azs += taz;
+          I.dus += tdu;
         }
-        ncand += (unsigned)cnt;
-      } else {
-        // no kept list: the cell scan with the pair functions of the cell-item kernels
-        GradForceOp::I F;
-        F.x = I.x; F.y = I.y; F.z = I.z; F.h = I.h;
-        F.H2lo = I.H2lo; F.H2hi = I.H2hi; F.invH = I.invH; F.c4 = I.c4;
-        F.vx = I.vx; F.vy = I.vy; F.vz = I.vz;
-        F.A = I.A; F.f = I.f; F.rho = I.rho; F.c = I.c;
-        F.B = I.B; F.av = I.av; F.acP = I.acP; F.u = I.u; F.P = I.P;
-        F.axs = F.axc = F.ays = F.ayc = F.azs = F.azc = F.dus = F.duc = F.dh = 0.0f;
-        F.vsig = I.vsig;
-        F.lap = 0.0f;
-        F.gcount = F.count = 0;
-        F.k = k;
-        lpp_scan(fop, F, g, a.nb.cell_start, (int)a.nb.skeys[k], live, ncand);
-        I.axs = F.axs; I.axc = F.axc; I.ays = F.ays; I.ayc = F.ayc; I.azs = F.azs; I.azc = F.azc;
-        I.dus = F.dus; I.duc = F.duc; I.dh = F.dh;
-        I.vsig = F.vsig; I.lap = F.lap; I.gcount = F.gcount; I.count = F.count;
+        e0 = n0;
+        e1 = n1;
       }
+      ncand += (unsigned)cnt;
       if (live) {
         ninter += I.count;
         const float ax = I.axs + I.axc, ay = I.ays + I.ayc, az = I.azs + I.azc, du = I.dus + I.duc;
@@ -1171,7 +1167,7 @@ __global__ void __launch_bounds__(kLoopThreads, 4) k_loop_lpp(LoopArgs a) {
     if (threadIdx.x < 8) {
       double x = 0.0;
       for (int ww = 0; ww < kWarpsPerBlock; ++ww) x += red[ww][threadIdx.x];
-      a.red_partial[blockIdx.x * 8 + threadIdx.x] = x;
+      a.red_partial[(a.red_offset + blockIdx.x) * 8 + threadIdx.x] = x;
     }
   }
   ninter = warp_sum(ninter);
@@ -1291,7 +1287,7 @@ int density_impl(Ctx* c, const float4* pos_in, const float4* vel_in, const uint8
   const void* kern = density_kernel(c->phys.kernel, (c->params.flags & SWIFT_GPU_NO_H_ITER) != 0, lpp);
   const size_t smem = dens_smem(c->phys.kernel, lpp);
   const int nblk = persistent_blocks(c, kern, smem);
-  cudaMemsetAsync(c->d_counters, 0, sizeof(int) * (size_t)(kCtrPerPass * (c->max_passes + 2) + 2), s);
+  cudaMemsetAsync(c->d_counters, 0, sizeof(int) * (size_t)kCtrCount(c->max_passes), s);
   DensArgs a;
   a.grid = c->d_grid;
   a.nb = nbr_of(c);
@@ -1330,20 +1326,18 @@ int density_impl(Ctx* c, const float4* pos_in, const float4* vel_in, const uint8
   // kept lists in the groups' layout (either engine), where the context holds the store for it
   const bool keep = c->d_nlist != nullptr && c->d_lcnt != nullptr && !(c->params.flags & SWIFT_GPU_ADAPTIVE);
   a.nlist = keep ? c->d_nlist : nullptr;
-  a.nl_cap = c->nl_cap;
-  a.nl_ctr = c->d_nl_ctr;
   a.item_nl = keep ? c->d_item_nl : nullptr;
   a.rep = c->d_rep;
   a.rep_stride = c->n;
   a.lcnt = c->d_lcnt;
   a.lpp_w = lpp_width_of(c->phys.kernel);
+  a.missing = c->d_counters + kCtrMissing(c->max_passes);  // zeroed with the counters above
   if (keep && !lpp && c->n > 0) cudaMemsetAsync(c->d_item_nl, 0, sizeof(int2) * (size_t)((c->n + 31) / 32), s);
   void* args[] = {&a};
   cudaError_t e = cudaLaunchCooperativeKernel(kern, dim3(nblk), dim3(kLoopThreads), args, smem, s);
   c->launches += 2;
   c->all_active = active == nullptr;
   // the kept lists are per group of the pass-0 list, whichever engine wrote them
-  c->nl_lmax = 0;
   c->lpp_lists = keep ? 1 : 0;
   return e == cudaSuccess ? SWIFT_GPU_OK : SWIFT_GPU_ERR_CUDA;
 }
@@ -1378,33 +1372,52 @@ static LoopArgs loop_args(Ctx* c, int* ticket, void* out) {
   a.red_partial = c->d_red_partial;
   a.st = c->d_status;
   a.stats = c->d_stats;
-  const bool lists = c->lpp_lists ? true : kept_lists_usable(c);
-  a.nlist = lists ? c->d_nlist : nullptr;
-  a.item_nl = lists ? c->d_item_nl : nullptr;
-  a.nl_ctr = c->d_nl_ctr;
-  a.nl_cap = c->nl_cap;
+  // the lane-per-particle loops read the density call's kept lists; the cell-item
+  // kernels (no kept lists: adaptive leaves) scan the cells
+  a.nlist = c->lpp_lists ? c->d_nlist : nullptr;
+  a.item_nl = c->lpp_lists ? c->d_item_nl : nullptr;
   a.lcnt = c->d_lcnt;
   a.gc = c->d_gc;
+  a.missing = c->d_counters + kCtrMissing(c->max_passes);
+  a.only_unlisted = 0;
+  a.red_offset = 0;
   return a;
 }
 
-// One gradient / force / both launch (mode 0 / 1 / 2): lane per particle over
-// the density call's groups when it ran that way, else cell items.
+// One gradient / force / both pass (mode 0 / 1 / 2). Over kept lists: the
+// lane-per-particle kernel, then the cell-item kernel for the particles of
+// groups without a kept list (it returns at once when the density call left
+// every group a list); without kept lists: the cell-item kernel alone. The
+// launches' block partials of the global sums are slots [0, *nblk_out).
 static int loop_launch(Ctx* c, int mode, LoopArgs& a, cudaStream_t s, int* nblk_out) {
   ensure_attrs(c);
-  const void* kern;
-  size_t smem = kLoopSmemBytes;
+  const void* cell_kern = mode == 0   ? gradient_kernel(c->phys.kernel)
+                          : mode == 1 ? force_kernel(c->phys.kernel)
+                                      : grad_force_kernel(c->phys.kernel);
+  int total = 0;
+  cudaError_t e = cudaSuccess;
   if (c->lpp_lists) {
-    kern = lpp_loop_kernel(mode, c->phys.kernel);
-    smem = 0;
+    const void* kern = lpp_loop_kernel(mode, c->phys.kernel);
+    const int nblk = persistent_blocks(c, kern, 0);
+    e = launch_loop(kern, nblk, a, s, 0);
+    c->launches += 1;
+    total = nblk;
+    LoopArgs b = a;
+    b.only_unlisted = 1;
+    b.red_offset = nblk;
+    b.ticket = c->d_counters + kCtrUnlistedTicket(c->max_passes);
+    cudaMemsetAsync(b.ticket, 0, sizeof(int), s);
+    const int nblk2 = min(persistent_blocks(c, cell_kern, kLoopSmemBytes), c->red_blocks - nblk);
+    if (e == cudaSuccess) e = launch_loop(cell_kern, nblk2, b, s, kLoopSmemBytes);
+    c->launches += 2;
+    total += nblk2;
   } else {
-    kern = mode == 0 ? gradient_kernel(c->phys.kernel) : mode == 1 ? force_kernel(c->phys.kernel)
-                                                                   : grad_force_kernel(c->phys.kernel);
+    const int nblk = persistent_blocks(c, cell_kern, kLoopSmemBytes);
+    e = launch_loop(cell_kern, nblk, a, s, kLoopSmemBytes);
+    c->launches += 2;
+    total = nblk;
   }
-  const int nblk = persistent_blocks(c, kern, smem);
-  if (nblk_out) *nblk_out = nblk;
-  const cudaError_t e = launch_loop(kern, nblk, a, s, smem);
-  c->launches += 2;
+  if (nblk_out) *nblk_out = total;
   return e == cudaSuccess ? SWIFT_GPU_OK : SWIFT_GPU_ERR_CUDA;
 }
 

@@ -406,8 +406,7 @@ int plain_density_impl(Ctx* c, const float4* pos_in, const float4* vel_in, const
   st.stats = c->d_stats;
   st.acc = Acc{reinterpret_cast<float*>(c->d_scratch4[0]), (int)c->n_max};
   c->all_active = active == nullptr;
-  c->nl_lmax = 0;  // no kept candidate lists from this path
-  c->lpp_lists = 0;
+  c->lpp_lists = 0;  // no kept candidate lists from this path
   if (c->n == 0) return SWIFT_GPU_OK;
   const int nb = min((c->n + 255) / 256, c->num_sms * 8);
   k_plain_dens_prologue<<<nb, 256, 0, s>>>(st);

@@ -70,7 +70,7 @@ constexpr StaticLayout static_layout() {
   L.plist0 = take(4 * n);
   L.plist1 = take(4 * n);
   L.plist2 = take(4 * n);
-  L.counters = take(sizeof(int) * (size_t)(kCtrPerPass * (kStaticMaxPasses + 2) + 2));
+  L.counters = take(sizeof(int) * (size_t)kCtrCount(kStaticMaxPasses));
   L.stats = take(sizeof(unsigned long long) * kStatCount);
   L.total = o;
   return L;

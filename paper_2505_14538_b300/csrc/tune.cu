@@ -17,6 +17,13 @@ static int run_loop(Ctx* c, int loop, cudaStream_t s) {
   if (loop == 0) return run_density(c, s);
   if (loop == 1) return gradient_impl(c, c->last_grad_out, s);
   if (loop == 3) return grad_force_impl(c, c->last_grad_out, c->last_force_out, c->last_dhdt, nullptr, s);
+  if (loop == 4) {  // the whole step after the cell build: density, ghost, gradient + force
+    int rc = run_density(c, s);
+    if (rc == SWIFT_GPU_OK) rc = ghost_impl(c, c->last_u, c->last_alpha_v, c->last_alpha_c, s);
+    if (rc == SWIFT_GPU_OK)
+      rc = grad_force_impl(c, c->last_grad_out, c->last_force_out, c->last_dhdt, nullptr, s);
+    return rc;
+  }
   return force_impl(c, c->last_force_out, c->last_dhdt, nullptr, s);
 }
 
@@ -30,14 +37,14 @@ static int run_ghost(Ctx* c, int loop, cudaStream_t s) {
 // path, whose lists the density call writes), so a gradient or force
 // candidate first re-runs the density call and the ghost step, untimed.
 static int prepare(Ctx* c, int loop, cudaStream_t s) {
-  if (loop == 0) return SWIFT_GPU_OK;
+  if (loop == 0 || loop == 4) return SWIFT_GPU_OK;
   int rc = run_density(c, s);
   if (rc == SWIFT_GPU_OK) rc = run_ghost(c, loop, s);
   return rc;
 }
 
 int autotune_impl(Ctx* c, int loop, cudaStream_t s) {
-  if ((loop == 1 || loop == 3) && !c->last_grad_out) return SWIFT_GPU_ERR_ORDER;
+  if ((loop == 1 || loop == 3 || loop == 4) && !c->last_grad_out) return SWIFT_GPU_ERR_ORDER;
   const int cand_l[6] = {1, 2, 4, 8, 16, 32};
   const int cand_b[3] = {0, 1, 2};
   swift_gpu_tuning best = c->tuning, orig = c->tuning;

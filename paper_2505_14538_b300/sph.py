@@ -81,6 +81,9 @@ class Context:
         _check(self.lib.swift_gpu_create(ctypes.byref(self.handle), ctypes.byref(self.params),
                                          ctypes.c_int64(self.n_max)), "swift_gpu_create")
         self.n = 0
+        # count of calls that replace the context's loop state (sorted arrays, sums, ghost records);
+        # the autograd functions below compare it to find out whether their forward state is still there
+        self.calls = 0
 
     def close(self):
         if self.handle:
@@ -106,6 +109,7 @@ class Context:
 
     # ------------------------------------------------------------ calls
     def build_cells(self, pos_h: torch.Tensor, min_cell_width: float = 0.0, stream=None):
+        self.calls += 1
         n = pos_h.shape[0]
         _check(self.lib.swift_gpu_build_cells(self.handle, _ptr(pos_h, _F32, 4, name="pos_h"), ctypes.c_int64(n),
                                               ctypes.c_float(min_cell_width), _stream(stream)),
@@ -114,6 +118,7 @@ class Context:
 
     def density(self, pos_h, vel_m, active=None, h_out=None, rho4=None, curl_div=None, ngb_count=None,
                 want_ngb=True, stream=None):
+        self.calls += 1
         n = self.n
         dev = pos_h.device
         if active is not None and (rho4 is None or curl_div is None):
@@ -131,6 +136,7 @@ class Context:
         return dict(h=h_out, rho4=rho4, curl_div=curl_div, ngb=ngb_count)
 
     def gradient(self, u, vsig_lapu=None, stream=None):
+        self.calls += 1
         n = self.n
         vsig_lapu = vsig_lapu if vsig_lapu is not None else torch.empty(n, 2, dtype=_F32, device=u.device)
         _check(self.lib.swift_gpu_gradient(self.handle, _ptr(u, _F32, None, n, "u"),
@@ -140,6 +146,7 @@ class Context:
 
     def force(self, u, alpha_v=None, alpha_c=None, accel_dudt=None, dh_dt=None, reductions=None,
               want_dh=True, want_reductions=True, stream=None):
+        self.calls += 1
         n = self.n
         dev = u.device
         accel_dudt = accel_dudt if accel_dudt is not None else torch.empty(n, 4, dtype=_F32, device=dev)
@@ -157,6 +164,7 @@ class Context:
     def gradient_force(self, u, alpha_v=None, alpha_c=None, vsig_lapu=None, accel_dudt=None, dh_dt=None,
                        reductions=None, want_dh=True, want_reductions=True, stream=None):
         """swift_gpu_gradient_force: the outputs of gradient() and force() from one pass over the pairs."""
+        self.calls += 1
         n = self.n
         dev = u.device
         vsig_lapu = vsig_lapu if vsig_lapu is not None else torch.empty(n, 2, dtype=_F32, device=dev)
@@ -239,6 +247,7 @@ class Context:
         _check(self.lib.swift_gpu_set_tuning(self.handle, ctypes.byref(t)), "swift_gpu_set_tuning")
 
     def autotune(self, loop: int, stream=None):
+        self.calls += 1
         _check(self.lib.swift_gpu_autotune(self.handle, ctypes.c_int(loop), _stream(stream)), "swift_gpu_autotune")
         return self.tuning()
 
@@ -363,7 +372,10 @@ class SphForces(torch.autograd.Function):
     ``lib_ctx`` a :class:`Context` created with ``flags=FLAG_NO_H_ITER`` so the
     given h is used as is. Runs build_cells, density, force. The backward pass
     calls swift_gpu_force_backward (h_mode 0), which reads the context's state
-    of this forward call: run backward before the context is used again.
+    of this forward call (sorted arrays, sums, ghost records); if the context
+    ran other calls in between (its call counter moved), backward first runs
+    this forward's calls again from the saved inputs, so the gradient is
+    always this forward's.
     """
 
     @staticmethod
@@ -374,15 +386,23 @@ class SphForces(torch.autograd.Function):
         pos_h = torch.cat([x, h[:, None]], 1).float().contiguous()
         vel_m = torch.cat([v, m[:, None]], 1).float().contiguous()
         uu = u.float().contiguous()
-        lib_ctx.build_cells(pos_h)
-        lib_ctx.density(pos_h, vel_m)
-        out = lib_ctx.force(uu, want_dh=False, want_reductions=False)
+        out = SphForces._run(lib_ctx, pos_h, vel_m, uu)
         ctx.lib_ctx = lib_ctx
+        ctx.calls = lib_ctx.calls
+        ctx.inputs = (pos_h, vel_m, uu)
         ad = out["accel_dudt"]
         return ad[:, :3].clone(), ad[:, 3].clone()
 
     @staticmethod
+    def _run(lib_ctx, pos_h, vel_m, uu):
+        lib_ctx.build_cells(pos_h)
+        lib_ctx.density(pos_h, vel_m)
+        return lib_ctx.force(uu, want_dh=False, want_reductions=False)
+
+    @staticmethod
     def backward(ctx, grad_a, grad_du):
+        if ctx.lib_ctx.calls != ctx.calls:  # the context moved on: restore this forward's state
+            SphForces._run(ctx.lib_ctx, *ctx.inputs)
         n = ctx.lib_ctx.n
         dev = grad_a.device if grad_a is not None else grad_du.device
         ga = grad_a if grad_a is not None else torch.zeros(n, 3, dtype=torch.float32, device=dev)
@@ -400,7 +420,8 @@ class SphForcesSolvedH(torch.autograd.Function):
     whose h_tol sets how close h is to the root. Runs build_cells, density,
     force; h is returned as a non-differentiable output. The backward pass calls
     swift_gpu_force_backward with h_mode 1: h moves with x through the implicit
-    function theorem. Run backward before the context is used again.
+    function theorem. If the context ran other calls in between, backward
+    first runs this forward's calls again from the saved inputs.
     """
 
     @staticmethod
@@ -411,16 +432,24 @@ class SphForcesSolvedH(torch.autograd.Function):
         pos_h = torch.cat([x, h0[:, None]], 1).float().contiguous()
         vel_m = torch.cat([v, m[:, None]], 1).float().contiguous()
         uu = u.float().contiguous()
-        d = lib_ctx.density_checked(pos_h, vel_m)
-        out = lib_ctx.force(uu, want_dh=False, want_reductions=False)
+        d, out = SphForcesSolvedH._run(lib_ctx, pos_h, vel_m, uu)
         ctx.lib_ctx = lib_ctx
+        ctx.calls = lib_ctx.calls
+        ctx.inputs = (pos_h, vel_m, uu)
         ad = out["accel_dudt"]
         h = d["h"].clone()
         ctx.mark_non_differentiable(h)
         return ad[:, :3].clone(), ad[:, 3].clone(), h
 
     @staticmethod
+    def _run(lib_ctx, pos_h, vel_m, uu):
+        d = lib_ctx.density_checked(pos_h, vel_m)
+        return d, lib_ctx.force(uu, want_dh=False, want_reductions=False)
+
+    @staticmethod
     def backward(ctx, grad_a, grad_du, grad_h):
+        if ctx.lib_ctx.calls != ctx.calls:  # the context moved on: restore this forward's state
+            SphForcesSolvedH._run(ctx.lib_ctx, *ctx.inputs)
         n = ctx.lib_ctx.n
         dev = grad_a.device if grad_a is not None else grad_du.device
         ga = grad_a if grad_a is not None else torch.zeros(n, 3, dtype=torch.float32, device=dev)
@@ -443,12 +472,19 @@ class StepGraph:
     """
 
     def __init__(self, ctx: Context, pos_h, vel_m, u, min_cell_width: float = 0.0, alpha_v=None, alpha_c=None,
-                 fused: bool = True):
+                 fused: bool = True, active=None, rho4=None, curl_div=None):
+        """``active`` (optional, uint8): only those particles are recomputed; ``rho4`` and ``curl_div`` then
+        give the inactive particles' values (copied into the step's own output arrays, where the inactive
+        entries stay from replay to replay)."""
         n = pos_h.shape[0]
         dev = pos_h.device
         self.ctx = ctx
-        self.out = dict(h=torch.empty(n, dtype=_F32, device=dev), rho4=torch.empty(n, 4, dtype=_F32, device=dev),
-                        curl_div=torch.empty(n, 4, dtype=_F32, device=dev),
+        if active is not None and (rho4 is None or curl_div is None):
+            raise ValueError("with an active subset, rho4 and curl_div carry the inactive particles' values")
+        self.out = dict(h=torch.empty(n, dtype=_F32, device=dev),
+                        rho4=rho4.clone() if rho4 is not None else torch.empty(n, 4, dtype=_F32, device=dev),
+                        curl_div=curl_div.clone() if curl_div is not None else torch.empty(n, 4, dtype=_F32,
+                                                                                          device=dev),
                         ngb=torch.zeros(n, dtype=torch.int32, device=dev),
                         vsig_lapu=torch.empty(n, 2, dtype=_F32, device=dev),
                         accel_dudt=torch.empty(n, 4, dtype=_F32, device=dev), dh_dt=torch.empty(n, dtype=_F32, device=dev),
@@ -457,7 +493,8 @@ class StepGraph:
 
         def body():
             ctx.build_cells(pos_h, min_cell_width)
-            ctx.density(pos_h, vel_m, h_out=o["h"], rho4=o["rho4"], curl_div=o["curl_div"], ngb_count=o["ngb"])
+            ctx.density(pos_h, vel_m, active, h_out=o["h"], rho4=o["rho4"], curl_div=o["curl_div"],
+                        ngb_count=o["ngb"])
             if fused:
                 ctx.gradient_force(u, alpha_v, alpha_c, vsig_lapu=o["vsig_lapu"], accel_dudt=o["accel_dudt"],
                                    dh_dt=o["dh_dt"], reductions=o["reductions"])
@@ -479,5 +516,6 @@ class StepGraph:
         self.launches_per_step = ctx.info()["launches"] - l0
 
     def replay(self):
+        self.ctx.calls += 1  # the replayed calls replace the context's state like direct ones
         self.graph.replay()
         return self.out

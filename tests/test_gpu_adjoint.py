@@ -1,10 +1,21 @@
-"""GPU adjoint (swift_gpu_force_backward, h fixed) against the FP64 references.
+"""GPU adjoint (swift_gpu_force_backward) against the FP64 references.
 
 References: the PyTorch FP64 pair-list autograd of the same pipeline
 (``oracle/torch_ref.py``, itself pinned to the C++ oracle and to its finite
 differences) on every particle, and central finite differences of the C++
-oracle on sampled components. Tolerance: 1e-4 of the largest gradient
-component of each array (the FP32 sums carry ~1e-6 relative error per term).
+oracle on sampled components.
+
+Tolerance, per element: |g - ref| <= 1e-4 |ref| + FLOOR max|ref|. The
+floor is the FP32 rounding of the sums: a gradient component is a sum over
+the pairs of two gathers (about 2 x 60 pair terms, each a chain of about 20
+FP32 operations), so its error is at most about 100 x 2^-24 = 6e-6 times the
+sum of its terms' magnitudes; with loss weights drawn from N(0, 1) the terms
+of one component cancel, and their magnitudes add up to at most about 30 x the
+array's largest component (3 sigma of a 100-term random sum), which bounds the
+error by about 2e-4 max|ref|. Measured (FP64 torch reference, fixed and solved
+h): at most 2.2e-5 max|ref|, most components below 1e-6 relative. FLOOR =
+5e-5 lies between the two. A component that is 100 % wrong fails unless it is
+below that floor.
 """
 import numpy as np
 import pytest
@@ -14,6 +25,18 @@ torch = pytest.importorskip("torch")
 from paper_2505_14538_b300 import ics
 
 pytestmark = pytest.mark.gpu
+
+FLOOR = 5e-5  # of the array's largest |component|: the FP32 rounding of the gathered sums (module docstring)
+
+
+def _within(got, ref, what):
+    """Per element |got - ref| <= 1e-4 |ref| + FLOOR max|ref|; returns the worst ratio to that bound."""
+    bound = 1e-4 * np.abs(ref) + FLOOR * np.abs(ref).max()
+    ratio = np.abs(got - ref) / bound
+    worst = int(np.argmax(ratio))
+    assert ratio.max() <= 1.0, (what, float(ratio.max()), float(np.ravel(got)[worst]), float(np.ravel(ref)[worst]),
+                                float(np.abs(ref).max()))
+    return float(ratio.max())
 
 
 def _run_gpu(d, vel, u, w, cw):
@@ -78,8 +101,7 @@ def test_adjoint_matches_torch_fp64(case):
     keep = ~_kink_mask(d, vel, u)
     assert keep.mean() > 0.9
     for got, ref, nm in ((gx, rx, "x"), (gv, rv, "v"), (gu, ru, "u")):
-        err = np.abs(got[keep] - ref[keep]).max()
-        assert err <= 1e-4 * np.abs(ref).max(), (name, nm, err, np.abs(ref).max())
+        _within(got[keep], ref[keep], (name, nm))
 
 
 def test_adjoint_matches_oracle_finite_differences(O):
@@ -121,7 +143,7 @@ def test_adjoint_matches_oracle_finite_differences(O):
                 continue
             got = {"x": gx, "v": gv, "u": gu}[nm]
             g = got[k, comp] if comp is not None else got[k]
-            assert abs(g - fds[0]) <= 1e-4 * scale[nm], (nm, k, comp, g, fds[0])
+            assert abs(g - fds[0]) <= 1e-4 * abs(fds[0]) + FLOOR * scale[nm], (nm, k, comp, g, fds[0])
             checked += 1
     assert checked >= 12
 
@@ -190,7 +212,7 @@ def test_adjoint_kh32_full_size_finite_differences(O):
                 continue  # a kink of the loss inside the stencil (support edge, mu = 0)
             got = {"x": gx, "v": gv, "u": gu}[nm]
             g = got[k, comp] if comp is not None else got[k]
-            assert abs(g - fds[0]) <= 1e-4 * scale[nm], (nm, k, comp, g, fds[0])
+            assert abs(g - fds[0]) <= 1e-4 * abs(fds[0]) + FLOOR * scale[nm], (nm, k, comp, g, fds[0])
             checked += 1
     assert checked >= 30
 
@@ -246,8 +268,7 @@ def test_adjoint_hsolved_matches_torch_fp64(O, kind):
     keep = ~mask
     assert keep.mean() > {0: 0.8, 1: 0.7}[kind]  # Wendland C2: more neighbours reach the kink
     for got, ref, nm in ((gx, rx, "x"), (gv, rv, "v"), (gu, ru, "u")):
-        err = np.abs(got[keep] - ref[keep]).max()
-        assert err <= 1e-4 * np.abs(ref).max(), (kind, nm, err, np.abs(ref).max())
+        _within(got[keep], ref[keep], (kind, nm))
     # the h term is not negligible here: the fixed-h gradient differs from it
     fixed = T.loss_and_grad(d["pos"], vel, u, d["m"], h, w, cw, box=d["box"], kernel_gamma=kg, kernel=kind)[1]
     assert np.abs(fixed - rx).max() > 1e-2 * np.abs(rx).max()
@@ -265,3 +286,41 @@ def test_hsolved_adjoint_refused_at_fixed_h():
     ctx.force(torch.from_numpy(d["u"].astype(np.float32)).cuda())
     with pytest.raises(sph.SwiftGPUError):
         ctx.force_backward(torch.zeros(n, 4, device="cuda"), h_mode=1)
+
+
+def test_backward_after_another_forward_on_the_same_context():
+    """Two SphForces forwards on one context, then the first one's backward: its gradient is still its own
+    (the context's state is restored from the saved inputs), bitwise equal to a backward taken at once."""
+    from paper_2505_14538_b300 import _lib, sph
+    name, d, vel, u = list(_cases())[1]
+    n = len(d["pos"])
+    rng = np.random.default_rng(21)
+    w = torch.from_numpy(rng.normal(size=(n, 3)).astype(np.float32)).cuda()
+    cw = torch.from_numpy(rng.normal(size=n).astype(np.float32)).cuda()
+    m = torch.from_numpy(d["m"].astype(np.float32)).cuda()
+    h = torch.from_numpy(d["h"].astype(np.float32)).cuda()
+
+    def leaves(shift):
+        x = torch.from_numpy(((d["pos"] + shift) % 1.0).astype(np.float32)).cuda().requires_grad_(True)
+        v = torch.from_numpy(vel.astype(np.float32)).cuda().requires_grad_(True)
+        uu = torch.from_numpy(u.astype(np.float32)).cuda().requires_grad_(True)
+        return x, v, uu
+
+    ctx = sph.Context(n, box=d["box"], flags=_lib.FLAG_NO_H_ITER)
+    # reference: forward and backward at once
+    x, v, uu = leaves(0.0)
+    a, du = sph.SphForces.apply(x, v, uu, m, h, ctx)
+    ((w * a).sum() + (cw * du).sum()).backward()
+    ref = [t.grad.clone() for t in (x, v, uu)]
+    # the same forward, then another one (other positions) on the same context, then the first backward
+    x, v, uu = leaves(0.0)
+    a, du = sph.SphForces.apply(x, v, uu, m, h, ctx)
+    x2, v2, u2 = leaves(0.01)
+    a2, du2 = sph.SphForces.apply(x2, v2, u2, m, h, ctx)
+    ((w * a).sum() + (cw * du).sum()).backward()
+    torch.cuda.synchronize()
+    for got, exp in zip((x.grad, v.grad, uu.grad), ref):
+        assert torch.equal(got, exp)
+    # and the second one's backward still gives its own gradient
+    ((w * a2).sum() + (cw * du2).sum()).backward()
+    assert not torch.equal(x2.grad, ref[0])
