@@ -251,6 +251,21 @@ int swift_gpu_gradient_force(swift_gpu_ctx* ctx, const float* u, const float* al
 int swift_gpu_force_backward(swift_gpu_ctx* ctx, const float* grad_accel_dudt, float* grad_x, float* grad_v,
                              float* grad_u, int h_mode, void* stream);
 
+/* Replace the density results of the particles marked in mask[n] (uint8,
+ * caller order, device) with values computed elsewhere: h_in[n] (also the h
+ * the later loops take for them), rho4[n] and curl_div[n] (float4, as
+ * swift_gpu_density writes them). For a domain decomposition over several
+ * GPUs (SWIFT keeps its CPU code's domain decomposition over MPI ranks with
+ * the GPU off-loading, Sec. 5): the ghost-layer particles of a rank are
+ * inactive in its density call, their owners compute them, and this call puts
+ * the owners' results in place before swift_gpu_gradient / swift_gpu_force /
+ * swift_gpu_gradient_force. The marked
+ * particles must have been inactive in the density call, and their h within
+ * the cell cap (device-side ERR_H_EXCEEDS_CELL otherwise). Requires density
+ * (ERR_ORDER otherwise; also with SWIFT_GPU_PLAIN). Asynchronous. */
+int swift_gpu_set_inactive(swift_gpu_ctx* ctx, const uint8_t* mask, const float* h_in, const float* rho4,
+                           const float* curl_div, void* stream);
+
 /* Wait for all work on the device (the calls may have been captured in a CUDA
  * graph and replayed on any stream) and read the device status word:
  * *status = first device-side error code (0 = none), *detail = its count or

@@ -41,7 +41,8 @@ EXPORTED = ("swift_gpu_default_params", "swift_gpu_create", "swift_gpu_destroy",
             "swift_gpu_force_backward", "swift_gpu_sync_status", "swift_gpu_get_info", "swift_gpu_get_cells",
             "swift_gpu_get_tuning", "swift_gpu_set_tuning", "swift_gpu_autotune", "swift_gpu_density_static",
             "swift_gpu_get_leaves", "swift_gpu_gradient_force", "swift_gpu_default_time_params",
-            "swift_gpu_kick_drift", "swift_gpu_viscosity_switch", "swift_gpu_kick_finish")
+            "swift_gpu_kick_drift", "swift_gpu_viscosity_switch", "swift_gpu_kick_finish",
+            "swift_gpu_set_inactive")
 
 STATIC_MAX_PARTICLES = 32768
 
@@ -143,6 +144,7 @@ _SIGS = {
                                       _VP, _VP]),
     "swift_gpu_get_leaves": (_I, [_VP, _VP, _VP, _VP, _I64, _VP]),
     "swift_gpu_gradient_force": (_I, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "swift_gpu_set_inactive": (_I, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "swift_gpu_default_time_params": (None, [ctypes.POINTER(TimeParams)]),
     "swift_gpu_kick_drift": (_I, [_VP, ctypes.POINTER(TimeParams), _VP, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
                                   _VP]),

@@ -348,6 +348,19 @@ int swift_gpu_force_backward(swift_gpu_ctx* h, const float* grad_accel_dudt, flo
                        reinterpret_cast<float4*>(grad_v), grad_u, h_mode, s);
 }
 
+int swift_gpu_set_inactive(swift_gpu_ctx* h, const uint8_t* mask, const float* h_in, const float* rho4,
+                           const float* curl_div, void* stream) {
+  Ctx* c = from(h);
+  if (!c) return SWIFT_GPU_ERR_ARG;
+  if (!(c->state & 2) || (c->params.flags & SWIFT_GPU_PLAIN)) return SWIFT_GPU_ERR_ORDER;
+  if (c->n > 0 && (!aligned(mask, 1) || !aligned(h_in, 4) || !aligned(rho4, 16) || !aligned(curl_div, 16)))
+    return SWIFT_GPU_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  c->last_stream = s;
+  return set_inactive_impl(c, mask, h_in, reinterpret_cast<const float4*>(rho4),
+                           reinterpret_cast<const float4*>(curl_div), s);
+}
+
 int swift_gpu_sync_status(swift_gpu_ctx* h, int* status, int64_t* detail) {
   Ctx* c = from(h);
   if (!c) return SWIFT_GPU_ERR_ARG;

@@ -118,6 +118,8 @@ int build_cells_impl(Ctx* c, const float4* pos_h, int n, float min_width, cudaSt
 int density_impl(Ctx* c, const float4* pos_h_in, const float4* vel_m, const uint8_t* active, float* h_out,
                  float4* rho4, float4* curl_div, uint32_t* ngb, cudaStream_t s);
 int ghost_impl(Ctx* c, const float* u, const float* alpha_v, const float* alpha_c, cudaStream_t s);
+int set_inactive_impl(Ctx* c, const uint8_t* mask, const float* h, const float4* rho4, const float4* cd,
+                      cudaStream_t s);
 int gradient_impl(Ctx* c, float2* vsig_lapu, cudaStream_t s);
 int force_impl(Ctx* c, float4* accel_dudt, float* dh_dt, double* reductions, cudaStream_t s);
 int grad_force_impl(Ctx* c, float2* vsig_lapu, float4* accel_dudt, float* dh_dt, double* reductions,

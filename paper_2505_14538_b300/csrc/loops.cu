@@ -1351,6 +1351,36 @@ int ghost_impl(Ctx* c, const float* u, const float* alpha_v, const float* alpha_
   return cudaGetLastError() == cudaSuccess ? SWIFT_GPU_OK : SWIFT_GPU_ERR_CUDA;
 }
 
+// The density results of the particles marked in mask (caller order) replaced
+// by values computed elsewhere: h (into the sorted positions), rho4, curl_div.
+// An h beyond the cell cap cannot be served by the kept lists or the cells:
+// ERR_H_EXCEEDS_CELL.
+__global__ void k_set_inactive(int n, const unsigned* __restrict__ perm, const Grid* __restrict__ g,
+                               const uint8_t* __restrict__ mask, const float* __restrict__ h,
+                               const float4* __restrict__ rho4_in, const float4* __restrict__ cd_in, float4* pos,
+                               float4* __restrict__ rho4, float4* __restrict__ cd, Status* st) {
+  const float hcap = g->hcap;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const unsigned src = perm[k];
+    if (!mask[src]) continue;
+    const float hk = h[src];
+    if (!(hk > 0.0f) || hk > hcap) set_error(st, cell_cap_flag(*g));
+    pos[k].w = hk;
+    rho4[k] = rho4_in[src];
+    cd[k] = cd_in[src];
+  }
+}
+
+int set_inactive_impl(Ctx* c, const uint8_t* mask, const float* h, const float4* rho4, const float4* cd,
+                      cudaStream_t s) {
+  if (c->n == 0) return SWIFT_GPU_OK;
+  const int nb = min((c->n + 255) / 256, c->num_sms * 8);
+  k_set_inactive<<<nb, 256, 0, s>>>(c->n, c->d_vals[c->sorted_buf], c->d_grid, mask, h, rho4, cd, c->d_pos,
+                                    c->d_rho4, c->d_cd, c->d_status);
+  c->launches++;
+  return cudaGetLastError() == cudaSuccess ? SWIFT_GPU_OK : SWIFT_GPU_ERR_CUDA;
+}
+
 static LoopArgs loop_args(Ctx* c, int* ticket, void* out) {
   LoopArgs a;
   a.grid = c->d_grid;

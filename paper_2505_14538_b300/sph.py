@@ -191,6 +191,15 @@ class Context:
             ctypes.c_int(h_mode), _stream(stream)), "swift_gpu_force_backward")
         return gx, gv, gu
 
+    def set_inactive(self, mask, h, rho4, curl_div, stream=None):
+        """swift_gpu_set_inactive: the density results of the particles in ``mask`` computed elsewhere."""
+        n = self.n
+        self.calls += 1
+        _check(self.lib.swift_gpu_set_inactive(
+            self.handle, _ptr(mask, torch.uint8, None, n, "mask"), _ptr(h, _F32, None, n, "h"),
+            _ptr(rho4, _F32, 4, n, "rho4"), _ptr(curl_div, _F32, 4, n, "curl_div"), _stream(stream)),
+            "swift_gpu_set_inactive")
+
     def sync_status(self):
         code = ctypes.c_int()
         detail = ctypes.c_int64()
