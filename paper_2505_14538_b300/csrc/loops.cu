@@ -924,6 +924,26 @@ __device__ __forceinline__ void force_item(const LoopArgs& a,
   }
 }
 
+// The block's partial of the eight global sums from its threads' FP32 TwoSum
+// pairs (sum, error): each warp combines its lanes' pairs in FP32 (TwoSum of
+// the sums, the errors added), and only the warps' pairs are carried into
+// FP64 and added in warp order. Lane-level FP64 shuffles would cost more:
+// FP64 issues at a small fraction of the FP32 rate on this part.
+__device__ __forceinline__ void block_partial(float (&acc)[8], float (&accc)[8], double (&red)[kWarpsPerBlock][8],
+                                              double* out) {
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    lsum2(acc[q], accc[q], 5);
+    if (lane_id() == 0) red[threadIdx.x >> 5][q] = (double)acc[q] + (double)accc[q];
+  }
+  __syncthreads();
+  if (threadIdx.x < 8) {
+    double x = 0.0;
+    for (int ww = 0; ww < kWarpsPerBlock; ++ww) x += red[ww][threadIdx.x];
+    out[threadIdx.x] = x;
+  }
+}
+
 template <bool kGrad, int K>
 __device__ __forceinline__ void force_kernel_body(const LoopArgs& a) {
   using Op = typename std::conditional<kGrad, GradForceOp, ForceOp>::type;
@@ -962,18 +982,7 @@ __device__ __forceinline__ void force_kernel_body(const LoopArgs& a) {
     force_item<kGrad>(a, op, g, w, it, t, ninter, nginter, ncand, acc, accc);
   }
   // block partial of the FP64 sums (summed in block order by k_reduce_partials)
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    double x = (double)acc[q] + (double)accc[q];
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
-    if (lane == 0) red[threadIdx.x >> 5][q] = x;
-  }
-  __syncthreads();
-  if (threadIdx.x < 8) {
-    double x = 0.0;
-    for (int ww = 0; ww < kWarpsPerBlock; ++ww) x += red[ww][threadIdx.x];
-    a.red_partial[(a.red_offset + blockIdx.x) * 8 + threadIdx.x] = x;
-  }
+  block_partial(acc, accc, red, a.red_partial + (long long)(a.red_offset + blockIdx.x) * 8);
   ninter = warp_sum(ninter);
   ncand = warp_sum(ncand);
   if (lane == 0) {
@@ -1157,18 +1166,13 @@ __global__ void __launch_bounds__(kLoopThreads, 4) k_loop_lpp(const __grid_const
     }
   }
   if constexpr (kMode != 0) {
+    float acc[8], accc[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      double x = (double)s_acc[q][threadIdx.x] + (double)s_acc[8 + q][threadIdx.x];
-      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
-      if (lane == 0) red[threadIdx.x >> 5][q] = x;
+      acc[q] = s_acc[q][threadIdx.x];
+      accc[q] = s_acc[8 + q][threadIdx.x];
     }
-    __syncthreads();
-    if (threadIdx.x < 8) {
-      double x = 0.0;
-      for (int ww = 0; ww < kWarpsPerBlock; ++ww) x += red[ww][threadIdx.x];
-      a.red_partial[(a.red_offset + blockIdx.x) * 8 + threadIdx.x] = x;
-    }
+    block_partial(acc, accc, red, a.red_partial + (long long)(a.red_offset + blockIdx.x) * 8);
   }
   ninter = warp_sum(ninter);
   ncand = warp_sum(ncand);
@@ -1187,9 +1191,13 @@ __global__ void __launch_bounds__(kLoopThreads, 4) k_loop_lpp(const __grid_const
 
 // One warp per quantity; lane l sums blocks l, l+32, ... and the warp then
 // combines the lanes in a fixed order, so the result does not depend on timing.
+// The unrolled loop issues eight loads before their adds (the order of the
+// adds is unchanged), so the lane's chain waits on one load latency per eight
+// blocks instead of per block.
 __global__ void k_reduce_partials(const double* __restrict__ part, int nblocks, double* __restrict__ out) {
   const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double x = 0.0;
+#pragma unroll 8
   for (int b = lane; b < nblocks; b += 32) x += part[b * 8 + q];
   for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
   if (lane == 0) out[q] = x;
