@@ -415,14 +415,12 @@ def run_ours(args, rank, world, pg):
     res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
            "ms_per_step": ms_per_step, "ms_per_step_median": statistics.median(gms), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": f"{WORKLOAD}: Sedov blast, {n} particles on a jittered 64^3 lattice "
-                                  "(+-0.1 spacing), u=1e-5, E=1 in the 32 central particles, periodic unit box",
-                      "particles": n, "nc": ctx.info()["nc"], "h_tol": float(ctx.params.h_tol),
-                      "density_passes": i1["density_passes"], "interactions_per_step": inter_step,
-                      "tuning": ctx.tuning(),
-                      "l2": "flushed between steps (256 MB write, twice the L2)", "parallelism": f"replicas x{world}",
-                      "launch": "whole step captured in one CUDA graph, replayed per step",
-                      "step": "build_cells -> density (h iteration) -> gradient + force (one fused call)"},
+           "config": workload_config(n, world),
+           "run": {"nc": ctx.info()["nc"], "h_tol_f32": float(ctx.params.h_tol),
+                   "density_passes": i1["density_passes"], "interactions_per_step": inter_step,
+                   "tuning": ctx.tuning(),
+                   "launch": "whole step captured in one CUDA graph, replayed per step",
+                   "step": "build_cells -> density (h iteration) -> gradient + force (one fused call)"},
            "roofline": roof, "gpu_launches": int(launches_graph), "clocks": clocks,
            "autotune": tune, "sustained": sustained, "h_tol_cost": h_tol_cost,
            "direct": {"value": value_direct, "ms_per_step": tmax_direct / K * 1e3,
@@ -1110,12 +1108,24 @@ def errors_vs_oracle(d, out, ctx):
     }
 
 
+def workload_config(n, world):
+    """The `config` of the bench line, the same dict in both arms (the workload, not the machinery)."""
+    return {"workload": f"{WORKLOAD}: Sedov blast, {n} particles on a jittered 64^3 lattice "
+                        "(+-0.1 spacing), u=1e-5, E=1 in the 32 central particles, periodic unit box",
+            "particles": n, "h_tol": BENCH_H_TOL,
+            "l2": "GPU arm: flushed between steps (256 MB write, twice the L2); reference arm: the FP64 oracle on "
+                  "the host cores",
+            "parallelism": f"replicas x{world}"}
+
+
 def run_reference(args, rank, world, pg, budget_s=90.0):
     """The oracle as the reference arm: rank 0 times it on the host cores, other ranks exit.
 
-    Exactly K steps of the same workload and h tolerance as our arm; each is
-    the whole workload when K whole oracle steps fit in about budget_s, else a
-    bounded sample (the particles of a central cube sized so that they do).
+    W untimed warm-up steps, then exactly K timed steps of the same workload and
+    h tolerance as our arm; each is the whole workload when K whole oracle steps
+    fit in about budget_s, else a bounded sample (the particles of a central
+    cube sized so that they do). The first warm-up step is a whole one and
+    sizes the sample.
     """
     if rank != 0:
         return None
@@ -1126,12 +1136,15 @@ def run_reference(args, rank, world, pg, budget_s=90.0):
     cores = os.cpu_count() or 1
     h_max = 0.0202860012650  # the cell cap of the workload's 27^3 grid, as our arm's h iteration has it
     K = args.steps
-    _, t_full = oracle_step_timed(d, cores, h_max)  # warm-up: one whole step, untimed
+    W = max(1, args.warmup)
+    _, t_full = oracle_step_timed(d, cores, h_max)  # warm-up 1: one whole step, untimed
     region, frac = None, 1.0
     if t_full * K > budget_s:
         frac = budget_s / K / t_full
         side = frac ** (1.0 / 3.0)
         region = (np.full(3, 0.5 - side / 2), np.full(3, 0.5 + side / 2))
+    for _ in range(W - 1):  # the other warm-up steps, the size of the timed ones
+        oracle_step_timed(d, cores, h_max, region=region)
     tot_i, tot_t = 0, 0.0
     for _ in range(K):
         i, t = oracle_step_timed(d, cores, h_max, region=region)
@@ -1143,11 +1156,9 @@ def run_reference(args, rank, world, pg, budget_s=90.0):
     sample = (f"{what} per step, {K} steps, h iteration to {BENCH_H_TOL:.0e}, gradient, force, FP64 oracle with "
               f"OpenMP over particles")
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
-            "warmup": 1, "ms_per_step": tot_t / K * 1e3, "higher_is_better": True,
+            "warmup": W, "ms_per_step": tot_t / K * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{WORKLOAD}: Sedov blast, {len(d['pos'])} particles on a jittered 64^3 lattice "
-                                   "(+-0.1 spacing), u=1e-5, E=1 in the 32 central particles, periodic unit box",
-                       "particles": len(d["pos"]), "h_tol": BENCH_H_TOL},
+            "config": workload_config(len(d["pos"]), world),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
