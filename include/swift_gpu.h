@@ -128,19 +128,27 @@ void swift_gpu_default_params(swift_gpu_params* p);
 
 /* Create a context for up to n_max particles on the current CUDA device.
  * Allocates every device buffer the calls need, so no later call allocates:
- * about 0.6 KB per particle, plus the cell arrays, the adaptive tree and leaf
- * lists (about 0.3 KB per particle), and on the uniform grid (a context
- * created without ADAPTIVE) the store of the candidate lists the density call
- * keeps for the later loops: 512 bytes per particle for the cubic spline,
- * scaled by (kernel_gamma / 1.825742)^3 up to 1 KB for the Wendland shapes. *ctx is owned by the
- * caller and freed with swift_gpu_destroy. Errors: ERR_ARG (null/invalid
- * params, n_max < 1 or > 2^26), ERR_NOMEM, ERR_CUDA. */
+ * about 0.3 KB per particle of sorted records, sums and work lists, plus the
+ * cell arrays, and then by the grid it is created for:
+ *   uniform grid (no ADAPTIVE): the store of the candidate lists the density
+ *     call keeps for the gradient and force loops, W x 4 bytes a particle
+ *     (W = 92 entries for the cubic spline, 128 Wendland C2, 160 Wendland C4),
+ *     and the pair-axis replicas of the lane-per-particle density path, 208
+ *     bytes a particle: 872 bytes a particle in all for the cubic spline;
+ *   ADAPTIVE: the octree, the leaves and their neighbour lists instead, 719
+ *     bytes a particle in all.
+ * *ctx is owned by the caller and freed with swift_gpu_destroy. Errors:
+ * ERR_ARG (null/invalid params, n_max < 1 or > 2^26), ERR_NOMEM, ERR_CUDA. */
 int swift_gpu_create(swift_gpu_ctx** ctx, const swift_gpu_params* p, int64_t n_max);
 
 /* Release every buffer of the context (synchronises the device). NULL is allowed. */
 int swift_gpu_destroy(swift_gpu_ctx* ctx);
 
-/* Replace the physics parameters (same rules as create). Host only. */
+/* Replace the physics parameters (same rules as create). Host only. A
+ * context created without ADAPTIVE holds no tree arrays: turning ADAPTIVE on
+ * here is ERR_ARG. A kernel shape wider than the one the context was created
+ * with leaves the kept-list store too small for its lists; the density call
+ * then keeps none, and the gradient and force loops scan the cells. */
 int swift_gpu_set_params(swift_gpu_ctx* ctx, const swift_gpu_params* p);
 
 /* Build the cell grid and the particle order (paper Sec. 2.2: cubic cells,

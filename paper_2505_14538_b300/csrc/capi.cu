@@ -136,23 +136,16 @@ int swift_gpu_create(swift_gpu_ctx** out, const swift_gpu_params* p, int64_t n_m
   c->node_cap = (int)node_cap;
   c->leaf_cap = (int)n;
   if (scan_m < node_cap + 1) scan_m = node_cap + 1;  // leaf flags of the tree nodes
-  // kept candidate lists: 128 entries per particle (a list that does not fit leaves its item to scan)
-  // Kept candidate lists (uniform grid only; adaptive leaves never keep them): the candidates within
-  // the cell cap's support, padded to the longest lane of each item. 128 entries a particle hold the
-  // cubic spline's (about 56 neighbours); the other shapes scale with their neighbour count, (H/h)^3.
-  int64_t per = 128;
-  if (p->kernel_gamma > 1.825742f) {
-    const double s = (double)p->kernel_gamma / 1.825742;
-    per = (int64_t)(16.0 * ceil(128.0 * s * s * s / 16.0));
-    if (per > 256) per = 256;
-  }
-  const bool keep_lists = (p->flags & SWIFT_GPU_ADAPTIVE) == 0;
-  // the lane-per-particle path keeps a fixed span of W entries a lane for every group of 32
-  const bool lpp = keep_lists && (p->flags & SWIFT_GPU_PLAIN) == 0;
+  // Kept candidate lists (uniform grid only; adaptive leaves never keep them): a fixed span of W
+  // entries a lane for every group of 32 particles (lpp_width_of: W = 92 for the cubic spline's
+  // about 56 candidates, more for the shapes with more neighbours). A context created for
+  // adaptive leaves holds the tree arrays instead; one created for the uniform grid holds none.
+  const bool adaptive = (p->flags & SWIFT_GPU_ADAPTIVE) != 0;
+  const bool lpp = !adaptive && (p->flags & SWIFT_GPU_PLAIN) == 0;
   const int64_t lpp_need = (int64_t)lpp_width_of(p->kernel) * 32 * ((n + 31) / 32);
-  if (lpp && lpp_need > per * n) per = (lpp_need + n - 1) / n;
-  c->nl_cap = !keep_lists ? 0 : per * n < ((int64_t)1 << 31) - 64 ? per * n : ((int64_t)1 << 31) - 64;
-  const bool lpp_fits = lpp && lpp_need <= c->nl_cap;
+  c->nl_cap = lpp && lpp_need <= ((int64_t)1 << 31) - 64 ? lpp_need : 0;
+  const bool lpp_fits = c->nl_cap > 0;
+  const int64_t ngroups = (n + 31) / 32 + 1;
   int64_t nbr_cap = 48 * n > ((int64_t)1 << 22) ? 48 * n : ((int64_t)1 << 22);  // at least 16 MB of lists
   c->nbr_cap = (int)(nbr_cap < (int64_t)INT32_MAX ? nbr_cap : (int64_t)INT32_MAX);
   c->red_blocks = c->num_sms * 32;
@@ -167,14 +160,14 @@ int swift_gpu_create(swift_gpu_ctx** out, const swift_gpu_params* p, int64_t n_m
             dalloc(&c->d_plist[1], n) && dalloc(&c->d_counters, kCtrCount(kMaxPasses)) &&
             dalloc(&c->d_stats, kStatCount) && dalloc(&c->d_red_partial, 8 * (size_t)c->red_blocks) &&
             dalloc(&c->d_scratch4[0], 4 * n) && dalloc(&c->d_scratch1[0], n) && dalloc(&c->d_scratch1[1], n) &&
-            dalloc(&c->d_plain_act, n) && dalloc(&c->d_aux[0], n) && dalloc(&c->d_aux[1], n) &&
-            dalloc(&c->d_node_range, node_cap) && dalloc(&c->d_node, 2 * node_cap) &&
-            dalloc(&c->d_node_link, node_cap) && dalloc(&c->d_node_parent, node_cap) &&
-            dalloc(&c->d_node_done, node_cap) && dalloc(&c->d_node_flag, node_cap + 1) &&
-            dalloc(&c->d_leaf_range, n) && dalloc(&c->d_leaf_hcap, n) && dalloc(&c->d_leaf_node, n) &&
-            dalloc(&c->d_nbr_span, n) && dalloc(&c->d_nbr, (size_t)c->nbr_cap) &&
-            dalloc(&c->d_tree_ctr, kTreeCtrCount) && (c->nl_cap == 0 || dalloc(&c->d_nlist, (size_t)c->nl_cap)) &&
-            dalloc(&c->d_item_nl, n) &&
+            dalloc(&c->d_plain_act, n) && dalloc(&c->d_tree_ctr, kTreeCtrCount) &&
+            (!adaptive ||
+             (dalloc(&c->d_aux[0], n) && dalloc(&c->d_aux[1], n) && dalloc(&c->d_node_range, node_cap) &&
+              dalloc(&c->d_node, 2 * node_cap) && dalloc(&c->d_node_link, node_cap) &&
+              dalloc(&c->d_node_parent, node_cap) && dalloc(&c->d_node_done, node_cap) &&
+              dalloc(&c->d_node_flag, node_cap + 1) && dalloc(&c->d_leaf_range, n) && dalloc(&c->d_leaf_hcap, n) &&
+              dalloc(&c->d_leaf_node, n) && dalloc(&c->d_nbr_span, n) && dalloc(&c->d_nbr, (size_t)c->nbr_cap))) &&
+            (c->nl_cap == 0 || dalloc(&c->d_nlist, (size_t)c->nl_cap)) && dalloc(&c->d_item_nl, ngroups) &&
             (!lpp_fits || (dalloc(&c->d_rep, (size_t)kAxes * n) && dalloc(&c->d_lcnt, n) && dalloc(&c->d_gc, n))) &&
             cudaMallocHost((void**)&c->h_status, sizeof(Status)) == cudaSuccess &&
             cudaMallocHost((void**)&c->h_stats, sizeof(unsigned long long) * kStatCount) == cudaSuccess;
@@ -211,6 +204,8 @@ int swift_gpu_destroy(swift_gpu_ctx* h) {
 int swift_gpu_set_params(swift_gpu_ctx* h, const swift_gpu_params* p) {
   Ctx* c = from(h);
   if (!c || !p) return SWIFT_GPU_ERR_ARG;
+  // adaptive leaves need the tree arrays, which only a context created with the flag holds
+  if ((p->flags & SWIFT_GPU_ADAPTIVE) && c->d_node == nullptr) return SWIFT_GPU_ERR_ARG;
   Phys ph;
   if (phys_from(p, &ph) != SWIFT_GPU_OK) return SWIFT_GPU_ERR_ARG;
   c->params = *p;

@@ -1280,12 +1280,20 @@ void reduce_partials(Ctx* c, int nblocks, double* out, cudaStream_t s) {
   c->launches++;
 }
 
+// Whether the kept-list store holds a span of W entries a lane (W of the
+// current kernel shape, which swift_gpu_set_params may have changed since the
+// store was sized) for every group of the current particles.
+static bool lpp_store_fits(const Ctx* c) {
+  return c->d_nlist != nullptr && c->d_lcnt != nullptr &&
+         (int64_t)lpp_width_of(c->phys.kernel) * 32 * (((int64_t)c->n + 31) / 32) <= c->nl_cap;
+}
+
 // The lane-per-particle path runs the persistent density call on the uniform
 // grid when the tuning asks for one lane a particle and the context holds the
 // replicas and the kept-list store.
 static bool use_lpp(const Ctx* c) {
-  return c->tuning.max_lanes_per_particle == 1 && c->d_rep != nullptr && c->d_nlist != nullptr &&
-         c->d_lcnt != nullptr && !(c->params.flags & (SWIFT_GPU_ADAPTIVE | SWIFT_GPU_PLAIN));
+  return c->tuning.max_lanes_per_particle == 1 && c->d_rep != nullptr && lpp_store_fits(c) &&
+         !(c->params.flags & (SWIFT_GPU_ADAPTIVE | SWIFT_GPU_PLAIN));
 }
 
 int density_impl(Ctx* c, const float4* pos_in, const float4* vel_in, const uint8_t* active, float* h_out,
@@ -1332,7 +1340,7 @@ int density_impl(Ctx* c, const float4* pos_in, const float4* vel_in, const uint8
   a.st = c->d_status;
   a.stats = c->d_stats;
   // kept lists in the groups' layout (either engine), where the context holds the store for it
-  const bool keep = c->d_nlist != nullptr && c->d_lcnt != nullptr && !(c->params.flags & SWIFT_GPU_ADAPTIVE);
+  const bool keep = lpp_store_fits(c) && !(c->params.flags & SWIFT_GPU_ADAPTIVE);
   a.nlist = keep ? c->d_nlist : nullptr;
   a.item_nl = keep ? c->d_item_nl : nullptr;
   a.rep = c->d_rep;
