@@ -57,6 +57,17 @@
  *  - Cell id: wrap x into [0,L) in FP64, cell = floor(x*nc/L) clamped to nc-1,
  *    linear id = cx + nc*(cy + nc*cz).
  *
+ * Pins (tests/test_oracle_*.py) tie most of these to values the paper or the
+ * mathematics fixes. Two coefficient forms have no such pin and are
+ * PARITY UNPINNED: their magnitude is checked only through conservation
+ * (momentum, energy), sign (heating under compression, zero for receding
+ * pairs; heat flowing down-gradient) and parity with the CUDA path:
+ *  - the viscosity coefficient nu_ij of Eq. 9 (the reading above) and its
+ *    heating term, in force_pair;
+ *  - the conduction term of Eqs. 19, 20 and 22 (alpha_c,ij, v_c,ij, the
+ *    kernel factor), in force_pair.
+ * The paper prints no worked example of either, and its Eq. 9 is garbled.
+ *
  * Build: g++ -O2 -std=c++17 -fopenmp -fPIC -shared -ffp-contract=off
  * (no FMA contraction, so every operation rounds exactly as written).
  */
