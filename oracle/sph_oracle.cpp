@@ -57,16 +57,13 @@
  *  - Cell id: wrap x into [0,L) in FP64, cell = floor(x*nc/L) clamped to nc-1,
  *    linear id = cx + nc*(cy + nc*cz).
  *
- * Pins (tests/test_oracle_*.py) tie most of these to values the paper or the
- * mathematics fixes. Two coefficient forms have no such pin and are
- * PARITY UNPINNED: their magnitude is checked only through conservation
- * (momentum, energy), sign (heating under compression, zero for receding
- * pairs; heat flowing down-gradient) and parity with the CUDA path:
- *  - the viscosity coefficient nu_ij of Eq. 9 (the reading above) and its
- *    heating term, in force_pair;
- *  - the conduction term of Eqs. 19, 20 and 22 (alpha_c,ij, v_c,ij, the
- *    kernel factor), in force_pair.
- * The paper prints no worked example of either, and its Eq. 9 is garbled.
+ * Pins (tests/test_oracle_*.py) tie these to values the paper or the
+ * mathematics fixes. The paper prints no worked example of the force terms,
+ * so their magnitudes are pinned to continuum limits: the pressure term to
+ * -(1/rho) dp/dr of the Gresho-Chan profile (Eq. 28), the viscosity (the
+ * Eq. 9 reading above) to its heating under homologous compression, the
+ * conduction (Eqs. 19, 20, 22) to its value at the minimum of a quadratic u,
+ * each in closed form in the kernel's radial moments.
  *
  * Build: g++ -O2 -std=c++17 -fopenmp -fPIC -shared -ffp-contract=off
  * (no FMA contraction, so every operation rounds exactly as written).

@@ -10,7 +10,11 @@ oracle does not compute:
 - the Balsara switch B = |div v| / (|div v| + |curl v| + 1e-4 c / h) for
   linear velocity fields whose divergence and curl are known in closed form
   (uniform compression -3 s, rigid rotation 2 Omega), on a perfect lattice
-  where the SPH estimators of Eqs. 3-4 carry one common lattice factor.
+  where the SPH estimators of Eqs. 3-4 carry one common lattice factor;
+- the viscous heating (Eqs. 7, 9-11, 16) under homologous compression and the
+  conduction (Eqs. 19, 20, 22) at the minimum of a quadratic u, against their
+  continuum limits in the kernel's radial moments, which the lattice sums
+  approach as h / dx grows.
 """
 import numpy as np
 
@@ -92,3 +96,88 @@ def test_balsara_compression_rotation_and_floor(O):
     # factor of div v, 0.99, enters here only)
     B, b_exp = _balsara(O, 1e-3, 0.0)
     assert np.all(np.abs(B / b_exp - 1) < 0.01) and 0.5 < B.mean() < 0.7
+
+
+def _moments(O, h):
+    """First and second radial moments of the kernel, M1 = int |r| W d^3r and M2 = int r^2 W d^3r, by
+    quadrature (M2 is 3 h^2 / 4 by the second-moment definition of H / h, checked here too)."""
+    r = np.linspace(0.0, O.KERNEL_GAMMA * h, 200001)
+    W, _ = O.kernel(r, h)
+    M0 = np.trapezoid(4 * np.pi * r ** 2 * W, r)
+    M1 = np.trapezoid(4 * np.pi * r ** 3 * W, r)
+    M2 = np.trapezoid(4 * np.pi * r ** 4 * W, r)
+    assert abs(M0 - 1) < 1e-9 and abs(M2 / (0.75 * h * h) - 1) < 1e-6
+    return M1, M2
+
+
+def _uniform_state(n_side, h_over_dx, gamma, u):
+    """Perfect lattice in the unit box, m = 1/N (rho = 1), the given h / dx; rho, f and B held at their
+    continuum values (1) so that only the term under test varies."""
+    x, dx = _lattice(n_side)
+    n = len(x)
+    one = np.ones(n)
+    return x, dx, np.full(n, 1.0 / n), np.full(n, h_over_dx * dx), one, (gamma - 1) * u, \
+        np.sqrt(gamma * (gamma - 1) * u), one, one
+
+
+def test_viscous_heating_under_homologous_compression(O):
+    """Viscosity (Eqs. 7, 9-11, 16 as read) under v = -s (x - x0) on a perfect lattice, in the continuum
+    limit. Every pair approaches: mu = v_ij . r_hat = -s r, v_sig = 2 c + beta s r, nu = alpha s r v_sig /
+    (rho_i + rho_j), and the heating of i, sum_j (1/2) m_j nu v_ij . (f_i grad W_i + f_j grad W_j) / 2,
+    becomes -(alpha s^2 / (4 rho)) sum_j m_j r^2 (2 c + beta s r) W'(r). With sum_j m_j F(r_j) ->
+    rho int F d^3r and int r^4 W' 4 pi dr = -4 M1, int r^5 W' 4 pi dr = -5 M2 (by parts):
+
+        du/dt = (alpha s^2 / 4) (8 c M1 + 5 beta s M2).
+
+    At h = 2 dx the lattice sum is within 0.2 % of it. A lost 1/2 in the pair term or in the heating,
+    rho_i rho_j for rho_i + rho_j (rho = 1 here), a lost alpha, or a v_sig without its beta term (at
+    s = 20 the beta term carries 67 % of the heating) is off by 30 % or more. The acceleration cancels
+    by symmetry."""
+    gamma, alpha, beta = 5.0 / 3.0, 0.7, 3.0
+    for h_over_dx, tol in ((2.0, 4e-3), (1.2348, 3e-2)):
+        x, dx, m, h, rho, P, c, f, B = _uniform_state(32, h_over_dx, gamma, np.ones(32 ** 3))
+        M1, M2 = _moments(O, h[0])
+        d = x - 0.5
+        inner = np.all(np.abs(d) < 0.5 - 1.2 * O.KERNEL_GAMMA * h[0], axis=1)  # no wrapped neighbour
+        assert inner.sum() > 1000
+        for s in (1.0, 20.0):
+            fo = O.force(O.Params(terms=2, alpha_v=alpha, beta_v=beta), x, -s * d, m, h, np.ones(len(x)), rho,
+                         f, P, c, B)
+            exp = alpha * s * s / 4 * (8 * c[0] * M1 + 5 * beta * s * M2)
+            rel = fo["dudt"][inner] / exp - 1
+            assert np.abs(rel).max() < tol, (h_over_dx, s, rel.min(), rel.max())
+            assert np.abs(fo["accel"][inner]).max() < 1e-9 * s * c[0]
+        if h_over_dx == 2.0:
+            share = 5 * beta * 20.0 * M2 / (8 * c[0] * M1 + 5 * beta * 20.0 * M2)
+            assert share > 0.6  # the beta term is tested, not drowned
+
+
+def test_conduction_at_the_minimum_of_a_quadratic_u(O):
+    """Conduction (Eqs. 19, 20, 22 as read) with v = 0, rho uniform and u = u0 + (k/2) (x - x0)^2, at the
+    particles of the plane x = x0. There u_i - u_j = -(k/2) r_x^2, P_i - P_j = (gamma-1) rho (u_i - u_j),
+    v_c = sqrt(2 |P_i - P_j| / (rho_i + rho_j)) = sqrt((gamma-1) k / 2) |r_x|, alpha_c,ij = alpha_c, and
+    du/dt_i = sum_j alpha_c v_c m_j (u_i - u_j) (f_i W'_i + f_j W'_j) / (rho_i + rho_j) becomes, with
+    int |x|^3 W'(r) d^3r = pi int r^5 W' dr = -(5/4) M2,
+
+        du/dt = alpha_c sqrt(gamma - 1) (k/2)^(3/2) (5/4) M2   (> 0: heat flows into the minimum).
+
+    At h = 2 dx the lattice sum is within 0.2 % of it. A v_c linear in |P_i - P_j| (scaling k^2, not
+    k^(3/2)), a lost 2 under the root, a lost kernel term, rho_i rho_j for rho_i + rho_j or a flipped sign
+    is off by 29 % or more."""
+    gamma, alpha_c = 5.0 / 3.0, 0.6
+    for h_over_dx, tol in ((2.0, 4e-3), (1.2348, 4e-2)):
+        x, dx, m, h, rho, _, _, f, B = _uniform_state(32, h_over_dx, gamma, np.ones(32 ** 3))
+        M1, M2 = _moments(O, h[0])
+        x0 = (16 + 0.5) * dx  # a lattice plane far from the x faces (the profile is not periodic in x)
+        plane = np.abs(x[:, 0] - x0) < 1e-12
+        assert plane.sum() == 32 * 32
+        got = {}
+        for k in (1.0, 4.0):
+            u = 1.0 + 0.5 * k * (x[:, 0] - x0) ** 2
+            fo = O.force(O.Params(terms=4, alpha_c=alpha_c), x, np.zeros((len(x), 3)), m, h, u, rho, f,
+                         (gamma - 1) * rho * u, np.sqrt(gamma * (gamma - 1) * u), B)
+            exp = alpha_c * np.sqrt(gamma - 1) * (k / 2) ** 1.5 * 1.25 * M2
+            rel = fo["dudt"][plane] / exp - 1
+            assert np.abs(rel).max() < tol, (h_over_dx, k, rel.min(), rel.max())
+            got[k] = fo["dudt"][plane]
+        assert np.allclose(got[4.0] / got[1.0], 8.0, rtol=1e-9, atol=0)  # k^(3/2)
