@@ -726,6 +726,8 @@ def run_zeldovich(dev, peak, fpi, steps=5, cpu=True):
     i0 = ctx.info()
     for k in range(steps):
         flush.zero_()
+        if k == steps - 1:
+            torch.cuda.nvtx.range_push("zeldovich_step")  # marks one step for profilers
         e = ev[k]
         e[0].record(stream)
         ctx.build_cells(pos_h)
@@ -734,6 +736,8 @@ def run_zeldovich(dev, peak, fpi, steps=5, cpu=True):
         e[2].record(stream)
         o.update(ctx.gradient_force(u))
         e[3].record(stream)
+        if k == steps - 1:
+            torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     i1 = ctx.info()
     loop = [statistics.median(ev[k][j].elapsed_time(ev[k][j + 1]) for k in range(steps)) for j in range(3)]
