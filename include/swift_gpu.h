@@ -249,11 +249,12 @@ int swift_gpu_gradient_force(swift_gpu_ctx* ctx, const float* u, const float* al
  * passes and a third gather adds the term. Exact at the root: the density
  * call should have converged (a tighter h_tol makes it closer); ERR_ARG with
  * SWIFT_GPU_NO_H_ITER (h is then an input, not a root).
- * Two gather passes over the same neighbour scan as the forward loops: the
- * force pair terms are reversed in both orientations of every pair, the
- * ghost step is reversed per particle, and the adjoints of each particle's
- * density sums are carried back through both particles' sums. No pair list is
- * stored; the per-particle sums of the forward calls are reused. grad_x and
+ * Two gather passes, each scanning the neighbour cells (or leaves) as the
+ * cell-item loops do: the force pair terms are reversed in both orientations
+ * of every pair, the ghost step is reversed per particle, and the adjoints of
+ * each particle's density sums are carried back through both particles' sums.
+ * The candidates are found again by the scan, not read from a stored pair
+ * list; the per-particle sums of the forward calls are reused. grad_x and
  * grad_v are float4 with w = 0. Requires force (ERR_ORDER otherwise); every
  * particle must have been active (ERR_ARG otherwise). */
 int swift_gpu_force_backward(swift_gpu_ctx* ctx, const float* grad_accel_dudt, float* grad_x, float* grad_v,
