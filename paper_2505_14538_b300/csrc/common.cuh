@@ -261,7 +261,6 @@ __device__ __forceinline__ float4 wrap_pos(float4 p, const float L[3]) {
 }
 
 // Warp-wide max of an int.
-__device__ __forceinline__ int warp_max(int v) { return __reduce_max_sync(0xffffffffu, v); }
 __device__ __forceinline__ unsigned warp_sum(unsigned v) { return __reduce_add_sync(0xffffffffu, v); }
 
 // Nanosecond timer for bounded waits.
