@@ -2,9 +2,11 @@
 // with the gradient loop's Eqs. 10-11 and Laplacian of u fused in) for the
 // lane-per-particle loop over kept lists, written for instruction count:
 //
-//  - j's kernel constants come precomputed from the ghost step (a fifth
-//    record: 1/H_j, C/H_j^4 and the two bounds of H_j^2's guard band), so a
-//    pair takes no division or band arithmetic for them;
+//  - four 16-byte records a neighbour: the ghost step writes each particle's
+//    position with 1/H in place of h, and a pair derives C/H_j^4 and the two
+//    bounds of H_j^2's guard band from 1/H_j (a few FP32 operations cost less
+//    than a fifth record's gather); h_j itself is read only inside the guard
+//    band, where the decision is taken in FP64;
 //  - 1/r is folded into the scalar factors (a_i -= (as/r) dx instead of
 //    as * (dx/r));
 //  - the gradient terms are masked by the exact r < H_i decision instead of
@@ -22,23 +24,21 @@
 
 namespace sg {
 
-// The five records of neighbour j.
+// The four records of neighbour j.
 struct LeanRec {
-  float4 p;   // (x, y, z, h)
+  float4 p;   // (x, y, z, 1/H): the ghost step's position record
   float4 v;   // (vx, vy, vz, m)
   float4 ga;  // (A = f P / rho^2, f, rho, c)
   float4 gb;  // (B, alpha_v, alpha_c P, u)
-  float4 gc;  // (1/H, C/H^4, H^2 - band, H^2 + band)
 };
 
-__device__ __forceinline__ void lean_load(const float4* __restrict__ pos, const float4* __restrict__ vel,
-                                          const float4* __restrict__ ga, const float4* __restrict__ gb,
-                                          const float4* __restrict__ gc, int j, LeanRec& r) {
-  r.p = pos[j];
+__device__ __forceinline__ void lean_load(const float4* __restrict__ xih, const float4* __restrict__ vel,
+                                          const float4* __restrict__ ga, const float4* __restrict__ gb, int j,
+                                          LeanRec& r) {
+  r.p = xih[j];
   r.v = vel[j];
   r.ga = ga[j];
   r.gb = gb[j];
-  r.gc = gc[j];
 }
 
 // The particle's state and sums.
@@ -51,38 +51,48 @@ struct LeanI {
   unsigned gcount, count;
 };
 
-// The run's constants, read from the kernel's parameters (constant bank) where used.
+// The run's constants, read from the kernel's parameters (constant bank) where
+// used; pos: the sorted (x, y, z, h) records, for h_j inside the guard band.
 struct LeanConst {
   const Phys& ph;
+  float Lmax;
+  const float4* __restrict__ pos;
   __device__ __forceinline__ float gm1() const { return ph.gamma_eos - 1.0f; }
 };
 
 // One kept-list entry (j with shift code) of particle I: the pair terms go
 // into the block sums (tax, tay, taz, tdu); the rest straight into I.
 template <int K, bool kGrad>
-__device__ __forceinline__ void lean_pair(LeanI& I, const LeanRec& R, unsigned code, const LeanConst& k,
+__device__ __forceinline__ void lean_pair(LeanI& I, const LeanRec& R, int j, unsigned code, const LeanConst& k,
                                           float& tax, float& tay, float& taz, float& tdu) {
   float xj = R.p.x, yj = R.p.y, zj = R.p.z;
+  // j's support from 1/H_j: the band bounds need H_j^2 only to within a small
+  // part of the band (2^-16 H^2), so an approximate reciprocal serves
+  const float iHj = R.p.w;
+  const float Hj = __fdividef(1.0f, iHj);
+  const float bdj = band_of(Hj, k.Lmax);
+  const float H2lo_j = fmaf(Hj, Hj, -bdj), H2hi_j = fmaf(Hj, Hj, bdj);
   shift_j(code, k.ph.L, xj, yj, zj);
   const float dx = I.x - xj, dy = I.y - yj, dz = I.z - zj;
   const float r2 = r2_of(dx, dy, dz);
   // membership in i's support (gradient) and in either support (force): FP32
   // outside the guard bands, the FP64 definition from the same floats inside
   bool in_i = r2 < I.H2lo;
-  bool in_f = in_i || r2 < R.gc.z;
-  const bool band_f = !in_f && r2 < fmaxf(I.H2hi, R.gc.w);
+  bool in_f = in_i || r2 < H2lo_j;
+  const bool band_f = !in_f && r2 < fmaxf(I.H2hi, H2hi_j);
   const bool band_i = kGrad && in_f && !in_i && r2 < I.H2hi;
   if (band_f || band_i) {
     const double e = exact_r2(I.x, I.y, I.z, R.p.x, R.p.y, R.p.z, k.ph.L[0], k.ph.L[1], k.ph.L[2]);
     const bool ei = e < exact_H2(k.ph.kg, I.h);
     in_i = ei;
-    in_f = in_f || ei || e < exact_H2(k.ph.kg, R.p.w);
+    in_f = in_f || ei || e < exact_H2(k.ph.kg, k.pos[j].w);
   }
   if (!(r2 > 0.0f) || !in_f) return;  // the particle itself, or outside both supports
   const float invr = rsqrtf(r2);
   const float r = r2 * invr;
   const float dWi = I.c4 * dkshape(K, r * I.invH);
-  const float dWj = R.gc.y * dkshape(K, r * R.gc.x);
+  const float i2j = iHj * iHj;
+  const float dWj = k.ph.knorm * (i2j * i2j) * dkshape(K, r * iHj);
   const float dvx = I.vx - R.v.x, dvy = I.vy - R.v.y, dvz = I.vz - R.v.z;
   const float vr = fmaf(dvz, dz, fmaf(dvy, dy, dvx * dx)) * invr;
   const float mj = R.v.w;

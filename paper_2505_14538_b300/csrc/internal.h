@@ -99,7 +99,7 @@ struct Ctx {
   // lists (n_max), and whether the last density call kept such lists
   float4* d_rep = nullptr;
   int* d_lcnt = nullptr;
-  float4* d_gc = nullptr;  // sorted (1/H, C/H^4, H^2 -/+ band) from the ghost step
+  float4* d_gc = nullptr;  // sorted (x, y, z, 1/H) from the ghost step: the force term's position record
 
   int lpp_lists = 0;
 

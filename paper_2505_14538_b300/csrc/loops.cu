@@ -717,13 +717,13 @@ __global__ void __launch_bounds__(kLoopThreads, kLPP ? 4 : 5) k_density(DensArgs
 // ============================================================== ghost step
 // Per particle (Eq. 8, equation of state, sound speed, Balsara switch):
 // ga = (A = f P / rho^2, f, rho, c), gb = (B, alpha_v, alpha_c P, u).
-// gc (may be NULL) = (1/H, C/H^4, H^2 - band, H^2 + band), the kernel constants
-// and guard band of the particle's support as the force pair term reads them.
+// gc (may be NULL) = (x, y, z, 1/H): the particle's position record for the
+// lane-per-particle force term (force_lpp.cuh), which derives its kernel
+// constants and guard band from 1/H.
 __global__ void k_ghost(int n, const unsigned* __restrict__ perm, const float4* __restrict__ pos,
                         const float4* __restrict__ rho4, const float4* __restrict__ cd, const float* __restrict__ u,
                         const float* __restrict__ alpha_v, const float* __restrict__ alpha_c, Phys ph,
                         float4* __restrict__ ga, float4* __restrict__ gb, float4* __restrict__ gc) {
-  const float Lmax = fmaxf(ph.L[0], fmaxf(ph.L[1], ph.L[2]));
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     const unsigned src = perm[k];
     const float h = pos[k].w;
@@ -744,10 +744,8 @@ __global__ void k_ghost(int n, const unsigned* __restrict__ perm, const float4* 
     ga[k] = make_float4(A, f, rho, c);
     gb[k] = make_float4(B, av, acoef * P, uk);
     if (gc) {
-      const float H = ph.kg * h;
-      const float iH = 1.0f / H;
-      const float bd = band_of(H, Lmax);
-      gc[k] = make_float4(iH, ph.knorm * iH * iH * iH * iH, H * H - bd, H * H + bd);
+      const float4 p = pos[k];
+      gc[k] = make_float4(p.x, p.y, p.z, 1.0f / (ph.kg * h));
     }
   }
 }
@@ -779,7 +777,7 @@ struct LoopArgs {
   const int* missing;    // set by the density call when some group has no kept list
   int only_unlisted;     // cell-item kernels: only particles whose group has no kept list
   int red_offset;        // first block slot of this launch's partial sums
-  const float4* gc; // sorted (1/H, C/H^4, H^2 - band, H^2 + band) from the ghost step
+  const float4* gc; // sorted (x, y, z, 1/H) from the ghost step (force_lpp.cuh)
 };
 
 
@@ -1043,7 +1041,7 @@ __global__ void __launch_bounds__(kLoopThreads, 4) k_loop_lpp(const __grid_const
   gop.kernel = K;
   gop.knorm = a.ph.knorm;
   gop.beta = a.ph.beta_v;
-  const LeanConst kc{a.ph};
+  const LeanConst kc{a.ph, Lmax, a.pos};
   for (;;) {
     const int t = take_ticket(a.ticket);
     if (t >= ng) break;
@@ -1107,13 +1105,14 @@ __global__ void __launch_bounds__(kLoopThreads, 4) k_loop_lpp(const __grid_const
       unsigned e1 = 1 < cnt ? lst[32] : (unsigned)k;
       for (int u = 0; u < m; u += 2) {
         LeanRec r0, r1;
-        lean_load(a.pos, a.vel, a.ga, a.gb, a.gc, (int)(e0 & kIndexMask), r0);
-        lean_load(a.pos, a.vel, a.ga, a.gb, a.gc, (int)(e1 & kIndexMask), r1);
+        lean_load(a.gc, a.vel, a.ga, a.gb, (int)(e0 & kIndexMask), r0);
+        lean_load(a.gc, a.vel, a.ga, a.gb, (int)(e1 & kIndexMask), r1);
         const unsigned n0 = u + 2 < cnt ? lst[(u + 2) * 32] : (unsigned)k;
         const unsigned n1 = u + 3 < cnt ? lst[(u + 3) * 32] : (unsigned)k;
         float tax = 0.0f, tay = 0.0f, taz = 0.0f, tdu = 0.0f;
-        if (u < cnt) lean_pair<K, kGrad>(I, r0, e0 >> kIndexBits, kc, tax, tay, taz, tdu);
-        if (u + 1 < cnt) lean_pair<K, kGrad>(I, r1, e1 >> kIndexBits, kc, tax, tay, taz, tdu);
+        if (u < cnt) lean_pair<K, kGrad>(I, r0, (int)(e0 & kIndexMask), e0 >> kIndexBits, kc, tax, tay, taz, tdu);
+        if (u + 1 < cnt)
+          lean_pair<K, kGrad>(I, r1, (int)(e1 & kIndexMask), e1 >> kIndexBits, kc, tax, tay, taz, tdu);
         if (a.ph.compensated) {
           two_sum_acc(I.axs, I.axc, tax);
           two_sum_acc(I.ays, I.ayc, tay);
