@@ -89,7 +89,10 @@ typedef struct {
 
 /* Work-distribution knobs (chosen by swift_gpu_autotune, or set by hand). */
 typedef struct {
-  int threads_per_block; /* 64..1024, multiple of 32 */
+  int threads_per_block; /* must be 256 (reserved). The loop kernels run fixed blocks of 128
+                            threads: four warps, each taking one cell or leaf item (or one group of
+                            32 particles) at a time from the device queue, so four cells a block
+                            are in flight; 64- and 256-thread blocks measured slower */
   int max_lanes_per_particle; /* 1, 2, 4, 8, 16 or 32: lanes that share one particle's neighbour scan;
                                  on the uniform grid 1 selects the lane-per-particle density call (each
                                  lane scans its own particle's neighbour cells through windows along the
