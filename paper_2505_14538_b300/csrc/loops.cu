@@ -52,6 +52,10 @@ __device__ __forceinline__ LaneMap lane_map(int cnt, int lmax) {
 }
 
 // ============================================================ density loop
+// Predicted convergence of the h iteration: a Newton step from a relative
+// residual below kPredict sqrt(h_tol) is taken as the last (dens_item).
+constexpr float kPredict = 0.8f;
+
 struct DensArgs {
   Grid* grid;
   Nbr nb;
@@ -252,13 +256,14 @@ __device__ __forceinline__ void dens_item(const DensArgs& a, const DensOp& op, c
     }
     bool done = !lm.live || retry || kFixedH;
     // a step whose relative residual G = |n h^3 - eta^3| / eta^3 is below
-    // this leaves, by Newton's quadratic convergence, a residual well inside
+    // this leaves, by Newton's quadratic convergence, a residual inside
     // h_tol: the walk that would only confirm it is skipped. With n nearly
-    // constant in h the next residual is about (2/3) G^2 (0.72-0.84 G^2 on a
-    // jittered lattice), so 0.6 sqrt(h_tol) leaves at most 0.36 c h_tol; a
-    // miss only costs the particle another pass, the final sums verify it
+    // constant in h the next residual is about c G^2 with c = 2/3 (0.72-0.84
+    // on a jittered lattice), so 0.8 sqrt(h_tol) leaves at most 0.64 c h_tol
+    // (any c below 1.56 converges); a miss only costs the particle another
+    // pass, the final sums verify it
     const float e3 = (float)a.ph.eta3;
-    const float pred = 0.6f * sqrtf((float)a.ph.h_tol);
+    const float pred = kPredict * sqrtf((float)a.ph.h_tol);
     for (int iter = 0;; ++iter) {
       float ns = 0.0f, nc = 0.0f, dn = 0.0f;
       unsigned np = 0;
@@ -448,10 +453,10 @@ __device__ __forceinline__ void dens_group(const DensArgs& a, const DensOp& op, 
   } else {
     bool done = !live || retry;
     // the predicted-convergence skip of dens_item: a relative residual below
-    // 0.6 sqrt(h_tol) leaves, by Newton's quadratic convergence, a residual
-    // well inside h_tol, and the final sums verify it
+    // kPredict sqrt(h_tol) leaves, by Newton's quadratic convergence, a
+    // residual inside h_tol, and the final sums verify it
     const float e3 = (float)a.ph.eta3;
-    const float pred = 0.6f * sqrtf((float)a.ph.h_tol);
+    const float pred = kPredict * sqrtf((float)a.ph.h_tol);
     for (int iter = 0;; ++iter) {
       float ns = 0.0f, nc = 0.0f, dn = 0.0f;
       unsigned np = 0;
