@@ -141,7 +141,8 @@ void swift_gpu_default_params(swift_gpu_params* p);
  *   ADAPTIVE: the octree, the leaves and their neighbour lists instead, 719
  *     bytes a particle in all.
  * *ctx is owned by the caller and freed with swift_gpu_destroy. Errors:
- * ERR_ARG (null/invalid params, n_max < 1 or > 2^26), ERR_NOMEM, ERR_CUDA. */
+ * ERR_ARG (null/invalid params, n_max < 1 or n_max >= 2^26: a list entry
+ * holds a particle index in 26 bits), ERR_NOMEM, ERR_CUDA. */
 int swift_gpu_create(swift_gpu_ctx** ctx, const swift_gpu_params* p, int64_t n_max);
 
 /* Release every buffer of the context (synchronises the device). NULL is allowed. */

@@ -143,7 +143,7 @@ int swift_gpu_create(swift_gpu_ctx** out, const swift_gpu_params* p, int64_t n_m
   const bool adaptive = (p->flags & SWIFT_GPU_ADAPTIVE) != 0;
   const bool lpp = !adaptive && (p->flags & SWIFT_GPU_PLAIN) == 0;
   const int64_t lpp_need = (int64_t)lpp_width_of(p->kernel) * 32 * ((n + 31) / 32);
-  c->nl_cap = lpp && lpp_need <= ((int64_t)1 << 31) - 64 ? lpp_need : 0;
+  c->nl_cap = lpp ? lpp_need : 0;  // every index into the store is 64-bit
   const bool lpp_fits = c->nl_cap > 0;
   const int64_t ngroups = (n + 31) / 32 + 1;
   int64_t nbr_cap = 48 * n > ((int64_t)1 << 22) ? 48 * n : ((int64_t)1 << 22);  // at least 16 MB of lists

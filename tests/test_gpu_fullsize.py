@@ -185,3 +185,30 @@ def test_zeldovich_256_adaptive_sampled(sph, O):
     check_sample(O, d, vel, u, h, out, sample, float(ctx.params.h_tol))
     red = o["reductions"].cpu().numpy()
     assert np.all(np.abs(red[:3]) <= 1e-6 * red[4])  # momentum, FP64 on the device
+
+
+def test_uniform_lattice_at_the_maximum_size_sampled(sph, O):
+    """The largest context (n_max = 2^26 - 1, the index width of a list entry) on a 406^3 jittered
+    lattice (66.9 M particles): one step on the uniform grid, sampled against the oracle. Its kept
+    lists (92 entries a lane, 6.2e9 in all) pass 2^32 entries, so every index into them is 64-bit;
+    the force loop reading them tests about 60 candidates a particle, not the 27-cell scan's 357."""
+    d = ics.lattice(406, jitter=0.1)
+    n = len(d["pos"])
+    rng = np.random.default_rng(406)
+    vel = rng.normal(0, 0.3, (n, 3)).astype(np.float32)
+    u = (d["u"] * rng.uniform(0.5, 1.5, n)).astype(np.float32)
+    pos_h = torch.from_numpy(np.concatenate([d["pos"], d["h"][:, None]], 1).astype(np.float32)).cuda()
+    vel_m = torch.from_numpy(np.concatenate([vel, d["m"][:, None]], 1).astype(np.float32)).cuda()
+    ut = torch.from_numpy(u).cuda()
+    ctx = sph.Context((1 << 26) - 1, h_tol=H_TOL)  # the largest n_max the library accepts
+    o = ctx.step(pos_h, vel_m, ut)
+    torch.cuda.synchronize()
+    assert o["status"][0] == 0, o["status"]
+    info = ctx.info()
+    assert info["candidates"][2] < 100 * n  # the kept lists, not a scan of the cells
+    out = {k: o[k].cpu().numpy() for k in ("h", "rho4", "ngb", "vsig_lapu", "accel_dudt")}
+    del o, ctx
+    torch.cuda.empty_cache()
+    h = out["h"]
+    sample = np.unique(np.concatenate([rng.choice(n, 24, replace=False), np.argsort(h)[:4], np.argsort(h)[-4:]]))
+    check_sample(O, d, vel, u, h, out, sample, H_TOL)
