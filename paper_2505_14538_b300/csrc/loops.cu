@@ -117,8 +117,11 @@ __device__ __forceinline__ void dens_load(DensOp::I& I, const DensArgs& a, float
 
 // Eqs. 5-6 at the lane particle's current h over its list (one step of the
 // h iteration). Entries go four at a time: the four position loads are issued
-// before any of them is used, so a warp keeps four loads in flight; the sums
-// are taken in list order, as one at a time would.
+// before any of them is used, so a warp keeps four loads in flight. The four
+// shape values are summed in FP32 and scaled once, and the block goes into
+// the compensated pair as one term: the running sum then carries at most
+// about 4 ulp of n of rounding, far inside h_tol (the final sums at the last
+// h, flush, compensate every term).
 __device__ __forceinline__ void number_walk(const DensOp& op, const DensOp::I& I, const WarpSmem& w, int cnt,
                                             float& ns, float& nc, float& dn, unsigned& npairs) {
   const unsigned lane = lane_id();
@@ -133,6 +136,7 @@ __device__ __forceinline__ void number_walk(const DensOp& op, const DensOp::I& I
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) pj[q] = op.pos[e[q] & kIndexMask];
+    float ws = 0.0f, ds = 0.0f;  // the block's sums of w(q) and r dw/dq
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       // branch-free: W and dW/dr vanish beyond the support (so entries of
@@ -147,13 +151,15 @@ __device__ __forceinline__ void number_walk(const DensOp& op, const DensOp::I& I
       const float r = r2 * invr;
       float wq, dwq;
       kshape(op.kernel, r * I.invH, wq, dwq);
-      const float W = valid ? I.c3 * wq : 0.0f;
-      const float D = valid ? fmaf(r, I.c4 * dwq, 3.0f * W) : 0.0f;
-      if (op.compensated) two_sum_acc(ns, nc, W);
-      else ns += W;
-      dn += D;
+      ws += valid ? wq : 0.0f;
+      ds = fmaf(r, valid ? dwq : 0.0f, ds);
       npairs += (valid && r2 < I.H2hi && j != I.k) ? 1u : 0u;
     }
+    // W = c3 w(q), dn term = r dW/dr + 3 W (Eq. 6 summed as -h dn/dh)
+    const float W = I.c3 * ws;
+    if (op.compensated) two_sum_acc(ns, nc, W);
+    else ns += W;
+    dn += fmaf(I.c4, ds, 3.0f * W);
   }
 }
 
@@ -383,6 +389,7 @@ __device__ __forceinline__ void walk_r2(const DensOp::I& I, const float* r2s, in
     float r2[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) r2[q] = t0 + q < cnt ? r2s[(t0 + q) * 32] : -1.0f;
+    float ws = 0.0f, ds = 0.0f;  // the block's sums, as number_walk
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const bool valid = r2[q] >= 0.0f;
@@ -391,13 +398,14 @@ __device__ __forceinline__ void walk_r2(const DensOp::I& I, const float* r2s, in
       const float r = rr * invr;
       float wq, dwq;
       kshape(K, r * I.invH, wq, dwq);
-      const float W = valid ? I.c3 * wq : 0.0f;
-      const float D = valid ? fmaf(r, I.c4 * dwq, 3.0f * W) : 0.0f;
-      if (compensated) two_sum_acc(ns, nc, W);
-      else ns += W;
-      dn += D;
+      ws += valid ? wq : 0.0f;
+      ds = fmaf(r, valid ? dwq : 0.0f, ds);
       npairs += (valid && rr > 0.0f && rr < I.H2hi) ? 1u : 0u;
     }
+    const float W = I.c3 * ws;
+    if (compensated) two_sum_acc(ns, nc, W);
+    else ns += W;
+    dn += fmaf(I.c4, ds, 3.0f * W);
   }
 }
 
