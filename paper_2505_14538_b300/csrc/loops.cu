@@ -142,7 +142,6 @@ __device__ __forceinline__ void number_walk(const DensOp& op, const DensOp::I& I
       // branch-free: W and dW/dr vanish beyond the support (so entries of
       // the list outside H add exact zeros), and padding is masked
       const bool valid = t0 + q < cnt;
-      const int j = (int)(e[q] & kIndexMask);
       float xj = pj[q].x, yj = pj[q].y, zj = pj[q].z;
       shift_j(e[q] >> kIndexBits, op.L, xj, yj, zj);
       const float dx = I.x - xj, dy = I.y - yj, dz = I.z - zj;
@@ -153,7 +152,7 @@ __device__ __forceinline__ void number_walk(const DensOp& op, const DensOp::I& I
       kshape(op.kernel, r * I.invH, wq, dwq);
       ws += valid ? wq : 0.0f;
       ds = fmaf(r, valid ? dwq : 0.0f, ds);
-      npairs += (valid && r2 < I.H2hi && j != I.k) ? 1u : 0u;
+      npairs += (valid && wq > 0.0f) ? 1u : 0u;  // r < H, the particle itself included
     }
     // W = c3 w(q), dn term = r dW/dr + 3 W (Eq. 6 summed as -h dn/dh)
     const float W = I.c3 * ws;
@@ -278,7 +277,7 @@ __device__ __forceinline__ void dens_item(const DensArgs& a, const DensOp& op, c
       dn = lsum(dn, lm.lsh);
       np = lsum_u(np, lm.lsh);
       if (!done) {
-        if (lm.s == 0) nhiter += np;
+        if (lm.s == 0 && np > 0) nhiter += np - 1;  // the walk counted the particle itself once
         float h1;
         const float h0 = I.h;
         if (newton_step(h0, ns, nc, dn, lo, hi, hcap, cap_flag, a.ph, iter == a.ph.max_iter - 1, h1, flag)) {
