@@ -18,6 +18,14 @@ constexpr float kPi = 3.14159265358979323846f;
 // FP64 from the same float inputs. A periodic image costs one FP32 rounding
 // of a coordinate (at most 2^-24 L), so the band has a relative part (FP32
 // rounding of r^2 and H^2) and a part proportional to H L.
+// r from r^2 >= 0 with the hardware's approximate square root (one
+// instruction, relative error about 2^-23, exact at 0).
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float r;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 __host__ __device__ __forceinline__ float band_of(float H, float Lmax) {
   return H * H * 1.52587890625e-05f + H * Lmax * 9.5367431640625e-07f;  // 2^-16 H^2 + 2^-20 H L
 }

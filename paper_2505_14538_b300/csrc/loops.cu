@@ -145,9 +145,7 @@ __device__ __forceinline__ void number_walk(const DensOp& op, const DensOp::I& I
       float xj = pj[q].x, yj = pj[q].y, zj = pj[q].z;
       shift_j(e[q] >> kIndexBits, op.L, xj, yj, zj);
       const float dx = I.x - xj, dy = I.y - yj, dz = I.z - zj;
-      const float r2 = r2_of(dx, dy, dz);
-      const float invr = r2 > 0.0f ? rsqrtf(r2) : 0.0f;
-      const float r = r2 * invr;
+      const float r = sqrt_approx(r2_of(dx, dy, dz));
       float wq, dwq;
       kshape(op.kernel, r * I.invH, wq, dwq);
       ws += valid ? wq : 0.0f;
@@ -393,8 +391,7 @@ __device__ __forceinline__ void walk_r2(const DensOp::I& I, const float* r2s, in
     for (int q = 0; q < 4; ++q) {
       const bool valid = r2[q] >= 0.0f;
       const float rr = fmaxf(r2[q], 0.0f);
-      const float invr = rr > 0.0f ? rsqrtf(rr) : 0.0f;
-      const float r = rr * invr;
+      const float r = sqrt_approx(rr);
       float wq, dwq;
       kshape(K, r * I.invH, wq, dwq);
       ws += valid ? wq : 0.0f;
