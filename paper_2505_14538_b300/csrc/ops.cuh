@@ -322,6 +322,17 @@ struct GradForceOp : ForceOp {
     interact(i, j, code, r);
   }
   __device__ __forceinline__ void interact(I& i, int j, unsigned code, const Rec& rec) const {
+    float t[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    interact_acc(i, j, code, rec, t);
+    commit(i, t);
+  }
+  // The pair term with its momentum and energy terms added to t (a_x, a_y,
+  // a_z, du/dt) instead of the compensated sums: flush2 adds two entries'
+  // terms in FP32 and commits them as one term (blocked compensation, as the
+  // lane-per-particle force loop: the error of a sum stays near 2^-24 of the
+  // sum of its terms' magnitudes). 1/r is folded into the scalar factors, and
+  // the gradient terms are masked by r < H_i instead of taken in a branch.
+  __device__ __forceinline__ void interact_acc(I& i, int j, unsigned code, const Rec& rec, float (&t)[4]) const {
     const float4 pj = rec.pj;
     float xj = pj.x, yj = pj.y, zj = pj.z;
     shift_j(code, L, xj, yj, zj);
@@ -348,50 +359,56 @@ struct GradForceOp : ForceOp {
     const float4 bj = rec.bj;  // (B, alpha_v, alpha_c P, u)
     const float invr = rsqrtf(r2);
     const float r = r2 * invr;
-    const float ex = dx * invr, ey = dy * invr, ez = dz * invr;
     const float dWi = i.c4 * dkshape(kernel, r * i.invH);
     const float dvx = i.vx - vj.x, dvy = i.vy - vj.y, dvz = i.vz - vj.z;
-    if (in_i) {  // gradient loop (as GradOp)
-      const float vrg = fmaf(dvz, dz, fmaf(dvy, dy, dvx * dx)) * invr;
-      i.vsig = fmaxf(i.vsig, fmaf(-beta, fminf(vrg, 0.0f), i.c + aj.w));
-      i.lap = fmaf(__fdividef(vj.w, aj.z) * (i.u - bj.w), dWi * invr, i.lap);
-      i.gcount += 1u;
-    }
+    const float vr = fmaf(dvz, dz, fmaf(dvy, dy, dvx * dx)) * invr;
+    const float mu = fminf(vr, 0.0f);
+    const float vsig = fmaf(-beta, mu, i.c + aj.w);
+    // gradient loop (as GradOp), for r < H_i
+    i.vsig = in_i ? fmaxf(i.vsig, vsig) : i.vsig;
+    const float lt = __fdividef(vj.w, aj.z) * (i.u - bj.w) * (dWi * invr);
+    i.lap += in_i ? lt : 0.0f;
+    i.gcount += in_i ? 1u : 0u;
     const float invHj = __fdividef(1.0f, Hj);
     const float ih2 = invHj * invHj;
     const float dWj = (knorm * ih2 * ih2) * dkshape(kernel, r * invHj);
-    const float vr = fmaf(dvz, ez, fmaf(dvy, ey, dvx * ex));
     const float mj = vj.w;
     const float fsum = fmaf(i.f, dWi, aj.y * dWj);
+    // pressure (Eq. 17) and its work (Eq. 18)
     const float ps = mj * fmaf(i.A, dWi, aj.x * dWj);
-    float du = mj * i.A * dWi * vr;
-    const float mu = fminf(vr, 0.0f);
-    const float vsig = fmaf(-beta, mu, i.c + aj.w);
+    // artificial viscosity (Eqs. 7, 9-11, 16) and its heating
     const float alpha = 0.25f * (i.av + bj.y) * (i.B + bj.x);
     const float irs = __fdividef(1.0f, i.rho + aj.z);
     const float nu = -alpha * mu * vsig * irs;
     const float vs = 0.5f * mj * nu * fsum;
-    du = fmaf(0.5f * vs, vr, du);
+    float du = vr * fmaf(mj * i.A, dWi, 0.5f * vs);
+    // artificial conduction (Eqs. 19, 20, 22)
     const float Pj = gm1 * aj.z * bj.w;
     const float Ps = i.P + Pj;
     const float ac = Ps > 0.0f ? __fdividef(i.acP + bj.z, Ps) : 0.0f;
     const float dP = 2.0f * fabsf(i.P - Pj) * irs;
     const float vc = fabsf(vr) + (dP > 0.0f ? dP * rsqrtf(dP) : 0.0f);
     du = fmaf(ac * vc * mj * (i.u - bj.w), fsum * irs, du);
-    const float as = ps + vs;
-    if (compensated) {
-      two_sum_acc(i.axs, i.axc, -as * ex);
-      two_sum_acc(i.ays, i.ayc, -as * ey);
-      two_sum_acc(i.azs, i.azc, -as * ez);
-      two_sum_acc(i.dus, i.duc, du);
-    } else {
-      i.axs = fmaf(-as, ex, i.axs);
-      i.ays = fmaf(-as, ey, i.ays);
-      i.azs = fmaf(-as, ez, i.azs);
-      i.dus += du;
-    }
+    const float asr = (ps + vs) * invr;
+    t[0] = fmaf(-asr, dx, t[0]);
+    t[1] = fmaf(-asr, dy, t[1]);
+    t[2] = fmaf(-asr, dz, t[2]);
+    t[3] += du;
     i.dh = fmaf(mj * dWi, vr, i.dh);
     i.count += 1u;
+  }
+  __device__ __forceinline__ void commit(I& i, const float (&t)[4]) const {
+    if (compensated) {
+      two_sum_acc(i.axs, i.axc, t[0]);
+      two_sum_acc(i.ays, i.ayc, t[1]);
+      two_sum_acc(i.azs, i.azc, t[2]);
+      two_sum_acc(i.dus, i.duc, t[3]);
+    } else {
+      i.axs += t[0];
+      i.ays += t[1];
+      i.azs += t[2];
+      i.dus += t[3];
+    }
   }
 };
 
