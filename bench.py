@@ -398,7 +398,15 @@ def run_ours(args, rank, world, pg):
                                     "frac_with_neighbour_tests": flops_tests[j] / (kernel_ms[j] * 1e-3) / 1e12
                                     / peak_max,
                                     "hw_fma_pipe_frac": (measured_counters(names[j]).get("fma_pipe_active_pct", 0) / 100
-                                                         or None)}
+                                                         or None),
+                                    # HBM: the ncu capture's DRAM bytes over this run's time, against the
+                                    # measured copy bandwidth (the loops are not memory-bound)
+                                    "dram_gbs": (measured_traffic(names[j]) / (kernel_ms[j] * 1e-3) / 1e9
+                                                 if measured_traffic(names[j]) else None),
+                                    "dram_frac_of_measured_hbm": (measured_traffic(names[j]) / (kernel_ms[j] * 1e-3)
+                                                                  / 1e9 / peaks["hbm_gbs"]
+                                                                  if measured_traffic(names[j])
+                                                                  and peaks.get("hbm_gbs") else None)}
                          for j in range(2)},
             "frac_note": "frac counts the algorithmic flops of the interacting pairs only (oracle op counts); "
                          "frac_with_neighbour_tests adds every candidate's squared distance (8 flops); "
