@@ -602,8 +602,8 @@ def run_clustered(dev, peak, fpi, steps=5):
     One active step = build_cells, density (h iteration for the active
     particles), gradient and force (one fused call, as in the benchmark step),
     timed on the uniform grid and with adaptive leaves after an all-active step
-    has set h, rho and curl/div. The adaptive run is also autotuned (whole
-    step) and then captured in a CUDA graph and replayed: the configuration's
+    has set h, rho and curl/div. The adaptive run is also autotuned (leaf_max,
+    then the tiles of the whole step) and then captured in a CUDA graph and replayed: the configuration's
     one persistent graph-captured launch per loop with autotuned tiles.
     """
     import numpy as np
@@ -652,6 +652,7 @@ def run_clustered(dev, peak, fpi, steps=5):
         direct(1)  # warm-up
         r = {}
         if flags:
+            r["leaf_tuning"] = ctx.tune_leaf_max(p2, vel_m, u, act, rho4, cd)
             r["autotune"] = {"default": ctx.tuning(),
                              "default_step_ms_median": statistics.median(sum(x) for x in direct(3))}
             r["autotune"]["picked"] = ctx.autotune(4)
@@ -704,7 +705,7 @@ def run_zeldovich(dev, peak, fpi, steps=5, cpu=True):
     density contrast 100), v proportional to the displacement, u = 1.
 
     A whole step (build, density with the h iteration, gradient + force) with
-    adaptive leaves, FP32 with compensated sums and FP64 reductions, captured
+    adaptive leaves (leaf_max picked by timing the step), FP32 with compensated sums and FP64 reductions, captured
     in a CUDA graph and replayed; per-loop times from direct calls. The steps
     start from the h a first untimed step solved from the lattice h (leaves
     are rebuilt around h as it grows), as the steps of a simulation start from
@@ -732,10 +733,11 @@ def run_zeldovich(dev, peak, fpi, steps=5, cpu=True):
     pos_h = pos_h.clone()
     pos_h[:, 3] = first["h"]
     del first
+    leaf_tuning = ctx.tune_leaf_max(pos_h, vel_m, u, steps=2)  # leaf size picked by timing the step
     res = {"workload": f"zeldovich256: {n} particles, 256^3 lattice displaced by a Gaussian random field with "
                        "P(k) ~ k^-2 scaled to a density contrast of 100, v = displacement, u = 1, periodic unit box",
            "particles": n, "steps": steps, "h_tol": BENCH_H_TOL, "ic_seconds": t_ic,
-           "start": "h of a first (untimed) step from the lattice h"}
+           "start": "h of a first (untimed) step from the lattice h", "leaf_tuning": leaf_tuning}
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
     o = {}
     i0 = ctx.info()
@@ -770,7 +772,8 @@ def run_zeldovich(dev, peak, fpi, steps=5, cpu=True):
                 "direct_ms": {"build": loop[0], "density": loop[1], "gradient_force": loop[2]},
                 "roofline": _loop_roofline(fpi, peak, i0, i1, steps, loop[1], loop[2]),
                 "status": list(ctx.sync_status()), "h_max_over_min": float(h.max() / h.min()),
-                "leaves": g1["n_leaves"], "nc": g1["nc"], "density_passes": g1["density_passes"],
+                "leaves": g1["n_leaves"], "leaf_max": int(ctx.params.leaf_max), "nc": g1["nc"],
+                "density_passes": g1["density_passes"],
                 "momentum_of_sum_abs": float(np.abs(red[:3]).max() / red[4]),
                 "launch": "whole step captured in one CUDA graph, replayed; adaptive leaves"})
     del graph, ctx

@@ -83,7 +83,8 @@ typedef struct {
   float cell_margin;   /* automatic cell width = (1 + cell_margin) * kernel_gamma * max h */
   int flags;           /* SWIFT_GPU_* flags above */
   int leaf_max;        /* ADAPTIVE: a node with more particles is split into its 8 octants (8..1024) */
-  float leaf_margin;   /* ADAPTIVE: the h cap of a leaf is (1 + leaf_margin) * its largest h at the build */
+  float leaf_margin;   /* ADAPTIVE: the h cap of a leaf is (1 + leaf_margin) * its largest h at the build;
+                          >= 0.01, since a rebuild after a capped iteration lets h grow by this factor */
   int kernel;          /* SWIFT_GPU_KERNEL_*: kernel shape (every loop and the adjoint) */
 } swift_gpu_params;
 

@@ -30,7 +30,7 @@ int phys_from(const swift_gpu_params* p, Phys* ph) {
     return SWIFT_GPU_ERR_ARG;
   if (p->kernel < SWIFT_GPU_KERNEL_CUBIC || p->kernel > SWIFT_GPU_KERNEL_WENDLAND_C4) return SWIFT_GPU_ERR_ARG;
   if ((p->flags & SWIFT_GPU_ADAPTIVE) &&
-      ((p->flags & SWIFT_GPU_PLAIN) || p->leaf_max < 8 || p->leaf_max > 1024 || !(p->leaf_margin >= 0.0f) ||
+      ((p->flags & SWIFT_GPU_PLAIN) || p->leaf_max < 8 || p->leaf_max > 1024 || !(p->leaf_margin >= 0.01f) ||
        !isfinite(p->leaf_margin)))
     return SWIFT_GPU_ERR_ARG;
   for (int a = 0; a < 3; ++a) ph->L[a] = p->box[a];

@@ -260,6 +260,41 @@ class Context:
         _check(self.lib.swift_gpu_autotune(self.handle, ctypes.c_int(loop), _stream(stream)), "swift_gpu_autotune")
         return self.tuning()
 
+    def tune_leaf_max(self, pos_h, vel_m, u, active=None, rho4=None, curl_div=None,
+                      candidates=(16, 24, 32, 48, 64), steps=3, stream=None) -> dict:
+        """Adaptive contexts: time one step (build_cells, density, fused gradient + force) with each
+        leaf_max of ``candidates`` (the median of ``steps`` after one untimed) and keep the fastest.
+
+        pos_h should hold settled h (an earlier step's output), so that no leaf cap is reached; a
+        candidate whose step ends with a status other than OK or ERR_H_NOT_CONVERGED is skipped.
+        The outputs left in the context are those of the last candidate run: run the step again
+        after tuning. Returns {"leaf_max": the choice, "step_ms": {candidate: median ms}}.
+        """
+        if not self.params.flags & _lib.FLAG_ADAPTIVE:
+            raise ValueError("tune_leaf_max needs a context with adaptive leaves")
+        s = stream if stream is not None else torch.cuda.current_stream()
+        old = int(self.params.leaf_max)
+        times = {}
+        for lm in candidates:
+            self.set_params(leaf_max=int(lm))
+            ms = []
+            for k in range(steps + 1):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+                self.build_cells(pos_h, stream=s)
+                self.density(pos_h, vel_m, active, rho4=rho4, curl_div=curl_div, stream=s)
+                self.gradient_force(u, stream=s)
+                e1.record(s)
+                e1.synchronize()
+                if k:
+                    ms.append(e0.elapsed_time(e1))
+            code, _ = self.sync_status()
+            if code in (_lib.OK, _lib.ERR_H_NOT_CONVERGED):
+                times[int(lm)] = sorted(ms)[len(ms) // 2]
+        best = min(times, key=times.get) if times else old
+        self.set_params(leaf_max=best)
+        return {"leaf_max": best, "step_ms": times}
+
     # ------------------------------------------------------- whole step
     def density_checked(self, pos_h, vel_m, active=None, rho4=None, curl_div=None, min_cell_width: float = 0.0,
                         check: bool = True, stream=None, **outs):
@@ -269,8 +304,9 @@ class Context:
         density call is repeated: on the uniform grid with cells twice as wide
         (up to a third of the box) from the same starting h; with adaptive
         leaves from the capped h, the leaves rebuilt around it (their caps grow
-        by 1 + leaf_margin), and with wider cells only when h reached the cell
-        cap. ``outs`` are optional output tensors of density() (h_out,
+        by 1 + leaf_margin; from the second rebuild on the margin doubles each
+        time, up to 4, and the caller's margin is set back afterwards), and
+        with wider cells only when h reached the cell cap. ``outs`` are optional output tensors of density() (h_out,
         ngb_count). Raises SwiftGPUError on any status other than OK and
         ERR_H_NOT_CONVERGED.
         """
@@ -282,23 +318,34 @@ class Context:
         box_third = min(float(b) for b in self.params.box) / 3.0
         adaptive = bool(self.params.flags & _lib.FLAG_ADAPTIVE)
         pos_cur = pos_h
-        for _ in range(32):
-            if code != _lib.ERR_H_EXCEEDS_CELL:
-                break
-            info = self.info()
-            width = max(info["cell_width"])
-            if not adaptive or float(d["h"].max()) >= 0.999 * info["h_cap"]:
-                if width >= 0.999 * box_third:
+        margin = float(self.params.leaf_margin)
+        grown = 0
+        try:
+            for _ in range(32):
+                if code != _lib.ERR_H_EXCEEDS_CELL:
                     break
-                min_w = max(min_cell_width, min(2.0 * width, box_third))
-            else:
-                min_w = min_cell_width  # only leaf caps were reached
-            if adaptive:
-                pos_cur = pos_cur.clone()
-                pos_cur[:, 3] = d["h"]
-            self.build_cells(pos_cur, min_w, stream)
-            d = self.density(pos_cur, vel_m, active, rho4=rho4, curl_div=curl_div, stream=stream, **outs)
-            code, detail = self.sync_status()
+                info = self.info()
+                width = max(info["cell_width"])
+                if not adaptive or float(d["h"].max()) >= 0.999 * info["h_cap"]:
+                    if width >= 0.999 * box_third:
+                        break
+                    min_w = max(min_cell_width, min(2.0 * width, box_third))
+                else:
+                    min_w = min_cell_width  # only leaf caps were reached
+                    if grown:
+                        # a capped h grows by 1 + leaf_margin a rebuild: from the second
+                        # rebuild on the margin doubles, so that a far-off h is reached soon
+                        self.set_params(leaf_margin=max(margin, min(margin * 2.0 ** grown, 4.0)))
+                    grown += 1
+                if adaptive:
+                    pos_cur = pos_cur.clone()
+                    pos_cur[:, 3] = d["h"]
+                self.build_cells(pos_cur, min_w, stream)
+                d = self.density(pos_cur, vel_m, active, rho4=rho4, curl_div=curl_div, stream=stream, **outs)
+                code, detail = self.sync_status()
+        finally:
+            if float(self.params.leaf_margin) != margin:
+                self.set_params(leaf_margin=margin)
         if code not in (_lib.OK, _lib.ERR_H_NOT_CONVERGED):
             raise SwiftGPUError(code, "density", detail)
         d["status"] = (code, detail)

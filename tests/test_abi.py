@@ -48,6 +48,13 @@ def test_default_params_and_argument_checks_without_gpu(lib):
     bad = _lib.default_params()
     bad.max_iter = 0
     assert L.swift_gpu_create(ctypes.byref(h), ctypes.byref(bad), ctypes.c_int64(10)) == _lib.ERR_ARG
+    bad = _lib.default_params()
+    bad.flags = _lib.FLAG_ADAPTIVE
+    bad.leaf_margin = 0.0  # a leaf cap equal to its largest h leaves no room to grow
+    assert L.swift_gpu_create(ctypes.byref(h), ctypes.byref(bad), ctypes.c_int64(10)) == _lib.ERR_ARG
+    bad.leaf_margin = 0.01
+    bad.leaf_max = 4
+    assert L.swift_gpu_create(ctypes.byref(h), ctypes.byref(bad), ctypes.c_int64(10)) == _lib.ERR_ARG
     assert L.swift_gpu_destroy(None) == _lib.OK
     assert L.swift_gpu_density(None, None, None, None, None, None, None, None, None) == _lib.ERR_ARG
 

@@ -93,6 +93,37 @@ def test_adaptive_clustered_matches_oracle(sph, O):
     check_against_oracle(O, d, vel, u, g, g["ctx"])
 
 
+def test_adaptive_far_start_with_a_small_leaf_margin(sph, O):
+    """Starting h at half the initial guess with leaf_margin 0.01: 32 rebuilds at a fixed margin
+    reach only 1.01^32 = 1.37 times the start, so step() doubles the margin on each rebuild after
+    the first and puts the caller's margin back afterwards."""
+    d, vel, u = clustered_state(seed=3)
+    d = dict(d, h=(0.5 * d["h"]).astype(np.float32))
+    g = run_step(sph, d, vel, u, h_tol=1e-6, flags=ADAPTIVE, leaf_margin=0.01)
+    assert g["status"][0] == 0, g["status"]
+    assert abs(float(g["ctx"].params.leaf_margin) - 0.01) < 1e-9
+    check_against_oracle(O, d, vel, u, g, g["ctx"])
+
+
+def test_tune_leaf_max_keeps_a_timed_candidate(sph):
+    """tune_leaf_max times each candidate from settled h, keeps the fastest, and the step after it
+    solves the same h."""
+    d, vel, u = clustered_state(seed=2)
+    g = run_step(sph, d, vel, u, h_tol=1e-6, flags=ADAPTIVE)
+    ctx = g["ctx"]
+    pos_h, vel_m, ut = dev_arrays(d, vel, u)
+    pos_h[:, 3] = torch.from_numpy(g["h"]).cuda()
+    t = ctx.tune_leaf_max(pos_h, vel_m, ut, candidates=(16, 32, 64), steps=1)
+    assert set(t["step_ms"]) == {16, 32, 64} and t["leaf_max"] == min(t["step_ms"], key=t["step_ms"].get)
+    assert int(ctx.params.leaf_max) == t["leaf_max"]
+    out = ctx.step(pos_h, vel_m, ut)
+    torch.cuda.synchronize()
+    assert ctx.sync_status()[0] == 0
+    assert np.max(np.abs(out["h"].cpu().numpy() / g["h"] - 1)) < 1e-5
+    with pytest.raises(ValueError):
+        sph.Context(8).tune_leaf_max(pos_h[:8], vel_m[:8], ut[:8])
+
+
 def test_adaptive_leaf_structure(sph):
     d, vel, u = clustered_state(seed=1)
     leaf_max = 16
