@@ -11,10 +11,10 @@
 //    as * (dx/r));
 //  - the gradient terms are masked by the exact r < H_i decision instead of
 //    taken in a branch;
-//  - compensation is blocked: the loop adds the terms of two entries in FP32
+//  - compensation is blocked: the loop adds the terms of four entries in FP32
 //    and carries that sum into the running TwoSum (Knuth) pair, which bounds
-//    the error of a sum by about 2^-24 times the sum of the terms' magnitudes,
-//    three orders below the 1e-4-of-the-force-scale tolerance.
+//    the error of a sum by a few times 2^-24 times the sum of the terms'
+//    magnitudes, far below the 1e-4-of-the-force-scale tolerance.
 //
 // Same pair set and the same exact neighbour decisions as ForceOp and
 // GradForceOp (ops.cuh): FP32 where the guard band allows, FP64 inside it.

@@ -1020,11 +1020,15 @@ __global__ void __launch_bounds__(kLoopThreads, 5) k_grad_force(LoopArgs a) { fo
 // uniform grid) is left to the cell-item kernel launched after this one,
 // which scans the cells of those particles only (LoopArgs::only_unlisted). kMode: 0 gradient, 1 force, 2 gradient + force
 // (one pass over the pairs). The force modes take the pair term of
-// force_lpp.cuh, two entries at a time: both entries' records are loaded
-// first, the next two entries are read meanwhile, and the two entries' terms
-// are summed in FP32 before the compensated sums take them.
+// force_lpp.cuh, kLppBatch entries at a time: the batch's records are loaded
+// first, the next batch's list entries are read meanwhile, and the batch's
+// terms are summed in FP32 before the compensated sums take them. Four
+// entries a batch at 3 blocks a SM (168 registers) keep 16 record loads in
+// flight a lane; on sedov64 that beat two entries at 4 blocks a SM (0.2043 ->
+// 0.2003 ms) and three or five entries, or eight at 2 blocks a SM.
+constexpr int kLppBatch = 4;
 template <int kMode, int K>
-__global__ void __launch_bounds__(kLoopThreads, 4) k_loop_lpp(const __grid_constant__ LoopArgs a) {
+__global__ void __launch_bounds__(kLoopThreads, 3) k_loop_lpp(const __grid_constant__ LoopArgs a) {
   constexpr int W = lpp_width<K>();
   constexpr bool kGrad = kMode != 1;
   __shared__ double red[kWarpsPerBlock][8];
@@ -1110,18 +1114,22 @@ __global__ void __launch_bounds__(kLoopThreads, 4) k_loop_lpp(const __grid_const
       I.lap = 0.0f;
       I.gcount = I.count = 0;
       const int m = __reduce_max_sync(kFull, cnt);
-      unsigned e0 = 0 < cnt ? lst[0] : (unsigned)k;
-      unsigned e1 = 1 < cnt ? lst[32] : (unsigned)k;
-      for (int u = 0; u < m; u += 2) {
-        LeanRec r0, r1;
-        lean_load(a.gc, a.vel, a.ga, a.gb, (int)(e0 & kIndexMask), r0);
-        lean_load(a.gc, a.vel, a.ga, a.gb, (int)(e1 & kIndexMask), r1);
-        const unsigned n0 = u + 2 < cnt ? lst[(u + 2) * 32] : (unsigned)k;
-        const unsigned n1 = u + 3 < cnt ? lst[(u + 3) * 32] : (unsigned)k;
+      constexpr int B = kLppBatch;
+      unsigned e[B];  // the batch's list entries (the particle itself past the list's end)
+#pragma unroll
+      for (int q = 0; q < B; ++q) e[q] = q < cnt ? lst[q * 32] : (unsigned)k;
+      for (int u = 0; u < m; u += B) {
+        LeanRec r[B];
+#pragma unroll
+        for (int q = 0; q < B; ++q) lean_load(a.gc, a.vel, a.ga, a.gb, (int)(e[q] & kIndexMask), r[q]);
+        unsigned nx[B];
+#pragma unroll
+        for (int q = 0; q < B; ++q) nx[q] = u + B + q < cnt ? lst[(u + B + q) * 32] : (unsigned)k;
         float tax = 0.0f, tay = 0.0f, taz = 0.0f, tdu = 0.0f;
-        if (u < cnt) lean_pair<K, kGrad>(I, r0, (int)(e0 & kIndexMask), e0 >> kIndexBits, kc, tax, tay, taz, tdu);
-        if (u + 1 < cnt)
-          lean_pair<K, kGrad>(I, r1, (int)(e1 & kIndexMask), e1 >> kIndexBits, kc, tax, tay, taz, tdu);
+#pragma unroll
+        for (int q = 0; q < B; ++q)
+          if (u + q < cnt)
+            lean_pair<K, kGrad>(I, r[q], (int)(e[q] & kIndexMask), e[q] >> kIndexBits, kc, tax, tay, taz, tdu);
         if (a.ph.compensated) {
           two_sum_acc(I.axs, I.axc, tax);
           two_sum_acc(I.ays, I.ayc, tay);
@@ -1133,8 +1141,8 @@ __global__ void __launch_bounds__(kLoopThreads, 4) k_loop_lpp(const __grid_const
           I.azs += taz;
           I.dus += tdu;
         }
-        e0 = n0;
-        e1 = n1;
+#pragma unroll
+        for (int q = 0; q < B; ++q) e[q] = nx[q];
       }
       ncand += (unsigned)cnt;
       if (live) {
