@@ -1010,7 +1010,10 @@ __global__ void __launch_bounds__(kLoopThreads, 4) k_force(LoopArgs a) { force_k
 
 // Gradient (Eqs. 10-11, Laplacian of u) and force in one pass over the pairs.
 template <int K>
-__global__ void __launch_bounds__(kLoopThreads, 5) k_grad_force(LoopArgs a) { force_kernel_body<true, K>(a); }
+// 4 blocks a SM (128 registers): at 5 (96 registers) the fused pair term spilled
+// 296 bytes a thread, and the adaptive plummer2M step's gradient + force took
+// 2.27 ms against 1.72 ms (zeldovich256: 40.9 against 35.2 ms).
+__global__ void __launch_bounds__(kLoopThreads, 4) k_grad_force(LoopArgs a) { force_kernel_body<true, K>(a); }
 
 // ================================== lane-per-particle gradient / force loops
 // One lane per particle over the kept list of its group (written by the

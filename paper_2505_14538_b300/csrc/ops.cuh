@@ -327,11 +327,9 @@ struct GradForceOp : ForceOp {
     commit(i, t);
   }
   // The pair term with its momentum and energy terms added to t (a_x, a_y,
-  // a_z, du/dt) instead of the compensated sums: flush2 adds two entries'
-  // terms in FP32 and commits them as one term (blocked compensation, as the
-  // lane-per-particle force loop: the error of a sum stays near 2^-24 of the
-  // sum of its terms' magnitudes). 1/r is folded into the scalar factors, and
-  // the gradient terms are masked by r < H_i instead of taken in a branch.
+  // a_z, du/dt) instead of the compensated sums, which commit() then takes.
+  // 1/r is folded into the scalar factors, and the gradient terms are masked
+  // by r < H_i instead of taken in a branch.
   __device__ __forceinline__ void interact_acc(I& i, int j, unsigned code, const Rec& rec, float (&t)[4]) const {
     const float4 pj = rec.pj;
     float xj = pj.x, yj = pj.y, zj = pj.z;
