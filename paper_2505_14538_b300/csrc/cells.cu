@@ -56,6 +56,7 @@ __device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned* smem, 
 // over key bits the cells do not use).
 __global__ void k_scan_tiles(const unsigned* __restrict__ in, int m, unsigned* __restrict__ tile_sums,
                              const int* __restrict__ gate) {
+  pdl_wait();
   __shared__ unsigned sm[32];
   if (gate && *gate == 0) return;
   const int base = blockIdx.x * kScanTile;
@@ -71,6 +72,7 @@ __global__ void k_scan_tiles(const unsigned* __restrict__ in, int m, unsigned* _
 }
 
 __global__ void k_scan_top(unsigned* __restrict__ tile_sums, int ntiles, const int* __restrict__ gate) {
+  pdl_wait();
   __shared__ unsigned sm[32];
   if (gate && *gate == 0) return;
   unsigned carry = 0;
@@ -98,6 +100,7 @@ __global__ void k_scan_top(unsigned* __restrict__ tile_sums, int ntiles, const i
 
 __global__ void k_scan_down(const unsigned* __restrict__ in, int m, const unsigned* __restrict__ tile_offs,
                             unsigned* __restrict__ out, const int* __restrict__ gate) {
+  pdl_wait();
   __shared__ unsigned sm[32];
   if (gate && *gate == 0) return;
   const int base = blockIdx.x * kScanTile;
@@ -125,9 +128,9 @@ void exclusive_scan(Ctx* c, const unsigned* in, unsigned* out, int m, unsigned* 
                     const int* gate) {
   if (m <= 0) return;
   int nt = scan_tiles_needed(m);
-  k_scan_tiles<<<nt, kScanThreads, 0, s>>>(in, m, tile_tmp, gate);
-  k_scan_top<<<1, kScanThreads, 0, s>>>(tile_tmp, nt, gate);
-  k_scan_down<<<nt, kScanThreads, 0, s>>>(in, m, tile_tmp, out, gate);
+  launch_pdl(k_scan_tiles, nt, kScanThreads, 0, s, in, m, tile_tmp, gate);
+  launch_pdl(k_scan_top, 1, kScanThreads, 0, s, tile_tmp, nt, gate);
+  launch_pdl(k_scan_down, nt, kScanThreads, 0, s, in, m, tile_tmp, out, gate);
   c->launches += 3;
 }
 
@@ -179,6 +182,7 @@ __device__ void grid_setup(float hmax, Grid* g, const Phys& ph, float margin, fl
 // (counted in hm[1]) sets up the grid from it. hm starts zeroed.
 __global__ void k_scan_h(const float4* __restrict__ pos_h, int n, unsigned* hm_words, Grid* g, Phys ph, float margin,
                          float min_width, int nc_cap, int host_passes, Status* st) {
+  pdl_wait();
   __shared__ bool s_last;
   float hm = 0.0f;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -237,6 +241,7 @@ __global__ void __launch_bounds__(kRadixThreads) k_cell_ids(const float4* __rest
                                                             unsigned* __restrict__ cell_out,
                                                             unsigned* __restrict__ morton_out,
                                                             unsigned* __restrict__ hist) {
+  pdl_wait();
   __shared__ unsigned hcount[256];
   // uniform grid: buffer g->sort_start; adaptive leaves: buffer 0 (their passes are all live)
   const int b = cell_out ? 0 : g->sort_start;
@@ -334,6 +339,7 @@ __global__ void __launch_bounds__(kRadixThreads) k_cell_ids(const float4* __rest
 // Morton-ordered particles become the keys of the cell-id passes, in buffer
 // g->sort_start (with their values) like the uniform grid's keys.
 __global__ void k_gather_keys(KeyBufs kb, const unsigned* __restrict__ cell_of, int n, const Grid* __restrict__ g) {
+  pdl_wait();
   const int b = g->sort_start;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     const unsigned v = kb.v[0][k];
@@ -355,6 +361,7 @@ __device__ __forceinline__ int pass_src(const Grid* g, int bits, int pass, int h
 
 __global__ void k_radix_count(KeyBufs kb, int host_src, int pass, int n, int shift, const Grid* __restrict__ g,
                               int bits, unsigned* __restrict__ hist) {
+  pdl_wait();
   __shared__ unsigned h[256];
   const bool live = shift < (bits >= 0 ? bits : g->key_bits);
   if (!live) return;  // its scan and scatter are skipped too
@@ -372,6 +379,7 @@ __global__ void k_radix_count(KeyBufs kb, int host_src, int pass, int n, int shi
 
 __global__ void k_radix_scatter(KeyBufs kb, int host_src, int pass, int n, int shift, const Grid* __restrict__ g,
                                 int bits, const unsigned* __restrict__ offs) {
+  pdl_wait();
   __shared__ unsigned run[256];
   __shared__ unsigned wcnt[kRadixThreads / 32][256];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -425,6 +433,7 @@ __global__ void k_radix_scatter(KeyBufs kb, int host_src, int pass, int n, int s
 
 __global__ void k_cell_start(const unsigned* __restrict__ skeys, int n, const Grid* __restrict__ g,
                              int* __restrict__ cell_start) {
+  pdl_wait();
   const int nct = g->ncells;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= n; k += gridDim.x * blockDim.x) {
     int lo = (k == 0) ? 0 : (int)skeys[k - 1] + 1;
@@ -442,9 +451,8 @@ int build_cells_impl(Ctx* c, const float4* pos_h, int n, float min_width, cudaSt
   const int host_passes = (c->max_key_bits + 7) / 8;
   if (n > 0) {
     cudaMemsetAsync(c->d_hmax_bits, 0, sizeof(unsigned) * kHmaxWords, s);
-    k_scan_h<<<min((n + 255) / 256, sm * 8), 256, 0, s>>>(pos_h, n, c->d_hmax_bits, c->d_grid, c->phys,
-                                                         c->params.cell_margin, min_width, nc_cap, host_passes,
-                                                         c->d_status);
+    launch_pdl(k_scan_h, min((n + 255) / 256, sm * 8), 256, 0, s, pos_h, n, c->d_hmax_bits, c->d_grid, c->phys,
+               c->params.cell_margin, min_width, nc_cap, host_passes, c->d_status);
   } else {
     k_grid_setup<<<1, 1, 0, s>>>(c->d_grid, c->phys, c->params.cell_margin, min_width, nc_cap, host_passes,
                                  c->d_status);
@@ -455,20 +463,20 @@ int build_cells_impl(Ctx* c, const float4* pos_h, int n, float min_width, cudaSt
     const KeyBufs kb{{c->d_keys[0], c->d_keys[1]}, {c->d_vals[0], c->d_vals[1]}};
     const int nb = (n + kRadixTile - 1) / kRadixTile;
     // the keys, and the counts of the first pass (its digit 0 is always live)
-    k_cell_ids<<<nb, kRadixThreads, 0, s>>>(pos_h, n, c->d_grid, kb, adaptive ? c->d_aux[0] : nullptr,
-                                            adaptive ? c->d_aux[1] : nullptr, c->d_hist);
+    launch_pdl(k_cell_ids, nb, kRadixThreads, 0, s, pos_h, n, c->d_grid, kb, adaptive ? c->d_aux[0] : nullptr,
+               adaptive ? c->d_aux[1] : nullptr, c->d_hist);
     c->launches++;
     int src = 0;  // host's view of the buffer a pass reads (as if every pass ran)
     bool counted = true;
     auto pass = [&](int p, int shift, int bits) {
       if (!counted) {
-        k_radix_count<<<nb, kRadixThreads, 0, s>>>(kb, src, p, n, shift, c->d_grid, bits, c->d_hist);
+        launch_pdl(k_radix_count, nb, kRadixThreads, 0, s, kb, src, p, n, shift, c->d_grid, bits, c->d_hist);
         c->launches++;
       }
       counted = false;
       const int* gate = bits >= 0 ? nullptr : &c->d_grid->pass_live[shift / 8];
       exclusive_scan(c, c->d_hist, c->d_hist, 256 * nb, c->d_scan_tmp, s, gate);
-      k_radix_scatter<<<nb, kRadixThreads, 0, s>>>(kb, src, p, n, shift, c->d_grid, bits, c->d_hist);
+      launch_pdl(k_radix_scatter, nb, kRadixThreads, 0, s, kb, src, p, n, shift, c->d_grid, bits, c->d_hist);
       c->launches++;
       src = 1 - src;
     };
@@ -476,7 +484,7 @@ int build_cells_impl(Ctx* c, const float4* pos_h, int n, float min_width, cudaSt
       // least significant key first: the Morton code inside the cell (four passes, ending in
       // buffer 0), then the cell id
       for (int shift = 0, p = 0; shift < 30; shift += 8, ++p) pass(p, shift, 30);
-      k_gather_keys<<<gb, 256, 0, s>>>(kb, c->d_aux[0], n, c->d_grid);
+      launch_pdl(k_gather_keys, gb, 256, 0, s, kb, c->d_aux[0], n, c->d_grid);
       c->launches++;
     }
     for (int shift = 0, p = 0; shift < c->max_key_bits; shift += 8, ++p) pass(p, shift, -1);
@@ -485,7 +493,7 @@ int build_cells_impl(Ctx* c, const float4* pos_h, int n, float min_width, cudaSt
   }
   {
     int gb = min((n + 1 + 255) / 256, sm * 8);
-    k_cell_start<<<max(gb, 1), 256, 0, s>>>(c->d_keys[c->sorted_buf], n, c->d_grid, c->d_cell_start);
+    launch_pdl(k_cell_start, max(gb, 1), 256, 0, s, c->d_keys[c->sorted_buf], n, c->d_grid, c->d_cell_start);
     c->launches++;
   }
   c->tree_built = 0;

@@ -26,6 +26,13 @@ __device__ __forceinline__ float sqrt_approx(float x) {
   return r;
 }
 
+// Programmatic dependent launch: a kernel launched with launch_pdl (internal.h)
+// may be scheduled while the kernel before it on the stream is finishing; it
+// waits here, as its first statement, until that kernel has completed and its
+// memory is visible, so only the launch latency overlaps, not the work. In a
+// kernel launched without the attribute the wait returns at once.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __host__ __device__ __forceinline__ float band_of(float H, float Lmax) {
   return H * H * 1.52587890625e-05f + H * Lmax * 9.5367431640625e-07f;  // 2^-16 H^2 + 2^-20 H L
 }

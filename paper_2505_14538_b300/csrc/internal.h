@@ -177,4 +177,25 @@ __host__ __device__ constexpr int kCtrUnlistedTicket(int passes) { return kCtrPe
 __host__ __device__ constexpr int kCtrMissing(int passes) { return kCtrPerPass * (passes + 2) + 3; }
 __host__ __device__ constexpr int kCtrCount(int passes) { return kCtrPerPass * (passes + 2) + 4; }
 
+// Launch of a kernel whose first statement is pdl_wait() (common.cuh), with
+// programmatic stream serialization: its blocks may be scheduled while the
+// previous kernel on the stream drains, which hides the launch gap between the
+// short kernels of a chain (the cell sort, the loop epilogues). Stream capture
+// records the dependency as a programmatic edge.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 }  // namespace sg

@@ -825,6 +825,7 @@ __device__ __forceinline__ void grad_item(const LoopArgs& a, const GradOp& op, c
 
 template <int K>
 __global__ void __launch_bounds__(kLoopThreads, 5) k_gradient(LoopArgs a) {
+  pdl_wait();
   extern __shared__ __align__(16) unsigned char smem[];
   const unsigned lane = lane_id();
   const Grid g = *a.grid;
@@ -953,6 +954,7 @@ __device__ __forceinline__ void block_partial(float (&acc)[8], float (&accc)[8],
 
 template <bool kGrad, int K>
 __device__ __forceinline__ void force_kernel_body(const LoopArgs& a) {
+  pdl_wait();
   using Op = typename std::conditional<kGrad, GradForceOp, ForceOp>::type;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[kWarpsPerBlock][8];
@@ -1032,6 +1034,7 @@ __global__ void __launch_bounds__(kLoopThreads, 4) k_grad_force(LoopArgs a) { fo
 constexpr int kLppBatch = 4;
 template <int kMode, int K>
 __global__ void __launch_bounds__(kLoopThreads, 3) k_loop_lpp(const __grid_constant__ LoopArgs a) {
+  pdl_wait();
   constexpr int W = lpp_width<K>();
   constexpr bool kGrad = kMode != 1;
   __shared__ double red[kWarpsPerBlock][8];
@@ -1214,6 +1217,7 @@ __global__ void __launch_bounds__(kLoopThreads, 3) k_loop_lpp(const __grid_const
 // adds is unchanged), so the lane's chain waits on one load latency per eight
 // blocks instead of per block.
 __global__ void k_reduce_partials(const double* __restrict__ part, int nblocks, double* __restrict__ out) {
+  pdl_wait();
   const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double x = 0.0;
 #pragma unroll 8
@@ -1289,13 +1293,25 @@ static void ensure_attrs(const Ctx* c) {
   if (dev >= 0 && dev < kMaxAttrDevices) __atomic_store_n(&g_attr_done[dev], 1, __ATOMIC_RELEASE);
 }
 
+// The loop kernels start with pdl_wait(): launched with programmatic stream
+// serialization, they may be scheduled while the kernel before them drains.
 static cudaError_t launch_loop(const void* f, int nblk, LoopArgs& a, cudaStream_t s, size_t smem = kLoopSmemBytes) {
   void* args[] = {&a};
-  return cudaLaunchKernel(f, dim3(nblk), dim3(kLoopThreads), args, smem, s);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nblk);
+  cfg.blockDim = dim3(kLoopThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, f, args);
 }
 
 void reduce_partials(Ctx* c, int nblocks, double* out, cudaStream_t s) {
-  k_reduce_partials<<<1, 256, 0, s>>>(c->d_red_partial, nblocks, out);
+  launch_pdl(k_reduce_partials, 1, 256, 0, s, (const double*)c->d_red_partial, nblocks, out);
   c->launches++;
 }
 
@@ -1502,7 +1518,7 @@ int force_impl(Ctx* c, float4* out, float* dhdt, double* reductions, cudaStream_
   const int rc = loop_launch(c, 1, a, s, &nblk);
   if (rc != SWIFT_GPU_OK) return rc;
   if (reductions) {
-    k_reduce_partials<<<1, 256, 0, s>>>(c->d_red_partial, nblk, reductions);
+    launch_pdl(k_reduce_partials, 1, 256, 0, s, (const double*)c->d_red_partial, nblk, reductions);
     c->launches++;
   }
   return cudaGetLastError() == cudaSuccess ? SWIFT_GPU_OK : SWIFT_GPU_ERR_CUDA;
@@ -1518,7 +1534,7 @@ int grad_force_impl(Ctx* c, float2* grad_out, float4* out, float* dhdt, double* 
   const int rc = loop_launch(c, 2, a, s, &nblk);
   if (rc != SWIFT_GPU_OK) return rc;
   if (reductions) {
-    k_reduce_partials<<<1, 256, 0, s>>>(c->d_red_partial, nblk, reductions);
+    launch_pdl(k_reduce_partials, 1, 256, 0, s, (const double*)c->d_red_partial, nblk, reductions);
     c->launches++;
   }
   return cudaGetLastError() == cudaSuccess ? SWIFT_GPU_OK : SWIFT_GPU_ERR_CUDA;
