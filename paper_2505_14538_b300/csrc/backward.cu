@@ -362,6 +362,7 @@ __device__ __forceinline__ void force_adj_item(const AdjArgs& a, const ForceAdjO
 }
 
 __global__ void __launch_bounds__(kAdjThreads, 5) k_force_adj(AdjArgs a) {
+  pdl_wait();
   extern __shared__ __align__(16) unsigned char smem[];
   const Grid g = *a.grid;
   WarpSmem& w = adj_smem(smem);
@@ -495,6 +496,7 @@ struct DensAdjOp {
 };
 
 __global__ void __launch_bounds__(kAdjThreads, 5) k_dens_adj(AdjArgs a) {
+  pdl_wait();
   extern __shared__ __align__(16) unsigned char smem[];
   const Grid g = *a.grid;
   WarpSmem& w = adj_smem(smem);
@@ -628,6 +630,7 @@ struct IftAdjOp {
 };
 
 __global__ void __launch_bounds__(kAdjThreads) k_ift_adj(AdjArgs a) {
+  pdl_wait();
   extern __shared__ __align__(16) unsigned char smem[];
   const Grid g = *a.grid;
   WarpSmem& w = adj_smem(smem);
@@ -675,6 +678,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_ift_adj(AdjArgs a) {
 
 __global__ void k_gather_weights(int n, const unsigned* __restrict__ perm, const float4* __restrict__ in,
                                  float4* __restrict__ out) {
+  pdl_wait();
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) out[k] = in[perm[k]];
 }
 
@@ -697,7 +701,8 @@ int backward_impl(Ctx* c, const float4* grad_ad, float4* grad_x, float4* grad_v,
   int* tickets = c->d_counters + kCtrPerPass * (c->max_passes + 1) + 2;
   cudaMemsetAsync(tickets, 0, 2 * sizeof(int), s);
   const int nbg = min((c->n + 255) / 256, c->num_sms * 8);
-  k_gather_weights<<<nbg, 256, 0, s>>>(c->n, c->d_vals[c->sorted_buf], grad_ad, c->d_scratch4[0]);
+  launch_pdl(k_gather_weights, nbg, 256, 0, s, c->n, (const unsigned*)c->d_vals[c->sorted_buf], grad_ad,
+             c->d_scratch4[0]);
   AdjArgs a;
   a.hmode = h_mode;
   a.grid = c->d_grid;
@@ -728,14 +733,14 @@ int backward_impl(Ctx* c, const float4* grad_ad, float4* grad_x, float4* grad_v,
   a.grad_v = grad_v;
   a.grad_u = grad_u;
   a.ticket = tickets;
-  k_force_adj<<<nb1, kAdjThreads, kAdjSmemBytes, s>>>(a);
+  launch_pdl(k_force_adj, nb1, kAdjThreads, kAdjSmemBytes, s, a);
   a.ticket = tickets + 1;
-  k_dens_adj<<<nb2, kAdjThreads, kAdjSmemBytes, s>>>(a);
+  launch_pdl(k_dens_adj, nb2, kAdjThreads, kAdjSmemBytes, s, a);
   c->launches += 4;
   if (h_mode == 1) {
     cudaMemsetAsync(tickets, 0, sizeof(int), s);  // k_force_adj's ticket, free again
     a.ticket = tickets;
-    k_ift_adj<<<nb2, kAdjThreads, kAdjSmemBytes, s>>>(a);
+    launch_pdl(k_ift_adj, nb2, kAdjThreads, kAdjSmemBytes, s, a);
     c->launches += 2;
   }
   return cudaGetLastError() == cudaSuccess ? SWIFT_GPU_OK : SWIFT_GPU_ERR_CUDA;

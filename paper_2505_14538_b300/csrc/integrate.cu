@@ -45,6 +45,7 @@ __global__ void __launch_bounds__(kIntThreads) k_kick_drift(swift_gpu_time_param
                                                              const float* __restrict__ dh_dt,
                                                              float4* __restrict__ vel_pred,
                                                              float* __restrict__ u_pred) {
+  pdl_wait();
   // every thread derives dt from fields this kernel does not write
   const float dt = step_size(ck, tp.dt_max);
   if (blockIdx.x == 0 && threadIdx.x == 0) ck->dt = dt;
@@ -77,6 +78,7 @@ __global__ void __launch_bounds__(kIntThreads) k_viscosity_switch(swift_gpu_time
                                                                    const float2* __restrict__ vsig_lapu,
                                                                    float* __restrict__ div_prev,
                                                                    float* __restrict__ alpha_v) {
+  pdl_wait();
   const float dt = ck->dt;
   const float c2 = gamma_eos * (gamma_eos - 1.0f);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -105,6 +107,7 @@ __global__ void __launch_bounds__(kIntThreads) k_kick_finish(swift_gpu_time_para
                                                               const float2* __restrict__ vsig_lapu,
                                                               const float* __restrict__ alpha_v,
                                                               float* __restrict__ alpha_c) {
+  pdl_wait();
   __shared__ float s_min[kIntThreads / 32];
   const float dt = ck->dt;
   const float hdt = 0.5f * dt;
@@ -212,7 +215,7 @@ int swift_gpu_kick_drift(swift_gpu_ctx* h, const swift_gpu_time_params* tp, swif
                 !aligned_to(u_pred, 4)))
     return SWIFT_GPU_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  k_kick_drift<<<blocks_for(c, (const void*)k_kick_drift, n), kIntThreads, 0, s>>>(
+  launch_pdl(k_kick_drift, blocks_for(c, (const void*)k_kick_drift, n), kIntThreads, 0, s,
       *tp, clock, (int)n, c->phys.L[0], c->phys.L[1], c->phys.L[2], reinterpret_cast<float4*>(pos_h),
       reinterpret_cast<float4*>(vel_m), u, reinterpret_cast<const float4*>(accel_dudt), dh_dt,
       reinterpret_cast<float4*>(vel_pred), u_pred);
@@ -230,7 +233,7 @@ int swift_gpu_viscosity_switch(swift_gpu_ctx* h, const swift_gpu_time_params* tp
     return SWIFT_GPU_ERR_ARG;
   if (n == 0) return SWIFT_GPU_OK;
   cudaStream_t s = (cudaStream_t)stream;
-  k_viscosity_switch<<<blocks_for(c, (const void*)k_viscosity_switch, n), kIntThreads, 0, s>>>(
+  launch_pdl(k_viscosity_switch, blocks_for(c, (const void*)k_viscosity_switch, n), kIntThreads, 0, s,
       *tp, c->phys.gamma_eos, c->phys.kg, clock, (int)n, hh, u, reinterpret_cast<const float4*>(curl_div),
       reinterpret_cast<const float2*>(vsig_lapu), div_prev, alpha_v);
   return launched(c);
@@ -248,7 +251,7 @@ int swift_gpu_kick_finish(swift_gpu_ctx* h, const swift_gpu_time_params* tp, swi
     return SWIFT_GPU_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   if (cudaMemsetAsync(&clock->dt_next, 0x7f, sizeof(float), s) != cudaSuccess) return SWIFT_GPU_ERR_CUDA;
-  k_kick_finish<<<blocks_for(c, (const void*)k_kick_finish, n), kIntThreads, 0, s>>>(
+  launch_pdl(k_kick_finish, blocks_for(c, (const void*)k_kick_finish, n), kIntThreads, 0, s,
       *tp, c->phys.kg, c->phys.alpha_v, clock, (int)n, hh, reinterpret_cast<float4*>(pos_h),
       reinterpret_cast<float4*>(vel_m), u, reinterpret_cast<const float4*>(accel_dudt),
       reinterpret_cast<const float2*>(vsig_lapu), alpha_v, alpha_c);

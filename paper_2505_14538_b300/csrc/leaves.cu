@@ -49,6 +49,7 @@ static_assert(kStack >= 27 + kDfsGap, "walk stack too small for its roots");
 __global__ void k_tree_gather(const float4* __restrict__ pos_h, const unsigned* __restrict__ perm,
                               const unsigned* __restrict__ morton, int n, const Grid* __restrict__ g,
                               float4* __restrict__ pos, unsigned* __restrict__ mk) {
+  pdl_wait();
   const float L[3] = {g->L[0], g->L[1], g->L[2]};
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     const unsigned src = perm[k];
@@ -90,6 +91,7 @@ static_assert(kIndexBits <= kLinkShift, "node and leaf indices must fit the link
 // Top-down, one launch per level: split decisions from the particle counts
 // alone (no particle is read but the Morton codes of the binary searches).
 __global__ void __launch_bounds__(kTreeThreads) k_tree_split(TreeArgs a, int level) {
+  pdl_wait();
   const unsigned lane = lane_id();
   const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -169,6 +171,7 @@ __global__ void __launch_bounds__(kTreeThreads) k_tree_split(TreeArgs a, int lev
 // Leaf index of every leaf node from the exclusive scan of the leaf flags.
 __global__ void k_leaf_number(const unsigned* __restrict__ scan, int node_cap, int* __restrict__ node_link,
                               int* __restrict__ leaf_node, int* __restrict__ tctr) {
+  pdl_wait();
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < node_cap; v += gridDim.x * blockDim.x) {
     const unsigned li = scan[v];
     if (scan[v + 1] != li) {
@@ -187,6 +190,7 @@ __global__ void k_leaf_number(const unsigned* __restrict__ scan, int node_cap, i
 // independently; every shuffle names only its group's lanes.
 constexpr int kFinishLanes = 8;
 __global__ void __launch_bounds__(kTreeThreads) k_leaf_finish(TreeArgs a) {
+  pdl_wait();
   const unsigned lane = lane_id();
   const unsigned gl = lane & (kFinishLanes - 1);
   const unsigned gmask = 0xffu << (lane & ~(unsigned)(kFinishLanes - 1));
@@ -403,6 +407,7 @@ __device__ __forceinline__ void walk_one_leaf(const WalkArgs& a, const Grid& g, 
 // longer than the buffer falls back to a walk per leaf. Each list is
 // contiguous; where the lists lie does not change any result.
 __global__ void __launch_bounds__(kWalkThreads) k_leaf_walk(WalkArgs a) {
+  pdl_wait();
   extern __shared__ __align__(16) unsigned wsmem[];
   unsigned* st = wsmem + (threadIdx.x >> 5) * (kStack + kOutBuf);
   unsigned* buf = st + kStack;
@@ -512,8 +517,8 @@ int leaves_build(Ctx* c, const float4* pos_h, cudaStream_t s) {
   const int sm = c->num_sms;
   const unsigned* perm = c->d_vals[c->sorted_buf];
   unsigned* mk = c->d_keys[1 - c->sorted_buf];  // free after the sort
-  k_tree_gather<<<min((n + 255) / 256, sm * 8), 256, 0, s>>>(pos_h, perm, c->d_aux[1], n, c->d_grid, c->d_pos,
-                                                               mk);
+  launch_pdl(k_tree_gather, min((n + 255) / 256, sm * 8), 256, 0, s, pos_h, perm, (const unsigned*)c->d_aux[1], n,
+             (const Grid*)c->d_grid, c->d_pos, mk);
   c->launches++;
   TreeArgs t;
   t.grid = c->d_grid;
@@ -536,13 +541,13 @@ int leaves_build(Ctx* c, const float4* pos_h, cudaStream_t s) {
   t.kg = c->phys.kg;
   const int tree_blocks = sm * 8;
   for (int level = 0; level <= kTreeLevels; ++level) {
-    k_tree_split<<<tree_blocks, kTreeThreads, 0, s>>>(t, level);
+    launch_pdl(k_tree_split, tree_blocks, kTreeThreads, 0, s, t, level);
     c->launches++;
   }
   exclusive_scan(c, c->d_node_flag, c->d_node_flag, c->node_cap + 1, c->d_scan_tmp, s);
-  k_leaf_number<<<min((c->node_cap + 255) / 256, sm * 16), 256, 0, s>>>(c->d_node_flag, c->node_cap,
-                                                                      c->d_node_link, c->d_leaf_node, c->d_tree_ctr);
-  k_leaf_finish<<<tree_blocks, kTreeThreads, 0, s>>>(t);
+  launch_pdl(k_leaf_number, min((c->node_cap + 255) / 256, sm * 16), 256, 0, s, (const unsigned*)c->d_node_flag,
+             c->node_cap, c->d_node_link, c->d_leaf_node, c->d_tree_ctr);
+  launch_pdl(k_leaf_finish, tree_blocks, kTreeThreads, 0, s, t);
   c->launches += 2;
   WalkArgs w;
   w.grid = c->d_grid;
@@ -555,7 +560,7 @@ int leaves_build(Ctx* c, const float4* pos_h, cudaStream_t s) {
   w.nbr_span = c->d_nbr_span;
   w.nbr = c->d_nbr;
   w.nbr_cap = c->nbr_cap;
-  k_leaf_walk<<<sm * 8, kWalkThreads, kWalkSmemBytes, s>>>(w);
+  launch_pdl(k_leaf_walk, sm * 8, kWalkThreads, kWalkSmemBytes, s, w);
   c->launches++;
   return cudaGetLastError() == cudaSuccess ? SWIFT_GPU_OK : SWIFT_GPU_ERR_CUDA;
 }

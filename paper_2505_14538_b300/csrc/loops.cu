@@ -733,6 +733,7 @@ __global__ void k_ghost(int n, const unsigned* __restrict__ perm, const float4* 
                         const float4* __restrict__ rho4, const float4* __restrict__ cd, const float* __restrict__ u,
                         const float* __restrict__ alpha_v, const float* __restrict__ alpha_c, Phys ph,
                         float4* __restrict__ ga, float4* __restrict__ gb, float4* __restrict__ gc) {
+  pdl_wait();
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     const unsigned src = perm[k];
     const float h = pos[k].w;
@@ -1396,8 +1397,8 @@ int density_impl(Ctx* c, const float4* pos_in, const float4* vel_in, const uint8
 int ghost_impl(Ctx* c, const float* u, const float* alpha_v, const float* alpha_c, cudaStream_t s) {
   if (c->n == 0) return SWIFT_GPU_OK;
   const int nb = min((c->n + 255) / 256, c->num_sms * 8);
-  k_ghost<<<nb, 256, 0, s>>>(c->n, c->d_vals[c->sorted_buf], c->d_pos, c->d_rho4, c->d_cd, u, alpha_v, alpha_c,
-                             c->phys, c->d_ga, c->d_gb, c->d_gc);
+  launch_pdl(k_ghost, nb, 256, 0, s, c->n, (const unsigned*)c->d_vals[c->sorted_buf], c->d_pos, c->d_rho4, c->d_cd,
+             u, alpha_v, alpha_c, c->phys, c->d_ga, c->d_gb, c->d_gc);
   c->launches++;
   return cudaGetLastError() == cudaSuccess ? SWIFT_GPU_OK : SWIFT_GPU_ERR_CUDA;
 }
