@@ -175,7 +175,9 @@ __host__ __device__ inline int ctr_index(int pass, int which) { return pass * kC
 // a lane-per-particle one, and the flag the density call sets when a group has no kept list.
 __host__ __device__ constexpr int kCtrUnlistedTicket(int passes) { return kCtrPerPass * (passes + 2) + 2; }
 __host__ __device__ constexpr int kCtrMissing(int passes) { return kCtrPerPass * (passes + 2) + 3; }
-__host__ __device__ constexpr int kCtrCount(int passes) { return kCtrPerPass * (passes + 2) + 4; }
+// finished-block counts of the loop launches' tickets: 0 gradient, 1 force, 2 unlisted
+__host__ __device__ constexpr int kCtrLoopDone(int passes, int which) { return kCtrPerPass * (passes + 2) + 4 + which; }
+__host__ __device__ constexpr int kCtrCount(int passes) { return kCtrPerPass * (passes + 2) + 7; }
 
 // Launch of a kernel whose first statement is pdl_wait() (common.cuh), with
 // programmatic stream serialization: its blocks may be scheduled while the

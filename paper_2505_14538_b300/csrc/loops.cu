@@ -775,6 +775,7 @@ struct LoopArgs {
   const int* plist;
   const int* ctr;   // item count at ctr[0]
   int* ticket;
+  int* done;             // finished blocks; the last one zeroes ticket and done (release_ticket)
   void* out;        // caller order: float2 (gradient) / float4 (force)
   float2* out2;     // fused gradient + force: the gradient's float2 output
   float* dhdt;      // force: caller order, may be NULL
@@ -790,6 +791,22 @@ struct LoopArgs {
   const float4* gc; // sorted (x, y, z, 1/H) from the ghost step (force_lpp.cuh)
 };
 
+// The end of a persistent loop launch: the last block to finish sets the
+// launch's ticket, and this count, back to zero, so the next launch on the
+// ticket needs no memset node between it and the kernel before it (a memset
+// ends a programmatic-launch chain). Every block reaches this once its warps
+// have taken their last ticket; a launch whose blocks all return before
+// taking one (nothing to do) touches neither counter.
+__device__ __forceinline__ void release_ticket(int* ticket, int* done) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(done, 1) == (int)gridDim.x - 1) {
+      atomicExch(ticket, 0);
+      atomicExch(done, 0);
+    }
+  }
+}
 
 __device__ __forceinline__ void grad_item(const LoopArgs& a, const GradOp& op, const Grid& g, WarpSmem& w,
                                           const Item& it, int t, float Lmax, unsigned& ninter, unsigned& ncand) {
@@ -857,6 +874,7 @@ __global__ void __launch_bounds__(kLoopThreads, 5) k_gradient(LoopArgs a) {
     atomicAdd(&a.stats[kStatInterGrad], (unsigned long long)ninter);
     atomicAdd(&a.stats[kStatCandGrad], (unsigned long long)ncand);
   }
+  release_ticket(a.ticket, a.done);
 }
 
 // =============================================================== force loop
@@ -1006,6 +1024,7 @@ __device__ __forceinline__ void force_kernel_body(const LoopArgs& a) {
       atomicAdd(&a.stats[kStatCandGrad], (unsigned long long)ncand);
     }
   }
+  release_ticket(a.ticket, a.done);
 }
 
 template <int K>
@@ -1210,6 +1229,7 @@ __global__ void __launch_bounds__(kLoopThreads, 3) k_loop_lpp(const __grid_const
       atomicAdd(&a.stats[kStatCandGrad], (unsigned long long)ncand);
     }
   }
+  release_ticket(a.ticket, a.done);
 }
 
 // One warp per quantity; lane l sums blocks l, l+32, ... and the warp then
@@ -1433,8 +1453,9 @@ int set_inactive_impl(Ctx* c, const uint8_t* mask, const float* h, const float4*
   return cudaGetLastError() == cudaSuccess ? SWIFT_GPU_OK : SWIFT_GPU_ERR_CUDA;
 }
 
-static LoopArgs loop_args(Ctx* c, int* ticket, void* out) {
+static LoopArgs loop_args(Ctx* c, int* ticket, int* done, void* out) {
   LoopArgs a;
+  a.done = done;
   a.grid = c->d_grid;
   a.nb = nbr_of(c);
   a.perm = c->d_vals[c->sorted_buf];
@@ -1488,7 +1509,7 @@ static int loop_launch(Ctx* c, int mode, LoopArgs& a, cudaStream_t s, int* nblk_
     b.only_unlisted = 1;
     b.red_offset = nblk;
     b.ticket = c->d_counters + kCtrUnlistedTicket(c->max_passes);
-    cudaMemsetAsync(b.ticket, 0, sizeof(int), s);
+    b.done = c->d_counters + kCtrLoopDone(c->max_passes, 2);
     const int nblk2 = min(persistent_blocks(c, cell_kern, kLoopSmemBytes), c->red_blocks - nblk);
     if (e == cudaSuccess) e = launch_loop(cell_kern, nblk2, b, s, kLoopSmemBytes);
     c->launches += 2;
@@ -1505,15 +1526,13 @@ static int loop_launch(Ctx* c, int mode, LoopArgs& a, cudaStream_t s, int* nblk_
 
 int gradient_impl(Ctx* c, float2* out, cudaStream_t s) {
   int* ticket = c->d_counters + kCtrPerPass * (c->max_passes + 1) + 0;
-  cudaMemsetAsync(ticket, 0, sizeof(int), s);
-  LoopArgs a = loop_args(c, ticket, out);
+  LoopArgs a = loop_args(c, ticket, c->d_counters + kCtrLoopDone(c->max_passes, 0), out);
   return loop_launch(c, 0, a, s, nullptr);
 }
 
 int force_impl(Ctx* c, float4* out, float* dhdt, double* reductions, cudaStream_t s) {
   int* ticket = c->d_counters + kCtrPerPass * (c->max_passes + 1) + 1;
-  cudaMemsetAsync(ticket, 0, sizeof(int), s);
-  LoopArgs a = loop_args(c, ticket, out);
+  LoopArgs a = loop_args(c, ticket, c->d_counters + kCtrLoopDone(c->max_passes, 1), out);
   a.dhdt = dhdt;
   int nblk = 0;
   const int rc = loop_launch(c, 1, a, s, &nblk);
@@ -1527,8 +1546,7 @@ int force_impl(Ctx* c, float4* out, float* dhdt, double* reductions, cudaStream_
 
 int grad_force_impl(Ctx* c, float2* grad_out, float4* out, float* dhdt, double* reductions, cudaStream_t s) {
   int* ticket = c->d_counters + kCtrPerPass * (c->max_passes + 1) + 1;
-  cudaMemsetAsync(ticket, 0, sizeof(int), s);
-  LoopArgs a = loop_args(c, ticket, out);
+  LoopArgs a = loop_args(c, ticket, c->d_counters + kCtrLoopDone(c->max_passes, 1), out);
   a.out2 = grad_out;
   a.dhdt = dhdt;
   int nblk = 0;
