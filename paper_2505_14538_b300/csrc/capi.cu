@@ -183,6 +183,7 @@ int swift_gpu_create(swift_gpu_ctx** out, const swift_gpu_params* p, int64_t n_m
   cudaMemset(c->d_status, 0, sizeof(Status));
   cudaMemset(c->d_stats, 0, sizeof(unsigned long long) * kStatCount);
   cudaMemset(c->d_counters, 0, sizeof(int) * kCtrCount(kMaxPasses));
+  cudaMemset(c->d_hmax_bits, 0, sizeof(unsigned) * kHmaxWords);  // k_scan_h leaves them zero after each call
   cudaMemset(c->d_tree_ctr, 0, sizeof(int) * kTreeCtrCount);
   if (cudaDeviceSynchronize() != cudaSuccess) {
     free_all(c);

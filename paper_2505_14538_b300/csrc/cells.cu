@@ -201,7 +201,9 @@ __global__ void k_scan_h(const float4* __restrict__ pos_h, int n, unsigned* hm_w
   __syncthreads();
   if (s_last && threadIdx.x == 0) {
     __threadfence();
-    grid_setup(__uint_as_float(atomicOr(&hm_words[0], 0u)), g, ph, margin, min_width, nc_cap, host_passes, st);
+    const float hmax = __uint_as_float(atomicExch(&hm_words[0], 0u));
+    atomicExch(&hm_words[1], 0u);  // both words zero again for the next call: no memset before it
+    grid_setup(hmax, g, ph, margin, min_width, nc_cap, host_passes, st);
   }
 }
 
@@ -450,7 +452,6 @@ int build_cells_impl(Ctx* c, const float4* pos_h, int n, float min_width, cudaSt
   const int nc_cap = adaptive && c->nc_cap > kAdaptiveNcCap ? kAdaptiveNcCap : c->nc_cap;
   const int host_passes = (c->max_key_bits + 7) / 8;
   if (n > 0) {
-    cudaMemsetAsync(c->d_hmax_bits, 0, sizeof(unsigned) * kHmaxWords, s);
     launch_pdl(k_scan_h, min((n + 255) / 256, sm * 8), 256, 0, s, pos_h, n, c->d_hmax_bits, c->d_grid, c->phys,
                c->params.cell_margin, min_width, nc_cap, host_passes, c->d_status);
   } else {
