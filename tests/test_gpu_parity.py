@@ -478,3 +478,40 @@ def test_autotune_picks_a_valid_setting_and_keeps_results(sph, O):
         assert torch.max(torch.abs(r_out[:, c] - r_ref[:, c])).item() < 1e-5 * sc, c
     sa = torch.abs(ref["accel_dudt"]).max().item()
     assert torch.max(torch.abs(out["accel_dudt"] - ref["accel_dudt"])).item() < 1e-4 * sa
+
+
+@pytest.mark.parametrize("flags", [0, 8])
+def test_repeated_loop_calls_and_builds_leave_their_counters_ready(sph, flags):
+    """Each loop launch's last block sets its work ticket back to zero, and the cell build's h scan
+    its max-h words, with no memset between launches. So the gradient, force and fused calls
+    repeated after one density call fill fresh (NaN-filled) outputs bit-identically, and a build
+    after one with twice the h gets the cell grid a fresh context gets."""
+    d, vel, u = lattice_state(16, seed=21, jitter=0.3)
+    n = len(d["pos"])
+    ctx = sph.Context(n, box=d["box"], flags=flags, leaf_max=8)
+    pos_h, vel_m, ut = dev_arrays(d, vel, u)
+    ctx.build_cells(pos_h)
+    ctx.density(pos_h, vel_m)
+    nan = float("nan")
+    runs = []
+    for _ in range(3):
+        o = ctx.gradient_force(ut, vsig_lapu=torch.full((n, 2), nan, device="cuda"),
+                               accel_dudt=torch.full((n, 4), nan, device="cuda"))
+        g = ctx.gradient(ut, vsig_lapu=torch.full((n, 2), nan, device="cuda"))
+        f = ctx.force(ut, accel_dudt=torch.full((n, 4), nan, device="cuda"))
+        runs.append((o["vsig_lapu"], o["accel_dudt"], g, f["accel_dudt"]))
+    torch.cuda.synchronize()
+    assert ctx.sync_status() == (0, 0)
+    for r in runs:
+        assert all(bool(torch.isfinite(t).all()) for t in r)
+        for t, t0 in zip(r, runs[0]):
+            assert torch.equal(t, t0)
+    big = pos_h.clone()
+    big[:, 3] *= 2.0
+    ctx.build_cells(big)
+    nc_big = ctx.info()["nc"]
+    ctx.build_cells(pos_h)
+    fresh = sph.Context(n, box=d["box"], flags=flags, leaf_max=8)
+    fresh.build_cells(pos_h)
+    assert ctx.info()["nc"] == fresh.info()["nc"] != nc_big
+    assert ctx.info()["cell_width"] == fresh.info()["cell_width"]
