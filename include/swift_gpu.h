@@ -95,16 +95,25 @@ typedef struct {
                             32 particles) at a time from the device queue, so four cells a block
                             are in flight; 64- and 256-thread blocks measured slower */
   int max_lanes_per_particle; /* 1, 2, 4, 8, 16 or 32: lanes that share one particle's neighbour scan;
-                                 on the uniform grid 1 selects the lane-per-particle density call (each
-                                 lane scans its own particle's neighbour cells through windows along the
-                                 13 pair axes, Sec. 2.2.2) and 2..32 the cell items (a warp shares one
-                                 cell's candidates); the gradient and force loops run one lane a particle
+                                 on the uniform grid 1 selects the lane-per-particle density call (a
+                                 warp takes 32 particles, one a lane; group_collect says how they find
+                                 their candidates) and 2..32 the cell items (a warp shares one cell's
+                                 candidates); the gradient and force loops run one lane a particle
                                  over the density call's kept lists either way */
   int blocks_per_sm;     /* persistent blocks per SM (0 = occupancy maximum) */
   int wait_limit_us;     /* limit of each bounded device-side wait (the density launch's grid barrier):
                             0 = 5 s; negative = give up at once (fault injection: the call then reports
                             ERR_TIMEOUT, its outputs are undefined, the context stays usable) */
+  int group_collect;     /* candidate search of the lane-per-particle density call:
+                            SWIFT_GPU_COLLECT_ROWS (0): the warp's lanes test, in step, every particle of
+                            the rows of cells their 27-cell neighbourhoods share (Sec. 2.2: self and pair
+                            interactions of neighbouring cells), one broadcast load a candidate;
+                            SWIFT_GPU_COLLECT_WINDOWS (1): each lane reads its own 26 neighbour cells
+                            through windows along the 13 pair axes (sorted pair interactions, Sec. 2.2.2) */
 } swift_gpu_tuning;
+
+#define SWIFT_GPU_COLLECT_ROWS 0
+#define SWIFT_GPU_COLLECT_WINDOWS 1
 
 typedef struct {
   int64_t n;               /* particles of the last build */

@@ -34,6 +34,8 @@ KERNEL_CUBIC = 0
 KERNEL_WENDLAND_C2 = 1
 KERNEL_WENDLAND_C4 = 2
 # H/h of each shape from the second-moment definition (sqrt(30)/3, sqrt(15)/2, sqrt(78)/4)
+COLLECT_ROWS = 0  # swift_gpu_tuning.group_collect
+COLLECT_WINDOWS = 1
 KERNEL_GAMMAS = {KERNEL_CUBIC: 1.825742, KERNEL_WENDLAND_C2: 1.936492, KERNEL_WENDLAND_C4: 2.207940}
 
 EXPORTED = ("swift_gpu_default_params", "swift_gpu_create", "swift_gpu_destroy", "swift_gpu_set_params",
@@ -73,6 +75,7 @@ class Tuning(ctypes.Structure):
         ("max_lanes_per_particle", ctypes.c_int),
         ("blocks_per_sm", ctypes.c_int),
         ("wait_limit_us", ctypes.c_int),
+        ("group_collect", ctypes.c_int),
     ]
 
 

@@ -115,6 +115,7 @@ int swift_gpu_create(swift_gpu_ctx** out, const swift_gpu_params* p, int64_t n_m
   c->tuning.threads_per_block = 256;
   c->tuning.max_lanes_per_particle = 32;  // one lane a particle below, where that path exists
   c->tuning.blocks_per_sm = 0;
+  c->tuning.group_collect = SWIFT_GPU_COLLECT_ROWS;
   int nc_cap = (int)floor(cbrt(2.0 * (double)n_max));
   if (nc_cap < 3) nc_cap = 3;
   if (nc_cap > 1024) nc_cap = 1024;
@@ -441,7 +442,8 @@ int swift_gpu_set_tuning(swift_gpu_ctx* h, const swift_gpu_tuning* t) {
   if (!c || !t) return SWIFT_GPU_ERR_ARG;
   const int l = t->max_lanes_per_particle;
   if (t->threads_per_block != 256 || !(l == 1 || l == 2 || l == 4 || l == 8 || l == 16 || l == 32) ||
-      t->blocks_per_sm < 0)
+      t->blocks_per_sm < 0 ||
+      !(t->group_collect == SWIFT_GPU_COLLECT_ROWS || t->group_collect == SWIFT_GPU_COLLECT_WINDOWS))
     return SWIFT_GPU_ERR_ARG;
   c->tuning = *t;
   return SWIFT_GPU_OK;

@@ -371,8 +371,14 @@ __host__ __device__ constexpr int lpp_width() {
 __host__ __device__ constexpr size_t lpp_warp_bytes(int kind) {
   return (size_t)lpp_width_of(kind) * 32 * 4;
 }
-__host__ __device__ constexpr size_t dens_warp_bytes(int kind, bool lpp) {
-  return lpp && lpp_warp_bytes(kind) > sizeof(WarpSmem) ? lpp_warp_bytes(kind) : sizeof(WarpSmem);
+// With the shared-row collect (lpp 2) the warp's staging area follows the
+// squared distances; later passes use the same memory as cell items.
+__host__ __device__ constexpr size_t dens_warp_bytes(int kind, int lpp) {
+  return lpp == 2 ? (lpp_warp_bytes(kind) + sizeof(RowStage) > sizeof(WarpSmem)
+                         ? lpp_warp_bytes(kind) + sizeof(RowStage)
+                         : sizeof(WarpSmem))
+         : lpp && lpp_warp_bytes(kind) > sizeof(WarpSmem) ? lpp_warp_bytes(kind)
+                                                          : sizeof(WarpSmem);
 }
 
 // Eqs. 5-6 at the lane particle's current h over its stored squared
@@ -406,14 +412,15 @@ __device__ __forceinline__ void walk_r2(const DensOp::I& I, const float* r2s, in
 }
 
 // Pass 0 of the density loop for group `grp` (pass-0 particle list entries
-// [32 grp, 32 grp + 32), one lane each): the windowed collect (lpp.cuh) into
+// [32 grp, 32 grp + 32), one lane each): the collect (lpp.cuh: kLPP 1 the
+// windows along the pair axes, 2 the shared rows of cells) into
 // the group's kept list and the lane's squared distances, the Newton
 // iteration on those distances, and the full sums at the final h over the
 // kept list. Particles whose candidates do not fit in W, and predicted
 // convergences that the final sums refute, continue as one-particle cell
 // items of the next pass. At fixed h (kFixedH) a particle whose candidates do
 // not fit scans its 27 cells instead.
-template <int K, bool kFixedH>
+template <int K, bool kFixedH, int kLPP>
 __device__ __forceinline__ void dens_group(const DensArgs& a, const DensOp& op, const Grid& g, float* r2w, int grp,
                                            int P, bool last, Item* items_next, int* plist_next, int* ctr_next,
                                            float Lmax, unsigned& ninter, unsigned& nhiter, unsigned& ncand) {
@@ -432,8 +439,13 @@ __device__ __forceinline__ void dens_group(const DensArgs& a, const DensOp& op, 
   float* r2s = r2w + lane;
   const int cell = (int)a.nb.skeys[k];
   bool ovf = false;
-  int cnt = lpp_collect<W>(g, a.nb.cell_start, a.pos, a.rep, a.rep_stride, I.x, I.y, I.z, cell, R2, Lmax, live,
-                           lst, r2s, ovf, ncand);
+  int cnt;
+  if constexpr (kLPP == 2)
+    cnt = rows_collect<W>(g, a.nb.cell_start, a.pos, I.x, I.y, I.z, cell, R2, live, lst, r2s,
+                          *reinterpret_cast<RowStage*>(r2w + W * 32), ovf, ncand);
+  else
+    cnt = lpp_collect<W>(g, a.nb.cell_start, a.pos, a.rep, a.rep_stride, I.x, I.y, I.z, cell, R2, Lmax, live, lst,
+                         r2s, ovf, ncand);
   if (!live) cnt = 0;
   cnt = min(cnt, W);
   // the group's kept list serves the later loops when every lane's candidates
@@ -488,16 +500,22 @@ __device__ __forceinline__ void dens_group(const DensArgs& a, const DensOp& op, 
   {
     const int fc = (live && !retry && !scan) ? cnt : 0;
     const int m = __reduce_max_sync(kFull, fc);
+    // the next batch's entries are read while the current batch's records load
+    unsigned e[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) e[q] = q < fc ? lst[q * 32] : (unsigned)k;
     for (int t0 = 0; t0 < m; t0 += 4) {
-      unsigned e[4];
       DensOp::DRec r[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) e[q] = t0 + q < fc ? lst[(t0 + q) * 32] : (unsigned)k;
-#pragma unroll
       for (int q = 0; q < 4; ++q) op.load_rec((int)(e[q] & kIndexMask), r[q]);
+      unsigned nx[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) nx[q] = t0 + 4 + q < fc ? lst[(t0 + 4 + q) * 32] : (unsigned)k;
 #pragma unroll
       for (int q = 0; q < 4; ++q)
         if (t0 + q < fc) op.interact(I, (int)(e[q] & kIndexMask), e[q] >> kIndexBits, r[q]);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) e[q] = nx[q];
     }
   }
   if constexpr (kFixedH) {
@@ -550,9 +568,13 @@ __device__ __forceinline__ void dens_group(const DensArgs& a, const DensOp& op, 
 
 // The loop kernels are instantiated per kernel shape K (kKernelCubic,
 // kKernelWendlandC2, kKernelWendlandC4), so the shape is fixed at compile time.
-// kLPP: pass 0 runs lane per particle over groups (dens_group), with the
-// replicas of every cell built in the prologue; later passes run cell items.
-template <int K, bool kFixedH, bool kLPP>
+// kLPP: pass 0 runs cell items (0) or lane per particle over groups
+// (dens_group) with the windowed collect (1, the replicas of every cell built
+// in the prologue) or the shared-row collect (2); later passes run cell items.
+// With the shared rows and every particle active, the pass-0 list is the
+// sorted order itself, so that a group is 32 consecutive particles, a few
+// cells of one row.
+template <int K, bool kFixedH, int kLPP>
 __global__ void __launch_bounds__(kLoopThreads, kLPP ? 4 : 5) k_density(DensArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const unsigned lane = lane_id();
@@ -627,7 +649,8 @@ __global__ void __launch_bounds__(kLoopThreads, kLPP ? 4 : 5) k_density(DensArgs
         s_base[1] = it ? atomicAdd(&a.ctr[ctr_index(0, 0)], it) : 0;
       }
       __syncthreads();
-      const int pbase = s_base[0] + s_tot[wib], ibase = s_base[1] + s_nit[wib];
+      const int pbase = (kLPP == 2 && a.active == nullptr) ? cs : s_base[0] + s_tot[wib];
+      const int ibase = s_base[1] + s_nit[wib];
       int wc = 0;
       for (int b = cs; b < ce; b += 32) {
         const int k = b + (int)lane;
@@ -643,7 +666,7 @@ __global__ void __launch_bounds__(kLoopThreads, kLPP ? 4 : 5) k_density(DensArgs
   }
   // ---- replicas of every cell along the 13 pair axes (one warp a cell), from
   // the same wrapped positions the gather above writes
-  if constexpr (kLPP) {
+  if constexpr (kLPP == 1) {
     const int nw = (int)((gridDim.x * blockDim.x) >> 5);
     for (int c = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); c < g.ncells; c += nw) {
       const int cs = a.nb.cell_start[c], m = a.nb.cell_start[c + 1] - cs;
@@ -682,8 +705,8 @@ __global__ void __launch_bounds__(kLoopThreads, kLPP ? 4 : 5) k_density(DensArgs
       for (;;) {
         const int t = take_ticket(&a.ctr[ctr_index(0, 2)]);
         if (t >= ng) break;
-        dens_group<K, kFixedH>(a, op, g, r2w, t, P, last, items_next, plist_next, ctr_next, Lmax, ninter, nhiter,
-                               ncand);
+        dens_group<K, kFixedH, kLPP>(a, op, g, r2w, t, P, last, items_next, plist_next, ctr_next, Lmax, ninter,
+                                     nhiter, ncand);
       }
     } else {
       for (;;) {
@@ -1259,11 +1282,12 @@ static int persistent_blocks(Ctx* c, const void* kern, size_t smem) {
 
 // The instantiation of each loop kernel for kernel shape `kind`.
 template <int K>
-static const void* density_kernel_k(bool fixed_h, bool lpp) {
-  if (lpp) return fixed_h ? (const void*)k_density<K, true, true> : (const void*)k_density<K, false, true>;
-  return fixed_h ? (const void*)k_density<K, true, false> : (const void*)k_density<K, false, false>;
+static const void* density_kernel_k(bool fixed_h, int lpp) {
+  if (lpp == 2) return fixed_h ? (const void*)k_density<K, true, 2> : (const void*)k_density<K, false, 2>;
+  if (lpp == 1) return fixed_h ? (const void*)k_density<K, true, 1> : (const void*)k_density<K, false, 1>;
+  return fixed_h ? (const void*)k_density<K, true, 0> : (const void*)k_density<K, false, 0>;
 }
-static const void* density_kernel(int kind, bool fixed_h, bool lpp) {
+static const void* density_kernel(int kind, bool fixed_h, int lpp) {
   return kind == kKernelWendlandC2   ? density_kernel_k<kKernelWendlandC2>(fixed_h, lpp)
          : kind == kKernelWendlandC4 ? density_kernel_k<kKernelWendlandC4>(fixed_h, lpp)
                                      : density_kernel_k<kKernelCubic>(fixed_h, lpp);
@@ -1294,7 +1318,7 @@ static const void* lpp_loop_kernel(int mode, int kind) {
   return mode == 0 ? lpp_loop_kernel_m<0>(kind) : mode == 1 ? lpp_loop_kernel_m<1>(kind) : lpp_loop_kernel_m<2>(kind);
 }
 
-static size_t dens_smem(int kind, bool lpp) { return dens_warp_bytes(kind, lpp) * kWarpsPerBlock; }
+static size_t dens_smem(int kind, int lpp) { return dens_warp_bytes(kind, lpp) * kWarpsPerBlock; }
 
 // Raise the dynamic shared-memory limit of every loop kernel, once per device
 // (function attributes belong to the device's context).
@@ -1305,9 +1329,9 @@ static void ensure_attrs(const Ctx* c) {
   if (dev >= 0 && dev < kMaxAttrDevices && __atomic_load_n(&g_attr_done[dev], __ATOMIC_ACQUIRE)) return;
   for (int kind = kKernelCubic; kind <= kKernelWendlandC4; ++kind) {
     for (int fh = 0; fh < 2; ++fh)
-      for (int lpp = 0; lpp < 2; ++lpp)
-        cudaFuncSetAttribute(density_kernel(kind, fh != 0, lpp != 0), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)dens_smem(kind, lpp != 0));
+      for (int lpp = 0; lpp < 3; ++lpp)
+        cudaFuncSetAttribute(density_kernel(kind, fh != 0, lpp), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)dens_smem(kind, lpp));
     for (const void* f : {gradient_kernel(kind), force_kernel(kind), grad_force_kernel(kind)})
       cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLoopSmemBytes);
   }
@@ -1346,16 +1370,20 @@ static bool lpp_store_fits(const Ctx* c) {
 
 // The lane-per-particle path runs the persistent density call on the uniform
 // grid when the tuning asks for one lane a particle and the context holds the
-// replicas and the kept-list store.
-static bool use_lpp(const Ctx* c) {
-  return c->tuning.max_lanes_per_particle == 1 && c->d_rep != nullptr && lpp_store_fits(c) &&
-         !(c->params.flags & (SWIFT_GPU_ADAPTIVE | SWIFT_GPU_PLAIN));
+// kept-list store (and, for the windowed collect, the replicas): 0 the cell
+// items, 1 the windowed collect, 2 the shared-row collect.
+static int use_lpp(const Ctx* c) {
+  if (c->tuning.max_lanes_per_particle != 1 || !lpp_store_fits(c) ||
+      (c->params.flags & (SWIFT_GPU_ADAPTIVE | SWIFT_GPU_PLAIN)))
+    return 0;
+  if (c->tuning.group_collect == SWIFT_GPU_COLLECT_WINDOWS) return c->d_rep != nullptr ? 1 : 0;
+  return 2;
 }
 
 int density_impl(Ctx* c, const float4* pos_in, const float4* vel_in, const uint8_t* active, float* h_out,
                  float4* rho4, float4* cd, uint32_t* ngb, cudaStream_t s) {
   ensure_attrs(c);
-  const bool lpp = use_lpp(c);
+  const int lpp = use_lpp(c);
   const void* kern = density_kernel(c->phys.kernel, (c->params.flags & SWIFT_GPU_NO_H_ITER) != 0, lpp);
   const size_t smem = dens_smem(c->phys.kernel, lpp);
   const int nblk = persistent_blocks(c, kern, smem);

@@ -249,6 +249,244 @@ __device__ __forceinline__ int lpp_collect(const Grid& g, const int* __restrict_
   return cnt;
 }
 
+// Plain per-lane collect over the 27 cells around `cell`, no windows: every
+// candidate j (itself included) with FP32 r^2 < R2 is appended to the lane's
+// list from position cnt on, the cells taken in the order q = 0..26 (x
+// fastest) and each cell in sorted order. Lanes with live = false take no
+// part. The fallback of rows_collect for lanes no shared row run covers.
+template <int W>
+__device__ __forceinline__ int cells_collect(const Grid& g, const int* __restrict__ cell_start,
+                                             const float4* __restrict__ pos, float xi, float yi, float zi, int cell,
+                                             float R2, bool live, unsigned* __restrict__ lst, float* r2s, int cnt,
+                                             bool& ovf, unsigned& ncand) {
+  if (!live) return cnt;
+  const int nx = g.nc[0], ny = g.nc[1];
+  const int cx = cell % nx, cy = (cell / nx) % ny, cz = cell / (nx * ny);
+#pragma unroll 1
+  for (int q = 0; q < 27; ++q) {
+    const NbrCell nbc = nbr_cell(g, cx, cy, cz, q);
+    const int cs = cell_start[nbc.c], ce = cell_start[nbc.c + 1];
+    const float xs = xi - nbc.sx, ys = yi - nbc.sy, zs = zi - nbc.sz;
+    const unsigned eb = nbc.code << kIndexBits;
+    for (int j = cs; j < ce; ++j) {
+      const float4 c = pos[j];
+      const float r2 = r2_of(xs - c.x, ys - c.y, zs - c.z);
+      if (r2 < R2) {
+        if (cnt < W) {
+          lst[cnt * 32] = (unsigned)j | eb;
+          r2s[cnt * 32] = r2;
+        } else {
+          ovf = true;
+        }
+        ++cnt;
+      }
+    }
+    ncand += (unsigned)(ce - cs);
+  }
+  return cnt;
+}
+
+// Shared rows (the uniform grid's lane-per-particle collect). The lanes of a
+// group whose particles lie in one row of cells (same y and z cell index),
+// within kRowSpan cells of each other in x, form a run. The union of their
+// 27-cell neighbourhoods is 9 rows of consecutive cells: x from the run's
+// smallest x - 1 to its largest x + 1, at y - 1..y + 1 and z - 1..z + 1, each
+// row a contiguous range of the sorted particles (cell ids run x fastest).
+// x - 1 below 0 and x + 1 past the last cell are the periodic images (shift
+// codes as shift_j reads them), so a row has up to three segments and every
+// (cell, image) pair of a lane's neighbourhood is read exactly once, in the
+// order cells_collect reads it: z, then y, then x ascending.
+//
+// Every lane of the run tests every candidate of those segments, in step.
+// The segments' records are staged in shared memory in chunks of up to 32
+// (one 16-byte cp.async a lane), kRowDepth - 1 chunks ahead of the chunk
+// being tested, so the tests read broadcast shared-memory values instead of
+// waiting on a load from L2 per batch. A chunk holds records of one segment
+// only, so the lane's shifted position is set once a chunk.
+//
+// A lane's list is therefore the one cells_collect writes, except that
+// candidates of cells two or more cells away in x that pass the FP32 test
+// are kept as well (the test's guard band admits a thin shell beyond a cell
+// width); they lie outside every support, which the exact decisions of the
+// later sums reject. At most kRowRuns runs are taken; lanes left over
+// (groups spread over many rows, as an active subset gives) go to
+// cells_collect. Dead lanes (live = false) take no part.
+constexpr int kRowSpan = 6;   // largest x extent of a run, in cells
+constexpr int kRowRuns = 2;   // shared runs a group takes before the per-lane fallback
+constexpr int kRowDepth = 3;  // staged chunks of a warp (kRowDepth - 1 in flight while one is tested)
+
+// A warp's staging area: the chunk ring and the run's segments (at most 27).
+struct RowStage {
+  float4 ring[kRowDepth][32];
+  int seg_start[32];
+  int seg_end[32];
+  unsigned seg_code[32];
+  int chunk_pref[33];  // chunks of the run before segment q
+  int pad[3];
+};
+static_assert(sizeof(RowStage) % 16 == 0, "the next warp's ring starts 16-byte aligned");
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// every group of this thread but the kRowDepth - 1 newest has landed
+__device__ __forceinline__ void cp_async_wait_older() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(kRowDepth - 1) : "memory");
+}
+
+// Segment of chunk c (binary search over the chunk prefix; nseg >= 1).
+__device__ __forceinline__ int row_chunk_seg(const RowStage& rs, int nseg, int c) {
+  int q = 0;
+#pragma unroll
+  for (int step = 16; step > 0; step >>= 1)
+    if (q + step < nseg && rs.chunk_pref[q + step] <= c) q += step;
+  return q;
+}
+
+// Chunk c (< nch) into ring slot c % kRowDepth: lane l copies record l of
+// the chunk, if the chunk has one. Every lane commits one group a call, so
+// the groups of all lanes count alike.
+__device__ __forceinline__ void row_stage(const float4* __restrict__ pos, RowStage& rs, int nseg, int nch, int c) {
+  if (c < nch) {
+    const int q = row_chunk_seg(rs, nseg, c);
+    const int j = rs.seg_start[q] + (c - rs.chunk_pref[q]) * 32 + (int)lane_id();
+    if (j < rs.seg_end[q]) cp_async16(&rs.ring[c % kRowDepth][lane_id()], pos + j);
+  }
+  cp_async_commit();
+}
+
+template <int W>
+__device__ __forceinline__ int rows_collect(const Grid& g, const int* __restrict__ cell_start,
+                                            const float4* __restrict__ pos, float xi, float yi, float zi, int cell,
+                                            float R2, bool live, unsigned* __restrict__ lst, float* r2s,
+                                            RowStage& rs, bool& ovf, unsigned& ncand) {
+  const unsigned lane = lane_id();
+  const int nx = g.nc[0], ny = g.nc[1], nz = g.nc[2];
+  const int cx = cell % nx, rw = cell / nx;  // rw = cy + ny cz
+  int cnt = 0;
+  unsigned pending = __ballot_sync(0xffffffffu, live);
+#pragma unroll 1
+  for (int run = 0; run < kRowRuns && pending != 0u; ++run) {
+    const int lead = __ffs(pending) - 1;
+    const int rrow = __shfl_sync(0xffffffffu, rw, lead);
+    const bool same = ((pending >> lane) & 1u) && rw == rrow;
+    const int x0 = __reduce_min_sync(0xffffffffu, same ? cx : 0x7fffffff);
+    const bool in = same && cx <= x0 + kRowSpan;
+    const int x1 = __reduce_max_sync(0xffffffffu, in ? cx : -1);
+    pending &= ~__ballot_sync(0xffffffffu, in);
+    const float R2in = in ? R2 : -1.0f;
+    // segment of lane l < 27: row l / 3 (y fastest, then z), part l % 3 (the
+    // image at x = -1, the cells inside the box, the image at x = nx)
+    int len = 0;
+    if (lane < 27u) {
+      const int ry = rrow % ny, rz = rrow / ny;
+      const int rq = (int)lane / 3, part = (int)lane % 3;
+      int y = ry + rq % 3 - 1, z = rz + rq / 3 - 1;
+      unsigned code = 0;
+      if (y < 0) { y += ny; code |= 8u; } else if (y >= ny) { y -= ny; code |= 4u; }
+      if (z < 0) { z += nz; code |= 32u; } else if (z >= nz) { z -= nz; code |= 16u; }
+      const int base = nx * (y + ny * z);
+      int xa = 0, xb = -1;
+      if (part == 0) {
+        if (x0 == 0) { xa = xb = nx - 1; code |= 2u; }
+      } else if (part == 1) {
+        xa = max(x0 - 1, 0);
+        xb = min(x1 + 1, nx - 1);
+      } else {
+        if (x1 == nx - 1) { xa = xb = 0; code |= 1u; }
+      }
+      int js = 0, je = 0;
+      if (xb >= xa) {
+        js = cell_start[base + xa];
+        je = cell_start[base + xb + 1];
+      }
+      rs.seg_start[lane] = js;
+      rs.seg_end[lane] = je;
+      rs.seg_code[lane] = code;
+      len = je - js;
+    }
+    int incl = (len + 31) >> 5;  // chunks of the segment
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if ((int)lane >= o) incl += y;
+    }
+    if (lane < 27u) rs.chunk_pref[lane + 1] = incl;
+    if (lane == 0) rs.chunk_pref[0] = 0;
+    const int nch = __shfl_sync(0xffffffffu, incl, 26);
+    const unsigned tested = (unsigned)__reduce_add_sync(0xffffffffu, (unsigned)len);
+    __syncwarp();
+#pragma unroll
+    for (int c = 0; c < kRowDepth - 1; ++c) row_stage(pos, rs, 27, nch, c);
+#pragma unroll 1
+    for (int c = 0; c < nch; ++c) {
+      row_stage(pos, rs, 27, nch, c + kRowDepth - 1);
+      cp_async_wait_older();
+      __syncwarp();  // every lane's copies of chunk c have landed
+      const int q = row_chunk_seg(rs, 27, c);
+      const int j0 = rs.seg_start[q] + (c - rs.chunk_pref[q]) * 32;
+      const int m = min(32, rs.seg_end[q] - j0);
+      const unsigned code = rs.seg_code[q];
+      // the lane's position less the segment's image shift S (as cells_collect takes it)
+      const float xs = xi - ((code & 1u) ? g.L[0] : (code & 2u) ? -g.L[0] : 0.0f);
+      const float ys = yi - ((code & 4u) ? g.L[1] : (code & 8u) ? -g.L[1] : 0.0f);
+      const float zs = zi - ((code & 16u) ? g.L[2] : (code & 32u) ? -g.L[2] : 0.0f);
+      const unsigned e0 = (unsigned)j0 | (code << kIndexBits);  // entry of the chunk's first record
+      const float4* ch = rs.ring[c % kRowDepth];
+      if (__all_sync(0xffffffffu, cnt + m <= W)) {
+        // no list can fill in this chunk. Eight tests at a time: the hit mask
+        // first (lanes outside the run test against -1: no hits), then each
+        // hit's place from a popcount of the hits before it, so that the
+        // stores do not wait on one another. Slots past m hold stale records
+        // and are masked out.
+        for (int b0 = 0; b0 < m; b0 += 8) {
+          float r2v[8];
+          unsigned hm = 0;
+#pragma unroll
+          for (int b = 0; b < 8; ++b) {
+            const float4 cj = ch[b0 + b];
+            r2v[b] = r2_of(xs - cj.x, ys - cj.y, zs - cj.z);
+            hm |= (r2v[b] < R2in && b0 + b < m) ? (1u << b) : 0u;
+          }
+          unsigned* lp = lst + cnt * 32;
+          float* rp = r2s + cnt * 32;
+#pragma unroll
+          for (int b = 0; b < 8; ++b) {
+            if (hm & (1u << b)) {
+              const int at = __popc(hm & ((1u << b) - 1u)) * 32;
+              lp[at] = e0 + (unsigned)(b0 + b);
+              rp[at] = r2v[b];
+            }
+          }
+          cnt += __popc(hm);
+        }
+      } else {
+        for (int b = 0; b < m; ++b) {
+          const float4 cj = ch[b];
+          const float r2 = r2_of(xs - cj.x, ys - cj.y, zs - cj.z);
+          if (r2 < R2in) {
+            if (cnt < W) {
+              lst[cnt * 32] = e0 + (unsigned)b;
+              r2s[cnt * 32] = r2;
+            } else {
+              ovf = true;
+            }
+            ++cnt;
+          }
+        }
+      }
+      __syncwarp();  // chunk c's slot is restaged by the next iteration
+    }
+    if (in) ncand += tested;
+  }
+  const bool rest = (pending >> lane) & 1u;
+  if (__any_sync(0xffffffffu, rest))
+    cnt = cells_collect<W>(g, cell_start, pos, xi, yi, zi, cell, R2, rest, lst, r2s, cnt, ovf, ncand);
+  return cnt;
+}
+
 // Per-lane scan of the 27 cells around `cell` without windows or lists: every
 // particle of every neighbour cell is handed to op.interact (which takes the
 // exact neighbour decision itself). The fallback of a group that has no kept

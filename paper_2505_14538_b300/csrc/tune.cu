@@ -45,7 +45,11 @@ static int prepare(Ctx* c, int loop, cudaStream_t s) {
 
 int autotune_impl(Ctx* c, int loop, cudaStream_t s) {
   if ((loop == 1 || loop == 3 || loop == 4) && !c->last_grad_out) return SWIFT_GPU_ERR_ORDER;
-  const int cand_l[6] = {1, 2, 4, 8, 16, 32};
+  // lanes per particle (1 twice: the shared-row and the windowed collect) x blocks per SM
+  const int cand_l[7] = {1, 1, 2, 4, 8, 16, 32};
+  const int cand_c[7] = {SWIFT_GPU_COLLECT_ROWS, SWIFT_GPU_COLLECT_WINDOWS, SWIFT_GPU_COLLECT_ROWS,
+                         SWIFT_GPU_COLLECT_ROWS, SWIFT_GPU_COLLECT_ROWS, SWIFT_GPU_COLLECT_ROWS,
+                         SWIFT_GPU_COLLECT_ROWS};
   const int cand_b[3] = {0, 1, 2};
   swift_gpu_tuning best = c->tuning, orig = c->tuning;
   float best_ms = 1e30f;
@@ -53,8 +57,9 @@ int autotune_impl(Ctx* c, int loop, cudaStream_t s) {
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return SWIFT_GPU_ERR_CUDA;
   int rc = SWIFT_GPU_OK;
   for (int bi = 0; bi < 3 && rc == SWIFT_GPU_OK; ++bi) {
-    for (int li = 0; li < 6 && rc == SWIFT_GPU_OK; ++li) {
+    for (int li = 0; li < 7 && rc == SWIFT_GPU_OK; ++li) {
       c->tuning.max_lanes_per_particle = cand_l[li];
+      c->tuning.group_collect = cand_c[li];
       c->tuning.blocks_per_sm = cand_b[bi];
       rc = prepare(c, loop, s);
       if (rc == SWIFT_GPU_OK) rc = run_loop(c, loop, s);  // warm-up

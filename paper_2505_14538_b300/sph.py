@@ -240,19 +240,22 @@ class Context:
         t = _lib.Tuning()
         _check(self.lib.swift_gpu_get_tuning(self.handle, ctypes.byref(t)), "swift_gpu_get_tuning")
         return dict(threads_per_block=t.threads_per_block, max_lanes_per_particle=t.max_lanes_per_particle,
-                    blocks_per_sm=t.blocks_per_sm, wait_limit_us=t.wait_limit_us)
+                    blocks_per_sm=t.blocks_per_sm, wait_limit_us=t.wait_limit_us, group_collect=t.group_collect)
 
-    def set_tuning(self, threads_per_block=None, max_lanes_per_particle=None, blocks_per_sm=None, wait_limit_us=None):
+    def set_tuning(self, threads_per_block=None, max_lanes_per_particle=None, blocks_per_sm=None, wait_limit_us=None,
+                   group_collect=None):
         """Set the work-distribution knobs; a knob not given keeps its current value.
 
-        max_lanes_per_particle = 1 selects the lane-per-particle path on the uniform grid (the default
-        there); 2-32 the cell items, whose particles share up to that many lanes of a warp."""
+        max_lanes_per_particle = 1 selects the lane-per-particle path on the uniform grid; 2-32 the cell
+        items, whose particles share up to that many lanes of a warp. group_collect picks the
+        lane-per-particle path's candidate search: _lib.COLLECT_ROWS (the warp's lanes share the rows of
+        cells around them) or _lib.COLLECT_WINDOWS (windows along the 13 pair axes, one lane each)."""
         cur = self.tuning()
         given = dict(threads_per_block=threads_per_block, max_lanes_per_particle=max_lanes_per_particle,
-                     blocks_per_sm=blocks_per_sm, wait_limit_us=wait_limit_us)
+                     blocks_per_sm=blocks_per_sm, wait_limit_us=wait_limit_us, group_collect=group_collect)
         cur.update({k: v for k, v in given.items() if v is not None})
         t = _lib.Tuning(cur["threads_per_block"], cur["max_lanes_per_particle"], cur["blocks_per_sm"],
-                        cur["wait_limit_us"])
+                        cur["wait_limit_us"], cur["group_collect"])
         _check(self.lib.swift_gpu_set_tuning(self.handle, ctypes.byref(t)), "swift_gpu_set_tuning")
 
     def autotune(self, loop: int, stream=None):

@@ -1,7 +1,8 @@
 """Full-size parity on sampled particles, in the launch configurations the benchmark times.
 
 * Sedov blast, 64^3 particles: the whole step captured in a CUDA graph and
-  replayed (the benchmark's headline configuration), uniform grid.
+  replayed (the benchmark's headline configuration), uniform grid, with
+  cell items and with the lane-per-particle shared-row collect.
 * Plummer mixture, 2^21 particles, 10 % active: one active step with
   adaptive leaves after an all-active step (the benchmark's clustered run).
 * Zel'dovich-displaced 256^3 lattice (16.7M particles, density contrast
@@ -105,7 +106,10 @@ def check_sample(O, d, vel, u, h, out, sample, h_tol, active_all=True):
     assert np.all(err_u <= 1e-4 * of["s_u"][sample] + 1e-30)
 
 
-def test_sedov64_graph_replay_sampled(sph, O):
+@pytest.mark.parametrize("lanes", [32, 1])
+def test_sedov64_graph_replay_sampled(sph, O, lanes):
+    """Both engines the benchmark's autotuner chooses between on this set: cell items (32 lanes) and
+    lane per particle with the shared-row collect (1 lane)."""
     d = ics.sedov(64)
     n = len(d["pos"])
     vel = d["vel"].astype(np.float32)
@@ -114,6 +118,7 @@ def test_sedov64_graph_replay_sampled(sph, O):
     vel_m = torch.from_numpy(np.concatenate([vel, d["m"][:, None]], 1).astype(np.float32)).cuda()
     ut = torch.from_numpy(u).cuda()
     ctx = sph.Context(n, h_tol=H_TOL)
+    ctx.set_tuning(max_lanes_per_particle=lanes, group_collect=0)
     first = ctx.step(pos_h, vel_m, ut, check=True)  # settles the cell width as the benchmark does
     torch.cuda.synchronize()
     min_width = max(ctx.info()["cell_width"]) if first["status"][0] != 0 else 0.0

@@ -44,13 +44,24 @@ def oracle_params(O, ctx_params, **kw):
     return p
 
 
-def run_gpu(sph, d, vel=None, u=None, min_cell_width=0.0, active=None, lanes=None, **params):
+# the density call's engines on the uniform grid, as tuning knobs: cell items (a warp shares a cell's
+# candidates), and lane per particle with the shared-row or the pair-axis-window collect
+ENGINES = {"cells": dict(lanes=32), "rows": dict(lanes=1, collect=0), "windows": dict(lanes=1, collect=1)}
+
+
+def run_gpu(sph, d, vel=None, u=None, min_cell_width=0.0, active=None, lanes=None, collect=None, engine=None,
+            **params):
     """One build, density, gradient and force pass; ``lanes`` sets the tuning's lanes per particle
-    (1: the lane-per-particle path of the uniform grid, the default there; 2-32: cell items)."""
+    (1: the lane-per-particle path of the uniform grid; 2-32: cell items) and ``collect`` its
+    candidate search; ``engine`` names one of ENGINES instead."""
+    if engine is not None:
+        lanes, collect = ENGINES[engine]["lanes"], ENGINES[engine].get("collect")
     n = len(d["pos"])
     ctx = sph.Context(max(n, 1), box=d["box"], **params)
     if lanes is not None:
         ctx.set_tuning(max_lanes_per_particle=lanes)
+    if collect is not None:
+        ctx.set_tuning(group_collect=collect)
     pos_h, vel_m, ut = dev_arrays(d, vel, u)
     act = None if active is None else torch.from_numpy(active.astype(np.uint8)).cuda()
     ctx.build_cells(pos_h, min_cell_width)
@@ -141,36 +152,38 @@ def test_cells_bit_exact(sph, O):
     assert np.array_equal(perm, np.argsort(ref, kind="stable"))
 
 
-@pytest.mark.parametrize("lanes", [1, 32])
-def test_lattice16_full_pipeline(sph, O, lanes):
+@pytest.mark.parametrize("engine", ["rows", "windows", "cells"])
+def test_lattice16_full_pipeline(sph, O, engine):
     """Jittered 16^3 lattice with random v and u, 4^3 cells (64 particles a cell, more than a cell
-    replica holds, so the lane-per-particle path reads them whole): every output against the oracle,
-    with both engines."""
+    replica holds, so the windowed collect reads them whole; a group of 32 is half a cell, and its
+    shared rows wrap periodically at both ends of the 4-cell rows): every output against the oracle,
+    with every engine."""
     d, vel, u = lattice_state(16)
-    g = run_gpu(sph, d, vel, u, min_cell_width=0.25, h_tol=1e-6, lanes=lanes)
+    g = run_gpu(sph, d, vel, u, min_cell_width=0.25, h_tol=1e-6, engine=engine)
     assert g["status"] == (0, 0), g["status"]
     check_against_oracle(O, d, vel, u, g, g["ctx"])
     inter = g["info"]["interactions"]
     assert inter[1] == g["ngb"].sum()
 
 
-@pytest.mark.parametrize("lanes", [1, 32])
-def test_sedov_small_auto_cells(sph, O, lanes):
+@pytest.mark.parametrize("engine", ["rows", "windows", "cells"])
+def test_sedov_small_auto_cells(sph, O, engine):
     """Sedov blast at 16^3 with automatic cell width (strong u contrast, viscosity, conduction), with
-    both engines; about 13 particles a cell, so the lane-per-particle path reads its neighbour cells
-    through the pair-axis windows."""
+    every engine; about 13 particles a cell, so the windowed collect reads its neighbour cells through
+    the pair-axis windows, and a group of 32 spans three or four cells, some of them across the end
+    of a row (two shared runs)."""
     d = ics.sedov(16)
     rng = np.random.default_rng(1)
     vel = rng.normal(0, 0.05, size=(len(d["pos"]), 3)).astype(np.float32)
-    g = run_gpu(sph, d, vel, d["u"], h_tol=1e-6, lanes=lanes)
+    g = run_gpu(sph, d, vel, d["u"], h_tol=1e-6, engine=engine)
     assert g["status"][0] in (0,), g["status"]
     check_against_oracle(O, d, vel, d["u"], g, g["ctx"])
 
 
-@pytest.mark.parametrize("lanes", [1, 32])
-def test_ragged_uniform_random(sph, O, lanes):
+@pytest.mark.parametrize("engine", ["rows", "windows", "cells"])
+def test_ragged_uniform_random(sph, O, engine):
     """3001 uniform random particles (ragged item sizes and tails: the last group of 32 is partial),
-    non-cubic box, random h, with both engines."""
+    non-cubic box, random h, with every engine."""
     rng = np.random.default_rng(7)
     n = 3001
     box = (1.0, 0.8, 1.25)
@@ -178,7 +191,7 @@ def test_ragged_uniform_random(sph, O, lanes):
     h = (rng.uniform(0.9, 1.1, n) * 1.2348 * (np.prod(box) / n) ** (1 / 3)).astype(np.float32)
     d = dict(pos=pos, h=h, m=np.full(n, 1.0 / n, np.float32), u=rng.uniform(0.5, 2, n).astype(np.float32),
              vel=rng.normal(0, 0.2, (n, 3)).astype(np.float32), box=box)
-    g = run_gpu(sph, d, d["vel"], d["u"], h_tol=1e-6, lanes=lanes)
+    g = run_gpu(sph, d, d["vel"], d["u"], h_tol=1e-6, engine=engine)
     assert g["status"][0] == 0, g["status"]
     check_against_oracle(O, d, d["vel"], d["u"], g, g["ctx"])
 
@@ -193,8 +206,8 @@ def test_fixed_h_counts_at_input_h(sph, O):
     assert np.max(np.abs(g["rho4"][:, 0] / st["rho"] - 1)) < 1e-5
 
 
-@pytest.mark.parametrize("lanes", [1, 32])
-def test_fixed_h_kept_lists_with_overflow(sph, O, lanes):
+@pytest.mark.parametrize("engine", ["rows", "windows", "cells"])
+def test_fixed_h_kept_lists_with_overflow(sph, O, engine):
     """NO_H_ITER keeps the density call's candidate lists for the gradient and force loops. On the
     Kelvin-Helmholtz slab (density ratio 2.2, the cells sized by the light layer's h) some lanes of
     the dense layer collect more candidates than a list holds: with cell items their items take the
@@ -206,7 +219,7 @@ def test_fixed_h_kept_lists_with_overflow(sph, O, lanes):
     n = len(d["pos"])
     vel = d["vel"] + rng.normal(0, 0.05, (n, 3)).astype(np.float32)
     u = d["u"]
-    g = run_gpu(sph, d, vel, u, flags=2, lanes=lanes)
+    g = run_gpu(sph, d, vel, u, flags=2, engine=engine)
     assert g["status"] == (0, 0) and g["status2"] == (0, 0)
     assert np.array_equal(g["h"], d["h"])
     pf = oracle_params(O, g["ctx"].params)
@@ -223,15 +236,15 @@ def test_fixed_h_kept_lists_with_overflow(sph, O, lanes):
     # force loops; the others read their kept lists
     cand = g["info"]["candidates"]
     assert cand[1] == cand[2], cand
-    if lanes != 1:
+    if engine != "windows":
         assert cand[2] < cand[0], cand
     # on a lattice no list overflows: the loops read kept lists only, fewer candidates than the
     # density call tested (the cell items' 27-cell scan, or lane per particle the pair-axis windows,
     # whose kept entries are its hits), with the same outputs as the iterating path's loops at that h
     d, vel, u = lattice_state(12, jitter=0.3)
-    g = run_gpu(sph, d, vel, u, flags=2, lanes=lanes)
+    g = run_gpu(sph, d, vel, u, flags=2, engine=engine)
     cand = g["info"]["candidates"]
-    assert cand[2] < (cand[0] / 3 if lanes != 1 else cand[0]), cand
+    assert cand[2] < (cand[0] / 3 if engine != "windows" else cand[0]), cand
     st = O.step(oracle_params(O, g["ctx"].params), d["pos"], vel, d["m"], u, d["h"], solve=False)
     a = g["accel_dudt"]
     assert np.all(np.linalg.norm(a[:, :3] - st["accel"], axis=1) <= 1e-4 * st["s_a"] + 1e-30)
@@ -246,13 +259,17 @@ def test_deterministic(sph):
         assert np.array_equal(a[k], b[k]), k
 
 
-def test_active_subset_matches_full(sph, O):
-    """Only active particles are recomputed; with the inactive state from a full pass they match it."""
+@pytest.mark.parametrize("engine", ["rows", "cells"])
+def test_active_subset_matches_full(sph, O, engine):
+    """Only active particles are recomputed; with the inactive state from a full pass they match it.
+    Lane per particle with shared rows, a group of 32 active particles spreads over many rows: two
+    shared runs, the other lanes each scanning its own 27 cells."""
     d, vel, u = lattice_state(16, seed=5)
     n = len(d["pos"])
-    full = run_gpu(sph, d, vel, u, h_tol=1e-6)
+    full = run_gpu(sph, d, vel, u, h_tol=1e-6, engine=engine)
     act = ics.active_hash(n, 123, 4)
     ctx = sph.Context(n, box=d["box"], h_tol=1e-6)
+    ctx.set_tuning(max_lanes_per_particle=ENGINES[engine]["lanes"], group_collect=ENGINES[engine].get("collect", 0))
     # previous state: converged h for everybody, rho4/curl_div from the full pass
     d2 = dict(d)
     d2["h"] = full["h"]
