@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint (force backward) timing")
     ap.add_argument("--no-autotune", action="store_true", help="time the default tuning (skip swift_gpu_autotune)")
     ap.add_argument("--no-c5", action="store_true", help="skip the 256^3 Zel'dovich (large cosmology-like) step")
+    ap.add_argument("--lanes", type=int, default=None,
+                    help="set the headline step's lanes per particle (1: lane per particle, shared-row collect) "
+                         "instead of running the autotuner")
     ap.add_argument("--sustained-steps", type=int, default=2000,
                     help="graph replays of the sustained timing (seconds of timed work)")
     return ap.parse_args()
@@ -250,6 +253,8 @@ def run_ours(args, rank, world, pg):
     vel_m = torch.from_numpy(vel_m_host).to(dev)
     u = torch.from_numpy(u_host).to(dev)
     ctx = sph.Context(n, h_tol=BENCH_H_TOL)
+    if args.lanes is not None:
+        ctx.set_tuning(max_lanes_per_particle=args.lanes, group_collect=0)
     # settle the cell width once (the h iteration may ask for wider cells)
     out = ctx.step(pos_h, vel_m, u, check=True)
     torch.cuda.synchronize()
@@ -289,14 +294,17 @@ def run_ours(args, rank, world, pg):
     # the autotuner (swift_gpu_autotune, whole step) against the default setting
     for _ in range(3):
         step(pos_h, vel_m, u)
-    default_tuning = ctx.tuning()
-    t_default = statistics.median(sum(x) for x in time_direct(10))
-    tune = {"default": default_tuning, "default_step_ms_median": t_default}
-    if not args.no_autotune:
+    if args.lanes is not None:
+        tune = {"set": ctx.tuning(), "note": "set by --lanes before the first call (no autotuner run)"}
+    else:
+        default_tuning = ctx.tuning()
+        t_default = statistics.median(sum(x) for x in time_direct(10))
+        tune = {"default": default_tuning, "default_step_ms_median": t_default}
+    if args.lanes is None and not args.no_autotune:
         tune["picked"] = ctx.autotune(4)
         tune["picked_step_ms_median"] = statistics.median(sum(x) for x in time_direct(10))
         tune["note"] = ("swift_gpu_autotune(loop 4: density, then gradient + force) timed every lanes-per-particle x "
-                        "blocks-per-SM setting and kept the fastest; the timed steps below run with it")
+                        "collect x blocks-per-SM setting and kept the fastest; the timed steps below run with it")
     for _ in range(args.warmup):
         step(pos_h, vel_m, u)
     torch.cuda.synchronize()
