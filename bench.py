@@ -467,7 +467,7 @@ def run_ours(args, rank, world, pg):
     if not args.no_gresho and rank == 0:
         res["gresho"] = run_gresho(dev)
     if not args.no_kernel_shapes and rank == 0:
-        res["kernel_shapes"] = run_kernel_shapes(dev, d, peak_max)
+        res["kernel_shapes"] = run_kernel_shapes(dev, d, peak_max, autotune=not args.no_autotune)
     if not args.no_adjoint and rank == 0:
         res["adjoint"] = run_adjoint(dev)
     if rank == 0 and not args.no_cpu_baseline:
@@ -795,11 +795,12 @@ def run_zeldovich(dev, peak, fpi, steps=5, cpu=True):
     return res
 
 
-def run_kernel_shapes(dev, d, peak_tflops, steps=30):
+def run_kernel_shapes(dev, d, peak_tflops, steps=30, autotune=True):
     """The benchmark step on the same workload with each kernel shape (cubic spline, Wendland C2, C4).
 
     Same eta, so the Wendland kernels (larger H/h) have about 57 and 85
-    neighbours against 48. Per shape: the graph-replayed step, the loop
+    neighbours against 48. Per shape: the autotuner's pick of the work
+    distribution (as for the headline step), the graph-replayed step, the loop
     kernels' times from direct calls, and their algorithmic FP32 rate from the
     oracle's per-interaction flop counts of that shape.
     """
@@ -824,6 +825,8 @@ def run_kernel_shapes(dev, d, peak_tflops, steps=30):
         first = ctx.step(pos_h, vel_m, u, check=True)
         torch.cuda.synchronize()
         width = max(ctx.info()["cell_width"]) if first["status"][0] != 0 else 0.0
+        ctx.step(pos_h, vel_m, u, min_cell_width=width)
+        tuning = ctx.autotune(4) if autotune else ctx.tuning()  # each shape with the autotuner's pick
         graph = sph.StepGraph(ctx, pos_h, vel_m, u, width)
         o = graph.out
         for _ in range(3):
@@ -864,7 +867,7 @@ def run_kernel_shapes(dev, d, peak_tflops, steps=30):
                      "k_density_frac": fd / (dms * 1e-3) / 1e12 / peak_tflops,
                      "k_grad_force_frac": fg / (gms * 1e-3) / 1e12 / peak_tflops,
                      "flops_per_interaction": dict(zip(("density", "gradient", "force", "h_iteration"), c)),
-                     "status": list(ctx.sync_status())}
+                     "tuning": tuning, "status": list(ctx.sync_status())}
         del graph, ctx
     return out
 

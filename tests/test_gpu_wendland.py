@@ -43,12 +43,15 @@ def test_wendland_full_pipeline(sph, O, kind):
     assert st["ngb"].sum() == g["ngb"].sum()
 
 
+@pytest.mark.parametrize("engine", ["cells", "rows"])
 @pytest.mark.parametrize("kind", [1, 2])
-def test_wendland_auto_cells_sedov(sph, O, kind):
+def test_wendland_auto_cells_sedov(sph, O, kind, engine):
+    """Both Wendland shapes with the cell items and with the shared-row collect, whose warps hold
+    the shapes' wider lists (W = 128 and 160 squared distances a lane) beside the staging ring."""
     d = ics.sedov(16)
     rng = np.random.default_rng(kind)
     vel = rng.normal(0, 0.05, size=(len(d["pos"]), 3)).astype(np.float32)
-    g = run_gpu(sph, d, vel, d["u"], h_tol=1e-6, kernel=kind)
+    g = run_gpu(sph, d, vel, d["u"], h_tol=1e-6, kernel=kind, engine=engine)
     assert g["status"][0] == 0, g["status"]
     check_against_oracle(O, d, vel, d["u"], g, g["ctx"])
 
