@@ -6,7 +6,10 @@
 // sums are combined.
 //
 // Candidates come from the 27 cells around the lane's own cell (Sec. 2.2:
-// self and pair interactions of cells no narrower than the support). For a
+// self and pair interactions of cells no narrower than the support), found
+// in one of two ways: the shared rows (rows_collect, below: the group's lanes
+// test, in step, every particle of the rows of cells their neighbourhoods
+// share), or per lane through windows on sorted replicas, as follows. For a
 // neighbour cell at offset o (one of 26), the cell's particles are read in
 // the order of their projection on o (SWIFT's sorted pair interactions,
 // Sec. 2.2.2: cells sorted along the 13 pair axes), and the lane stops at the
