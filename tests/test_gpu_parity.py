@@ -196,6 +196,19 @@ def test_ragged_uniform_random(sph, O, engine):
     check_against_oracle(O, d, d["vel"], d["u"], g, g["ctx"])
 
 
+def test_rows_engine_smallest_grid(sph, O):
+    """The shared-row collect on the smallest grid (the build never makes fewer than 3 cells a
+    side): an 8^3 jittered lattice in cells of width 1/3. With 3 cells a row, a run
+    covering x = 0..2 reads the row's images at x = -1 and x = 3, which are cells of the row itself
+    (shifted by -L and +L). Every output against the oracle; candidates past a list's width take
+    the multi-pass route."""
+    d, vel, u = lattice_state(8, seed=11)
+    g = run_gpu(sph, d, vel, u, min_cell_width=0.3, h_tol=1e-6, engine="rows")
+    assert tuple(g["info"]["nc"]) == (3, 3, 3), g["info"]["nc"]
+    assert g["status"] == (0, 0), g["status"]
+    check_against_oracle(O, d, vel, u, g, g["ctx"])
+
+
 def test_fixed_h_counts_at_input_h(sph, O):
     """NO_H_ITER: one density pass at the input h; counts bit-exact at that h."""
     d, vel, u = lattice_state(12, jitter=0.3)
