@@ -70,7 +70,8 @@ __device__ __forceinline__ void lean_pair(LeanI& I, const LeanRec& R, int j, uns
   // part of the band (2^-16 H^2), so an approximate reciprocal serves
   const float iHj = R.p.w;
   const float Hj = __fdividef(1.0f, iHj);
-  const float bdj = band_of(Hj, k.Lmax);
+  // band_of(Hj, Lmax) as Hj (2^-16 Hj + 2^-20 Lmax): the same band to rounding, two operations
+  const float bdj = Hj * fmaf(Hj, 1.52587890625e-05f, k.Lmax * 9.5367431640625e-07f);
   const float H2lo_j = fmaf(Hj, Hj, -bdj), H2hi_j = fmaf(Hj, Hj, bdj);
   shift_j(code, k.ph.L, xj, yj, zj);
   const float dx = I.x - xj, dy = I.y - yj, dz = I.z - zj;
@@ -107,20 +108,21 @@ __device__ __forceinline__ void lean_pair(LeanI& I, const LeanRec& R, int j, uns
   }
   // pressure (Eq. 17) and its work (Eq. 18)
   const float ps = mj * fmaf(I.A, dWi, R.ga.x * dWj);
-  // artificial viscosity (Eqs. 7, 9-11, 16) and its heating
+  // artificial viscosity (Eqs. 7, 9-11, 16) and its heating: the viscous term is
+  // vs = 0.5 m_j nu fsum with nu = -(1/4)(alpha_i + alpha_j)(B_i + B_j) mu v_sig / (rho_i + rho_j);
+  // vsh = vs / 2 folds the constants into one factor, -1/16
   const float irs = __fdividef(1.0f, I.rho + R.ga.z);
-  const float alpha = 0.25f * (I.av + R.gb.y) * (I.B + R.gb.x);
-  const float nu = -alpha * mu * vsig * irs;
-  const float vs = 0.5f * mj * nu * fsum;
-  float du = vr * fmaf(mj * I.A, dWi, 0.5f * vs);
+  const float a16 = -0.0625f * (I.av + R.gb.y) * (I.B + R.gb.x);
+  const float vsh = mj * fsum * (a16 * mu * vsig * irs);
+  float du = vr * fmaf(mj * I.A, dWi, vsh);
   // artificial conduction (Eqs. 19, 20, 22)
   const float Pj = k.gm1() * R.ga.z * R.gb.w;
   const float Ps = I.P + Pj;
   const float ac = Ps > 0.0f ? __fdividef(I.acP + R.gb.z, Ps) : 0.0f;
   const float dP = 2.0f * fabsf(I.P - Pj) * irs;
-  const float vc = fabsf(vr) + (dP > 0.0f ? dP * rsqrtf(dP) : 0.0f);
+  const float vc = fabsf(vr) + sqrt_approx(dP);  // exact at dP = 0
   du = fmaf(ac * vc * mj * (I.u - R.gb.w), fsum * irs, du);
-  const float asr = (ps + vs) * invr;
+  const float asr = fmaf(2.0f, vsh, ps) * invr;
   tax = fmaf(-asr, dx, tax);
   tay = fmaf(-asr, dy, tay);
   taz = fmaf(-asr, dz, taz);
