@@ -374,20 +374,21 @@ struct GradForceOp : ForceOp {
     const float fsum = fmaf(i.f, dWi, aj.y * dWj);
     // pressure (Eq. 17) and its work (Eq. 18)
     const float ps = mj * fmaf(i.A, dWi, aj.x * dWj);
-    // artificial viscosity (Eqs. 7, 9-11, 16) and its heating
-    const float alpha = 0.25f * (i.av + bj.y) * (i.B + bj.x);
+    // artificial viscosity (Eqs. 7, 9-11, 16) and its heating: the viscous term is
+    // vs = 0.5 m_j nu fsum with nu = -(1/4)(alpha_i + alpha_j)(B_i + B_j) mu v_sig / (rho_i + rho_j);
+    // vsh = vs / 2 folds the constants into one factor, -1/16
+    const float a16 = -0.0625f * (i.av + bj.y) * (i.B + bj.x);
     const float irs = __fdividef(1.0f, i.rho + aj.z);
-    const float nu = -alpha * mu * vsig * irs;
-    const float vs = 0.5f * mj * nu * fsum;
-    float du = vr * fmaf(mj * i.A, dWi, 0.5f * vs);
+    const float vsh = mj * fsum * (a16 * mu * vsig * irs);
+    float du = vr * fmaf(mj * i.A, dWi, vsh);
     // artificial conduction (Eqs. 19, 20, 22)
     const float Pj = gm1 * aj.z * bj.w;
     const float Ps = i.P + Pj;
     const float ac = Ps > 0.0f ? __fdividef(i.acP + bj.z, Ps) : 0.0f;
     const float dP = 2.0f * fabsf(i.P - Pj) * irs;
-    const float vc = fabsf(vr) + (dP > 0.0f ? dP * rsqrtf(dP) : 0.0f);
+    const float vc = fabsf(vr) + sqrt_approx(dP);  // exact at dP = 0
     du = fmaf(ac * vc * mj * (i.u - bj.w), fsum * irs, du);
-    const float asr = (ps + vs) * invr;
+    const float asr = fmaf(2.0f, vsh, ps) * invr;
     t[0] = fmaf(-asr, dx, t[0]);
     t[1] = fmaf(-asr, dy, t[1]);
     t[2] = fmaf(-asr, dz, t[2]);
